@@ -1,0 +1,385 @@
+"""Pins of the FP64 CPU oracle to facts outside itself (no GPU).
+
+Each test fixes the oracle against something it does not compute itself:
+library special functions, the paper's printed constants, the exact conjugate
+posterior at S = 1, the log evidence by 2-D quadrature at S = 2, a Monte-Carlo
+estimate of Eq. 11 from scipy densities, the coordinate-ascent property of
+Eq. 12 (ELBO non-decrease and zero gradient after every factor update), the
+profile-grouped identity, and recovery of the paper's synthetic truths
+(Section 4, Table 1).
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.integrate
+import scipy.special
+import scipy.stats as st
+
+from oracle import oracle as O
+from paper_2401_10068_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return json.load(f)
+
+
+def _rich_prior(S, seed=0):
+    """A proper prior with every constant away from the paper's values, so that
+    each ELBO term is visible in the checks."""
+    M = S - 1
+    rng = np.random.default_rng(seed)
+    A = rng.normal(size=(M, M))
+    L0inv = 0.02 * (A @ A.T / max(M, 1) + np.eye(M))
+    return O.paper_prior(S, K0=rng.uniform(0.1, 0.4, size=M), q0=0.8, n0=M + 2.0, a0=2.0, b0=0.3, L0inv=L0inv)
+
+
+# --------------------------------------------------------------------------- #
+def test_digamma_matches_scipy():
+    xs = np.concatenate([np.logspace(-3, 9, 400), [1.0, 1.4616321449683622, 2.5, 9.999, 10.0, 10.001]])
+    for x in xs:
+        ref = scipy.special.digamma(x)
+        assert abs(O.digamma(x) - ref) <= 1e-13 * max(1.0, abs(ref)), x
+
+
+def test_paper_prior_constants_match_golden():
+    g = _golden("paper_constants.json")["prior"]
+    p = O.paper_prior(3)
+    np.testing.assert_allclose(p["K0"], g["K0"], rtol=0, atol=1e-15)
+    assert (p["a0"], p["b0"], p["q0"], p["n0"]) == (g["a0"], g["b0"], g["q0"], g["n0"])
+    np.testing.assert_allclose(p["L0inv"], g["Lambda0_inv"], rtol=0, atol=1e-18)
+    t = _golden("paper_constants.json")["synthetic_truth"]
+    np.testing.assert_allclose(synth.truth_covariance(2), t["Lambda_inv"], rtol=0, atol=1e-18)
+
+
+# --------------------------------------------------------------------------- #
+# S = 1: r_i ~ N(d_i, 1/rho), rho ~ Gamma(a0, b0): the exact posterior is a Gamma
+# and the ELBO at it equals the log evidence.
+# --------------------------------------------------------------------------- #
+@pytest.mark.parametrize("a0,b0", [(0.5, 0.5), (3.0, 0.2)])
+def test_S1_exact_conjugate_posterior_and_evidence(a0, b0):
+    rng = np.random.default_rng(5)
+    V = 37
+    d = rng.integers(0, 2, size=(V, 1)).astype(np.float32)
+    r = (d[:, 0] + rng.normal(scale=0.3, size=V)).astype(np.float32)
+    p = O.paper_prior(1, a0=a0, b0=b0)
+    f = O.fit(r, d, p, tol=1e-14, max_iter=5)
+    y = r.astype(np.float64) - d[:, 0].astype(np.float64)
+    aN, bN = a0 + V / 2.0, b0 + 0.5 * np.sum(y * y)
+    assert f["a_rho"] == pytest.approx(aN, rel=1e-15)
+    assert f["b_rho"] == pytest.approx(bN, rel=1e-13)
+
+    # log evidence by 1-D quadrature over rho of Gamma(rho | a0, b0) prod_i N(r_i | d_i, 1/rho)
+    def integrand(u, shift):
+        rho = math.exp(u)
+        lp = st.gamma.logpdf(rho, a0, scale=1.0 / b0) + u
+        lp += np.sum(st.norm.logpdf(y, 0.0, 1.0 / math.sqrt(rho)))
+        return math.exp(lp - shift)
+    umode = math.log(aN / bN)
+    shift = math.log(integrand(umode, 0.0))
+    val, err = scipy.integrate.quad(integrand, umode - 30, umode + 30, args=(shift,), epsabs=0, epsrel=1e-13,
+                                    limit=400, points=[umode])
+    logZ = math.log(val) + shift
+    closed = a0 * math.log(b0) - math.lgamma(a0) + math.lgamma(aN) - aN * math.log(bN) - 0.5 * V * math.log(2 * math.pi)
+    assert logZ == pytest.approx(closed, rel=1e-10)
+    for L in f["trace"]:
+        assert L == pytest.approx(logZ, rel=1e-10, abs=1e-9)
+
+
+# --------------------------------------------------------------------------- #
+# S = 2 (M = 1): ELBO <= ln p(r), with ln p(r) from 2-D quadrature over (rho, Lambda)
+# after integrating beta and K analytically.
+# --------------------------------------------------------------------------- #
+def _log_evidence_S2(r, d, p, n=801):
+    y = r.astype(np.float64) - d[:, 1].astype(np.float64)
+    D = d[:, 0].astype(np.float64) - d[:, 1].astype(np.float64)
+    V = y.shape[0]
+    W0 = 1.0 / p["L0inv"][0, 0]
+    K0, q0 = p["K0"][0], p["q0"]
+
+    def logf(u, w):
+        rho, lam = np.exp(u), np.exp(w)
+        C = np.zeros(u.shape + (V, V))
+        idx = np.arange(V)
+        C[..., idx, idx] = D[None, :] ** 2 / lam[..., None] + 1.0 / rho[..., None]
+        C += np.outer(D, D)[None, :, :] / (q0 * lam)[..., None, None]
+        sign, logdet = np.linalg.slogdet(C)
+        m = y - D * K0
+        quad = np.einsum("...i,...i->...", m, np.linalg.solve(C, np.broadcast_to(m, u.shape + (V,))[..., None])[..., 0])
+        ll = -0.5 * V * math.log(2 * math.pi) - 0.5 * logdet - 0.5 * quad
+        lp = st.gamma.logpdf(rho, p["a0"], scale=1.0 / p["b0"]) + st.gamma.logpdf(lam, 0.5 * p["n0"], scale=2 * W0)
+        return ll + lp + u + w
+
+    def grid_logZ(ulo, uhi, wlo, whi, n):
+        us, ws = np.linspace(ulo, uhi, n), np.linspace(wlo, whi, n)
+        U, Wg = np.meshgrid(us, ws, indexing="ij")
+        F = logf(U, Wg)
+        wu = np.ones(n); wu[1:-1:2] = 4; wu[2:-1:2] = 2; wu *= (us[1] - us[0]) / 3
+        ww = np.ones(n); ww[1:-1:2] = 4; ww[2:-1:2] = 2; ww *= (ws[1] - ws[0]) / 3
+        return scipy.special.logsumexp(F + np.log(wu)[:, None] + np.log(ww)[None, :]), F, us, ws
+
+    _, F, us, ws = grid_logZ(-12, 16, -12, 20, 161)
+    keep = F > F.max() - 45
+    iu, iw = np.nonzero(keep)
+    box = (us[max(iu.min() - 2, 0)], us[min(iu.max() + 2, len(us) - 1)],
+           ws[max(iw.min() - 2, 0)], ws[min(iw.max() + 2, len(ws) - 1)])
+    lz1, _, _, _ = grid_logZ(*box, n)
+    lz2, _, _, _ = grid_logZ(*box, (n - 1) // 2 + 1)
+    return lz1, abs(lz1 - lz2)
+
+
+@pytest.mark.parametrize("which", ["paper", "rich"])
+def test_S2_elbo_below_quadrature_log_evidence(which):
+    V = 6
+    r, d, _ = synth.generate(V, 2, seed=77, K_true=[0.35])
+    p = O.paper_prior(2) if which == "paper" else _rich_prior(2, seed=3)
+    logZ, qerr = _log_evidence_S2(r, d, p)
+    assert qerr < 1e-7
+    f = O.fit(r, d, p, tol=1e-13, max_iter=500)
+    assert not f["const_dropped"]
+    assert np.all(f["trace"] <= logZ + 1e-7)
+    # mean-field gap: positive and modest for six observations
+    assert 0.0 < logZ - f["elbo"] < 3.0
+
+
+# --------------------------------------------------------------------------- #
+# Monte-Carlo estimate of Eq. 11 for an arbitrary Q, from scipy densities of
+# Eq. 3-7 (the joint) and of the factors of Eq. 13.
+# --------------------------------------------------------------------------- #
+def _mvn_logpdf_prec(x, mean, P):
+    """log N(x | mean, P^{-1}) for stacks of precision matrices P (..., M, M)."""
+    M = x.shape[-1]
+    dx = x - mean
+    sign, ld = np.linalg.slogdet(P)
+    return -0.5 * M * math.log(2 * math.pi) + 0.5 * ld - 0.5 * np.einsum("...i,...ij,...j->...", dx, P, dx)
+
+
+def test_elbo_matches_monte_carlo_estimate():
+    S, V, N = 3, 5, 400_000
+    M = S - 1
+    p = _rich_prior(S, seed=11)
+    r, d, _ = synth.generate(V, S, seed=5)
+    f = O.fit(r, d, p, tol=0, max_iter=3)
+    mu, Sig = O.beta_update(r, d, p, f)
+    sums = O.sums_from_beta(r, d, p, mu, Sig)
+    # an arbitrary (not optimal) global factor set, so every term is exercised
+    g = dict(f)
+    g.update(a_rho=f["a_rho"] * 1.3, b_rho=f["b_rho"] * 0.7, kappa=f["kappa"] + np.array([0.05, -0.03]),
+             Winv=f["Winv"] * 1.2 + 0.01 * np.array([[0.0, 1.0], [1.0, 0.0]]), nu=f["nu"] + 2.0, lam=3.7)
+    L, dropped = O.elbo(p, sums, g)
+    assert not dropped
+
+    rng = np.random.default_rng(1234)
+    W = np.linalg.inv(g["Winv"])
+    rho = st.gamma.rvs(g["a_rho"], scale=1.0 / g["b_rho"], size=N, random_state=rng)
+    Lam = st.wishart.rvs(df=g["nu"], scale=W, size=N, random_state=rng)
+    Lk = np.linalg.cholesky(np.linalg.inv(g["lam"] * Lam))
+    K = g["kappa"] + np.einsum("nij,nj->ni", Lk, rng.normal(size=(N, M)))
+    y = r.astype(np.float64) - d[:, M].astype(np.float64)
+    D = d[:, :M].astype(np.float64) - d[:, M:].astype(np.float64)
+    logp = st.gamma.logpdf(rho, p["a0"], scale=1.0 / p["b0"])
+    logp += st.wishart.logpdf(np.moveaxis(Lam, 0, -1), df=p["n0"], scale=np.linalg.inv(p["L0inv"]))
+    logp += _mvn_logpdf_prec(K, p["K0"], p["q0"] * Lam)
+    logq = st.gamma.logpdf(rho, g["a_rho"], scale=1.0 / g["b_rho"])
+    logq += st.wishart.logpdf(np.moveaxis(Lam, 0, -1), df=g["nu"], scale=W)
+    logq += _mvn_logpdf_prec(K, g["kappa"], g["lam"] * Lam)
+    for i in range(V):
+        b = st.multivariate_normal.rvs(mean=mu[i], cov=Sig[i], size=N, random_state=rng).reshape(N, M)
+        logq += st.multivariate_normal.logpdf(b, mean=mu[i], cov=Sig[i])
+        logp += _mvn_logpdf_prec(b, K, Lam)
+        logp += st.norm.logpdf(y[i], b @ D[i], 1.0 / np.sqrt(rho))
+    diff = logp - logq
+    est, se = diff.mean(), diff.std() / math.sqrt(N)
+    assert se < 0.02
+    assert abs(L - est) < 5 * se, (L, est, se)
+
+
+# --------------------------------------------------------------------------- #
+# Coordinate ascent (Eq. 12): every factor update does not decrease the ELBO,
+# and right after it the ELBO's gradient in that factor's parameters is zero.
+# --------------------------------------------------------------------------- #
+def _sweep_states(r, d, p, sweeps):
+    """Yields (name, mu, Sig, glob) after every coordinate update."""
+    V = r.shape[0]
+    mu, Sig = O.beta_init(p, V)
+    s = O.sums_from_beta(r, d, p, mu, Sig)
+    g = O.KLambda_update(p, s, O.rho_update(p, s))
+    yield "init", mu, Sig, g
+    for _ in range(sweeps):
+        mu, Sig = O.beta_update(r, d, p, g)
+        yield "beta", mu, Sig, g
+        s = O.sums_from_beta(r, d, p, mu, Sig)
+        g = O.rho_update(p, s, g)
+        yield "rho", mu, Sig, g
+        g = O.KLambda_update(p, s, g)
+        yield "KLambda", mu, Sig, g
+
+
+def _L(r, d, p, mu, Sig, g):
+    return O.elbo(p, O.sums_from_beta(r, d, p, mu, Sig), g)[0]
+
+
+@pytest.mark.parametrize("S,prior", [(3, "paper"), (3, "rich"), (5, "rich"), (2, "paper")])
+def test_elbo_non_decreasing_at_every_coordinate_step(S, prior):
+    r, d, _ = synth.generate(300, S, seed=21 + S)
+    p = O.paper_prior(S) if prior == "paper" else _rich_prior(S, seed=S)
+    prev = None
+    for name, mu, Sig, g in _sweep_states(r, d, p, 15):
+        L = _L(r, d, p, mu, Sig, g)
+        if prev is not None:
+            assert L >= prev - 1e-10 * abs(L), (name, L, prev)
+        prev = L
+
+
+def _central(fun, x, h):
+    return (fun(x + h) - fun(x - h)) / (2 * h)
+
+
+def test_updates_are_stationary_points_of_the_elbo():
+    S, V = 3, 40
+    M = S - 1
+    r, d, _ = synth.generate(V, S, seed=9)
+    p = _rich_prior(S, seed=4)
+    states = list(_sweep_states(r, d, p, 4))
+    checks = 0
+    for name, mu, Sig, g in states[-3:]:
+        sums = O.sums_from_beta(r, d, p, mu, Sig)
+
+        def L_glob(**kw):
+            gg = dict(g)
+            gg.update(kw)
+            return O.elbo(p, sums, gg)[0]
+
+        def grad_glob(gbase):
+            out = []
+            for key in ("a_rho", "b_rho", "nu", "lam"):
+                x0 = gbase[key]
+                out.append(x0 * _central(lambda x: O.elbo(p, sums, {**gbase, key: x})[0], x0, 1e-5 * x0))
+            for j in range(M):
+                def fk(x, j=j):
+                    k = gbase["kappa"].copy(); k[j] = x
+                    return O.elbo(p, sums, {**gbase, "kappa": k})[0]
+                out.append(_central(fk, gbase["kappa"][j], 1e-6))
+            for j in range(M):
+                for k in range(j + 1):
+                    def fw(x, j=j, k=k):
+                        W = gbase["Winv"].copy(); W[j, k] = x; W[k, j] = x
+                        return O.elbo(p, sums, {**gbase, "Winv": W})[0]
+                    x0 = gbase["Winv"][j, k]
+                    out.append(abs(gbase["Winv"][j, j]) * _central(fw, x0, 1e-6 * abs(gbase["Winv"][j, j])))
+            return np.array(out)
+
+        if name == "rho":
+            gr = grad_glob(g)[:2]
+            far = grad_glob({**g, "a_rho": g["a_rho"] * 1.2, "b_rho": g["b_rho"] * 0.9})[:2]
+            assert np.all(np.abs(gr) < 1e-6), gr
+            assert np.any(np.abs(far) > 1e-2)
+            checks += 1
+        if name == "KLambda":
+            gr = grad_glob(g)[2:]
+            far = grad_glob({**g, "kappa": g["kappa"] + 0.02, "nu": g["nu"] * 1.1})[2:]
+            assert np.all(np.abs(gr) < 1e-5), gr
+            assert np.any(np.abs(far) > 1e-2)
+            checks += 1
+        if name == "beta":
+            for i in (0, 7, 23):
+                for j in range(M):
+                    def fm(x, i=i, j=j):
+                        m2 = mu.copy(); m2[i, j] = x
+                        return _L(r, d, p, m2, Sig, g)
+                    assert abs(_central(fm, mu[i, j], 1e-6)) < 1e-5
+                    assert abs(_central(fm, mu[i, j] + 0.05, 1e-6)) > 1e-3
+                for j in range(M):
+                    for k in range(j + 1):
+                        def fs(x, i=i, j=j, k=k):
+                            s2 = Sig.copy(); s2[i, j, k] = x; s2[i, k, j] = x
+                            return _L(r, d, p, mu, s2, g)
+                        h = 1e-7 * Sig[i, j, j]
+                        assert abs(Sig[i, j, j] * _central(fs, Sig[i, j, k], h)) < 1e-5
+            checks += 1
+    assert checks == 3
+
+
+# --------------------------------------------------------------------------- #
+# Profile-grouped identity: sums from per-profile (n, sum y, sum y^2) equal the
+# per-observation sums.
+# --------------------------------------------------------------------------- #
+@pytest.mark.parametrize("S", [1, 2, 3, 6])
+def test_profile_grouped_identity(S):
+    r, d, _ = synth.generate(5000, S, seed=40 + S, p_const=0.05)
+    p = O.paper_prior(S)
+    groups = O.group_profiles(r, d, S)
+    mu, Sig = O.beta_init(p, r.shape[0])
+    a = O.sums_from_beta(r, d, p, mu, Sig)
+    b = O.sums_grouped(groups, p, None, init=True)
+    f = O.fit(r, d, p, tol=0, max_iter=3)
+    mu, Sig = O.beta_update(r, d, p, f)
+    c = O.sums_from_beta(r, d, p, mu, Sig)
+    e = O.sums_grouped(groups, p, f, init=False)
+    for x, y in ((a, b), (c, e)):
+        assert x["V"] == y["V"]
+        for key in ("sum_S", "sum_logdet"):
+            assert y[key] == pytest.approx(x[key], rel=1e-10, abs=1e-9)
+        np.testing.assert_allclose(y["sum_mu"], x["sum_mu"], rtol=1e-10, atol=1e-9)
+        np.testing.assert_allclose(y["sum_Ebb"], x["sum_Ebb"], rtol=1e-10, atol=1e-9)
+    fg = O.fit_grouped(groups, p, tol=0, max_iter=3)
+    np.testing.assert_allclose(fg["kappa"], f["kappa"], rtol=1e-10, atol=1e-12)
+    np.testing.assert_allclose(fg["Winv"], f["Winv"], rtol=1e-9, atol=1e-9)
+    np.testing.assert_allclose(fg["trace"], f["trace"], rtol=1e-10)
+
+
+# --------------------------------------------------------------------------- #
+# Statistical sanity against the paper's synthetic experiment (Section 4).
+# --------------------------------------------------------------------------- #
+def test_recovers_table1_truths():
+    t1 = _golden("paper_constants.json")["table1"]
+    errs, rhos = [], []
+    for n, K in enumerate(t1["actual"]):
+        r, d, _ = synth.generate(6000, 3, seed=100 + n, K_true=K)
+        f = O.fit(r, d, O.paper_prior(3), tol=1e-8, max_iter=3000)
+        assert f["converged"]
+        assert np.all(np.diff(f["trace"]) >= -1e-10 * np.abs(f["trace"][1:]))
+        errs.append(np.linalg.norm(f["kappa"] - np.asarray(K)))
+        rhos.append(f["a_rho"] / f["b_rho"])
+    # the paper reports a mean Euclidean error of 0.0094 with its own profiles
+    assert np.mean(errs) < 3 * t1["vb_mean_euclidean_error"], errs
+    # rho = 100 in the paper's synthetic data; noise and beta spread are only
+    # weakly separable with S = 3, so allow 15 %
+    assert np.all(np.abs(np.array(rhos) - 100.0) < 15.0), rhos
+
+
+def test_large_S_runs_and_is_monotone():
+    r, d, _ = synth.generate(400, 32, seed=8, alpha=0.5)
+    f = O.fit(r, d, O.paper_prior(32), tol=0, max_iter=6)
+    assert f["const_dropped"]
+    assert np.all(np.diff(f["trace"]) >= -1e-10 * np.abs(f["trace"][1:]))
+
+
+def test_philox_known_answers():
+    kat = _golden("philox_kat.json")["vectors"]
+    for v in kat:
+        c = [int(x, 16) for x in v["counter"]]
+        k = [int(x, 16) for x in v["key"]]
+        out = synth.philox4x32_10(*c, *k)
+        assert [int(x) for x in out] == [int(x, 16) for x in v["out"]]
+
+
+def test_generator_prefix_and_recipe():
+    r1, d1, t = synth.generate(3000, 4, seed=99, p_const=0.1)
+    r2, d2, _ = synth.generate(1000, 4, seed=99, p_const=0.1, start=2000)
+    np.testing.assert_array_equal(r1[2000:], r2)
+    np.testing.assert_array_equal(d1[2000:], d2)
+    assert set(np.unique(d1).tolist()) <= {0.0, 1.0}
+    const = np.all(d1 == d1[:, :1], axis=1)
+    # 10 % forced constant, plus 2 of the 16 random 4-bit profiles by chance
+    assert const.mean() == pytest.approx(0.1 + 0.9 * 2 / 16, abs=0.03)
+    # residual variance of the generative model: Var(r | d) = D^T Sigma_beta D + 1/rho
+    D = d1[:, :3] - d1[:, 3:]
+    resid = r1 - d1[:, 3] - D @ t["K_true"]
+    pred = np.einsum("ij,jk,ik->i", D, t["Sigma_beta"], D) + 1.0 / t["rho"]
+    assert np.mean(resid ** 2 / pred) == pytest.approx(1.0, abs=0.08)
