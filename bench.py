@@ -1,0 +1,329 @@
+"""Throughput of the fused CAVI sweep on one GB300 (or N independent replicas).
+
+A step is one sweep of the whole hot path over the at-scale synthetic data set
+(N = 4,194,304 cells x G = 96 genes = V = 402,653,184 observations, S = 8
+subpopulations, 5 % constant profiles, K_true ~ Dirichlet(0.5), seed 2):
+Q(beta) for every observation -> reduction of the sufficient statistics ->
+Q(rho), Q(K, Lambda) -> ELBO and convergence test.  The metric is
+observation x subpopulation CAVI updates per second (cell . gene . K updates/s
+with V = N G and S = K), V * S * steps / time.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+``--impl reference`` times the FP64 CPU oracle (the reference arm) on a
+bounded prefix of the same data set on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import glob
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = {"name": "at-scale single data set", "cells": 4_194_304, "genes": 96, "S": 8, "p_const": 0.05,
+            "alpha": 0.5, "seed": 2}
+V_FULL = WORKLOAD["cells"] * WORKLOAD["genes"]
+METRIC = "cell.gene.K CAVI updates/s (observation x subpopulation updates per second, FP32 fused sweep)"
+UNIT = "updates/s"
+CPU_SAMPLE_V = 1 << 20          # oracle prefix for the cpu_baseline leg
+CPU_SAMPLE_SWEEPS = 5
+REF_SAMPLE_V = 1 << 17          # oracle prefix per step of the reference arm
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def _kernel_hash():
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2401_10068_gb300", "csrc", "*"))):
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(bytes_alg):
+    """DRAM bytes per launch of the sweep kernel from the committed ncu capture,
+    or None if the kernel source changed since it was taken."""
+    p = os.path.join(ROOT, "profiles", "sweep_kernel_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        j = json.load(f)
+    if j.get("kernel_hash") != _kernel_hash():
+        return None
+    return float(j["dram_bytes_per_obs"]) * V_FULL
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,utilization.gpu,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(device_index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "50"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [ln.strip().split(",") for ln in self.f.read().splitlines() if ln.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for row in rows:
+            try:
+                clk, cmax, util = float(row[0]), float(row[1]), float(row[2])
+            except (ValueError, IndexError):
+                continue
+            mx.append(cmax)
+            if util < 50:            # keep samples taken under load
+                continue
+            sm.append(clk)
+            for nm, v in zip(names, row[3:7]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples_under_load": len(sm), "samples": len(rows)}
+
+
+def _oracle_sweeps(V, S, sweeps, warm=1):
+    """Time `sweeps` oracle sweeps (Q(beta), sums, Q(rho), Q(K,Lambda), ELBO) on
+    the first V observations of the workload; returns seconds."""
+    from oracle import oracle as O
+    from paper_2401_10068_gb300 import synth
+    r, d, _ = synth.generate(V, S, seed=WORKLOAD["seed"], alpha=WORKLOAD["alpha"], p_const=WORKLOAD["p_const"])
+    p = O.paper_prior(S)
+    g = O.fit(r, d, p, tol=0.0, max_iter=warm)
+    t0 = time.perf_counter()
+    for _ in range(sweeps):
+        mu, Sig = O.beta_update(r, d, p, g)
+        s = O.sums_from_beta(r, d, p, mu, Sig)
+        g = O.KLambda_update(p, s, O.rho_update(p, s, g))
+        O.elbo(p, s, g)
+    return time.perf_counter() - t0
+
+
+def run_reference(args):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return 0
+    S = WORKLOAD["S"]
+    from oracle import oracle as O
+    from paper_2401_10068_gb300 import synth
+    V = REF_SAMPLE_V
+    r, d, _ = synth.generate(V, S, seed=WORKLOAD["seed"], alpha=WORKLOAD["alpha"], p_const=WORKLOAD["p_const"])
+    p = O.paper_prior(S)
+    g = O.fit(r, d, p, tol=0.0, max_iter=0)
+
+    def step(g):
+        mu, Sig = O.beta_update(r, d, p, g)
+        s = O.sums_from_beta(r, d, p, mu, Sig)
+        g = O.KLambda_update(p, s, O.rho_update(p, s, g))
+        O.elbo(p, s, g)
+        return g
+
+    for _ in range(args.warmup):
+        g = step(g)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        g = step(g)
+    el = time.perf_counter() - t0
+    value = V * S * args.steps / el
+    sample = f"first {V} of the {V_FULL} observations per step (same seeded recipe), S = {S}"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD["name"], "N_cells": WORKLOAD["cells"], "G_genes": WORKLOAD["genes"],
+                       "S": S, "V": V_FULL, "sample_V": V},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = _dist()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2401_10068_gb300 import _build
+    _build.build_all()
+    from paper_2401_10068_gb300 import synth, vbh
+
+    S, V = WORKLOAD["S"], V_FULL
+    stream = torch.cuda.Stream(dev)
+    with torch.cuda.stream(stream):
+        r, d, _ = synth.generate_device(V, S, seed=WORKLOAD["seed"], alpha=WORKLOAD["alpha"],
+                                        p_const=WORKLOAD["p_const"], device=dev)
+    stream.synchronize()
+    h = vbh.Handle(local, stream)
+    total = args.warmup + args.steps
+    h.fit_begin(r, d, S, None, tol=0.0, max_iter=total)
+    clocks = Clocks(local)
+    time.sleep(0.3)                                     # let the sampler start
+    if args.warmup:
+        h.fit_step(args.warmup)
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    ev0.record(stream)
+    h.fit_step(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    res = h.fit_result()
+    assert res["iters"] == total, res["iters"]
+    t = torch.tensor([ms], device=dev, dtype=torch.float64)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    units = float(V) * S * args.steps * world
+    value = units / (ms_max * 1e-3)
+    ms_step = ms_max / args.steps
+
+    # roofline of the dominant kernel (the fused sweep: one launch per step)
+    bytes_alg = float(V) * (S + 1) * 4
+    peak, peak_kind = _peaks()
+    achieved = bytes_alg / (ms_step * 1e-3) / 1e9
+    traffic = _traffic(bytes_alg)
+
+    # end to end through the C ABI from pinned host buffers: one vbh_fit call
+    # per timed repetition (H2D of r and d, sweep 0 + `steps` sweeps, result D2H)
+    e2e_steps = args.steps
+    e2e = None
+    if not args.no_e2e:
+        e2e = _e2e(h, r, d, V, S, e2e_steps, dev, dist, world)
+    del r, d
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        sec = _oracle_sweeps(CPU_SAMPLE_V, S, CPU_SAMPLE_SWEEPS)
+        cpu = {"value": CPU_SAMPLE_V * S * CPU_SAMPLE_SWEEPS / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"first {CPU_SAMPLE_V} observations of the workload, {CPU_SAMPLE_SWEEPS} sweeps after "
+                         f"sweep 0, single-threaded FP64 oracle ({sec:.1f} s)"}
+    h.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD["name"], "N_cells": WORKLOAD["cells"], "G_genes": WORKLOAD["genes"],
+                           "S": S, "V": V, "p_const": WORKLOAD["p_const"], "seed": WORKLOAD["seed"],
+                           "inputs_bytes": bytes_alg, "l2": "inputs larger than L2 (129 MB), no flush",
+                           "parallelism": f"replicas x{world}",
+                           "e2e": "one vbh_fit call from pinned host buffers per repetition: H2D of r and d once, "
+                                  f"sweep 0 + {e2e_steps} sweeps, result D2H; bytes per step = per call / steps"},
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak, "traffic": traffic,
+                             "kernel": f"sweep_kernel<{S}>", "peak_kind": peak_kind,
+                             "bytes_per_launch": bytes_alg},
+                "cpu_baseline": cpu,
+                "e2e": e2e,
+                "gpu_launches": args.steps + 1,
+                "clocks": clk}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def _e2e(h, r, d, V, S, e2e_steps, dev, dist, world):
+    import torch
+    rh = torch.empty(V, dtype=torch.float32, pin_memory=True)
+    dh = torch.empty((V, S), dtype=torch.float32, pin_memory=True)
+    rh.copy_(r)
+    dh.copy_(d)
+    torch.cuda.synchronize(dev)
+    h.fit(rh, dh, S, None, tol=0.0, max_iter=2)            # staging buffers + graph warm
+    reps = 2
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        out = h.fit(rh, dh, S, None, tol=0.0, max_iter=e2e_steps)
+    t_e2e = (time.perf_counter() - t0) / reps
+    assert out["iters"] == e2e_steps
+    te = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
+    if dist:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = float(V) * S * e2e_steps * world / float(te.item())
+    h2d = V * 4 + V * S * 4
+    d2h = ctypes_result_bytes()
+    return {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d / e2e_steps,
+            "d2h_bytes_per_step": d2h / e2e_steps}
+
+
+def ctypes_result_bytes():
+    """Device -> host bytes of one vbh_fit call: three read-backs of the fit state."""
+    from paper_2401_10068_gb300 import vbh
+    return 3 * vbh.state_bytes()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cells", type=int, default=WORKLOAD["cells"],
+                    help="N cells (x 96 genes); smaller values give the small case used for ncu captures")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
+    args = ap.parse_args()
+    global V_FULL
+    if args.cells != WORKLOAD["cells"]:
+        WORKLOAD["cells"] = args.cells
+        WORKLOAD["name"] = "at-scale recipe, reduced N (profiling case)"
+        V_FULL = WORKLOAD["cells"] * WORKLOAD["genes"]
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,147 @@
+/*
+ * vbh.h -- C ABI of the GB300 (sm_103a) implementation of the mean-field
+ * variational-Bayes (CAVI) iteration for the conjugate-exponential model of
+ * cancer-tissue heterogeneity (arXiv 2401.10068, Sections 3.3-3.5).
+ *
+ * Model (Section 3.3).  There are V observations r_i (one gene-expression ratio
+ * each) with known expression profiles d_i in R^S over S subpopulations (the
+ * paper's N).  With M = S - 1, mu_i = d_{i,S}, D_i = d_{i,1:M} - d_{i,S}:
+ *   r_i    ~ N(D_i^T beta_i + mu_i, 1/rho)             Eq. 3
+ *   beta_i ~ N(K, Lambda^{-1})                         Eq. 4
+ *   rho ~ Gamma(a0, b0),  K | Lambda ~ N(K0, (q0 Lambda)^{-1}),
+ *   Lambda ~ Wishart(n0, scale Lambda_0)               Eq. 5-7
+ * The posterior is approximated by Q(rho) Q(beta) Q(K, Lambda) (Eq. 13) and
+ * fitted by coordinate ascent: Q(beta) (Eq. 19-21), Q(rho) (Eq. 16-18),
+ * Q(K, Lambda) (Eq. 22-25), with the expectations of Eq. 26-31 and the lower
+ * bound L_Q of Eq. 10-11 as the convergence monitor.
+ *
+ * Conventions for every entry point:
+ *   - Return 0 (VBH_OK) or a negative VBH_E* code; vbh_strerror() names it.
+ *   - Calls are synchronous on the handle's stream: when a call returns, its
+ *     results are in host memory and no work of the call is in flight.
+ *   - The caller owns every buffer it passes; the library only reads r and d.
+ *   - A handle is not thread-safe; use one handle per host thread.
+ *   - r and d may be device pointers (any CUDA allocation on the handle's
+ *     device) or host pointers (pageable or pinned); host inputs are copied to
+ *     a device buffer owned by the handle, inside the call.
+ *   - r: V floats.  d: V x S floats, row-major (the S entries of profile d_i
+ *     are contiguous).  Device pointers must be 16-byte aligned.
+ *   - The sweep is FP32 per observation with FP64 accumulation across blocks
+ *     and FP64 global updates; non-finite results return VBH_ENONFINITE.
+ */
+#ifndef VBH_H
+#define VBH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define VBH_SMAX 32              /* largest number of subpopulations S */
+#define VBH_MMAX 31              /* largest M = S - 1 */
+
+/* status codes */
+#define VBH_OK 0
+#define VBH_EINVAL (-1)          /* invalid argument (null pointer, size, alignment, S) */
+#define VBH_ENOMEM (-2)          /* device or host allocation failed */
+#define VBH_ECUDA (-3)           /* a CUDA runtime call failed */
+#define VBH_ENONFINITE (-4)      /* a global update or the ELBO became NaN/Inf */
+#define VBH_ETIMEOUT (-5)        /* a bounded device wait ran out (the kernel returned early) */
+#define VBH_ESTATE (-6)          /* call out of order (e.g. vbh_fit_step before vbh_fit_begin) */
+#define VBH_EUNSUPPORTED (-7)    /* valid request this build does not implement (e.g. S above the FP32 sweep limit) */
+
+/* precision of the per-observation sweep */
+#define VBH_FP32 0
+
+/* initial state of a fit */
+#define VBH_INIT_PAPER 0         /* Q(beta_i) = N(K0, Lambda_0^{-1}) before sweep 0 (Section 3.5) */
+#define VBH_INIT_GIVEN 1         /* start from the global factors in vbh_opts.init_state (warm start / resume) */
+
+typedef struct vbh_handle vbh_handle;
+
+/* Prior constants of Eq. 5-7.  vbh_prior_default() fills the paper's values
+ * (Section 3.5): K0 = (1/S, ..., 1/S), q0 = 0.001, n0 = 1, a0 = b0 = 0.5 and
+ * Lambda_0^{-1} = 0.005 * 1 1^T + diag(0.005, 0.003, 0.005, 0.003, ...),
+ * which is the paper's [[0.01, 0.005], [0.005, 0.008]] for S = 3. */
+typedef struct {
+    int S;                       /* 1 .. VBH_SMAX */
+    const double *K0;            /* M entries (host memory), or NULL for 1/S each */
+    double q0, n0, a0, b0;       /* q0 > 0, n0 > 0, a0 > 0, b0 > 0 */
+    const double *Lambda0_inv;   /* M x M row-major symmetric positive definite (host), or NULL for the default */
+} vbh_prior;
+
+/* Posterior summary, also usable as a checkpoint (vbh_opts.init_state). */
+typedef struct {
+    int S, iters, converged, status, elbo_const_dropped;
+    double kappa[VBH_MMAX];      /* E[K] = K_{0K}, Eq. 24/30 */
+    double weights[VBH_SMAX];    /* (kappa, 1 - sum kappa): all S subpopulation weights (Section 3.3) */
+    double W_inv[VBH_MMAX * VBH_MMAX]; /* Lambda_{0Lambda}^{-1}, Eq. 25 (M x M row-major) */
+    double nu, lambda;           /* n0 + V (Eq. 23), q0 + V (Eq. 22) */
+    double a_rho, b_rho;         /* Q(rho) = Gamma(a_rho, b_rho), Eq. 16-18 */
+    double rho_mean, rho_mode;   /* a_rho / b_rho (Eq. 29), (a_rho - 1) / b_rho */
+    double elbo;                 /* L_Q of Eq. 11 after the last sweep */
+} vbh_result;
+
+typedef struct {
+    double tol;                  /* stop after sweep t >= 1 when |L_t - L_{t-1}| < tol |L_t|; 0 runs max_iter sweeps */
+    int max_iter;                /* sweeps after sweep 0, >= 0 */
+    int precision;               /* VBH_FP32 */
+    int init;                    /* VBH_INIT_PAPER or VBH_INIT_GIVEN */
+    const vbh_result *init_state;/* global factors to start from when init == VBH_INIT_GIVEN */
+    double *elbo_trace;          /* optional host array of max_iter + 1 doubles: L_0 .. L_iters */
+} vbh_opts;
+
+/* Fill *p with the paper's prior for S subpopulations (Section 3.5). */
+void vbh_prior_default(int S, vbh_prior *p);
+
+/* Fill *o with tol = 1e-8, max_iter = 200, VBH_FP32, VBH_INIT_PAPER, no trace. */
+void vbh_opts_default(vbh_opts *o);
+
+/* Create a handle on CUDA device `device` that issues all work on `stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  The stream is borrowed:
+ * it must outlive the handle.  Returns VBH_EINVAL for a bad device. */
+int vbh_create(vbh_handle **h, int device, void *stream);
+
+/* Release every resource of the handle (NULL is allowed). */
+void vbh_destroy(vbh_handle *h);
+
+/* Name of a status code (static string). */
+const char *vbh_strerror(int status);
+
+/* Bytes of the device-resident fit state that each vbh_fit_begin,
+ * vbh_fit_step and vbh_fit_result call copies back to the host (a vbh_fit
+ * call copies it three times); for accounting of host<->device traffic. */
+size_t vbh_state_bytes(void);
+
+/* Fit Q(rho) Q(beta) Q(K, Lambda) to (r, d): sweep 0 from the initial state,
+ * then up to o->max_iter sweeps of Q(beta) -> Q(rho) -> Q(K, Lambda) -> ELBO
+ * (Section 3.5), run on the device as one CUDA graph with a conditional while
+ * loop.  out receives the final global factors; out->converged = 0 when the
+ * sweep limit was reached first (not an error).  V = 0 is allowed: the
+ * posterior is then the prior. */
+int vbh_fit(vbh_handle *h, const float *r, const float *d, int64_t V, int S, const vbh_prior *p,
+            const vbh_opts *o, vbh_result *out);
+
+/* Step-wise form of vbh_fit.  vbh_fit_begin validates, stages the inputs and
+ * runs sweep 0; vbh_fit_step runs up to nsweeps further sweeps (fewer if the
+ * fit converges or reaches o->max_iter) and reports the convergence flag;
+ * vbh_fit_result copies the current global factors out.  The inputs must stay
+ * valid and unchanged until the next vbh_fit_begin / vbh_fit / vbh_destroy. */
+int vbh_fit_begin(vbh_handle *h, const float *r, const float *d, int64_t V, int S, const vbh_prior *p,
+                  const vbh_opts *o);
+int vbh_fit_step(vbh_handle *h, int nsweeps, int *converged);
+int vbh_fit_result(vbh_handle *h, vbh_result *out);
+
+/* ELBO (Eq. 11) of the global factors in *q (kappa, W_inv, nu, lambda,
+ * a_rho, b_rho) with Q(beta) set from them by Eq. 19-21: one data pass and no
+ * update of *q. */
+int vbh_elbo(vbh_handle *h, const float *r, const float *d, int64_t V, int S, const vbh_prior *p,
+             const vbh_result *q, double *elbo);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VBH_H */

@@ -1,0 +1,618 @@
+// vbh_api.cu -- the C ABI declared in include/vbh.h: handle, argument
+// checks, input staging, the CUDA-graph sweep loop and result read-back.
+// All arithmetic of the method runs in the kernels of vbh_sweep.cuh.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "vbh.h"
+#include "vbh_dispatch.cuh"
+#include "vbh_internal.cuh"
+
+using vbh::DevState;
+using vbh::KernelInfo;
+
+struct vbh_handle {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int nsm = 0;
+    DevState *st = nullptr;            // device state of the step-wise fit
+    DevState *st_aux = nullptr;        // device state used by vbh_elbo
+    DevState *mirror = nullptr;        // pinned host copy of a DevState
+    double *partials = nullptr;
+    size_t partials_cap = 0;           // doubles
+    double *trace = nullptr;
+    int trace_cap = 0;
+    float *stage_r = nullptr, *stage_d = nullptr;
+    size_t stage_cap_r = 0, stage_cap_d = 0;   // bytes
+    // current fit
+    bool begun = false;
+    int S = 0;
+    long long V = 0;
+    const float *r = nullptr, *d = nullptr;    // device pointers used by the kernels
+    int max_iter = 0;
+    double *user_trace = nullptr;
+    KernelInfo ki{};
+    int grid = 0;
+    // cached graph of the sweep loop
+    cudaGraphExec_t gexec = nullptr;
+    int g_S = -1, g_grid = -1;
+    long long g_V = -1;
+    const float *g_r = nullptr, *g_d = nullptr;
+    const double *g_partials = nullptr;
+    bool attr_set[vbh::SMAX + 1] = {};
+};
+
+namespace vbh {
+
+// Sweep budget of one vbh_fit_step call: the graph loop runs while iter < target.
+__global__ void set_target_kernel(DevState *st, int nsweeps)
+{
+    if (threadIdx.x == 0) {
+        long long t = (long long)st->iter + nsweeps;
+        st->target = t > st->max_iter ? st->max_iter : int(t);
+    }
+}
+
+} // namespace vbh
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+#define VBH_CK(call)                                                                                                   \
+    do {                                                                                                               \
+        cudaError_t e_ = (call);                                                                                       \
+        if (e_ != cudaSuccess) {                                                                                       \
+            (void)cudaGetLastError();                                                                                  \
+            return e_ == cudaErrorMemoryAllocation ? VBH_ENOMEM : VBH_ECUDA;                                           \
+        }                                                                                                              \
+    } while (0)
+
+bool kernel_info(int S, KernelInfo *ki)
+{
+    return vbh::kernel_info_s1_4(S, ki) || vbh::kernel_info_s5_8(S, ki) || vbh::kernel_info_s9_11(S, ki);
+}
+
+// The default Lambda_0^{-1}: 0.005 * 1 1^T + diag(0.005, 0.003, 0.005, ...).
+void default_L0inv(int M, double *out)
+{
+    for (int r = 0; r < M; ++r)
+        for (int c = 0; c < M; ++c) out[r * M + c] = 0.005 + (r == c ? (r % 2 == 0 ? 0.005 : 0.003) : 0.0);
+}
+
+bool host_spd(int M, const double *A)
+{
+    double L[vbh::MMAX * vbh::MMAX];
+    for (int j = 0; j < M; ++j) {
+        for (int i = 0; i < M; ++i)
+            if (!std::isfinite(A[i * M + j]) || A[i * M + j] != A[j * M + i]) return false;
+        double s = A[j * M + j];
+        for (int k = 0; k < j; ++k) s -= L[j * M + k] * L[j * M + k];
+        if (!(s > 0.0)) return false;
+        L[j * M + j] = std::sqrt(s);
+        for (int i = j + 1; i < M; ++i) {
+            double t = A[i * M + j];
+            for (int k = 0; k < j; ++k) t -= L[i * M + k] * L[j * M + k];
+            L[i * M + j] = t / L[j * M + j];
+        }
+    }
+    return true;
+}
+
+bool pos_finite(double x) { return std::isfinite(x) && x > 0.0; }
+
+int check_prior(const vbh_prior *p, int S)
+{
+    if (!p || p->S != S) return VBH_EINVAL;
+    if (!pos_finite(p->q0) || !pos_finite(p->n0) || !pos_finite(p->a0) || !pos_finite(p->b0)) return VBH_EINVAL;
+    const int M = S - 1;
+    if (p->K0)
+        for (int j = 0; j < M; ++j)
+            if (!std::isfinite(p->K0[j])) return VBH_EINVAL;
+    if (p->Lambda0_inv && !host_spd(M, p->Lambda0_inv)) return VBH_EINVAL;
+    return VBH_OK;
+}
+
+// Device pointer usable as-is (16-byte aligned, on this device), host pointer
+// to stage, or invalid.
+enum PtrKind { PTR_DEVICE, PTR_HOST, PTR_BAD };
+
+PtrKind classify(const void *p, int device)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return PTR_HOST;
+    }
+    switch (at.type) {
+    case cudaMemoryTypeDevice:
+        if (at.device != device) return PTR_BAD;
+        return (reinterpret_cast<uintptr_t>(p) % 16 == 0) ? PTR_DEVICE : PTR_BAD;
+    case cudaMemoryTypeManaged:
+        return (reinterpret_cast<uintptr_t>(p) % 16 == 0) ? PTR_DEVICE : PTR_HOST;
+    default:
+        return PTR_HOST;
+    }
+}
+
+int ensure(void **buf, size_t *cap, size_t bytes)
+{
+    if (*cap >= bytes && *buf) return VBH_OK;
+    if (*buf) cudaFree(*buf);
+    *buf = nullptr;
+    *cap = 0;
+    if (bytes == 0) return VBH_OK;
+    if (cudaMalloc(buf, bytes) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return VBH_ENOMEM;
+    }
+    *cap = bytes;
+    return VBH_OK;
+}
+
+// Resolve (r, d) to device pointers, copying host inputs into the handle's
+// staging buffers on the handle's stream.
+int stage_inputs(vbh_handle *h, const float *r, const float *d, long long V, int S, const float **rd,
+                 const float **dd)
+{
+    if (V == 0) {
+        *rd = nullptr;
+        *dd = nullptr;
+        return VBH_OK;
+    }
+    const PtrKind kr = classify(r, h->device), kd = classify(d, h->device);
+    if (kr == PTR_BAD || kd == PTR_BAD) return VBH_EINVAL;
+    const size_t br = size_t(V) * 4, bd = size_t(V) * size_t(S) * 4;
+    if (kr == PTR_HOST) {
+        int rc = ensure(reinterpret_cast<void **>(&h->stage_r), &h->stage_cap_r, br);
+        if (rc) return rc;
+        VBH_CK(cudaMemcpyAsync(h->stage_r, r, br, cudaMemcpyHostToDevice, h->stream));
+        *rd = h->stage_r;
+    } else {
+        *rd = r;
+    }
+    if (kd == PTR_HOST) {
+        int rc = ensure(reinterpret_cast<void **>(&h->stage_d), &h->stage_cap_d, bd);
+        if (rc) return rc;
+        VBH_CK(cudaMemcpyAsync(h->stage_d, d, bd, cudaMemcpyHostToDevice, h->stream));
+        *dd = h->stage_d;
+    } else {
+        *dd = d;
+    }
+    return VBH_OK;
+}
+
+void fill_prior(DevState *s, const vbh_prior *p, int S, long long V)
+{
+    const int M = S - 1;
+    s->S = S;
+    s->M = M;
+    s->V = double(V);
+    s->q0 = p->q0;
+    s->n0 = p->n0;
+    s->a0 = p->a0;
+    s->b0 = p->b0;
+    for (int j = 0; j < M; ++j) s->K0[j] = p->K0 ? p->K0[j] : 1.0 / S;
+    if (p->Lambda0_inv)
+        std::memcpy(s->L0inv, p->Lambda0_inv, sizeof(double) * M * M);
+    else
+        default_L0inv(M, s->L0inv);
+}
+
+int prepare_kernel(vbh_handle *h, int S, long long V, KernelInfo *ki, int *grid)
+{
+    if (!kernel_info(S, ki)) return VBH_EUNSUPPORTED;
+    if (!h->attr_set[S]) {
+        VBH_CK(cudaFuncSetAttribute(ki->sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, int(ki->smem)));
+        h->attr_set[S] = true;
+    }
+    int per_sm = 0;
+    VBH_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ki->sweep, ki->threads, ki->smem));
+    if (per_sm < 1) return VBH_ECUDA;
+    long long tiles = (V + ki->tile - 1) / ki->tile;
+    long long g = (long long)h->nsm * per_sm;
+    if (tiles < g) g = tiles;
+    if (g < 1) g = 1;
+    *grid = int(g);
+    int rc = ensure(reinterpret_cast<void **>(&h->partials), &h->partials_cap,
+                    size_t(g) * size_t(ki->nstat) * sizeof(double));
+    return rc;
+}
+
+int launch_sweep(vbh_handle *h, DevState *st, int mode, const KernelInfo &ki, int grid, const float *r,
+                 const float *d, long long V)
+{
+    vbh::SweepArgs a{};
+    a.r = r;
+    a.d = d;
+    a.V = V;
+    a.st = st;
+    a.partials = h->partials;
+    a.use_cond = 0;
+    a.mode = mode;
+    void *args[] = {&a};
+    VBH_CK(cudaLaunchKernel(ki.sweep, dim3(grid), dim3(ki.threads), args, ki.smem, h->stream));
+    return VBH_OK;
+}
+
+int launch_setup(vbh_handle *h, DevState *st, const KernelInfo &ki, int init)
+{
+    void *args[] = {&st, &init};
+    VBH_CK(cudaLaunchKernel(ki.setup, dim3(1), dim3(32), args, 0, h->stream));
+    return VBH_OK;
+}
+
+int build_graph(vbh_handle *h)
+{
+    if (h->gexec && h->g_S == h->S && h->g_grid == h->grid && h->g_V == h->V && h->g_r == h->r && h->g_d == h->d &&
+        h->g_partials == h->partials)
+        return VBH_OK;
+    if (h->gexec) {
+        cudaGraphExecDestroy(h->gexec);
+        h->gexec = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    VBH_CK(cudaGraphCreate(&g, 0));
+    int rc = VBH_OK;
+    cudaGraphConditionalHandle cond;
+    cudaGraphNodeParams cp{};
+    cudaGraphNode_t wnode, knode;
+    cudaGraphNodeParams kp{};
+    vbh::SweepArgs a{};
+    void *args[] = {&a};
+    if (cudaGraphConditionalHandleCreate(&cond, g, 1u, cudaGraphCondAssignDefault) != cudaSuccess) {
+        rc = VBH_ECUDA;
+        goto out;
+    }
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    if (cudaGraphAddNode(&wnode, g, nullptr, nullptr, 0, &cp) != cudaSuccess) {
+        rc = VBH_ECUDA;
+        goto out;
+    }
+    a.r = h->r;
+    a.d = h->d;
+    a.V = h->V;
+    a.st = h->st;
+    a.partials = h->partials;
+    a.cond = cond;
+    a.use_cond = 1;
+    a.mode = vbh::MODE_ITER;
+    kp.type = cudaGraphNodeTypeKernel;
+    kp.kernel.func = const_cast<void *>(h->ki.sweep);
+    kp.kernel.gridDim = dim3(h->grid);
+    kp.kernel.blockDim = dim3(h->ki.threads);
+    kp.kernel.sharedMemBytes = (unsigned)h->ki.smem;
+    kp.kernel.kernelParams = args;
+    if (cudaGraphAddNode(&knode, cp.conditional.phGraph_out[0], nullptr, nullptr, 0, &kp) != cudaSuccess) {
+        rc = VBH_ECUDA;
+        goto out;
+    }
+    if (cudaGraphInstantiate(&h->gexec, g, 0) != cudaSuccess) {
+        h->gexec = nullptr;
+        rc = VBH_ECUDA;
+        goto out;
+    }
+    h->g_S = h->S;
+    h->g_grid = h->grid;
+    h->g_V = h->V;
+    h->g_r = h->r;
+    h->g_d = h->d;
+    h->g_partials = h->partials;
+out:
+    if (rc) (void)cudaGetLastError();
+    cudaGraphDestroy(g);
+    return rc;
+}
+
+int read_state(vbh_handle *h, DevState *st)
+{
+    VBH_CK(cudaMemcpyAsync(h->mirror, st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+    VBH_CK(cudaStreamSynchronize(h->stream));
+    return VBH_OK;
+}
+
+void to_result(const DevState &s, vbh_result *out)
+{
+    std::memset(out, 0, sizeof(*out));
+    const int M = s.M;
+    out->S = s.S;
+    out->iters = s.iter;
+    out->converged = s.converged;
+    out->status = s.status;
+    out->elbo_const_dropped = s.const_dropped;
+    double sum = 0.0;
+    for (int j = 0; j < M; ++j) {
+        out->kappa[j] = s.kappa[j];
+        out->weights[j] = s.kappa[j];
+        sum += s.kappa[j];
+    }
+    out->weights[M] = 1.0 - sum;
+    std::memcpy(out->W_inv, s.Winv, sizeof(double) * M * M);
+    out->nu = s.nu;
+    out->lambda = s.lam;
+    out->a_rho = s.a_rho;
+    out->b_rho = s.b_rho;
+    out->rho_mean = s.a_rho / s.b_rho;
+    out->rho_mode = (s.a_rho - 1.0) / s.b_rho;
+    out->elbo = s.elbo;
+}
+
+int check_common(vbh_handle *h, const float *r, const float *d, int64_t V, int S)
+{
+    if (!h) return VBH_EINVAL;
+    if (S < 1 || S > VBH_SMAX) return VBH_EINVAL;
+    if (V < 0 || V > (int64_t(1) << 40)) return VBH_EINVAL;
+    if (V > 0 && (!r || !d)) return VBH_EINVAL;
+    return VBH_OK;
+}
+
+} // namespace
+
+extern "C" {
+
+void vbh_prior_default(int S, vbh_prior *p)
+{
+    if (!p) return;
+    p->S = S;
+    p->K0 = nullptr;
+    p->q0 = 1e-3;
+    p->n0 = 1.0;
+    p->a0 = 0.5;
+    p->b0 = 0.5;
+    p->Lambda0_inv = nullptr;
+}
+
+void vbh_opts_default(vbh_opts *o)
+{
+    if (!o) return;
+    o->tol = 1e-8;
+    o->max_iter = 200;
+    o->precision = VBH_FP32;
+    o->init = VBH_INIT_PAPER;
+    o->init_state = nullptr;
+    o->elbo_trace = nullptr;
+}
+
+const char *vbh_strerror(int status)
+{
+    switch (status) {
+    case VBH_OK: return "ok";
+    case VBH_EINVAL: return "invalid argument";
+    case VBH_ENOMEM: return "out of memory";
+    case VBH_ECUDA: return "CUDA runtime error";
+    case VBH_ENONFINITE: return "non-finite global update or ELBO";
+    case VBH_ETIMEOUT: return "bounded device wait ran out";
+    case VBH_ESTATE: return "call out of order";
+    case VBH_EUNSUPPORTED: return "unsupported configuration";
+    default: return "unknown status";
+    }
+}
+
+size_t vbh_state_bytes(void) { return sizeof(DevState); }
+
+int vbh_create(vbh_handle **hp, int device, void *stream)
+{
+    if (!hp) return VBH_EINVAL;
+    *hp = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return VBH_ECUDA;
+    }
+    if (device < 0 || device >= ndev) return VBH_EINVAL;
+    DeviceGuard g(device);
+    if (!g.ok) return VBH_ECUDA;
+    vbh_handle *h = new (std::nothrow) vbh_handle();
+    if (!h) return VBH_ENOMEM;
+    h->device = device;
+    h->stream = static_cast<cudaStream_t>(stream);
+    int rc = VBH_OK;
+    if (cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) rc = VBH_ECUDA;
+    if (!rc && cudaMalloc(&h->st, sizeof(DevState)) != cudaSuccess) rc = VBH_ENOMEM;
+    if (!rc && cudaMalloc(&h->st_aux, sizeof(DevState)) != cudaSuccess) rc = VBH_ENOMEM;
+    if (!rc && cudaMallocHost(&h->mirror, sizeof(DevState)) != cudaSuccess) rc = VBH_ENOMEM;
+    if (rc) {
+        (void)cudaGetLastError();
+        vbh_destroy(h);
+        return rc;
+    }
+    *hp = h;
+    return VBH_OK;
+}
+
+void vbh_destroy(vbh_handle *h)
+{
+    if (!h) return;
+    DeviceGuard g(h->device);
+    cudaStreamSynchronize(h->stream);
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    cudaFree(h->st);
+    cudaFree(h->st_aux);
+    cudaFree(h->partials);
+    cudaFree(h->trace);
+    cudaFree(h->stage_r);
+    cudaFree(h->stage_d);
+    if (h->mirror) cudaFreeHost(h->mirror);
+    (void)cudaGetLastError();
+    delete h;
+}
+
+int vbh_fit_begin(vbh_handle *h, const float *r, const float *d, int64_t V, int S, const vbh_prior *p,
+                  const vbh_opts *o)
+{
+    int rc = check_common(h, r, d, V, S);
+    if (rc) return rc;
+    if ((rc = check_prior(p, S))) return rc;
+    if (!o || o->max_iter < 0 || !(o->tol >= 0.0) || !std::isfinite(o->tol) || o->precision != VBH_FP32)
+        return VBH_EINVAL;
+    if (o->init != VBH_INIT_PAPER && o->init != VBH_INIT_GIVEN) return VBH_EINVAL;
+    if (o->init == VBH_INIT_GIVEN && (!o->init_state || o->init_state->S != S)) return VBH_EINVAL;
+    DeviceGuard g(h->device);
+    if (!g.ok) return VBH_ECUDA;
+    h->begun = false;
+    KernelInfo ki;
+    int grid = 0;
+    if ((rc = prepare_kernel(h, S, V, &ki, &grid))) return rc;
+    const float *rd = nullptr, *dd = nullptr;
+    if ((rc = stage_inputs(h, r, d, V, S, &rd, &dd))) return rc;
+    if (o->max_iter + 1 > h->trace_cap) {
+        size_t cap = 0;
+        cudaFree(h->trace);
+        h->trace = nullptr;
+        h->trace_cap = 0;
+        if ((rc = ensure(reinterpret_cast<void **>(&h->trace), &cap, sizeof(double) * size_t(o->max_iter + 1))))
+            return rc;
+        h->trace_cap = o->max_iter + 1;
+    }
+    DevState *s = h->mirror;
+    VBH_CK(cudaStreamSynchronize(h->stream));     // the mirror may still be a copy target
+    std::memset(s, 0, sizeof(DevState));
+    fill_prior(s, p, S, V);
+    s->tol = o->tol;
+    s->max_iter = o->max_iter;
+    s->target = 0;
+    s->trace = h->trace;
+    const int M = S - 1;
+    if (o->init == VBH_INIT_GIVEN) {
+        const vbh_result *q = o->init_state;
+        if (!pos_finite(q->a_rho) || !pos_finite(q->b_rho) || !(q->nu > M - 1.0) || !pos_finite(q->lambda))
+            return VBH_EINVAL;
+        if (!host_spd(M, q->W_inv)) return VBH_EINVAL;
+        s->a_rho = q->a_rho;
+        s->b_rho = q->b_rho;
+        s->nu = q->nu;
+        s->lam = q->lambda;
+        for (int j = 0; j < M; ++j) s->kappa[j] = q->kappa[j];
+        std::memcpy(s->Winv, q->W_inv, sizeof(double) * M * M);
+    }
+    VBH_CK(cudaMemcpyAsync(h->st, s, sizeof(DevState), cudaMemcpyHostToDevice, h->stream));
+    if (o->init == VBH_INIT_GIVEN) {
+        // sweep 0 = the ELBO of the given factors (Q(beta) from them); the
+        // sweeps that follow update all factors
+        if ((rc = launch_setup(h, h->st, ki, 0))) return rc;
+        if ((rc = launch_sweep(h, h->st, vbh::MODE_ELBO, ki, grid, rd, dd, V))) return rc;
+    } else {
+        if ((rc = launch_setup(h, h->st, ki, 1))) return rc;
+        if ((rc = launch_sweep(h, h->st, vbh::MODE_INIT, ki, grid, rd, dd, V))) return rc;
+    }
+    if ((rc = read_state(h, h->st))) return rc;
+    if (h->mirror->status) return h->mirror->status;
+    h->begun = true;
+    h->S = S;
+    h->V = V;
+    h->r = rd;
+    h->d = dd;
+    h->ki = ki;
+    h->grid = grid;
+    h->max_iter = o->max_iter;
+    h->user_trace = o->elbo_trace;
+    return VBH_OK;
+}
+
+int vbh_fit_step(vbh_handle *h, int nsweeps, int *converged)
+{
+    if (!h || nsweeps < 0) return VBH_EINVAL;
+    if (!h->begun) return VBH_ESTATE;
+    DeviceGuard g(h->device);
+    if (!g.ok) return VBH_ECUDA;
+    int rc = build_graph(h);
+    if (rc) return rc;
+    vbh::set_target_kernel<<<1, 32, 0, h->stream>>>(h->st, nsweeps);
+    VBH_CK(cudaGetLastError());
+    VBH_CK(cudaGraphLaunch(h->gexec, h->stream));
+    if ((rc = read_state(h, h->st))) return rc;
+    if (converged) *converged = h->mirror->converged;
+    return h->mirror->status;
+}
+
+int vbh_fit_result(vbh_handle *h, vbh_result *out)
+{
+    if (!h || !out) return VBH_EINVAL;
+    if (!h->begun) return VBH_ESTATE;
+    DeviceGuard g(h->device);
+    if (!g.ok) return VBH_ECUDA;
+    int rc = read_state(h, h->st);
+    if (rc) return rc;
+    to_result(*h->mirror, out);
+    if (h->user_trace) {
+        const int n = h->mirror->iter + 1;
+        VBH_CK(cudaMemcpyAsync(h->user_trace, h->trace, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
+        VBH_CK(cudaStreamSynchronize(h->stream));
+    }
+    return out->status;
+}
+
+int vbh_fit(vbh_handle *h, const float *r, const float *d, int64_t V, int S, const vbh_prior *p,
+            const vbh_opts *o, vbh_result *out)
+{
+    if (!out) return VBH_EINVAL;
+    int rc = vbh_fit_begin(h, r, d, V, S, p, o);
+    if (rc) return rc;
+    int conv = 0;
+    if (o->max_iter > 0) {
+        rc = vbh_fit_step(h, o->max_iter, &conv);
+        if (rc) {
+            vbh_fit_result(h, out);
+            return rc;
+        }
+    }
+    return vbh_fit_result(h, out);
+}
+
+int vbh_elbo(vbh_handle *h, const float *r, const float *d, int64_t V, int S, const vbh_prior *p,
+             const vbh_result *q, double *elbo)
+{
+    int rc = check_common(h, r, d, V, S);
+    if (rc) return rc;
+    if ((rc = check_prior(p, S))) return rc;
+    if (!q || !elbo || q->S != S) return VBH_EINVAL;
+    const int M = S - 1;
+    if (!pos_finite(q->a_rho) || !pos_finite(q->b_rho) || !(q->nu > M - 1.0) || !pos_finite(q->lambda))
+        return VBH_EINVAL;
+    if (!host_spd(M, q->W_inv)) return VBH_EINVAL;
+    DeviceGuard g(h->device);
+    if (!g.ok) return VBH_ECUDA;
+    KernelInfo ki;
+    int grid = 0;
+    if ((rc = prepare_kernel(h, S, V, &ki, &grid))) return rc;
+    const float *rd = nullptr, *dd = nullptr;
+    if ((rc = stage_inputs(h, r, d, V, S, &rd, &dd))) return rc;
+    if (h->begun && (rd != h->r || dd != h->d)) h->begun = false;   // staging buffers were reused
+    DevState *s = h->mirror;
+    VBH_CK(cudaStreamSynchronize(h->stream));
+    std::memset(s, 0, sizeof(DevState));
+    fill_prior(s, p, S, V);
+    s->a_rho = q->a_rho;
+    s->b_rho = q->b_rho;
+    s->nu = q->nu;
+    s->lam = q->lambda;
+    for (int j = 0; j < M; ++j) s->kappa[j] = q->kappa[j];
+    std::memcpy(s->Winv, q->W_inv, sizeof(double) * M * M);
+    VBH_CK(cudaMemcpyAsync(h->st_aux, s, sizeof(DevState), cudaMemcpyHostToDevice, h->stream));
+    if ((rc = launch_setup(h, h->st_aux, ki, 0))) return rc;
+    if ((rc = launch_sweep(h, h->st_aux, vbh::MODE_ELBO, ki, grid, rd, dd, V))) return rc;
+    if ((rc = read_state(h, h->st_aux))) return rc;
+    *elbo = h->mirror->elbo;
+    return h->mirror->status;
+}
+
+} // extern "C"

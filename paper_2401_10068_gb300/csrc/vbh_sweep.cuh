@@ -1,0 +1,654 @@
+// vbh_sweep.cuh -- the fused CAVI sweep for one data set (FP32 per
+// observation, FP64 across blocks and in the global update).
+//
+// One launch = one sweep of Section 3.5:
+//   (a) per observation, with Sigma0 = E[Lambda]^{-1} = L L^T, kappa, E[rho]:
+//       D_i = d_{i,1:M} - d_{i,S},  y_i = r_i - d_{i,S}
+//       q_i = D_i^T Sigma0 D_i = |L^T D_i|^2,  t_i = kappa^T D_i,  e_i = y_i - t_i
+//   (b) the exact Q(beta_i) of Eq. 20-21 in rank-1 form (Sherman-Morrison on
+//       Eq. 20, never materialised):
+//       c_i = E[rho] / (1 + E[rho] q_i),  w_i = c_i e_i
+//       Sigma_i = Sigma0 - c_i u_i u_i^T,  mu_{beta_i} = kappa + w_i u_i,  u_i = Sigma0 D_i
+//       braces of Eq. 17:  S_i = e_i^2 / (1 + E[rho] q_i)^2 + q_i / (1 + E[rho] q_i)
+//       ln|Sigma_i| = ln|Sigma0| - ln(1 + E[rho] q_i)   (matrix determinant lemma)
+//   (c) block-local sums g = sum w_i D_i, G = sum (w_i^2 - c_i) D_i D_i^T,
+//       T3 = sum S_i, T4 = sum ln(1 + E[rho] q_i): FP32 over chunks of 64
+//       observations per thread, warp butterfly, FP64 from there on;
+//   (d) the last block to finish adds the per-block FP64 partials in block
+//       order (deterministic) and runs the closed-form updates of Eq. 16-18,
+//       22-25 and 28-31 in FP64, written in centred form:
+//       s = Sigma0 g, delta = (s + q0 (K0 - kappa)) / (q0 + V), kappa' = kappa + delta
+//       W'^{-1} = Lambda_0^{-1} + V Sigma0 + Sigma0 G Sigma0 + q0 (K0-kappa)(K0-kappa)^T
+//                 - (q0 + V) delta delta^T        (= Eq. 25 exactly)
+//   (e) the ELBO of Eq. 11 and the convergence test, and the FP32 globals of
+//       the next sweep.
+// The inputs (r, d) are read from HBM exactly once per sweep, through 1-D
+// bulk copies (cp.async.bulk) into a ring of shared-memory stages.
+#pragma once
+
+#include "vbh_internal.cuh"
+
+namespace vbh {
+
+template <int S>
+struct SweepCfg {
+    static constexpr int M = S - 1;
+    static constexpr int MA = M > 0 ? M : 1;                // array extent
+    static constexpr int NG = M * (M + 1) / 2;              // packed lower G
+    static constexpr int NSTAT = NG + M + 2;                // G, g, T3, T4
+    static constexpr int NGRP = (NSTAT + 31) / 32;          // 32-wide butterfly groups
+    static constexpr int THREADS = 256;
+    static constexpr int OPT = 2;                           // observations per thread per tile
+    static constexpr int T = THREADS * OPT;                 // observations per tile
+    static constexpr int STAGES = 4;
+    static constexpr int FLUSH_TILES = 32;                  // 64 observations per thread per FP32 chunk
+    static constexpr uint32_t R_BYTES = T * 4u;
+    static constexpr uint32_t D_BYTES = T * S * 4u;
+    static constexpr uint32_t STAGE_BYTES = R_BYTES + D_BYTES;
+    static constexpr size_t RING_BYTES = size_t(STAGES) * STAGE_BYTES;
+    static constexpr size_t SMEM_BYTES = RING_BYTES + 64;   // + mbarriers
+};
+
+// Load the S profile entries of row j of a shared-memory tile.  The vector
+// width is the largest power of two (<= 4) dividing S; for S a multiple of 8
+// the 16-byte quads of a row are visited in an order rotated by row, so that
+// the 8 rows of one shared-memory phase hit distinct banks.
+template <int S>
+__device__ __forceinline__ void load_row(const float *__restrict__ dt, int j, float (&x)[S])
+{
+    if constexpr (S % 4 == 0) {
+        constexpr int NQ = S / 4;
+        const float4 *p = reinterpret_cast<const float4 *>(dt + size_t(j) * S);
+        const int rot = (S % 8 == 0) ? (((j * S) >> 5) % NQ) : 0;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            int qq = q + rot;
+            if (qq >= NQ) qq -= NQ;
+            const float4 v = p[qq];
+            // scatter by the rotated index; unrolled selects keep x in registers
+#pragma unroll
+            for (int z = 0; z < NQ; ++z) {
+                if (z == qq) {
+                    x[4 * z + 0] = v.x;
+                    x[4 * z + 1] = v.y;
+                    x[4 * z + 2] = v.z;
+                    x[4 * z + 3] = v.w;
+                }
+            }
+        }
+    } else if constexpr (S % 2 == 0) {
+        const float2 *p = reinterpret_cast<const float2 *>(dt + size_t(j) * S);
+#pragma unroll
+        for (int q = 0; q < S / 2; ++q) {
+            const float2 v = p[q];
+            x[2 * q] = v.x;
+            x[2 * q + 1] = v.y;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < S; ++q) x[q] = dt[size_t(j) * S + q];
+    }
+}
+
+// Steps (a)-(b) and the accumulation of (c) for one observation.
+template <int S>
+__device__ __forceinline__ void observe(const float (&x)[S], float rr, const float (&L)[SweepCfg<S>::NG > 0 ? SweepCfg<S>::NG : 1],
+                                        const float (&kap)[SweepCfg<S>::MA], float erho,
+                                        float (&acc)[SweepCfg<S>::NSTAT])
+{
+    using C = SweepCfg<S>;
+    constexpr int M = C::M;
+    constexpr int NG = C::NG;
+    const float dS = x[S - 1];
+    const float y = rr - dS;
+    float D[C::MA];
+    float q = 0.0f, t = 0.0f;
+#pragma unroll
+    for (int j = 0; j < M; ++j) D[j] = x[j] - dS;
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+        float v = 0.0f;                                    // (L^T D)_j
+#pragma unroll
+        for (int k = j; k < M; ++k) v = fmaf(L[k * (k + 1) / 2 + j], D[k], v);
+        q = fmaf(v, v, q);
+        t = fmaf(kap[j], D[j], t);
+    }
+    const float e = y - t;
+    const float den = fmaf(erho, q, 1.0f);
+    const float inv = __frcp_rn(den);
+    const float c = erho * inv;
+    const float w = c * e;
+    const float gam = fmaf(w, w, -c);
+    const float ei = e * inv;
+    acc[NG + M] += fmaf(ei, ei, q * inv);                  // S_i
+    acc[NG + M + 1] += log1pf(erho * q);                   // ln(1 + E[rho] q_i)
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+        acc[NG + j] = fmaf(w, D[j], acc[NG + j]);
+        const float gd = gam * D[j];
+#pragma unroll
+        for (int k = 0; k <= j; ++k) acc[j * (j + 1) / 2 + k] = fmaf(gd, D[k], acc[j * (j + 1) / 2 + k]);
+    }
+}
+
+// Move the FP32 chunk sums of a warp into FP64: a butterfly reduce-scatter
+// over each group of 32 statistics leaves lane l with the warp total of
+// statistic 32 g + l, which it adds to its FP64 accumulator.
+template <int NSTAT, int NGRP>
+__device__ __forceinline__ void flush_warp(float (&acc)[NSTAT], double (&acc64)[NGRP], int lane)
+{
+#pragma unroll
+    for (int g = 0; g < NGRP; ++g) {
+        float v[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = (g * 32 + i < NSTAT) ? acc[(g * 32 + i < NSTAT) ? g * 32 + i : 0] : 0.0f;
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) {
+            const bool up = (lane & off) != 0;
+#pragma unroll
+            for (int i = 0; i < off; ++i) {
+                const float keep = up ? v[i + off] : v[i];
+                const float send = up ? v[i] : v[i + off];
+                v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+            }
+        }
+        acc64[g] += static_cast<double>(v[0]);
+    }
+#pragma unroll
+    for (int i = 0; i < NSTAT; ++i) acc[i] = 0.0f;
+}
+
+// ---------------------------------------------------------------------------
+// Cholesky factor L (lower, row-major) of a symmetric positive-definite M x M
+// matrix A in shared memory, column by column, by one warp.  Returns nonzero
+// in every lane when A is not positive definite (a unit pivot is used then).
+// ---------------------------------------------------------------------------
+template <int M>
+__device__ int warp_cholesky(const double *A, double *L, int lane)
+{
+    int fail = 0;
+    for (int i = lane; i < M * M; i += 32) L[i] = 0.0;
+    __syncwarp();
+    for (int j = 0; j < M; ++j) {
+        if (lane == 0) {
+            double s = A[j * M + j];
+            for (int k = 0; k < j; ++k) s -= L[j * M + k] * L[j * M + k];
+            if (!(s > 0.0) || !isfinite(s)) {
+                fail = 1;
+                s = 1.0;
+            }
+            L[j * M + j] = sqrt(s);
+        }
+        __syncwarp();
+        for (int i = j + 1 + lane; i < M; i += 32) {
+            double s = A[i * M + j];
+            for (int k = 0; k < j; ++k) s -= L[i * M + k] * L[j * M + k];
+            L[i * M + j] = s / L[j * M + j];
+        }
+        __syncwarp();
+    }
+    return __shfl_sync(0xffffffffu, fail, 0);
+}
+
+// What the next data pass reads, from W^{-1} and nu (Eq. 28: E[Lambda] = nu W,
+// so Sigma0 = W^{-1}/nu): the FP32 Cholesky factor of Sigma0, Sigma0 itself
+// and ln|Sigma0|.  Sweep 0 uses (Lambda_0^{-1}, nu = 1).  One warp; Lw
+// receives chol(W^{-1}).  The global update and the set-up kernel both use
+// this function, so a fit resumed from saved factors continues bit for bit.
+template <int M>
+__device__ int derive_pass_globals(DevState *st, const double *Wn, double nu, double *Lw, int lane)
+{
+    const int fail = warp_cholesky<M>(Wn, Lw, lane);
+    const double rs = rsqrt(nu);
+    for (int i = lane; i < M; i += 32)
+        for (int k = 0; k <= i; ++k) st->sw.L[i * (i + 1) / 2 + k] = static_cast<float>(Lw[i * M + k] * rs);
+    for (int i = lane; i < M * M; i += 32) st->Sigma0[i] = Wn[i] / nu;
+    if (lane == 0) {
+        double ld = 0.0;
+        for (int j = 0; j < M; ++j) ld += 2.0 * log(Lw[j * M + j]);
+        st->lndetSigma0 = ld - M * log(nu);
+    }
+    return fail;
+}
+
+// ---------------------------------------------------------------------------
+// (d)+(e): FP64 global update, ELBO and control, run by the whole last block.
+// ws: shared-memory workspace of at least gu_ws_doubles<M>() doubles.
+// ---------------------------------------------------------------------------
+template <int M>
+constexpr int gu_ws_doubles()
+{
+    return ((M * (M + 1) / 2 + M + 2 + 31) / 32) * 32 + 10 * (M > 0 ? M * M : 1) + 8 * (M > 0 ? M : 1) + 64;
+}
+
+__device__ __forceinline__ double wishart_lnB_d(int M, double lndetW, double nu, const double *lg)
+{
+    // ln B(W, nu) = -nu/2 ln|W| - nu M/2 ln 2 - M(M-1)/4 ln pi - sum_j lnGamma((nu+1-j)/2)
+    double s = -0.5 * nu * lndetW - 0.5 * nu * M * 0.69314718055994530942 - 0.25 * M * (M - 1) * 1.1447298858494002;
+    for (int j = 0; j < M; ++j) s -= lg[j];
+    return s;
+}
+
+template <int M>
+__device__ void global_update(DevState *st, const double *__restrict__ part, int nblk, const SweepArgs &a,
+                              double *ws)
+{
+    constexpr int NG = M * (M + 1) / 2;
+    constexpr int NSTAT = NG + M + 2;
+    constexpr int MM = M > 0 ? M * M : 1;
+    constexpr int MV = M > 0 ? M : 1;
+    constexpr int MD = M > 0 ? M : 1;               // divisor (loops over M*M entries are empty at M = 0)
+    constexpr double LN2PI = 1.8378770664093454836;
+    const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
+    const int mode = a.mode;
+
+    double *stat = ws;
+    double *Sg = stat + ((NSTAT + 31) / 32) * 32;   // Sigma0 of this sweep
+    double *G = Sg + MM;                            // sum (w^2 - c) D D^T (full)
+    double *A = G + MM;                             // Sigma0 G
+    double *B = A + MM;                             // Sigma0 G Sigma0
+    double *Wn = B + MM;                            // new W^{-1}
+    double *Lw = Wn + MM;                           // chol(W^{-1})
+    double *Li = Lw + MM;                           // Lw^{-1}
+    double *EL = Li + MM;                           // E[Lambda] = nu W
+    double *Cm = EL + MM;                           // sum_i E[(beta_i - kappa')(beta_i - kappa')^T]
+    double *Wk = Cm + MM;                           // spare
+    double *gv = Wk + MM;                           // g
+    double *sv = gv + MV;                           // Sigma0 g
+    double *dv = sv + MV;                           // delta
+    double *ko = dv + MV;                           // kappa (this sweep)
+    double *kn = ko + MV;                           // kappa'
+    double *psi = kn + MV;                          // psi((nu+1-j)/2)
+    double *lgv = psi + MV;                         // lnGamma((nu+1-j)/2)
+    double *av = lgv + MV;                          // K0 - kappa
+    double *sc = av + MV;                           // scalars
+    __shared__ int s_fail;
+
+    // 1. partials -> totals, fixed order per statistic
+    for (int j = warp; j < NSTAT; j += nwarp) {
+        double s = 0.0;
+#pragma unroll 4
+        for (int b = lane; b < nblk; b += 32) s += __ldcg(part + size_t(b) * NSTAT + j);
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        if (lane == 0) stat[j] = s;
+    }
+    if (tid == 0) {
+        s_fail = 0;
+        // ln|Sigma0| of this pass, kept before step 5 overwrites the state's copy
+        sc[1] = (mode == MODE_INIT) ? st->lndetL0inv : st->lndetSigma0;
+    }
+    for (int i = tid; i < M * M; i += nth) Sg[i] = (mode == MODE_INIT) ? st->L0inv[i] : st->Sigma0[i];
+    for (int i = tid; i < M; i += nth) {
+        ko[i] = (mode == MODE_INIT) ? st->K0[i] : st->kappa[i];
+        av[i] = st->K0[i] - ko[i];
+    }
+    __syncthreads();
+
+    const double V = st->V;
+    const double T3 = stat[NG + M], T4 = stat[NG + M + 1];
+    const double lndetS0 = sc[1];
+    const double q0 = st->q0, n0 = st->n0, a0 = st->a0, b0 = st->b0;
+    const double lam = (mode == MODE_ELBO) ? st->lam : q0 + V;      // Eq. 22
+    const double nu = (mode == MODE_ELBO) ? st->nu : n0 + V;        // Eq. 23
+
+    // 2. G (full), s = Sigma0 g, A = Sigma0 G
+    for (int i = tid; i < M * M; i += nth) {
+        const int r = i / MD, c = i % MD;
+        G[i] = (r >= c) ? stat[r * (r + 1) / 2 + c] : stat[c * (c + 1) / 2 + r];
+    }
+    for (int i = tid; i < M; i += nth) gv[i] = stat[NG + i];
+    __syncthreads();
+    for (int i = tid; i < M * M; i += nth) {
+        const int r = i / MD, c = i % MD;
+        double s = 0.0;
+        for (int k = 0; k < M; ++k) s = fma(Sg[r * M + k], G[k * M + c], s);
+        A[i] = s;
+    }
+    for (int i = tid; i < M; i += nth) {
+        double s = 0.0;
+        for (int k = 0; k < M; ++k) s = fma(Sg[i * M + k], gv[k], s);
+        sv[i] = s;
+    }
+    __syncthreads();
+    // 3. B = Sigma0 G Sigma0, delta, kappa'
+    for (int i = tid; i < M * M; i += nth) {
+        const int r = i / MD, c = i % MD;
+        double s = 0.0;
+        for (int k = 0; k < M; ++k) s = fma(A[r * M + k], Sg[k * M + c], s);
+        B[i] = s;
+    }
+    for (int i = tid; i < M; i += nth) {
+        const double dl = (mode == MODE_ELBO) ? 0.0 : (sv[i] + q0 * av[i]) / lam;   // Eq. 24, centred
+        dv[i] = dl;
+        kn[i] = ko[i] + dl;
+    }
+    __syncthreads();
+    // 4. W'^{-1} (Eq. 25, centred) and C
+    for (int i = tid; i < M * M; i += nth) {
+        const int r = i / MD, c = i % MD;
+        const double Bs = 0.5 * (B[r * M + c] + B[c * M + r]);
+        if (mode == MODE_ELBO) {
+            Wn[i] = st->Winv[i];
+        } else {
+            Wn[i] = st->L0inv[i] + V * Sg[i] + Bs + q0 * av[r] * av[c] - lam * dv[r] * dv[c];
+        }
+        // C = V Sigma0 + Sigma0 G Sigma0 - s delta^T - delta s^T + V delta delta^T
+        Cm[i] = V * Sg[i] + Bs - sv[r] * dv[c] - dv[r] * sv[c] + V * dv[r] * dv[c];
+    }
+    __syncthreads();
+    // 5. Cholesky of W'^{-1} (warp 0) and, unless only the ELBO is wanted,
+    //    the Sigma0 / FP32 factor of the next data pass
+    if (warp == 0) {
+        int fail;
+        if (mode == MODE_ELBO) {
+            fail = warp_cholesky<M>(Wn, Lw, lane);
+        } else {
+            fail = derive_pass_globals<M>(st, Wn, nu, Lw, lane);
+        }
+        if (lane == 0 && fail) s_fail = 1;
+        __syncwarp();
+        // Lw^{-1}: lane c solves Lw x = e_c (forward substitution)
+        for (int c = lane; c < M; c += 32) {
+            for (int i = 0; i < M; ++i) Li[i * M + c] = 0.0;
+            for (int i = c; i < M; ++i) {
+                double s = (i == c) ? 1.0 : 0.0;
+                for (int k = c; k < i; ++k) s -= Lw[i * M + k] * Li[k * M + c];
+                Li[i * M + c] = s / Lw[i * M + i];
+            }
+        }
+    }
+    // special functions of nu (any warp): psi and lnGamma at (nu + 1 - j)/2, j = 1..M
+    for (int j = tid; j < M; j += nth) {
+        const double x = 0.5 * (nu - j);
+        psi[j] = digamma_d(x);
+        lgv[j] = lgamma(x);
+    }
+    __syncthreads();
+    // 6. E[Lambda] = nu Li^T Li (Eq. 28)
+    for (int i = tid; i < M * M; i += nth) {
+        const int r = i / MD, c = i % MD;
+        double s = 0.0;
+        for (int k = (r > c ? r : c); k < M; ++k) s = fma(Li[k * M + r], Li[k * M + c], s);
+        EL[i] = nu * s;
+    }
+    __syncthreads();
+    // 7. scalars, ELBO and control (thread 0)
+    if (tid == 0) {
+        double lndetWn = 0.0;
+        for (int j = 0; j < M; ++j) lndetWn += 2.0 * log(Lw[j * M + j]);
+        const double lndetW = -lndetWn;
+        double trELC = 0.0, trL0EL = 0.0, quadK = 0.0, sumpsi = 0.0;
+        for (int r = 0; r < M; ++r) {
+            sumpsi += psi[r];
+            for (int c = 0; c < M; ++c) {
+                trELC = fma(EL[r * M + c], Cm[c * M + r], trELC);
+                trL0EL = fma(st->L0inv[r * M + c], EL[c * M + r], trL0EL);
+                quadK = fma((kn[r] - st->K0[r]) * EL[r * M + c], kn[c] - st->K0[c], quadK);
+            }
+        }
+        const double a_rho = (mode == MODE_ELBO) ? st->a_rho : a0 + 0.5 * V;      // Eq. 16
+        const double b_rho = (mode == MODE_ELBO) ? st->b_rho : b0 + 0.5 * T3;     // Eq. 17
+        const double Er = a_rho / b_rho;                                         // Eq. 29
+        const double psia = digamma_d(a_rho);
+        const double Elr = psia - log(b_rho);
+        const double ElL = sumpsi + M * 0.69314718055994530942 + lndetW;
+        const double lnBq = wishart_lnB_d(M, lndetW, nu, lgv);
+        double lnB0 = 0.0;
+        int dropped = 0;
+        if (M > 0) {
+            if (n0 > M - 1.0) {
+                double lg0 = 0.0;
+                for (int j = 0; j < M; ++j) lg0 += lgamma(0.5 * (n0 - j));
+                lnB0 = 0.5 * n0 * st->lndetL0inv - 0.5 * n0 * M * 0.69314718055994530942
+                     - 0.25 * M * (M - 1) * 1.1447298858494002 - lg0;
+            } else {
+                dropped = 1;
+            }
+        }
+        double L = 0.0;
+        L += 0.5 * V * (Elr - LN2PI) - 0.5 * Er * T3;                                   // E ln p(r | beta, rho)
+        L += 0.5 * V * (ElL - M * LN2PI) - 0.5 * trELC - 0.5 * V * M / lam;            // E ln p(beta | K, Lambda)
+        L += 0.5 * M * (log(q0) - LN2PI) + 0.5 * ElL - 0.5 * q0 * (quadK + M / lam);     // E ln p(K | Lambda)
+        L += lnB0 + 0.5 * (n0 - M - 1.0) * ElL - 0.5 * trL0EL;                          // E ln p(Lambda)
+        L += a0 * log(b0) - lgamma(a0) + (a0 - 1.0) * Elr - b0 * Er;                     // E ln p(rho)
+        L += 0.5 * (V * lndetS0 - T4) + 0.5 * V * M * (1.0 + LN2PI);                    // H[Q(beta)]
+        L += -0.5 * ElL - 0.5 * M * (log(lam) - LN2PI) + 0.5 * M;                        // H[Q(K | Lambda)]
+        if (M > 0) L += -lnBq - 0.5 * (nu - M - 1.0) * ElL + 0.5 * nu * M;              // H[Q(Lambda)]
+        L += a_rho - log(b_rho) + lgamma(a_rho) + (1.0 - a_rho) * psia;                  // H[Q(rho)]
+
+        bool finite = isfinite(L) && isfinite(a_rho) && isfinite(b_rho) && b_rho > 0.0 && !s_fail;
+        for (int j = 0; j < M; ++j) finite = finite && isfinite(kn[j]);
+        st->elbo = L;
+        st->const_dropped = dropped;
+        if (mode != MODE_ELBO) {
+            st->a_rho = a_rho;
+            st->b_rho = b_rho;
+            st->nu = nu;
+            st->lam = lam;
+            st->erho = Er;
+            if (mode == MODE_INIT) {
+                st->iter = 0;
+                st->converged = 0;
+            } else {
+                st->iter += 1;
+                st->converged = (fabs(L - st->elbo_prev) < st->tol * fabs(L)) ? 1 : 0;
+            }
+            if (st->trace && st->iter <= st->max_iter) st->trace[st->iter] = L;
+            st->elbo_prev = L;
+        } else {
+            // sweep 0 of a fit started from given factors: L_0 of that state
+            st->elbo_prev = L;
+            if (st->trace) st->trace[0] = L;
+        }
+        if (!finite && st->status == ST_OK) st->status = ST_ENONFINITE;
+        sc[0] = Er;
+    }
+    __syncthreads();
+    // 8. write the new globals and the FP32 inputs of the next sweep
+    if (mode != MODE_ELBO) {
+        for (int i = tid; i < M * M; i += nth) st->Winv[i] = Wn[i];
+        for (int i = tid; i < M; i += nth) {
+            st->kappa[i] = kn[i];
+            st->sw.kappa[i] = static_cast<float>(kn[i]);
+        }
+        if (tid == 0) st->sw.erho = static_cast<float>(sc[0]);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        const int keep = (mode == MODE_ITER || mode == MODE_INIT) && st->status == ST_OK && !st->converged &&
+                         st->iter < st->target && st->iter < st->max_iter;
+        if (a.use_cond) cudaGraphSetConditional(a.cond, keep ? 1u : 0u);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The fused sweep kernel.
+// ---------------------------------------------------------------------------
+template <int S>
+__global__ void __launch_bounds__(SweepCfg<S>::THREADS) sweep_kernel(SweepArgs a)
+{
+    using C = SweepCfg<S>;
+    constexpr int M = C::M, NG = C::NG, NSTAT = C::NSTAT, NGRP = C::NGRP;
+    constexpr int THREADS = C::THREADS, T = C::T, STAGES = C::STAGES;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + C::RING_BYTES);
+    __shared__ double s_red[THREADS / 32][NGRP * 32];
+    __shared__ int s_bad, s_last;
+
+    DevState *st = a.st;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_bad = 0;
+
+    // Every block takes the same decision: the control fields are only written
+    // by the last block of a launch, after all other blocks have finished.
+    const bool run = (a.mode != MODE_ITER) ||
+                     (st->status == ST_OK && !st->converged && st->iter < st->target && st->iter < st->max_iter);
+
+    float acc[NSTAT];
+    double acc64[NGRP];
+#pragma unroll
+    for (int i = 0; i < NSTAT; ++i) acc[i] = 0.0f;
+#pragma unroll
+    for (int g = 0; g < NGRP; ++g) acc64[g] = 0.0;
+
+    if (run) {
+        float L[NG > 0 ? NG : 1], kap[C::MA];
+        float erho;
+        if (a.mode == MODE_INIT) {
+            erho = 0.0f;                         // c_i = 0: Q(beta_i) = N(K0, Lambda_0^{-1})
+        } else {
+            erho = st->sw.erho;
+        }
+#pragma unroll
+        for (int i = 0; i < NG; ++i) L[i] = st->sw.L[i];
+#pragma unroll
+        for (int i = 0; i < M; ++i) kap[i] = st->sw.kappa[i];
+        if constexpr (NG == 0) L[0] = 0.0f;
+        if constexpr (M == 0) kap[0] = 0.0f;
+
+        const long long V = a.V;
+        const long long ntf = V / T;                         // full tiles
+        const long long bid = blockIdx.x, nb = gridDim.x;
+        const long long nk = (ntf > bid) ? (ntf - bid + nb - 1) / nb : 0;   // my full tiles
+
+        if (tid == 0) {
+            for (int s = 0; s < STAGES; ++s) mbar_init(&full[s], 1);
+            fence_mbar_init();
+        }
+        __syncthreads();
+        if (tid == 0) {
+            for (long long k = 0; k < nk && k < STAGES; ++k) {
+                const long long tile = bid + k * nb;
+                unsigned char *stage = smem + size_t(k) * C::STAGE_BYTES;
+                mbar_arrive_expect_tx(&full[k], C::STAGE_BYTES);
+                bulk_load(stage, a.r + tile * T, C::R_BYTES, &full[k]);
+                bulk_load(stage + C::R_BYTES, a.d + tile * T * S, C::D_BYTES, &full[k]);
+            }
+        }
+        long long k = 0;
+        int ftile = 0;
+        for (; k < nk; ++k) {
+            const int s = int(k % STAGES);
+            const uint32_t parity = uint32_t((k / STAGES) & 1);
+            const bool ok = mbar_wait_bounded(&full[s], parity, 2000000000ull);
+            if (ok) {
+                const float *rt = reinterpret_cast<const float *>(smem + size_t(s) * C::STAGE_BYTES);
+                const float *dt = rt + T;
+#pragma unroll
+                for (int u = 0; u < C::OPT; ++u) {
+                    const int j = tid + u * THREADS;
+                    float x[S];
+                    load_row<S>(dt, j, x);
+                    observe<S>(x, rt[j], L, kap, erho, acc);
+                }
+            }
+            if (__syncthreads_or(!ok)) {
+                if (tid == 0) s_bad = 1;
+                break;
+            }
+            if (tid == 0 && k + STAGES < nk) {
+                const long long tile = bid + (k + STAGES) * nb;
+                unsigned char *stage = smem + size_t(s) * C::STAGE_BYTES;
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(&full[s], C::STAGE_BYTES);
+                bulk_load(stage, a.r + tile * T, C::R_BYTES, &full[s]);
+                bulk_load(stage + C::R_BYTES, a.d + tile * T * S, C::D_BYTES, &full[s]);
+            }
+            if (++ftile == C::FLUSH_TILES) {
+                flush_warp<NSTAT, NGRP>(acc, acc64, lane);
+                ftile = 0;
+            }
+        }
+        __syncthreads();
+        if (s_bad) {
+            // a wait ran out: record it, then let the copies this block issued
+            // and did not consume land before the block exits (bounded)
+            if (tid == 0) {
+                atomicCAS(&st->status, ST_OK, ST_ETIMEOUT);
+                for (long long kk = k; kk < nk && kk < k + STAGES; ++kk)
+                    (void)mbar_wait_bounded(&full[kk % STAGES], uint32_t((kk / STAGES) & 1), 200000000ull);
+            }
+        } else {
+            // ragged tail: the observations after the last full tile, plain loads
+            const long long tail0 = ntf * T;
+            if (tail0 < V && bid == (ntf % nb)) {
+                for (long long i = tail0 + tid; i < V; i += THREADS) {
+                    float x[S];
+#pragma unroll
+                    for (int q = 0; q < S; ++q) x[q] = __ldg(a.d + i * S + q);
+                    observe<S>(x, __ldg(a.r + i), L, kap, erho, acc);
+                }
+            }
+        }
+    }
+    flush_warp<NSTAT, NGRP>(acc, acc64, lane);
+
+    // block reduction in FP64, fixed order, then this block's partials
+#pragma unroll
+    for (int g = 0; g < NGRP; ++g) s_red[warp][g * 32 + lane] = acc64[g];
+    __syncthreads();
+    for (int j = tid; j < NSTAT; j += THREADS) {
+        double s = 0.0;
+#pragma unroll
+        for (int w = 0; w < THREADS / 32; ++w) s += s_red[w][j];
+        a.partials[size_t(blockIdx.x) * NSTAT + j] = s;
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = (atomicAdd(&st->ticket, 1u) == gridDim.x - 1) ? 1 : 0;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (run && !s_bad) {
+        // the ring is idle here (every copy of this block has landed), so its
+        // shared memory serves as the workspace of the global update
+        global_update<M>(st, a.partials, gridDim.x, a, reinterpret_cast<double *>(smem));
+    } else if (tid == 0 && a.use_cond) {
+        cudaGraphSetConditional(a.cond, 0u);
+    }
+    if (tid == 0) st->ticket = 0u;
+}
+
+// ---------------------------------------------------------------------------
+// Set-up before the first data pass of a fit (one warp):
+//   init != 0: sweep 0 reads Sigma0 = Lambda_0^{-1}, kappa = K0, E[rho] = 0;
+//   init == 0: it reads Sigma0 = W^{-1}/nu, kappa, E[rho] = a_rho / b_rho of
+//              the given global factors.
+// Also ln|Lambda_0^{-1}| for the prior term of the ELBO.
+// ---------------------------------------------------------------------------
+template <int M>
+__global__ void setup_kernel(DevState *st, int init)
+{
+    constexpr int MM = M > 0 ? M * M : 1;
+    __shared__ double A[MM], Lc[MM];
+    const int lane = threadIdx.x;
+    if (threadIdx.x >= 32) return;
+    for (int i = lane; i < M * M; i += 32) A[i] = st->L0inv[i];
+    __syncwarp();
+    int fail = warp_cholesky<M>(A, Lc, lane);
+    if (lane == 0) {
+        double l0 = 0.0;
+        for (int j = 0; j < M; ++j) l0 += 2.0 * log(Lc[j * M + j]);
+        st->lndetL0inv = l0;
+    }
+    __syncwarp();
+    if (!init)
+        for (int i = lane; i < M * M; i += 32) A[i] = st->Winv[i];
+    __syncwarp();
+    fail |= derive_pass_globals<M>(st, A, init ? 1.0 : st->nu, Lc, lane);
+    for (int i = lane; i < M; i += 32) {
+        const double kv = init ? st->K0[i] : st->kappa[i];
+        st->sw.kappa[i] = static_cast<float>(kv);
+        if (init) st->kappa[i] = kv;
+    }
+    if (lane == 0) {
+        st->erho = init ? 0.0 : st->a_rho / st->b_rho;
+        st->sw.erho = static_cast<float>(st->erho);
+        st->ticket = 0u;
+        if (fail) st->status = ST_ENONFINITE;
+    }
+}
+
+} // namespace vbh

@@ -1,0 +1,259 @@
+"""Thin ctypes binding of ``libvbh.so`` (C ABI in ``include/vbh.h``).
+
+Argument marshalling only: every step of the CAVI sweep runs in the CUDA
+kernels of the library.  Inputs may be torch tensors (device or pinned host
+memory) or numpy arrays (host memory); PyTorch is used only for device memory
+and streams.  The library must have been built (``__graft_entry__.build()``);
+there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+SMAX = 32
+MMAX = 31
+FP32 = 0
+INIT_PAPER = 0
+INIT_GIVEN = 1
+
+STATUS = {0: "VBH_OK", -1: "VBH_EINVAL", -2: "VBH_ENOMEM", -3: "VBH_ECUDA", -4: "VBH_ENONFINITE",
+          -5: "VBH_ETIMEOUT", -6: "VBH_ESTATE", -7: "VBH_EUNSUPPORTED"}
+
+
+class VBHError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {STATUS.get(status, status)} ({_lib().vbh_strerror(status).decode()})")
+
+
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+class Prior(ctypes.Structure):
+    _fields_ = [("S", ctypes.c_int), ("K0", _dp), ("q0", ctypes.c_double), ("n0", ctypes.c_double),
+                ("a0", ctypes.c_double), ("b0", ctypes.c_double), ("Lambda0_inv", _dp)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("S", ctypes.c_int), ("iters", ctypes.c_int), ("converged", ctypes.c_int), ("status", ctypes.c_int),
+                ("elbo_const_dropped", ctypes.c_int), ("kappa", ctypes.c_double * MMAX),
+                ("weights", ctypes.c_double * SMAX), ("W_inv", ctypes.c_double * (MMAX * MMAX)),
+                ("nu", ctypes.c_double), ("lam", ctypes.c_double), ("a_rho", ctypes.c_double),
+                ("b_rho", ctypes.c_double), ("rho_mean", ctypes.c_double), ("rho_mode", ctypes.c_double),
+                ("elbo", ctypes.c_double)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("precision", ctypes.c_int),
+                ("init", ctypes.c_int), ("init_state", ctypes.POINTER(Result)), ("elbo_trace", _dp)]
+
+
+_LIB = None
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        path = _build.lib_path("vbh")
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build the CUDA library first (__graft_entry__.build())")
+        lib = ctypes.CDLL(path)
+        vp, i64, ci = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+        P, R, O = ctypes.POINTER(Prior), ctypes.POINTER(Result), ctypes.POINTER(Opts)
+        sigs = {
+            "vbh_prior_default": (None, [ci, P]),
+            "vbh_opts_default": (None, [O]),
+            "vbh_create": (ci, [ctypes.POINTER(vp), ci, vp]),
+            "vbh_destroy": (None, [vp]),
+            "vbh_strerror": (ctypes.c_char_p, [ci]),
+            "vbh_state_bytes": (ctypes.c_size_t, []),
+            "vbh_fit": (ci, [vp, vp, vp, i64, ci, P, O, R]),
+            "vbh_fit_begin": (ci, [vp, vp, vp, i64, ci, P, O]),
+            "vbh_fit_step": (ci, [vp, ci, ctypes.POINTER(ci)]),
+            "vbh_fit_result": (ci, [vp, R]),
+            "vbh_elbo": (ci, [vp, vp, vp, i64, ci, P, R, _dp]),
+        }
+        for name, (res, args) in sigs.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = lib
+    return _LIB
+
+
+def state_bytes() -> int:
+    return int(_lib().vbh_state_bytes())
+
+
+def library_path() -> str:
+    return _build.lib_path("vbh")
+
+
+def _ptr(x):
+    """Address of a torch tensor or numpy array (contiguous float32)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("inputs must be contiguous")
+        return ctypes.c_void_p(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.float32 or not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("numpy inputs must be C-contiguous float32")
+        return ctypes.c_void_p(x.ctypes.data)
+    raise TypeError("expected a torch tensor or a numpy array")
+
+
+class _PriorArgs:
+    """Keeps the numpy buffers of a Prior alive."""
+
+    def __init__(self, prior: dict | None, S: int):
+        self.c = Prior()
+        _lib().vbh_prior_default(S, ctypes.byref(self.c))
+        self._k = self._l = None
+        if prior:
+            M = S - 1
+            for key in ("q0", "n0", "a0", "b0"):
+                if key in prior:
+                    setattr(self.c, key, float(prior[key]))
+            if prior.get("K0") is not None:
+                self._k = np.ascontiguousarray(np.asarray(prior["K0"], dtype=np.float64).reshape(M))
+                self.c.K0 = self._k.ctypes.data_as(_dp)
+            if prior.get("L0inv") is not None:
+                self._l = np.ascontiguousarray(np.asarray(prior["L0inv"], dtype=np.float64).reshape(M, M))
+                self.c.Lambda0_inv = self._l.ctypes.data_as(_dp)
+
+
+def result_to_dict(res: Result) -> dict:
+    S = res.S
+    M = S - 1
+    return {"S": S, "iters": res.iters, "converged": bool(res.converged), "status": res.status,
+            "const_dropped": bool(res.elbo_const_dropped), "kappa": np.array(res.kappa[:M]),
+            "weights": np.array(res.weights[:S]), "Winv": np.array(res.W_inv[:M * M]).reshape(M, M),
+            "nu": res.nu, "lam": res.lam, "a_rho": res.a_rho, "b_rho": res.b_rho, "rho_mean": res.rho_mean,
+            "rho_mode": res.rho_mode, "elbo": res.elbo}
+
+
+def dict_to_result(g: dict, S: int) -> Result:
+    M = S - 1
+    res = Result()
+    res.S = S
+    k = np.asarray(g["kappa"], dtype=np.float64).reshape(M)
+    W = np.asarray(g["Winv"], dtype=np.float64).reshape(M * M)
+    for j in range(M):
+        res.kappa[j] = k[j]
+    for j in range(M * M):
+        res.W_inv[j] = W[j]
+    res.nu, res.lam, res.a_rho, res.b_rho = float(g["nu"]), float(g["lam"]), float(g["a_rho"]), float(g["b_rho"])
+    return res
+
+
+class Handle:
+    """One ``vbh_handle``: a device and a borrowed stream (a torch stream, a
+    raw cudaStream_t integer, or None for the legacy default stream)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        lib = _lib()
+        if stream is not None and hasattr(stream, "cuda_stream"):
+            stream = stream.cuda_stream
+        self._stream = stream
+        self._h = ctypes.c_void_p()
+        rc = lib.vbh_create(ctypes.byref(self._h), int(device), ctypes.c_void_p(stream) if stream else None)
+        if rc != 0:
+            raise VBHError(rc, "vbh_create")
+        self._keep = None
+        self._trace = None
+
+    def close(self):
+        if self._h:
+            _lib().vbh_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @staticmethod
+    def _opts(tol, max_iter, init_state, S, trace):
+        o = Opts()
+        _lib().vbh_opts_default(ctypes.byref(o))
+        o.tol = float(tol)
+        o.max_iter = int(max_iter)
+        keep = []
+        if init_state is not None:
+            st = dict_to_result(init_state, S) if isinstance(init_state, dict) else init_state
+            keep.append(st)
+            o.init = INIT_GIVEN
+            o.init_state = ctypes.pointer(st)
+        buf = None
+        if trace:
+            buf = np.zeros(int(max_iter) + 1)
+            o.elbo_trace = buf.ctypes.data_as(_dp)
+        return o, keep, buf
+
+    def fit(self, r, d, S: int, prior: dict | None = None, tol: float = 1e-8, max_iter: int = 200,
+            init_state=None, trace: bool = False, V: int | None = None) -> dict:
+        V = int(V if V is not None else (r.shape[0] if r is not None else 0))
+        pa = _PriorArgs(prior, S)
+        o, keep, buf = self._opts(tol, max_iter, init_state, S, trace)
+        res = Result()
+        rc = _lib().vbh_fit(self._h, _ptr(r), _ptr(d), V, int(S), ctypes.byref(pa.c), ctypes.byref(o),
+                            ctypes.byref(res))
+        if rc != 0:
+            raise VBHError(rc, "vbh_fit")
+        out = result_to_dict(res)
+        if buf is not None:
+            out["trace"] = buf[:res.iters + 1].copy()
+        return out
+
+    def fit_begin(self, r, d, S: int, prior: dict | None = None, tol: float = 1e-8, max_iter: int = 200,
+                  init_state=None, trace: bool = False, V: int | None = None):
+        V = int(V if V is not None else (r.shape[0] if r is not None else 0))
+        pa = _PriorArgs(prior, S)
+        o, keep, buf = self._opts(tol, max_iter, init_state, S, trace)
+        rc = _lib().vbh_fit_begin(self._h, _ptr(r), _ptr(d), V, int(S), ctypes.byref(pa.c), ctypes.byref(o))
+        if rc != 0:
+            raise VBHError(rc, "vbh_fit_begin")
+        self._keep = (r, d, keep)
+        self._trace = buf
+
+    def fit_step(self, nsweeps: int) -> bool:
+        conv = ctypes.c_int()
+        rc = _lib().vbh_fit_step(self._h, int(nsweeps), ctypes.byref(conv))
+        if rc != 0:
+            raise VBHError(rc, "vbh_fit_step")
+        return bool(conv.value)
+
+    def fit_result(self) -> dict:
+        res = Result()
+        rc = _lib().vbh_fit_result(self._h, ctypes.byref(res))
+        if rc != 0:
+            raise VBHError(rc, "vbh_fit_result")
+        out = result_to_dict(res)
+        if self._trace is not None:
+            out["trace"] = self._trace[:res.iters + 1].copy()
+        return out
+
+    def elbo(self, r, d, S: int, state: dict, prior: dict | None = None, V: int | None = None) -> float:
+        V = int(V if V is not None else (r.shape[0] if r is not None else 0))
+        pa = _PriorArgs(prior, S)
+        q = dict_to_result(state, S)
+        out = ctypes.c_double()
+        rc = _lib().vbh_elbo(self._h, _ptr(r), _ptr(d), V, int(S), ctypes.byref(pa.c), ctypes.byref(q),
+                             ctypes.byref(out))
+        if rc != 0:
+            raise VBHError(rc, "vbh_elbo")
+        return out.value

@@ -1,0 +1,63 @@
+"""The C-ABI libraries load and export every function their headers declare
+(no GPU needed: nothing here launches work on a device)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2401_10068_gb300 import _build, vbh
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADERS = {"vbh": os.path.join(ROOT, "include", "vbh.h"),
+           "vbh_synth": os.path.join(ROOT, "include", "vbh_synth.h")}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    _build.build_all()
+
+
+def _declared(header):
+    text = open(header).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^[A-Za-z_][\w\s\*]*?\b(vbh_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.mark.parametrize("lib", sorted(HEADERS))
+def test_library_exports_every_declared_symbol(lib):
+    names = _declared(HEADERS[lib])
+    assert names, "no declarations parsed"
+    so = ctypes.CDLL(_build.lib_path(lib))
+    for n in names:
+        assert hasattr(so, n), n
+    out = subprocess.run(["nm", "-D", "--defined-only", _build.lib_path(lib)], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (vbh_\w+)", out))
+    assert set(names) <= exported
+
+
+def test_every_include_header_is_covered():
+    hs = sorted(f for f in os.listdir(os.path.join(ROOT, "include")) if f.endswith(".h"))
+    assert hs == sorted(os.path.basename(p) for p in HEADERS.values())
+
+
+def test_host_only_entry_points():
+    lib = vbh._lib()
+    assert lib.vbh_strerror(0) == b"ok"
+    assert lib.vbh_strerror(-1) == b"invalid argument"
+    assert lib.vbh_strerror(-12345) == b"unknown status"
+    p = vbh.Prior()
+    lib.vbh_prior_default(3, ctypes.byref(p))
+    assert (p.S, p.q0, p.n0, p.a0, p.b0) == (3, 1e-3, 1.0, 0.5, 0.5)
+    assert not p.K0 and not p.Lambda0_inv
+    o = vbh.Opts()
+    lib.vbh_opts_default(ctypes.byref(o))
+    assert (o.tol, o.max_iter, o.precision, o.init) == (1e-8, 200, vbh.FP32, vbh.INIT_PAPER)
+
+
+def test_result_struct_layout_matches_header():
+    # offsets of the ctypes mirror against the C layout rules of the header
+    assert ctypes.sizeof(vbh.Result) == 4 * 5 + 4 + 8 * (31 + 32 + 31 * 31) + 8 * 7
+    assert vbh.Opts.init_state.offset == 24 and vbh.Opts.elbo_trace.offset == 32

@@ -1,0 +1,276 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Same seeded inputs, same schedule (sweep 0 from the initial Q(beta), then t
+sweeps of Q(beta) -> Q(rho) -> Q(K, Lambda) -> ELBO), same number of sweeps.
+Tolerances: every variational parameter block (kappa, W^{-1}, b_rho, E[rho])
+within 1e-4 relative (norm-wise); the ELBO within 1e-6 relative; a_rho, nu and
+lambda are exact functions of V and must agree to rounding.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2401_10068_gb300 import synth, vbh
+
+pytestmark = pytest.mark.gpu
+
+TOL_PARAM = 1e-4
+TOL_ELBO = 1e-6
+
+
+@pytest.fixture(scope="module")
+def handle():
+    from paper_2401_10068_gb300 import _build
+    _build.build_all()
+    h = vbh.Handle(0, torch.cuda.current_stream())
+    yield h
+    h.close()
+
+
+def _dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def rel(a, b):
+    a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def assert_parity(got, ref, tol_param=TOL_PARAM, tol_elbo=TOL_ELBO, what=""):
+    M = len(ref["kappa"])
+    if M:
+        assert rel(got["kappa"], ref["kappa"]) < tol_param, (what, "kappa", got["kappa"], ref["kappa"])
+        assert rel(got["Winv"], ref["Winv"]) < tol_param, (what, "Winv", rel(got["Winv"], ref["Winv"]))
+    assert rel(got["b_rho"], ref["b_rho"]) < tol_param, (what, "b_rho", got["b_rho"], ref["b_rho"])
+    assert rel(got["a_rho"] / got["b_rho"], ref["a_rho"] / ref["b_rho"]) < tol_param, (what, "E[rho]")
+    for key in ("a_rho", "nu", "lam"):
+        assert got[key] == pytest.approx(ref[key], rel=1e-14), (what, key)
+    assert abs(got["elbo"] - ref["elbo"]) <= tol_elbo * abs(ref["elbo"]), (what, "elbo", got["elbo"], ref["elbo"])
+
+
+CASES = [
+    # (S, V, seed, sweeps, p_const)
+    (1, 5003, 1, 3, 0.0),
+    (2, 20011, 2, 10, 0.0),
+    (3, 96000, 1, 25, 0.0),          # the single-data-set workload shape (2,000 cells x 48 genes, S = 3)
+    (3, 1_500_007, 7, 4, 0.0),       # several tiles per block: the shared-memory ring wraps
+    (4, 33333, 4, 8, 0.05),
+    (5, 40000, 5, 8, 0.05),
+    (6, 25000, 6, 6, 0.0),
+    (7, 20000, 7, 6, 0.05),
+    (8, 60013, 8, 10, 0.05),         # the at-scale workload's S = 8 and 5 % constant profiles
+    (8, 1_200_001, 9, 3, 0.05),
+    (9, 15000, 10, 5, 0.0),
+    (10, 15000, 11, 5, 0.05),
+    (11, 12000, 12, 5, 0.0),
+]
+
+
+@pytest.mark.parametrize("S,V,seed,sweeps,p_const", CASES)
+def test_parity_fixed_sweeps(handle, S, V, seed, sweeps, p_const):
+    alpha = 1.0 if S == 3 else 0.5
+    r, d, _ = synth.generate(V, S, seed=seed, alpha=alpha, p_const=p_const)
+    prior = O.paper_prior(S)
+    ref = O.fit(r, d, prior, tol=0.0, max_iter=sweeps)
+    got = handle.fit(_dev(r), _dev(d), S, prior, tol=0.0, max_iter=sweeps, trace=True)
+    assert got["iters"] == sweeps and not got["converged"]
+    assert got["const_dropped"] == ref["const_dropped"]
+    assert_parity(got, ref, what=(S, V))
+    # the whole ELBO trace
+    np.testing.assert_allclose(got["trace"], ref["trace"], rtol=TOL_ELBO)
+
+
+def test_parity_converged_fit_single_dataset(handle):
+    """2,000 x 48 = 96,000 observations, S = 3, run to rel dELBO < 1e-8."""
+    S, V = 3, 96000
+    r, d, _ = synth.generate(V, S, seed=1)
+    prior = O.paper_prior(S)
+    ref = O.fit(r, d, prior, tol=1e-8, max_iter=2000)
+    got = handle.fit(_dev(r), _dev(d), S, prior, tol=1e-8, max_iter=2000)
+    assert ref["converged"] and got["converged"]
+    assert abs(got["iters"] - ref["iters"]) <= max(3, ref["iters"] // 50)
+    assert_parity(got, ref)
+
+
+def test_sweep_zero_only(handle):
+    S, V = 3, 7777
+    r, d, _ = synth.generate(V, S, seed=3)
+    prior = O.paper_prior(S)
+    ref = O.fit(r, d, prior, tol=0.0, max_iter=0)
+    got = handle.fit(_dev(r), _dev(d), S, prior, tol=0.0, max_iter=0)
+    assert got["iters"] == 0
+    assert_parity(got, ref)
+
+
+@pytest.mark.parametrize("V", [0, 1, 2, 511, 512, 513, 1024 * 3])
+def test_edge_sizes(handle, V):
+    S = 4
+    prior = O.paper_prior(4, n0=5.0)          # proper Wishart prior so V = 0 has a finite ELBO
+    r, d, _ = synth.generate(max(V, 1), S, seed=V + 17)
+    r, d = r[:V], d[:V]
+    ref = O.fit(r, d, prior, tol=0.0, max_iter=4)
+    if V == 0:
+        got = handle.fit(None, None, S, prior, tol=0.0, max_iter=4, V=0)
+        np.testing.assert_allclose(got["kappa"], prior["K0"], rtol=1e-12)
+        np.testing.assert_allclose(got["Winv"], prior["L0inv"], rtol=1e-12)
+        assert abs(got["elbo"] - ref["elbo"]) < 1e-9 * max(1.0, abs(ref["elbo"]))
+    else:
+        got = handle.fit(_dev(r), _dev(d), S, prior, tol=0.0, max_iter=4)
+        assert_parity(got, ref, what=V)
+
+
+def test_all_constant_profiles(handle):
+    """D_i = 0 everywhere: Q(K, Lambda) only sees its prior and V."""
+    S, V = 5, 10000
+    r, d, _ = synth.generate(V, S, seed=55, p_const=1.0)
+    prior = O.paper_prior(S, n0=6.0)
+    ref = O.fit(r, d, prior, tol=0.0, max_iter=5)
+    got = handle.fit(_dev(r), _dev(d), S, prior, tol=0.0, max_iter=5)
+    assert_parity(got, ref)
+
+
+def test_real_valued_profiles(handle):
+    """Eq. 20 allows real profiles; the kernel reads any FP32 d."""
+    S, V = 6, 30000
+    rng = np.random.default_rng(3)
+    d = rng.uniform(0, 1, size=(V, S)).astype(np.float32)
+    r = (d @ np.full(S, 1.0 / S) + rng.normal(scale=0.1, size=V)).astype(np.float32)
+    prior = O.paper_prior(S)
+    ref = O.fit(r, d, prior, tol=0.0, max_iter=6)
+    got = handle.fit(_dev(r), _dev(d), S, prior, tol=0.0, max_iter=6)
+    assert_parity(got, ref)
+
+
+def test_nondefault_prior(handle):
+    S, V = 5, 30000
+    rng = np.random.default_rng(9)
+    A = rng.normal(size=(4, 4))
+    prior = O.paper_prior(S, K0=[0.1, 0.2, 0.3, 0.15], q0=0.7, n0=7.0, a0=2.0, b0=0.3,
+                          L0inv=0.02 * (A @ A.T / 4 + np.eye(4)))
+    r, d, _ = synth.generate(V, S, seed=99)
+    ref = O.fit(r, d, prior, tol=0.0, max_iter=7)
+    got = handle.fit(_dev(r), _dev(d), S, prior, tol=0.0, max_iter=7)
+    assert not got["const_dropped"]
+    assert_parity(got, ref)
+
+
+def test_host_inputs_match_device_inputs(handle):
+    S, V = 8, 40000
+    r, d, _ = synth.generate(V, S, seed=12, alpha=0.5)
+    prior = O.paper_prior(S)
+    a = handle.fit(_dev(r), _dev(d), S, prior, tol=0.0, max_iter=5)
+    b = handle.fit(r, d, S, prior, tol=0.0, max_iter=5)                       # pageable numpy
+    c = handle.fit(torch.from_numpy(r).pin_memory(), torch.from_numpy(d).pin_memory(), S, prior, tol=0.0,
+                   max_iter=5)                                                # pinned torch
+    for x in (b, c):
+        np.testing.assert_array_equal(x["kappa"], a["kappa"])
+        np.testing.assert_array_equal(x["Winv"], a["Winv"])
+        assert x["elbo"] == a["elbo"]
+
+
+def test_bitwise_deterministic(handle):
+    S, V = 8, 300000
+    r, d, _ = synth.generate(V, S, seed=13, alpha=0.5, p_const=0.05)
+    rg, dg = _dev(r), _dev(d)
+    prior = O.paper_prior(S)
+    runs = [handle.fit(rg, dg, S, prior, tol=0.0, max_iter=6, trace=True) for _ in range(3)]
+    for x in runs[1:]:
+        np.testing.assert_array_equal(x["kappa"], runs[0]["kappa"])
+        np.testing.assert_array_equal(x["Winv"], runs[0]["Winv"])
+        np.testing.assert_array_equal(x["trace"], runs[0]["trace"])
+
+
+def test_stepwise_equals_one_call(handle):
+    S, V = 5, 50000
+    r, d, _ = synth.generate(V, S, seed=21)
+    rg, dg = _dev(r), _dev(d)
+    prior = O.paper_prior(S)
+    one = handle.fit(rg, dg, S, prior, tol=0.0, max_iter=9, trace=True)
+    handle.fit_begin(rg, dg, S, prior, tol=0.0, max_iter=9, trace=True)
+    assert not handle.fit_step(2)
+    assert not handle.fit_step(0)
+    assert not handle.fit_step(3)
+    assert not handle.fit_step(100)          # capped at max_iter
+    many = handle.fit_result()
+    assert many["iters"] == 9
+    np.testing.assert_array_equal(many["kappa"], one["kappa"])
+    np.testing.assert_array_equal(many["trace"], one["trace"])
+
+
+def test_resume_from_saved_state(handle):
+    """vbh_result as a checkpoint: resuming after t sweeps reproduces the
+    remaining sweeps of an uninterrupted fit exactly."""
+    S, V = 4, 60000
+    r, d, _ = synth.generate(V, S, seed=31)
+    rg, dg = _dev(r), _dev(d)
+    prior = O.paper_prior(S)
+    full = handle.fit(rg, dg, S, prior, tol=0.0, max_iter=10)
+    part = handle.fit(rg, dg, S, prior, tol=0.0, max_iter=6)
+    res = handle.fit(rg, dg, S, prior, tol=0.0, max_iter=4, init_state=part, trace=True)
+    np.testing.assert_array_equal(res["kappa"], full["kappa"])
+    np.testing.assert_array_equal(res["Winv"], full["Winv"])
+    assert res["elbo"] == full["elbo"]
+    # sweep 0 of the resumed fit is the ELBO of the saved factors
+    e0, _ = O.elbo_at(r, d, prior, part)
+    assert abs(res["trace"][0] - e0) <= TOL_ELBO * abs(e0)
+
+
+@pytest.mark.parametrize("S", [2, 3, 8])
+def test_elbo_entry_point(handle, S):
+    V = 25000
+    r, d, _ = synth.generate(V, S, seed=40 + S)
+    prior = O.paper_prior(S)
+    state = O.fit(r, d, prior, tol=0.0, max_iter=5)
+    state = dict(state, kappa=state["kappa"] + 0.01, b_rho=state["b_rho"] * 1.1)
+    ref, _ = O.elbo_at(r, d, prior, state)
+    got = handle.elbo(_dev(r), _dev(d), S, state, prior)
+    assert abs(got - ref) <= TOL_ELBO * abs(ref)
+
+
+def test_invalid_arguments(handle):
+    S, V = 3, 1000
+    r, d, _ = synth.generate(V, S, seed=1)
+    rg, dg = _dev(r), _dev(d)
+    bad = [
+        dict(S=0), dict(S=33),
+        dict(prior=O.paper_prior(3, q0=-1.0)),
+        dict(prior=O.paper_prior(3, L0inv=[[1.0, 2.0], [2.0, 1.0]])),      # not positive definite
+        dict(max_iter=-1), dict(tol=-1.0),
+    ]
+    for kw in bad:
+        S_ = kw.get("S", S)
+        prior = kw.get("prior", O.paper_prior(3) if S_ == 3 else None)
+        with pytest.raises(vbh.VBHError) as e:
+            handle.fit(rg, dg, S_, prior, tol=kw.get("tol", 0.0), max_iter=kw.get("max_iter", 2))
+        assert e.value.status == -1, kw
+    # misaligned device pointer
+    rbig = torch.zeros(V + 1, device="cuda")
+    with pytest.raises(vbh.VBHError) as e:
+        handle.fit(rbig[1:], dg, S, O.paper_prior(3), tol=0.0, max_iter=1)
+    assert e.value.status == -1
+    # null data with V > 0
+    with pytest.raises(vbh.VBHError):
+        handle.fit(None, None, S, O.paper_prior(3), tol=0.0, max_iter=1, V=10)
+    # step before begin on a fresh handle
+    with vbh.Handle(0, torch.cuda.current_stream()) as h2:
+        with pytest.raises(vbh.VBHError) as e:
+            h2.fit_step(1)
+        assert e.value.status == -6
+    # the handle still works after the errors
+    got = handle.fit(rg, dg, S, O.paper_prior(3), tol=0.0, max_iter=2)
+    assert got["iters"] == 2
+
+
+def test_device_generator_matches_host_generator():
+    for S, p_const in ((3, 0.0), (8, 0.05), (1, 0.0), (11, 0.2)):
+        V, start = 200003, 12345
+        r, d, _ = synth.generate(V, S, seed=77, alpha=0.5, p_const=p_const, start=start)
+        rg, dg, _ = synth.generate_device(V, S, seed=77, alpha=0.5, p_const=p_const, start=start)
+        np.testing.assert_array_equal(dg.cpu().numpy(), d)
+        rc = rg.cpu().numpy()
+        ulp = np.abs(rc.view(np.int32).astype(np.int64) - r.view(np.int32).astype(np.int64))
+        assert ulp.max() <= 1 and (ulp > 0).mean() < 1e-4
