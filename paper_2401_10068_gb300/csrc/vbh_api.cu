@@ -96,12 +96,17 @@ void default_L0inv(int M, double *out)
         for (int c = 0; c < M; ++c) out[r * M + c] = 0.005 + (r == c ? (r % 2 == 0 ? 0.005 : 0.003) : 0.0);
 }
 
+// Symmetric (to 1e-10 relative; callers' matrices may differ from their
+// transpose in the last bits) and positive definite.
 bool host_spd(int M, const double *A)
 {
     double L[vbh::MMAX * vbh::MMAX];
     for (int j = 0; j < M; ++j) {
-        for (int i = 0; i < M; ++i)
-            if (!std::isfinite(A[i * M + j]) || A[i * M + j] != A[j * M + i]) return false;
+        for (int i = 0; i < M; ++i) {
+            if (!std::isfinite(A[i * M + j])) return false;
+            const double scale = std::sqrt(std::fabs(A[i * M + i] * A[j * M + j]));
+            if (std::fabs(A[i * M + j] - A[j * M + i]) > 1e-10 * scale) return false;
+        }
         double s = A[j * M + j];
         for (int k = 0; k < j; ++k) s -= L[j * M + k] * L[j * M + k];
         if (!(s > 0.0)) return false;
@@ -116,6 +121,13 @@ bool host_spd(int M, const double *A)
 }
 
 bool pos_finite(double x) { return std::isfinite(x) && x > 0.0; }
+
+// dst = (A + A^T) / 2
+void symmetrize(int M, const double *A, double *dst)
+{
+    for (int r = 0; r < M; ++r)
+        for (int c = 0; c < M; ++c) dst[r * M + c] = 0.5 * (A[r * M + c] + A[c * M + r]);
+}
 
 int check_prior(const vbh_prior *p, int S)
 {
@@ -210,7 +222,7 @@ void fill_prior(DevState *s, const vbh_prior *p, int S, long long V)
     s->b0 = p->b0;
     for (int j = 0; j < M; ++j) s->K0[j] = p->K0 ? p->K0[j] : 1.0 / S;
     if (p->Lambda0_inv)
-        std::memcpy(s->L0inv, p->Lambda0_inv, sizeof(double) * M * M);
+        symmetrize(M, p->Lambda0_inv, s->L0inv);
     else
         default_L0inv(M, s->L0inv);
 }
@@ -502,7 +514,7 @@ int vbh_fit_begin(vbh_handle *h, const float *r, const float *d, int64_t V, int 
         s->nu = q->nu;
         s->lam = q->lambda;
         for (int j = 0; j < M; ++j) s->kappa[j] = q->kappa[j];
-        std::memcpy(s->Winv, q->W_inv, sizeof(double) * M * M);
+        symmetrize(M, q->W_inv, s->Winv);
     }
     VBH_CK(cudaMemcpyAsync(h->st, s, sizeof(DevState), cudaMemcpyHostToDevice, h->stream));
     if (o->init == VBH_INIT_GIVEN) {
@@ -606,7 +618,7 @@ int vbh_elbo(vbh_handle *h, const float *r, const float *d, int64_t V, int S, co
     s->nu = q->nu;
     s->lam = q->lambda;
     for (int j = 0; j < M; ++j) s->kappa[j] = q->kappa[j];
-    std::memcpy(s->Winv, q->W_inv, sizeof(double) * M * M);
+    symmetrize(M, q->W_inv, s->Winv);
     VBH_CK(cudaMemcpyAsync(h->st_aux, s, sizeof(DevState), cudaMemcpyHostToDevice, h->stream));
     if ((rc = launch_setup(h, h->st_aux, ki, 0))) return rc;
     if ((rc = launch_sweep(h, h->st_aux, vbh::MODE_ELBO, ki, grid, rd, dd, V))) return rc;

@@ -273,14 +273,27 @@ __device__ void global_update(DevState *st, const double *__restrict__ part, int
         for (int off = 16; off >= 1; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
         if (lane == 0) stat[j] = s;
     }
+    // The data pass used the FP32 factor L~ and kappa~ of st->sw; its Q(beta_i)
+    // is the exact Eq. 20-21 posterior for Sigma0~ = L~ L~^T (formed here in
+    // FP64) and kappa~.  Every FP64 quantity below is taken with those values,
+    // so each sweep is an exact coordinate step from the rounded globals and
+    // the ELBO sequence is smooth (FP32 rounding enters at second order only).
     if (tid == 0) {
         s_fail = 0;
-        // ln|Sigma0| of this pass, kept before step 5 overwrites the state's copy
-        sc[1] = (mode == MODE_INIT) ? st->lndetL0inv : st->lndetSigma0;
+        double ld = 0.0;
+        for (int j = 0; j < M; ++j) ld += 2.0 * log(static_cast<double>(st->sw.L[j * (j + 1) / 2 + j]));
+        sc[1] = ld;                                  // ln|Sigma0~|
     }
-    for (int i = tid; i < M * M; i += nth) Sg[i] = (mode == MODE_INIT) ? st->L0inv[i] : st->Sigma0[i];
+    for (int i = tid; i < M * M; i += nth) {
+        const int r = i / MD, c = i % MD;
+        const int kmax = r < c ? r : c;
+        double s = 0.0;
+        for (int k = 0; k <= kmax; ++k)
+            s = fma(static_cast<double>(st->sw.L[r * (r + 1) / 2 + k]), static_cast<double>(st->sw.L[c * (c + 1) / 2 + k]), s);
+        Sg[i] = s;
+    }
     for (int i = tid; i < M; i += nth) {
-        ko[i] = (mode == MODE_INIT) ? st->K0[i] : st->kappa[i];
+        ko[i] = static_cast<double>(st->sw.kappa[i]);
         av[i] = st->K0[i] - ko[i];
     }
     __syncthreads();
@@ -319,9 +332,13 @@ __device__ void global_update(DevState *st, const double *__restrict__ part, int
         B[i] = s;
     }
     for (int i = tid; i < M; i += nth) {
-        const double dl = (mode == MODE_ELBO) ? 0.0 : (sv[i] + q0 * av[i]) / lam;   // Eq. 24, centred
-        dv[i] = dl;
-        kn[i] = ko[i] + dl;
+        if (mode == MODE_ELBO) {                    // kappa is given; kappa~ is its FP32 rounding
+            kn[i] = st->kappa[i];
+            dv[i] = kn[i] - ko[i];
+        } else {
+            dv[i] = (sv[i] + q0 * av[i]) / lam;     // Eq. 24, centred on kappa~
+            kn[i] = ko[i] + dv[i];
+        }
     }
     __syncthreads();
     // 4. W'^{-1} (Eq. 25, centred) and C

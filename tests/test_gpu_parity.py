@@ -40,7 +40,14 @@ def rel(a, b):
     return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
 
 
-def assert_parity(got, ref, tol_param=TOL_PARAM, tol_elbo=TOL_ELBO, what=""):
+def elbo_close(a, b, V, tol=TOL_ELBO):
+    """|a - b| <= tol * max(|b|, V): relative to the ELBO, or per observation
+    when the ELBO (a sum of V per-observation log densities of order one)
+    passes near zero during the transient."""
+    return abs(a - b) <= tol * max(abs(b), float(V))
+
+
+def assert_parity(got, ref, tol_param=TOL_PARAM, tol_elbo=TOL_ELBO, what="", V=None):
     M = len(ref["kappa"])
     if M:
         assert rel(got["kappa"], ref["kappa"]) < tol_param, (what, "kappa", got["kappa"], ref["kappa"])
@@ -49,7 +56,8 @@ def assert_parity(got, ref, tol_param=TOL_PARAM, tol_elbo=TOL_ELBO, what=""):
     assert rel(got["a_rho"] / got["b_rho"], ref["a_rho"] / ref["b_rho"]) < tol_param, (what, "E[rho]")
     for key in ("a_rho", "nu", "lam"):
         assert got[key] == pytest.approx(ref[key], rel=1e-14), (what, key)
-    assert abs(got["elbo"] - ref["elbo"]) <= tol_elbo * abs(ref["elbo"]), (what, "elbo", got["elbo"], ref["elbo"])
+    V = V if V is not None else ref["nu"]     # n0 + V: the observation count up to the prior's n0
+    assert elbo_close(got["elbo"], ref["elbo"], V, tol_elbo), (what, "elbo", got["elbo"], ref["elbo"])
 
 
 CASES = [
@@ -81,7 +89,8 @@ def test_parity_fixed_sweeps(handle, S, V, seed, sweeps, p_const):
     assert got["const_dropped"] == ref["const_dropped"]
     assert_parity(got, ref, what=(S, V))
     # the whole ELBO trace
-    np.testing.assert_allclose(got["trace"], ref["trace"], rtol=TOL_ELBO)
+    for t, (a, b) in enumerate(zip(got["trace"], ref["trace"])):
+        assert elbo_close(a, b, V), (t, a, b)
 
 
 def test_parity_converged_fit_single_dataset(handle):
@@ -94,6 +103,8 @@ def test_parity_converged_fit_single_dataset(handle):
     assert ref["converged"] and got["converged"]
     assert abs(got["iters"] - ref["iters"]) <= max(3, ref["iters"] // 50)
     assert_parity(got, ref)
+    # at a converged fit the ELBO is far from zero: the plain relative form holds too
+    assert abs(got["elbo"] - ref["elbo"]) <= TOL_ELBO * abs(ref["elbo"])
 
 
 def test_sweep_zero_only(handle):
@@ -216,7 +227,7 @@ def test_resume_from_saved_state(handle):
     assert res["elbo"] == full["elbo"]
     # sweep 0 of the resumed fit is the ELBO of the saved factors
     e0, _ = O.elbo_at(r, d, prior, part)
-    assert abs(res["trace"][0] - e0) <= TOL_ELBO * abs(e0)
+    assert elbo_close(res["trace"][0], e0, V)
 
 
 @pytest.mark.parametrize("S", [2, 3, 8])
@@ -228,7 +239,7 @@ def test_elbo_entry_point(handle, S):
     state = dict(state, kappa=state["kappa"] + 0.01, b_rho=state["b_rho"] * 1.1)
     ref, _ = O.elbo_at(r, d, prior, state)
     got = handle.elbo(_dev(r), _dev(d), S, state, prior)
-    assert abs(got - ref) <= TOL_ELBO * abs(ref)
+    assert elbo_close(got, ref, V)
 
 
 def test_invalid_arguments(handle):
