@@ -94,16 +94,39 @@ def test_parity_fixed_sweeps(handle, S, V, seed, sweeps, p_const):
 
 
 def test_parity_converged_fit_single_dataset(handle):
-    """2,000 x 48 = 96,000 observations, S = 3, run to rel dELBO < 1e-8."""
+    """2,000 x 48 = 96,000 observations, S = 3, run to convergence.
+
+    With binary profiles the FP32 rounding of the terms that depend on the
+    profile only (q_i, ln(1 + E[rho] q_i), c_i) repeats for every observation
+    of a profile, so the sweep's ELBO carries a rounding floor of about
+    V * 2^-24 / sqrt(2^S) (~2e-8 V here, ~4e-8 |L|).  The stopping test is
+    therefore checked at rel dELBO < 1e-6, well above that floor; at the
+    workload's own 1e-8 the 200-sweep cap binds first for both sides."""
     S, V = 3, 96000
     r, d, _ = synth.generate(V, S, seed=1)
     prior = O.paper_prior(S)
-    ref = O.fit(r, d, prior, tol=1e-8, max_iter=2000)
-    got = handle.fit(_dev(r), _dev(d), S, prior, tol=1e-8, max_iter=2000)
+    ref = O.fit(r, d, prior, tol=1e-6, max_iter=2000)
+    got = handle.fit(_dev(r), _dev(d), S, prior, tol=1e-6, max_iter=2000, trace=True)
     assert ref["converged"] and got["converged"]
     assert abs(got["iters"] - ref["iters"]) <= max(3, ref["iters"] // 50)
+    # monotone up to the rounding floor
+    assert np.all(np.diff(got["trace"]) >= -1e-7 * V)
     assert_parity(got, ref)
     # at a converged fit the ELBO is far from zero: the plain relative form holds too
+    assert abs(got["elbo"] - ref["elbo"]) <= TOL_ELBO * abs(ref["elbo"])
+
+
+def test_workload_cap_200_sweeps(handle):
+    """The single-data-set workload's stopping rule (rel dELBO < 1e-8 or 200
+    sweeps): the oracle hits the cap; the GPU result after the same number of
+    sweeps matches it."""
+    S, V = 3, 96000
+    r, d, _ = synth.generate(V, S, seed=1)
+    prior = O.paper_prior(S)
+    ref = O.fit(r, d, prior, tol=1e-8, max_iter=200)
+    assert not ref["converged"] and ref["iters"] == 200
+    got = handle.fit(_dev(r), _dev(d), S, prior, tol=0.0, max_iter=200)
+    assert_parity(got, ref)
     assert abs(got["elbo"] - ref["elbo"]) <= TOL_ELBO * abs(ref["elbo"])
 
 
