@@ -101,7 +101,11 @@ void vbh_opts_default(vbh_opts *o);
 
 /* Create a handle on CUDA device `device` that issues all work on `stream`
  * (a cudaStream_t; NULL = the legacy default stream).  The stream is borrowed:
- * it must outlive the handle.  Returns VBH_EINVAL for a bad device. */
+ * it must outlive the handle.  Returns VBH_EINVAL for a bad device.
+ * The sweep loop runs as a CUDA graph with a conditional while node; with the
+ * environment variable VBH_LAUNCH=direct at creation the handle instead issues
+ * one kernel launch per sweep (same kernels and results; for profilers that
+ * cannot look inside conditional graphs). */
 int vbh_create(vbh_handle **h, int device, void *stream);
 
 /* Release every resource of the handle (NULL is allowed). */

@@ -44,6 +44,7 @@ struct vbh_handle {
     const float *g_r = nullptr, *g_d = nullptr;
     const double *g_partials = nullptr;
     bool attr_set[vbh::SMAX + 1] = {};
+    bool direct = false;               // VBH_LAUNCH=direct: one stream launch per sweep, no graph
 };
 
 namespace vbh {
@@ -437,6 +438,8 @@ int vbh_create(vbh_handle **hp, int device, void *stream)
     if (!h) return VBH_ENOMEM;
     h->device = device;
     h->stream = static_cast<cudaStream_t>(stream);
+    const char *launch = std::getenv("VBH_LAUNCH");
+    h->direct = launch && std::strcmp(launch, "direct") == 0;
     int rc = VBH_OK;
     if (cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) rc = VBH_ECUDA;
     if (!rc && cudaMalloc(&h->st, sizeof(DevState)) != cudaSuccess) rc = VBH_ENOMEM;
@@ -546,11 +549,19 @@ int vbh_fit_step(vbh_handle *h, int nsweeps, int *converged)
     if (!h->begun) return VBH_ESTATE;
     DeviceGuard g(h->device);
     if (!g.ok) return VBH_ECUDA;
-    int rc = build_graph(h);
-    if (rc) return rc;
+    int rc = VBH_OK;
     vbh::set_target_kernel<<<1, 32, 0, h->stream>>>(h->st, nsweeps);
     VBH_CK(cudaGetLastError());
-    VBH_CK(cudaGraphLaunch(h->gexec, h->stream));
+    if (h->direct) {
+        // each launch checks the control fields first and does nothing once the
+        // fit has converged or reached its target
+        const int n = nsweeps < h->max_iter ? nsweeps : h->max_iter;
+        for (int i = 0; i < n; ++i)
+            if ((rc = launch_sweep(h, h->st, vbh::MODE_ITER, h->ki, h->grid, h->r, h->d, h->V))) return rc;
+    } else {
+        if ((rc = build_graph(h))) return rc;
+        VBH_CK(cudaGraphLaunch(h->gexec, h->stream));
+    }
     if ((rc = read_state(h, h->st))) return rc;
     if (converged) *converged = h->mirror->converged;
     return h->mirror->status;

@@ -30,6 +30,17 @@ struct SweepGlobalsF32 {
     int pad;
 };
 
+// Functions of (a_rho, nu, lambda) that the ELBO needs.  In a fit these are
+// fixed by V (Eq. 16, 22, 23), so they are evaluated once per fit by the
+// set-up kernel instead of once per sweep.
+struct ElboConst {
+    double a_rho, nu, lam;
+    double lgamma_a, psi_a;          // lnGamma(a_rho), psi(a_rho)
+    double sum_psi_nu;               // sum_{j=1..M} psi((nu + 1 - j)/2)
+    double sum_lgamma_nu;            // sum_{j=1..M} lnGamma((nu + 1 - j)/2)
+    double log_lam;
+};
+
 // FP64 state of one fit, resident in device memory.
 struct DevState {
     // prior, Eq. 5-7
@@ -53,6 +64,12 @@ struct DevState {
     unsigned int ticket;             // last-block-done counter of a sweep launch
     int pad0;
     double *trace;                   // device array [max_iter + 1] (may be null)
+    // per-fit constants: kc_upd for (a0 + V/2, n0 + V, q0 + V), kc_given for
+    // the factors a fit or vbh_elbo starts from; prior_const collects the
+    // prior-only terms of the ELBO (dropping ln B(Lambda_0, n0) when improper)
+    ElboConst kc_upd, kc_given;
+    double prior_const;
+    int prior_dropped, pad1;
     SweepGlobalsF32 sw;
 };
 

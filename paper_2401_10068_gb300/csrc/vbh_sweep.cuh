@@ -1,19 +1,21 @@
 // vbh_sweep.cuh -- the fused CAVI sweep for one data set (FP32 per
-// observation, FP64 across blocks and in the global update).
+// observation, FP64 across chunks, blocks and in the global update).
 //
 // One launch = one sweep of Section 3.5:
 //   (a) per observation, with Sigma0 = E[Lambda]^{-1} = L L^T, kappa, E[rho]:
 //       D_i = d_{i,1:M} - d_{i,S},  y_i = r_i - d_{i,S}
 //       q_i = D_i^T Sigma0 D_i = |L^T D_i|^2,  t_i = kappa^T D_i,  e_i = y_i - t_i
 //   (b) the exact Q(beta_i) of Eq. 20-21 in rank-1 form (Sherman-Morrison on
-//       Eq. 20, never materialised):
+//       Eq. 20; it is never materialised):
 //       c_i = E[rho] / (1 + E[rho] q_i),  w_i = c_i e_i
 //       Sigma_i = Sigma0 - c_i u_i u_i^T,  mu_{beta_i} = kappa + w_i u_i,  u_i = Sigma0 D_i
 //       braces of Eq. 17:  S_i = e_i^2 / (1 + E[rho] q_i)^2 + q_i / (1 + E[rho] q_i)
 //       ln|Sigma_i| = ln|Sigma0| - ln(1 + E[rho] q_i)   (matrix determinant lemma)
 //   (c) block-local sums g = sum w_i D_i, G = sum (w_i^2 - c_i) D_i D_i^T,
-//       T3 = sum S_i, T4 = sum ln(1 + E[rho] q_i): FP32 over chunks of 64
-//       observations per thread, warp butterfly, FP64 from there on;
+//       T3 = sum S_i and T4 = sum ln(1 + E[rho] q_i): FP32 over chunks of 64
+//       observations per thread, a warp butterfly, FP64 from there on.  T4 is
+//       carried as a running product of (1 + E[rho] q_i) whose binary exponent
+//       is peeled off every two observations; one log per chunk;
 //   (d) the last block to finish adds the per-block FP64 partials in block
 //       order (deterministic) and runs the closed-form updates of Eq. 16-18,
 //       22-25 and 28-31 in FP64, written in centred form:
@@ -35,13 +37,16 @@ struct SweepCfg {
     static constexpr int M = S - 1;
     static constexpr int MA = M > 0 ? M : 1;                // array extent
     static constexpr int NG = M * (M + 1) / 2;              // packed lower G
-    static constexpr int NSTAT = NG + M + 2;                // G, g, T3, T4
+    static constexpr int NGA = NG > 0 ? NG : 1;
+    static constexpr int I_G = 0, I_g = NG, I_T3 = NG + M, I_T4 = NG + M + 1, I_E4 = NG + M + 2;
+    static constexpr int NSTAT = NG + M + 3;                // G, g, T3, T4 (ln of mantissas), E4 (exponents)
     static constexpr int NGRP = (NSTAT + 31) / 32;          // 32-wide butterfly groups
     static constexpr int THREADS = 256;
-    static constexpr int OPT = 2;                           // observations per thread per tile
+    static constexpr int MINB = (S <= 8) ? 2 : 1;           // resident blocks per SM the registers are sized for
+    static constexpr int OPT = 4;                           // observations per thread per tile
     static constexpr int T = THREADS * OPT;                 // observations per tile
-    static constexpr int STAGES = 4;
-    static constexpr int FLUSH_TILES = 32;                  // 64 observations per thread per FP32 chunk
+    static constexpr int STAGES = 3;
+    static constexpr int FLUSH_TILES = 16;                  // 64 observations per thread per FP32 chunk
     static constexpr uint32_t R_BYTES = T * 4u;
     static constexpr uint32_t D_BYTES = T * S * 4u;
     static constexpr uint32_t STAGE_BYTES = R_BYTES + D_BYTES;
@@ -49,32 +54,22 @@ struct SweepCfg {
     static constexpr size_t SMEM_BYTES = RING_BYTES + 64;   // + mbarriers
 };
 
-// Load the S profile entries of row j of a shared-memory tile.  The vector
-// width is the largest power of two (<= 4) dividing S; for S a multiple of 8
-// the 16-byte quads of a row are visited in an order rotated by row, so that
-// the 8 rows of one shared-memory phase hit distinct banks.
+// Load the S profile entries of row j of a shared-memory tile with the widest
+// vector loads S allows (16, 8 or 4 bytes).  For S = 8 two consecutive rows of
+// a phase of eight threads share banks (a 2-way conflict); the load/store
+// unit has the headroom, and fixing it would cost selects in the FP32 pipe.
 template <int S>
 __device__ __forceinline__ void load_row(const float *__restrict__ dt, int j, float (&x)[S])
 {
     if constexpr (S % 4 == 0) {
-        constexpr int NQ = S / 4;
         const float4 *p = reinterpret_cast<const float4 *>(dt + size_t(j) * S);
-        const int rot = (S % 8 == 0) ? (((j * S) >> 5) % NQ) : 0;
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            int qq = q + rot;
-            if (qq >= NQ) qq -= NQ;
-            const float4 v = p[qq];
-            // scatter by the rotated index; unrolled selects keep x in registers
-#pragma unroll
-            for (int z = 0; z < NQ; ++z) {
-                if (z == qq) {
-                    x[4 * z + 0] = v.x;
-                    x[4 * z + 1] = v.y;
-                    x[4 * z + 2] = v.z;
-                    x[4 * z + 3] = v.w;
-                }
-            }
+        for (int q = 0; q < S / 4; ++q) {
+            const float4 v = p[q];
+            x[4 * q + 0] = v.x;
+            x[4 * q + 1] = v.y;
+            x[4 * q + 2] = v.z;
+            x[4 * q + 3] = v.w;
         }
     } else if constexpr (S % 2 == 0) {
         const float2 *p = reinterpret_cast<const float2 *>(dt + size_t(j) * S);
@@ -90,15 +85,22 @@ __device__ __forceinline__ void load_row(const float *__restrict__ dt, int j, fl
     }
 }
 
-// Steps (a)-(b) and the accumulation of (c) for one observation.
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Steps (a)-(b) and the accumulation of (c) for one observation.  prod
+// collects the product of (1 + E[rho] q_i).
 template <int S>
-__device__ __forceinline__ void observe(const float (&x)[S], float rr, const float (&L)[SweepCfg<S>::NG > 0 ? SweepCfg<S>::NG : 1],
+__device__ __forceinline__ void observe(const float (&x)[S], float rr, const float (&L)[SweepCfg<S>::NGA],
                                         const float (&kap)[SweepCfg<S>::MA], float erho,
-                                        float (&acc)[SweepCfg<S>::NSTAT])
+                                        float (&acc)[SweepCfg<S>::NSTAT], float &prod)
 {
     using C = SweepCfg<S>;
     constexpr int M = C::M;
-    constexpr int NG = C::NG;
     const float dS = x[S - 1];
     const float y = rr - dS;
     float D[C::MA];
@@ -115,30 +117,49 @@ __device__ __forceinline__ void observe(const float (&x)[S], float rr, const flo
     }
     const float e = y - t;
     const float den = fmaf(erho, q, 1.0f);
-    const float inv = __frcp_rn(den);
+    float inv = rcp_approx(den);
+    inv = fmaf(inv, fmaf(-den, inv, 1.0f), inv);           // one Newton step
     const float c = erho * inv;
     const float w = c * e;
     const float gam = fmaf(w, w, -c);
     const float ei = e * inv;
-    acc[NG + M] += fmaf(ei, ei, q * inv);                  // S_i
-    acc[NG + M + 1] += log1pf(erho * q);                   // ln(1 + E[rho] q_i)
+    acc[C::I_T3] += fmaf(ei, ei, q * inv);                 // S_i
+    prod *= den;
 #pragma unroll
     for (int j = 0; j < M; ++j) {
-        acc[NG + j] = fmaf(w, D[j], acc[NG + j]);
+        acc[C::I_g + j] = fmaf(w, D[j], acc[C::I_g + j]);
         const float gd = gam * D[j];
 #pragma unroll
         for (int k = 0; k <= j; ++k) acc[j * (j + 1) / 2 + k] = fmaf(gd, D[k], acc[j * (j + 1) / 2 + k]);
     }
 }
 
-// Move the FP32 chunk sums of a warp into FP64: a butterfly reduce-scatter
-// over each group of 32 statistics leaves lane l with the warp total of
-// statistic 32 g + l, which it adds to its FP64 accumulator.
-template <int NSTAT, int NGRP>
-__device__ __forceinline__ void flush_warp(float (&acc)[NSTAT], double (&acc64)[NGRP], int lane)
+// prod = m 2^(E - 127) with m in [1, 2): keep m, add E - 127 to ex.  Valid
+// while prod stays finite, i.e. for (1 + E[rho] q_i) < 2^62 per observation.
+__device__ __forceinline__ void peel_exponent(float &prod, int &ex)
 {
+    const uint32_t b = __float_as_uint(prod);
+    ex += int(b >> 23) - 127;
+    prod = __uint_as_float((b & 0x007fffffu) | 0x3f800000u);
+}
+
+// Move the FP32 chunk sums of a warp into FP64: first the product into
+// (ln mantissa, exponent), then a butterfly reduce-scatter over each group of
+// 32 statistics leaves lane l with the warp total of statistic 32 g + l,
+// which it adds to its FP64 accumulator.
+template <int S>
+__device__ __forceinline__ void flush_warp(float (&acc)[SweepCfg<S>::NSTAT], double (&acc64)[SweepCfg<S>::NGRP],
+                                           float &prod, int &ex, int lane)
+{
+    using C = SweepCfg<S>;
+    constexpr int NSTAT = C::NSTAT;
+    peel_exponent(prod, ex);
+    acc[C::I_T4] += logf(prod);
+    acc[C::I_E4] += static_cast<float>(ex);                // exact: |ex| < 2^24
+    prod = 1.0f;
+    ex = 0;
 #pragma unroll
-    for (int g = 0; g < NGRP; ++g) {
+    for (int g = 0; g < C::NGRP; ++g) {
         float v[32];
 #pragma unroll
         for (int i = 0; i < 32; ++i) v[i] = (g * 32 + i < NSTAT) ? acc[(g * 32 + i < NSTAT) ? g * 32 + i : 0] : 0.0f;
@@ -180,35 +201,42 @@ __device__ int warp_cholesky(const double *A, double *L, int lane)
             L[j * M + j] = sqrt(s);
         }
         __syncwarp();
+        const double rjj = 1.0 / L[j * M + j];
         for (int i = j + 1 + lane; i < M; i += 32) {
             double s = A[i * M + j];
             for (int k = 0; k < j; ++k) s -= L[i * M + k] * L[j * M + k];
-            L[i * M + j] = s / L[j * M + j];
+            L[i * M + j] = s * rjj;
         }
         __syncwarp();
     }
     return __shfl_sync(0xffffffffu, fail, 0);
 }
 
-// What the next data pass reads, from W^{-1} and nu (Eq. 28: E[Lambda] = nu W,
-// so Sigma0 = W^{-1}/nu): the FP32 Cholesky factor of Sigma0, Sigma0 itself
-// and ln|Sigma0|.  Sweep 0 uses (Lambda_0^{-1}, nu = 1).  One warp; Lw
-// receives chol(W^{-1}).  The global update and the set-up kernel both use
-// this function, so a fit resumed from saved factors continues bit for bit.
-template <int M>
-__device__ int derive_pass_globals(DevState *st, const double *Wn, double nu, double *Lw, int lane)
+// Sum over the lanes of a warp (fixed order).
+__device__ __forceinline__ double warp_sum(double v)
 {
-    const int fail = warp_cholesky<M>(Wn, Lw, lane);
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+// What the next data pass reads, from W^{-1} and nu (Eq. 28: E[Lambda] = nu W,
+// so Sigma0 = W^{-1}/nu): the FP32 Cholesky factor of Sigma0 (plus Sigma0 and
+// ln|Sigma0| for information).  Sweep 0 uses (Lambda_0^{-1}, nu = 1).  One
+// warp; Lw receives chol(W^{-1}); returns ln|W^{-1}| in every lane.  The
+// global update and the set-up kernel both use this function, so a fit
+// resumed from saved factors continues bit for bit.
+template <int M>
+__device__ double derive_pass_globals(DevState *st, const double *Wn, double nu, double *Lw, int lane, int *fail)
+{
+    *fail = warp_cholesky<M>(Wn, Lw, lane);
     const double rs = rsqrt(nu);
     for (int i = lane; i < M; i += 32)
         for (int k = 0; k <= i; ++k) st->sw.L[i * (i + 1) / 2 + k] = static_cast<float>(Lw[i * M + k] * rs);
     for (int i = lane; i < M * M; i += 32) st->Sigma0[i] = Wn[i] / nu;
-    if (lane == 0) {
-        double ld = 0.0;
-        for (int j = 0; j < M; ++j) ld += 2.0 * log(Lw[j * M + j]);
-        st->lndetSigma0 = ld - M * log(nu);
-    }
-    return fail;
+    const double ld = warp_sum(lane < M ? 2.0 * log(Lw[lane * M + lane]) : 0.0);
+    if (lane == 0) st->lndetSigma0 = ld - M * log(nu);
+    return ld;
 }
 
 // ---------------------------------------------------------------------------
@@ -218,71 +246,63 @@ __device__ int derive_pass_globals(DevState *st, const double *Wn, double nu, do
 template <int M>
 constexpr int gu_ws_doubles()
 {
-    return ((M * (M + 1) / 2 + M + 2 + 31) / 32) * 32 + 10 * (M > 0 ? M * M : 1) + 8 * (M > 0 ? M : 1) + 64;
-}
-
-__device__ __forceinline__ double wishart_lnB_d(int M, double lndetW, double nu, const double *lg)
-{
-    // ln B(W, nu) = -nu/2 ln|W| - nu M/2 ln 2 - M(M-1)/4 ln pi - sum_j lnGamma((nu+1-j)/2)
-    double s = -0.5 * nu * lndetW - 0.5 * nu * M * 0.69314718055994530942 - 0.25 * M * (M - 1) * 1.1447298858494002;
-    for (int j = 0; j < M; ++j) s -= lg[j];
-    return s;
+    return ((M * (M + 1) / 2 + M + 3 + 31) / 32) * 32 + 9 * (M > 0 ? M * M : 1) + 6 * (M > 0 ? M : 1) + 32;
 }
 
 template <int M>
 __device__ void global_update(DevState *st, const double *__restrict__ part, int nblk, const SweepArgs &a,
                               double *ws)
 {
-    constexpr int NG = M * (M + 1) / 2;
-    constexpr int NSTAT = NG + M + 2;
+    using C = SweepCfg<M + 1>;
+    constexpr int NSTAT = C::NSTAT;
     constexpr int MM = M > 0 ? M * M : 1;
     constexpr int MV = M > 0 ? M : 1;
     constexpr int MD = M > 0 ? M : 1;               // divisor (loops over M*M entries are empty at M = 0)
     constexpr double LN2PI = 1.8378770664093454836;
+    constexpr double LN2 = 0.69314718055994530942;
+    constexpr double LNPI = 1.1447298858494002;
     const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
     const int mode = a.mode;
 
     double *stat = ws;
-    double *Sg = stat + ((NSTAT + 31) / 32) * 32;   // Sigma0 of this sweep
+    double *Sg = stat + ((NSTAT + 31) / 32) * 32;   // Sigma0~ = L~ L~^T of this pass
     double *G = Sg + MM;                            // sum (w^2 - c) D D^T (full)
-    double *A = G + MM;                             // Sigma0 G
-    double *B = A + MM;                             // Sigma0 G Sigma0
+    double *A = G + MM;                             // Sigma0~ G
+    double *B = A + MM;                             // Sigma0~ G Sigma0~
     double *Wn = B + MM;                            // new W^{-1}
     double *Lw = Wn + MM;                           // chol(W^{-1})
     double *Li = Lw + MM;                           // Lw^{-1}
     double *EL = Li + MM;                           // E[Lambda] = nu W
     double *Cm = EL + MM;                           // sum_i E[(beta_i - kappa')(beta_i - kappa')^T]
-    double *Wk = Cm + MM;                           // spare
-    double *gv = Wk + MM;                           // g
-    double *sv = gv + MV;                           // Sigma0 g
-    double *dv = sv + MV;                           // delta
-    double *ko = dv + MV;                           // kappa (this sweep)
+    double *sv = Cm + MM;                           // Sigma0~ g
+    double *dv = sv + MV;                           // kappa' - kappa~
+    double *ko = dv + MV;                           // kappa~ (this pass)
     double *kn = ko + MV;                           // kappa'
-    double *psi = kn + MV;                          // psi((nu+1-j)/2)
-    double *lgv = psi + MV;                         // lnGamma((nu+1-j)/2)
-    double *av = lgv + MV;                          // K0 - kappa
-    double *sc = av + MV;                           // scalars
+    double *av = kn + MV;                           // K0 - kappa~
+    double *gv = av + MV;                           // g
+    double *sc = gv + MV;                           // scalars
     __shared__ int s_fail;
 
-    // 1. partials -> totals, fixed order per statistic
+    // 1. partials -> totals (fixed order per statistic); Sigma0~, kappa~.
+    //    The data pass used the FP32 factor L~ and kappa~ of st->sw; its
+    //    Q(beta_i) is the exact Eq. 20-21 posterior for Sigma0~ = L~ L~^T and
+    //    kappa~, so every FP64 quantity below is taken with those values: each
+    //    sweep is an exact coordinate step from the rounded globals and the
+    //    ELBO sequence is smooth (FP32 rounding enters at second order only).
     for (int j = warp; j < NSTAT; j += nwarp) {
         double s = 0.0;
 #pragma unroll 4
         for (int b = lane; b < nblk; b += 32) s += __ldcg(part + size_t(b) * NSTAT + j);
-#pragma unroll
-        for (int off = 16; off >= 1; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        s = warp_sum(s);
         if (lane == 0) stat[j] = s;
     }
-    // The data pass used the FP32 factor L~ and kappa~ of st->sw; its Q(beta_i)
-    // is the exact Eq. 20-21 posterior for Sigma0~ = L~ L~^T (formed here in
-    // FP64) and kappa~.  Every FP64 quantity below is taken with those values,
-    // so each sweep is an exact coordinate step from the rounded globals and
-    // the ELBO sequence is smooth (FP32 rounding enters at second order only).
-    if (tid == 0) {
-        s_fail = 0;
-        double ld = 0.0;
-        for (int j = 0; j < M; ++j) ld += 2.0 * log(static_cast<double>(st->sw.L[j * (j + 1) / 2 + j]));
-        sc[1] = ld;                                  // ln|Sigma0~|
+    if (warp == nwarp - 1) {
+        const double ld = warp_sum(lane < M ? 2.0 * log(static_cast<double>(st->sw.L[lane * (lane + 1) / 2 + lane]))
+                                            : 0.0);
+        if (lane == 0) {
+            sc[1] = ld;                                  // ln|Sigma0~|
+            s_fail = 0;
+        }
     }
     for (int i = tid; i < M * M; i += nth) {
         const int r = i / MD, c = i % MD;
@@ -298,19 +318,19 @@ __device__ void global_update(DevState *st, const double *__restrict__ part, int
     }
     __syncthreads();
 
+    const ElboConst kc = (mode == MODE_ELBO) ? st->kc_given : st->kc_upd;
     const double V = st->V;
-    const double T3 = stat[NG + M], T4 = stat[NG + M + 1];
-    const double lndetS0 = sc[1];
-    const double q0 = st->q0, n0 = st->n0, a0 = st->a0, b0 = st->b0;
-    const double lam = (mode == MODE_ELBO) ? st->lam : q0 + V;      // Eq. 22
-    const double nu = (mode == MODE_ELBO) ? st->nu : n0 + V;        // Eq. 23
+    const double T3 = stat[C::I_T3];
+    const double T4 = stat[C::I_T4] + LN2 * stat[C::I_E4];
+    const double q0 = st->q0, n0 = st->n0, b0 = st->b0, a0 = st->a0;
+    const double lam = kc.lam, nu = kc.nu;
 
-    // 2. G (full), s = Sigma0 g, A = Sigma0 G
+    // 2. G (full), g, s = Sigma0~ g, A = Sigma0~ G
     for (int i = tid; i < M * M; i += nth) {
         const int r = i / MD, c = i % MD;
         G[i] = (r >= c) ? stat[r * (r + 1) / 2 + c] : stat[c * (c + 1) / 2 + r];
     }
-    for (int i = tid; i < M; i += nth) gv[i] = stat[NG + i];
+    for (int i = tid; i < M; i += nth) gv[i] = stat[C::I_g + i];
     __syncthreads();
     for (int i = tid; i < M * M; i += nth) {
         const int r = i / MD, c = i % MD;
@@ -324,7 +344,7 @@ __device__ void global_update(DevState *st, const double *__restrict__ part, int
         sv[i] = s;
     }
     __syncthreads();
-    // 3. B = Sigma0 G Sigma0, delta, kappa'
+    // 3. B = Sigma0~ G Sigma0~, delta, kappa'
     for (int i = tid; i < M * M; i += nth) {
         const int r = i / MD, c = i % MD;
         double s = 0.0;
@@ -350,36 +370,34 @@ __device__ void global_update(DevState *st, const double *__restrict__ part, int
         } else {
             Wn[i] = st->L0inv[i] + V * Sg[i] + Bs + q0 * av[r] * av[c] - lam * dv[r] * dv[c];
         }
-        // C = V Sigma0 + Sigma0 G Sigma0 - s delta^T - delta s^T + V delta delta^T
+        // C = V Sigma0~ + Sigma0~ G Sigma0~ - s delta^T - delta s^T + V delta delta^T
         Cm[i] = V * Sg[i] + Bs - sv[r] * dv[c] - dv[r] * sv[c] + V * dv[r] * dv[c];
     }
     __syncthreads();
     // 5. Cholesky of W'^{-1} (warp 0) and, unless only the ELBO is wanted,
-    //    the Sigma0 / FP32 factor of the next data pass
+    //    the FP32 factor of the next data pass; Lw^{-1}
     if (warp == 0) {
         int fail;
+        double lndetWn;
         if (mode == MODE_ELBO) {
             fail = warp_cholesky<M>(Wn, Lw, lane);
+            lndetWn = warp_sum(lane < M ? 2.0 * log(Lw[lane * M + lane]) : 0.0);
         } else {
-            fail = derive_pass_globals<M>(st, Wn, nu, Lw, lane);
+            lndetWn = derive_pass_globals<M>(st, Wn, nu, Lw, lane, &fail);
         }
-        if (lane == 0 && fail) s_fail = 1;
+        if (lane == 0) {
+            if (fail) s_fail = 1;
+            sc[2] = lndetWn;
+        }
         __syncwarp();
-        // Lw^{-1}: lane c solves Lw x = e_c (forward substitution)
-        for (int c = lane; c < M; c += 32) {
-            for (int i = 0; i < M; ++i) Li[i * M + c] = 0.0;
+        for (int c = lane; c < M; c += 32) {        // lane c solves Lw x = e_c
+            for (int i = 0; i < c; ++i) Li[i * M + c] = 0.0;
             for (int i = c; i < M; ++i) {
                 double s = (i == c) ? 1.0 : 0.0;
                 for (int k = c; k < i; ++k) s -= Lw[i * M + k] * Li[k * M + c];
                 Li[i * M + c] = s / Lw[i * M + i];
             }
         }
-    }
-    // special functions of nu (any warp): psi and lnGamma at (nu + 1 - j)/2, j = 1..M
-    for (int j = tid; j < M; j += nth) {
-        const double x = 0.5 * (nu - j);
-        psi[j] = digamma_d(x);
-        lgv[j] = lgamma(x);
     }
     __syncthreads();
     // 6. E[Lambda] = nu Li^T Li (Eq. 28)
@@ -390,76 +408,64 @@ __device__ void global_update(DevState *st, const double *__restrict__ part, int
         EL[i] = nu * s;
     }
     __syncthreads();
-    // 7. scalars, ELBO and control (thread 0)
-    if (tid == 0) {
-        double lndetWn = 0.0;
-        for (int j = 0; j < M; ++j) lndetWn += 2.0 * log(Lw[j * M + j]);
-        const double lndetW = -lndetWn;
-        double trELC = 0.0, trL0EL = 0.0, quadK = 0.0, sumpsi = 0.0;
-        for (int r = 0; r < M; ++r) {
-            sumpsi += psi[r];
-            for (int c = 0; c < M; ++c) {
-                trELC = fma(EL[r * M + c], Cm[c * M + r], trELC);
-                trL0EL = fma(st->L0inv[r * M + c], EL[c * M + r], trL0EL);
-                quadK = fma((kn[r] - st->K0[r]) * EL[r * M + c], kn[c] - st->K0[c], quadK);
-            }
+    // 7. traces (warp 0), then the ELBO and control (thread 0)
+    if (warp == 0) {
+        double t1 = 0.0, t2 = 0.0, t3 = 0.0;
+        for (int i = lane; i < M * M; i += 32) {
+            const int r = i / MD, c = i % MD;
+            t1 = fma(EL[i], Cm[i], t1);                                   // tr(E[Lambda] C), both symmetric
+            t2 = fma(st->L0inv[i], EL[i], t2);                            // tr(Lambda_0^{-1} E[Lambda])
+            t3 = fma((kn[r] - st->K0[r]) * EL[i], kn[c] - st->K0[c], t3);  // (kappa'-K0)^T E[Lambda] (kappa'-K0)
         }
-        const double a_rho = (mode == MODE_ELBO) ? st->a_rho : a0 + 0.5 * V;      // Eq. 16
-        const double b_rho = (mode == MODE_ELBO) ? st->b_rho : b0 + 0.5 * T3;     // Eq. 17
-        const double Er = a_rho / b_rho;                                         // Eq. 29
-        const double psia = digamma_d(a_rho);
-        const double Elr = psia - log(b_rho);
-        const double ElL = sumpsi + M * 0.69314718055994530942 + lndetW;
-        const double lnBq = wishart_lnB_d(M, lndetW, nu, lgv);
-        double lnB0 = 0.0;
-        int dropped = 0;
-        if (M > 0) {
-            if (n0 > M - 1.0) {
-                double lg0 = 0.0;
-                for (int j = 0; j < M; ++j) lg0 += lgamma(0.5 * (n0 - j));
-                lnB0 = 0.5 * n0 * st->lndetL0inv - 0.5 * n0 * M * 0.69314718055994530942
-                     - 0.25 * M * (M - 1) * 1.1447298858494002 - lg0;
-            } else {
-                dropped = 1;
-            }
-        }
-        double L = 0.0;
-        L += 0.5 * V * (Elr - LN2PI) - 0.5 * Er * T3;                                   // E ln p(r | beta, rho)
-        L += 0.5 * V * (ElL - M * LN2PI) - 0.5 * trELC - 0.5 * V * M / lam;            // E ln p(beta | K, Lambda)
-        L += 0.5 * M * (log(q0) - LN2PI) + 0.5 * ElL - 0.5 * q0 * (quadK + M / lam);     // E ln p(K | Lambda)
-        L += lnB0 + 0.5 * (n0 - M - 1.0) * ElL - 0.5 * trL0EL;                          // E ln p(Lambda)
-        L += a0 * log(b0) - lgamma(a0) + (a0 - 1.0) * Elr - b0 * Er;                     // E ln p(rho)
-        L += 0.5 * (V * lndetS0 - T4) + 0.5 * V * M * (1.0 + LN2PI);                    // H[Q(beta)]
-        L += -0.5 * ElL - 0.5 * M * (log(lam) - LN2PI) + 0.5 * M;                        // H[Q(K | Lambda)]
-        if (M > 0) L += -lnBq - 0.5 * (nu - M - 1.0) * ElL + 0.5 * nu * M;              // H[Q(Lambda)]
-        L += a_rho - log(b_rho) + lgamma(a_rho) + (1.0 - a_rho) * psia;                  // H[Q(rho)]
+        const double trELC = warp_sum(t1), trL0EL = warp_sum(t2), quadK = warp_sum(t3);
+        if (lane == 0) {
+            const double lndetS0 = sc[1];
+            const double lndetW = -sc[2];
+            const double a_rho = kc.a_rho;                                           // Eq. 16
+            const double b_rho = (mode == MODE_ELBO) ? st->b_rho : b0 + 0.5 * T3;    // Eq. 17
+            const double Er = a_rho / b_rho;                                         // Eq. 29
+            const double logb = log(b_rho);
+            const double Elr = kc.psi_a - logb;
+            const double ElL = kc.sum_psi_nu + M * LN2 + lndetW;
+            const double lnBq = -0.5 * nu * lndetW - 0.5 * nu * M * LN2 - 0.25 * M * (M - 1) * LNPI - kc.sum_lgamma_nu;
+            double L = st->prior_const;
+            L += 0.5 * V * (Elr - LN2PI) - 0.5 * Er * T3;                            // E ln p(r | beta, rho)
+            L += 0.5 * V * (ElL - M * LN2PI) - 0.5 * trELC - 0.5 * V * M / lam;     // E ln p(beta | K, Lambda)
+            L += 0.5 * ElL - 0.5 * q0 * (quadK + M / lam);                           // E ln p(K | Lambda)
+            L += 0.5 * (n0 - M - 1.0) * ElL - 0.5 * trL0EL;                          // E ln p(Lambda)
+            L += (a0 - 1.0) * Elr - b0 * Er;                                         // E ln p(rho)
+            L += 0.5 * (V * lndetS0 - T4) + 0.5 * V * M * (1.0 + LN2PI);             // H[Q(beta)]
+            L += -0.5 * ElL - 0.5 * M * (kc.log_lam - LN2PI) + 0.5 * M;              // H[Q(K | Lambda)]
+            if (M > 0) L += -lnBq - 0.5 * (nu - M - 1.0) * ElL + 0.5 * nu * M;      // H[Q(Lambda)]
+            L += a_rho - logb + kc.lgamma_a + (1.0 - a_rho) * kc.psi_a;              // H[Q(rho)]
 
-        bool finite = isfinite(L) && isfinite(a_rho) && isfinite(b_rho) && b_rho > 0.0 && !s_fail;
-        for (int j = 0; j < M; ++j) finite = finite && isfinite(kn[j]);
-        st->elbo = L;
-        st->const_dropped = dropped;
-        if (mode != MODE_ELBO) {
-            st->a_rho = a_rho;
-            st->b_rho = b_rho;
-            st->nu = nu;
-            st->lam = lam;
-            st->erho = Er;
-            if (mode == MODE_INIT) {
-                st->iter = 0;
-                st->converged = 0;
+            bool finite = isfinite(L) && isfinite(b_rho) && b_rho > 0.0 && !s_fail;
+            for (int j = 0; j < M; ++j) finite = finite && isfinite(kn[j]);
+            st->elbo = L;
+            st->const_dropped = st->prior_dropped;
+            if (mode != MODE_ELBO) {
+                st->a_rho = a_rho;
+                st->b_rho = b_rho;
+                st->nu = nu;
+                st->lam = lam;
+                st->erho = Er;
+                if (mode == MODE_INIT) {
+                    st->iter = 0;
+                    st->converged = 0;
+                } else {
+                    st->iter += 1;
+                    st->converged = (fabs(L - st->elbo_prev) < st->tol * fabs(L)) ? 1 : 0;
+                }
+                if (st->trace && st->iter <= st->max_iter) st->trace[st->iter] = L;
+                st->elbo_prev = L;
             } else {
-                st->iter += 1;
-                st->converged = (fabs(L - st->elbo_prev) < st->tol * fabs(L)) ? 1 : 0;
+                // sweep 0 of a fit started from given factors: L_0 of that state
+                st->elbo_prev = L;
+                if (st->trace) st->trace[0] = L;
             }
-            if (st->trace && st->iter <= st->max_iter) st->trace[st->iter] = L;
-            st->elbo_prev = L;
-        } else {
-            // sweep 0 of a fit started from given factors: L_0 of that state
-            st->elbo_prev = L;
-            if (st->trace) st->trace[0] = L;
+            if (!finite && st->status == ST_OK) st->status = ST_ENONFINITE;
+            sc[0] = Er;
         }
-        if (!finite && st->status == ST_OK) st->status = ST_ENONFINITE;
-        sc[0] = Er;
     }
     __syncthreads();
     // 8. write the new globals and the FP32 inputs of the next sweep
@@ -484,14 +490,13 @@ __device__ void global_update(DevState *st, const double *__restrict__ part, int
 // The fused sweep kernel.
 // ---------------------------------------------------------------------------
 template <int S>
-__global__ void __launch_bounds__(SweepCfg<S>::THREADS) sweep_kernel(SweepArgs a)
+__global__ void __launch_bounds__(SweepCfg<S>::THREADS, SweepCfg<S>::MINB) sweep_kernel(SweepArgs a)
 {
     using C = SweepCfg<S>;
     constexpr int M = C::M, NG = C::NG, NSTAT = C::NSTAT, NGRP = C::NGRP;
     constexpr int THREADS = C::THREADS, T = C::T, STAGES = C::STAGES;
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + C::RING_BYTES);
-    __shared__ double s_red[THREADS / 32][NGRP * 32];
     __shared__ int s_bad, s_last;
 
     DevState *st = a.st;
@@ -505,19 +510,16 @@ __global__ void __launch_bounds__(SweepCfg<S>::THREADS) sweep_kernel(SweepArgs a
 
     float acc[NSTAT];
     double acc64[NGRP];
+    float prod = 1.0f;
+    int ex = 0;
 #pragma unroll
     for (int i = 0; i < NSTAT; ++i) acc[i] = 0.0f;
 #pragma unroll
     for (int g = 0; g < NGRP; ++g) acc64[g] = 0.0;
 
     if (run) {
-        float L[NG > 0 ? NG : 1], kap[C::MA];
-        float erho;
-        if (a.mode == MODE_INIT) {
-            erho = 0.0f;                         // c_i = 0: Q(beta_i) = N(K0, Lambda_0^{-1})
-        } else {
-            erho = st->sw.erho;
-        }
+        float L[C::NGA], kap[C::MA];
+        const float erho = (a.mode == MODE_INIT) ? 0.0f : st->sw.erho;   // sweep 0: c_i = 0
 #pragma unroll
         for (int i = 0; i < NG; ++i) L[i] = st->sw.L[i];
 #pragma unroll
@@ -558,7 +560,8 @@ __global__ void __launch_bounds__(SweepCfg<S>::THREADS) sweep_kernel(SweepArgs a
                     const int j = tid + u * THREADS;
                     float x[S];
                     load_row<S>(dt, j, x);
-                    observe<S>(x, rt[j], L, kap, erho, acc);
+                    observe<S>(x, rt[j], L, kap, erho, acc, prod);
+                    if (u & 1) peel_exponent(prod, ex);
                 }
             }
             if (__syncthreads_or(!ok)) {
@@ -574,7 +577,7 @@ __global__ void __launch_bounds__(SweepCfg<S>::THREADS) sweep_kernel(SweepArgs a
                 bulk_load(stage + C::R_BYTES, a.d + tile * T * S, C::D_BYTES, &full[s]);
             }
             if (++ftile == C::FLUSH_TILES) {
-                flush_warp<NSTAT, NGRP>(acc, acc64, lane);
+                flush_warp<S>(acc, acc64, prod, ex, lane);
                 ftile = 0;
             }
         }
@@ -595,21 +598,24 @@ __global__ void __launch_bounds__(SweepCfg<S>::THREADS) sweep_kernel(SweepArgs a
                     float x[S];
 #pragma unroll
                     for (int q = 0; q < S; ++q) x[q] = __ldg(a.d + i * S + q);
-                    observe<S>(x, __ldg(a.r + i), L, kap, erho, acc);
+                    observe<S>(x, __ldg(a.r + i), L, kap, erho, acc, prod);
+                    peel_exponent(prod, ex);
                 }
             }
         }
     }
-    flush_warp<NSTAT, NGRP>(acc, acc64, lane);
+    flush_warp<S>(acc, acc64, prod, ex, lane);
+    __syncthreads();   // the ring is idle from here on: reuse it for the block reduction
 
     // block reduction in FP64, fixed order, then this block's partials
+    double *s_red = reinterpret_cast<double *>(smem);      // [THREADS / 32][NGRP * 32]
 #pragma unroll
-    for (int g = 0; g < NGRP; ++g) s_red[warp][g * 32 + lane] = acc64[g];
+    for (int g = 0; g < NGRP; ++g) s_red[warp * (NGRP * 32) + g * 32 + lane] = acc64[g];
     __syncthreads();
     for (int j = tid; j < NSTAT; j += THREADS) {
         double s = 0.0;
 #pragma unroll
-        for (int w = 0; w < THREADS / 32; ++w) s += s_red[w][j];
+        for (int w = 0; w < THREADS / 32; ++w) s += s_red[w * (NGRP * 32) + j];
         a.partials[size_t(blockIdx.x) * NSTAT + j] = s;
     }
     __threadfence();
@@ -619,8 +625,8 @@ __global__ void __launch_bounds__(SweepCfg<S>::THREADS) sweep_kernel(SweepArgs a
     if (!s_last) return;
     __threadfence();
     if (run && !s_bad) {
-        // the ring is idle here (every copy of this block has landed), so its
-        // shared memory serves as the workspace of the global update
+        // every copy of this block has landed, so the ring's shared memory
+        // serves as the workspace of the global update
         global_update<M>(st, a.partials, gridDim.x, a, reinterpret_cast<double *>(smem));
     } else if (tid == 0 && a.use_cond) {
         cudaGraphSetConditional(a.cond, 0u);
@@ -633,28 +639,68 @@ __global__ void __launch_bounds__(SweepCfg<S>::THREADS) sweep_kernel(SweepArgs a
 //   init != 0: sweep 0 reads Sigma0 = Lambda_0^{-1}, kappa = K0, E[rho] = 0;
 //   init == 0: it reads Sigma0 = W^{-1}/nu, kappa, E[rho] = a_rho / b_rho of
 //              the given global factors.
-// Also ln|Lambda_0^{-1}| for the prior term of the ELBO.
+// Also the per-fit constants of the ELBO: ln|Lambda_0^{-1}|, the prior-only
+// terms, and the special functions of (a_rho, nu, lambda) for the updates of
+// this data set (Eq. 16, 22, 23) and for the given factors.
 // ---------------------------------------------------------------------------
+__device__ inline void elbo_const(ElboConst *k, int M, double a_rho, double nu, double lam, int lane)
+{
+    double sp = 0.0, sl = 0.0;
+    for (int j = lane; j < M; j += 32) {
+        const double x = 0.5 * (nu - j);                 // (nu + 1 - (j + 1)) / 2
+        sp += digamma_d(x);
+        sl += lgamma(x);
+    }
+    sp = warp_sum(sp);
+    sl = warp_sum(sl);
+    if (lane == 0) {
+        k->a_rho = a_rho;
+        k->nu = nu;
+        k->lam = lam;
+        k->lgamma_a = lgamma(a_rho);
+        k->psi_a = digamma_d(a_rho);
+        k->sum_psi_nu = sp;
+        k->sum_lgamma_nu = sl;
+        k->log_lam = log(lam);
+    }
+}
+
 template <int M>
 __global__ void setup_kernel(DevState *st, int init)
 {
     constexpr int MM = M > 0 ? M * M : 1;
+    constexpr double LN2PI = 1.8378770664093454836;
+    constexpr double LN2 = 0.69314718055994530942;
+    constexpr double LNPI = 1.1447298858494002;
     __shared__ double A[MM], Lc[MM];
     const int lane = threadIdx.x;
     if (threadIdx.x >= 32) return;
     for (int i = lane; i < M * M; i += 32) A[i] = st->L0inv[i];
     __syncwarp();
     int fail = warp_cholesky<M>(A, Lc, lane);
+    const double l0 = warp_sum(lane < M ? 2.0 * log(Lc[lane * M + lane]) : 0.0);
+    // prior-only terms: M/2 (ln q0 - ln 2 pi) + a0 ln b0 - lnGamma(a0) + ln B(Lambda_0, n0)
+    const double n0 = st->n0;
+    const bool proper = (M == 0) || (n0 > M - 1.0);
+    const double lg0 = warp_sum((lane < M && proper) ? lgamma(0.5 * (n0 - lane)) : 0.0);
     if (lane == 0) {
-        double l0 = 0.0;
-        for (int j = 0; j < M; ++j) l0 += 2.0 * log(Lc[j * M + j]);
         st->lndetL0inv = l0;
+        double pc = 0.5 * M * (log(st->q0) - LN2PI) + st->a0 * log(st->b0) - lgamma(st->a0);
+        if (M > 0 && proper)                            // ln B(W0, n0), ln|W0| = -ln|Lambda_0^{-1}|
+            pc += 0.5 * n0 * l0 - 0.5 * n0 * M * LN2 - 0.25 * M * (M - 1) * LNPI - lg0;
+        st->prior_const = pc;
+        st->prior_dropped = (M > 0 && !proper) ? 1 : 0;
     }
+    const double V = st->V;
+    elbo_const(&st->kc_upd, M, st->a0 + 0.5 * V, n0 + V, st->q0 + V, lane);
+    if (!init) elbo_const(&st->kc_given, M, st->a_rho, st->nu, st->lam, lane);
     __syncwarp();
     if (!init)
         for (int i = lane; i < M * M; i += 32) A[i] = st->Winv[i];
     __syncwarp();
-    fail |= derive_pass_globals<M>(st, A, init ? 1.0 : st->nu, Lc, lane);
+    int fail2 = 0;
+    (void)derive_pass_globals<M>(st, A, init ? 1.0 : st->nu, Lc, lane, &fail2);
+    fail |= fail2;
     for (int i = lane; i < M; i += 32) {
         const double kv = init ? st->K0[i] : st->kappa[i];
         st->sw.kappa[i] = static_cast<float>(kv);

@@ -308,3 +308,20 @@ def test_device_generator_matches_host_generator():
         rc = rg.cpu().numpy()
         ulp = np.abs(rc.view(np.int32).astype(np.int64) - r.view(np.int32).astype(np.int64))
         assert ulp.max() <= 1 and (ulp > 0).mean() < 1e-4
+
+
+def test_direct_launch_mode_matches_graph(monkeypatch):
+    """VBH_LAUNCH=direct (one launch per sweep) gives the graph loop's results,
+    including where a converged fit stops."""
+    S, V = 4, 50000
+    r, d, _ = synth.generate(V, S, seed=61)
+    rg, dg = _dev(r), _dev(d)
+    prior = O.paper_prior(S)
+    with vbh.Handle(0, torch.cuda.current_stream()) as hg:
+        a = hg.fit(rg, dg, S, prior, tol=1e-6, max_iter=500, trace=True)
+    monkeypatch.setenv("VBH_LAUNCH", "direct")
+    with vbh.Handle(0, torch.cuda.current_stream()) as hd:
+        b = hd.fit(rg, dg, S, prior, tol=1e-6, max_iter=500, trace=True)
+    assert a["converged"] and b["converged"] and a["iters"] == b["iters"]
+    np.testing.assert_array_equal(a["kappa"], b["kappa"])
+    np.testing.assert_array_equal(a["trace"], b["trace"])
