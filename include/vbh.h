@@ -144,6 +144,44 @@ int vbh_fit_result(vbh_handle *h, vbh_result *out);
 int vbh_elbo(vbh_handle *h, const float *r, const float *d, int64_t V, int S, const vbh_prior *p,
              const vbh_result *q, double *elbo);
 
+/* ---------------------------------------------------------------------------
+ * vbh_fit_static: the same fit as vbh_fit, for callers that cannot allocate
+ * device memory.  The paper has no counterpart of this entry point.
+ *
+ * vbh_fit and the other entry points work through a handle, which allocates
+ * device buffers (cudaMalloc) and builds a CUDA graph.  Some callers cannot
+ * allow that: cudaMalloc and cudaFree synchronise the whole device and stall
+ * latency-sensitive work on other streams; frameworks that serve all device
+ * memory from their own pool may leave a foreign cudaMalloc without memory;
+ * plug-in hosts and fixed-budget deployments forbid allocations beyond the
+ * budget fixed when the library is loaded.  vbh_fit_static needs no handle
+ * and performs no allocation (no cudaMalloc, cudaFree, graph or pool call):
+ * its scratch -- the fit state, the per-block partial sums and the ELBO
+ * trace -- is one statically sized __device__ array of
+ * VBH_STATIC_SCRATCH_BYTES that every GPU loading the library holds from load
+ * until process exit.
+ *
+ *   r, d:    device pointers on `device` (16-byte aligned), layout as for
+ *            vbh_fit; host pointers are rejected (staging them would allocate).
+ *   p, o:    as for vbh_fit; with o->elbo_trace set, o->max_iter + 1 must not
+ *            exceed VBH_STATIC_TRACE_MAX (else VBH_EINVAL).  S above the FP32
+ *            sweep limit returns VBH_EUNSUPPORTED, as for vbh_fit.
+ *   out:     the result, as for vbh_fit.
+ *   stream:  a cudaStream_t on `device` (NULL = legacy default stream); the
+ *            call is synchronous on it.
+ * The sweeps run as one kernel launch each (a launch after convergence
+ * returns at once).  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress, with that device current); make that first
+ * call before any stream capture.  All calls on a device share the one array
+ * and every call rewrites the whole fit state before its first kernel, so
+ * nothing of an earlier call carries over; but calls whose work overlaps on
+ * the GPU (other host threads, other streams) race on the array and must be
+ * serialised by the caller. */
+#define VBH_STATIC_SCRATCH_BYTES (512 * 1024)
+#define VBH_STATIC_TRACE_MAX 4097
+int vbh_fit_static(const float *r, const float *d, int64_t V, int S, const vbh_prior *p, const vbh_opts *o,
+                   vbh_result *out, int device, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

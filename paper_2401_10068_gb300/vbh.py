@@ -77,6 +77,7 @@ def _lib():
             "vbh_fit_step": (ci, [vp, ci, ctypes.POINTER(ci)]),
             "vbh_fit_result": (ci, [vp, R]),
             "vbh_elbo": (ci, [vp, vp, vp, i64, ci, P, R, _dp]),
+            "vbh_fit_static": (ci, [vp, vp, i64, ci, P, O, R, ci, vp]),
         }
         for name, (res, args) in sigs.items():
             f = getattr(lib, name)
@@ -257,3 +258,27 @@ class Handle:
         if rc != 0:
             raise VBHError(rc, "vbh_elbo")
         return out.value
+
+
+STATIC_TRACE_MAX = 4097
+
+
+def fit_static(r, d, S: int, prior: dict | None = None, tol: float = 1e-8, max_iter: int = 200,
+               init_state=None, trace: bool = False, device: int = 0, stream=None, V: int | None = None) -> dict:
+    """``vbh_fit_static``: the fit of ``Handle.fit`` for callers that cannot
+    allocate device memory (no handle; the scratch is a static device array of
+    the library).  r and d must be device tensors."""
+    V = int(V if V is not None else (r.shape[0] if r is not None else 0))
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    pa = _PriorArgs(prior, S)
+    o, keep, buf = Handle._opts(tol, max_iter, init_state, S, trace)
+    res = Result()
+    rc = _lib().vbh_fit_static(_ptr(r), _ptr(d), V, int(S), ctypes.byref(pa.c), ctypes.byref(o), ctypes.byref(res),
+                               int(device), ctypes.c_void_p(stream) if stream else None)
+    if rc != 0:
+        raise VBHError(rc, "vbh_fit_static")
+    out = result_to_dict(res)
+    if buf is not None:
+        out["trace"] = buf[:res.iters + 1].copy()
+    return out
