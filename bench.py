@@ -17,7 +17,6 @@ from __future__ import annotations
 
 import argparse
 import hashlib
-import glob
 import json
 import os
 import subprocess
@@ -56,10 +55,14 @@ def _peaks():
     return 6800.0, "fallback"
 
 
+SWEEP_SOURCES = ("vbh_sweep.cuh", "vbh_internal.cuh", "vbh_dispatch.cuh", "vbh_sweep_s5_8.cu")
+
+
 def _kernel_hash():
+    """Hash of the sources that define sweep_kernel<8> (the timed kernel)."""
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2401_10068_gb300", "csrc", "*"))):
-        with open(f, "rb") as fh:
+    for name in SWEEP_SOURCES:
+        with open(os.path.join(ROOT, "paper_2401_10068_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
@@ -74,7 +77,7 @@ def _traffic(bytes_alg):
         j = json.load(f)
     if j.get("kernel_hash") != _kernel_hash():
         return None
-    return float(j["dram_bytes_per_obs"]) * V_FULL
+    return float(j["dram_read_bytes_per_obs"]) * V_FULL + float(j["dram_write_bytes_per_launch"])
 
 
 class Clocks:
