@@ -138,6 +138,24 @@ int vbh_fit_begin(vbh_handle *h, const float *r, const float *d, int64_t V, int 
 int vbh_fit_step(vbh_handle *h, int nsweeps, int *converged);
 int vbh_fit_result(vbh_handle *h, vbh_result *out);
 
+/* Fit B independent data sets in one device loop (the batched form).  Data
+ * set b has V[b] observations and S[b] subpopulations (1 .. 11), inputs r[b]
+ * (V[b] floats) and d[b] (V[b] x S[b] floats, row-major): for each b both
+ * device pointers (16-byte aligned) or both host pointers (staged by the call).
+ * p: B priors, or NULL for vbh_prior_default(S[b]) each.  o: one set of options
+ * for all data sets; with o->init == VBH_INIT_GIVEN, o->init_state points to B
+ * results; o->elbo_trace, if set, holds B * (o->max_iter + 1) doubles (row b
+ * is L_0 .. L_iters of data set b).  out: B results.
+ * Each data set follows exactly the schedule of vbh_fit (sweep 0, then sweeps
+ * until its own convergence test or o->max_iter) and retires when done; one
+ * batched sweep is, per class of equal S, a persistent data-pass kernel over
+ * chunks of contiguous observations taken from a work queue and one FP64
+ * update per data set, and the loop is a CUDA graph with a conditional while
+ * node.  The chunk size is autotuned by timing one data pass per candidate.
+ * Returns the first non-zero per-data-set status (also in out[b].status). */
+int vbh_fit_batched(vbh_handle *h, int B, const int64_t *V, const int *S, const float *const *r,
+                    const float *const *d, const vbh_prior *p, const vbh_opts *o, vbh_result *out);
+
 /* ELBO (Eq. 11) of the global factors in *q (kappa, W_inv, nu, lambda,
  * a_rho, b_rho) with Q(beta) set from them by Eq. 19-21: one data pass and no
  * update of *q. */

@@ -9,6 +9,7 @@
 #include <new>
 
 #include "vbh.h"
+#include "vbh_batched_host.h"
 #include "vbh_dispatch.cuh"
 #include "vbh_internal.cuh"
 
@@ -45,6 +46,7 @@ struct vbh_handle {
     const double *g_partials = nullptr;
     bool attr_set[vbh::SMAX + 1] = {};
     bool direct = false;               // VBH_LAUNCH=direct: one stream launch per sweep, no graph
+    vbh::BatchedHost batched;          // buffers of vbh_fit_batched
 };
 
 namespace vbh {
@@ -467,6 +469,8 @@ void vbh_destroy(vbh_handle *h)
     cudaFree(h->stage_r);
     cudaFree(h->stage_d);
     if (h->mirror) cudaFreeHost(h->mirror);
+    cudaFree(h->batched.arena);
+    if (h->batched.host_states) cudaFreeHost(h->batched.host_states);
     (void)cudaGetLastError();
     delete h;
 }
@@ -599,6 +603,16 @@ int vbh_fit(vbh_handle *h, const float *r, const float *d, int64_t V, int S, con
         }
     }
     return vbh_fit_result(h, out);
+}
+
+int vbh_fit_batched(vbh_handle *h, int B, const int64_t *V, const int *S, const float *const *r,
+                    const float *const *d, const vbh_prior *p, const vbh_opts *o, vbh_result *out)
+{
+    if (!h) return VBH_EINVAL;
+    DeviceGuard g(h->device);
+    if (!g.ok) return VBH_ECUDA;
+    h->begun = false;                  // the step-wise fit's staging buffers are not touched, but keep it simple
+    return vbh::fit_batched_impl(h->batched, h->stream, h->nsm, B, V, S, r, d, p, o, out, h->direct);
 }
 
 int vbh_elbo(vbh_handle *h, const float *r, const float *d, int64_t V, int S, const vbh_prior *p,

@@ -1,0 +1,305 @@
+// vbh_batched.cuh -- CAVI sweeps of many independent data sets at once.
+//
+// Every data set b (V_b observations, S_b subpopulations) has its own device
+// state (DevState) and follows exactly the schedule of a single fit.  One
+// batched sweep is, for each class of data sets with the same S:
+//   data pass  (batched_pass_kernel<S>): persistent blocks take chunks --
+//              contiguous observation ranges of one data set -- from an
+//              atomic work queue (largest chunks first), stream them through
+//              the same shared-memory ring and per-observation algebra as the
+//              single-data-set kernel, and write one FP64 partial per chunk;
+//   update     (batched_update_kernel<M>): one block per data set adds its
+//              chunks' partials in chunk order and runs the FP64 global
+//              update, ELBO and convergence test of that data set;
+// then batched_control_kernel counts the data sets still running and sets
+// the while condition of the CUDA graph that repeats the sweep.  Data sets
+// that have converged (or reached their sweep limit) drop out: their chunks
+// are skipped and their states are left as they are.
+#pragma once
+
+#include "vbh_sweep.cuh"
+
+namespace vbh {
+
+// Per-class work description (device memory, built by the host).
+struct BatchClass {
+    const float *const *r;          // [B] device pointers (all data sets)
+    const float *const *d;          // [B]
+    DevState *states;               // [B]
+    const int *chunk_ds;            // [nchunks] data set of each chunk
+    const long long *chunk_lo;      // [nchunks] first observation
+    const long long *chunk_hi;      // [nchunks] one past the last observation
+    const long long *ds_V;          // [B] observations per data set
+    const int *order;               // [nchunks] scheduling order (chunk ids)
+    int nchunks;
+    double *partials;               // [nchunks][NSTAT]
+    unsigned int *next;             // work-queue counter of this class
+    const int *ds_list;             // [nds] data sets of this class
+    const int *ds_first_chunk;      // [B] first chunk id of each data set (within its class)
+    const int *ds_nchunks;          // [B]
+    int nds;
+    int mode;
+    struct BatchControl *ctl;
+};
+
+struct BatchControl {
+    int status;                     // ST_ETIMEOUT if a bounded wait of a data pass ran out
+    unsigned int active;            // data sets still running after this sweep's updates
+    unsigned int sweep;             // batched sweeps done
+    unsigned int max_sweeps;
+    unsigned int nclasses;
+    unsigned int *class_next[SMAX + 1];
+};
+
+__device__ __forceinline__ bool ds_running(const DevState *st)
+{
+    return st->status == ST_OK && !st->converged && st->iter < st->target && st->iter < st->max_iter;
+}
+
+// Stage metadata written by the producer thread when it fills a stage.
+struct StageMeta {
+    int chunk;                      // -1: end of work
+    int ds;
+    long long obs0;                 // first observation of the unit
+    int flags;                      // UNIT_TAIL | UNIT_LAST
+    int pad;
+};
+enum : int { UNIT_TAIL = 1, UNIT_LAST = 2 };
+
+template <int S>
+struct BatchCfg {
+    using C = SweepCfg<S>;
+    static constexpr int THREADS = 256;
+    static constexpr int OPT = 3;                           // observations per thread per tile
+    static constexpr int T = THREADS * OPT;                 // 768 observations per tile
+    static constexpr int STAGES = 3;
+    static constexpr uint32_t R_BYTES = T * 4u;
+    static constexpr uint32_t D_BYTES = T * S * 4u;
+    static constexpr uint32_t STAGE_BYTES = R_BYTES + D_BYTES;
+    static constexpr size_t RING_BYTES = size_t(STAGES) * STAGE_BYTES;
+    static constexpr size_t SMEM_BYTES = RING_BYTES + 64;
+};
+
+// Producer state (thread 0 of a block): the chunk being issued and the next unit.
+struct Cursor {
+    int chunk;                      // current chunk (-1: none)
+    int ds;
+    long long next_obs;             // first observation of the next unit to issue
+    long long hi;                   // end of the chunk
+    long long full_hi;              // end of the chunk's full tiles
+    int tail_done;
+    int done;                       // no more work
+};
+
+template <int S>
+__device__ __forceinline__ bool cursor_advance(Cursor &cu, const BatchClass &bc, int mode)
+{
+    using B = BatchCfg<S>;
+    while (true) {
+        if (cu.chunk >= 0 && (cu.next_obs < cu.full_hi || !cu.tail_done)) return true;
+        const unsigned int q = atomicAdd(bc.next, 1u);
+        if (q >= unsigned(bc.nchunks)) {
+            cu.done = 1;
+            return false;
+        }
+        const int c = bc.order[q];
+        const int ds = bc.chunk_ds[c];
+        if (mode == MODE_ITER && !ds_running(bc.states + ds)) continue;      // retired data set
+        cu.chunk = c;
+        cu.ds = ds;
+        cu.next_obs = bc.chunk_lo[c];
+        cu.hi = bc.chunk_hi[c];
+        // full tiles are those whose observations all lie in the chunk; chunk
+        // boundaries are multiples of the tile except at the data set's end.
+        // A chunk without observations still yields one (empty) tail unit, so
+        // that its partial is written.
+        const long long ntiles = (cu.hi - cu.next_obs) / B::T;
+        cu.full_hi = cu.next_obs + ntiles * B::T;
+        cu.tail_done = (cu.full_hi == cu.hi && cu.hi > cu.next_obs) ? 1 : 0;
+        return true;
+    }
+}
+
+// Fill stage s with the next unit (a full tile by bulk copy, or the ragged
+// tail of a chunk, read later with plain loads), or with the end mark.
+template <int S>
+__device__ __forceinline__ void issue_unit(Cursor &cu, const BatchClass &bc, int mode, unsigned char *stage,
+                                           uint64_t *bar, StageMeta *meta)
+{
+    using B = BatchCfg<S>;
+    if (cu.done || !cursor_advance<S>(cu, bc, mode)) {
+        meta->chunk = -1;
+        mbar_arrive_expect_tx(bar, 0u);
+        return;
+    }
+    meta->chunk = cu.chunk;
+    meta->ds = cu.ds;
+    meta->obs0 = cu.next_obs;
+    if (cu.next_obs < cu.full_hi) {
+        const long long o = cu.next_obs;
+        cu.next_obs += B::T;
+        const bool last = (cu.next_obs == cu.full_hi) && cu.tail_done;
+        meta->flags = last ? UNIT_LAST : 0;
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(bar, B::STAGE_BYTES);
+        bulk_load(stage, bc.r[cu.ds] + o, B::R_BYTES, bar);
+        bulk_load(stage + B::R_BYTES, bc.d[cu.ds] + o * S, B::D_BYTES, bar);
+    } else {
+        meta->flags = UNIT_TAIL | UNIT_LAST;
+        cu.tail_done = 1;
+        cu.next_obs = cu.hi;
+        mbar_arrive_expect_tx(bar, 0u);
+    }
+}
+
+template <int S>
+__global__ void __launch_bounds__(BatchCfg<S>::THREADS, SweepCfg<S>::MINB) batched_pass_kernel(BatchClass bc)
+{
+    using C = SweepCfg<S>;
+    using B = BatchCfg<S>;
+    constexpr int M = C::M, NG = C::NG, NSTAT = C::NSTAT, NGRP = C::NGRP;
+    constexpr int THREADS = B::THREADS, T = B::T, STAGES = B::STAGES;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + B::RING_BYTES);
+    __shared__ StageMeta meta[STAGES];
+    __shared__ double s_red[THREADS / 32][NGRP * 32];
+    __shared__ float s_glob[C::NGA + C::MA + 1];
+    __shared__ int s_bad;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int mode = bc.mode;
+
+    if (tid == 0) {
+        s_bad = 0;
+        for (int s = 0; s < STAGES; ++s) mbar_init(&full[s], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    Cursor cu{-1, 0, 0, 0, 0, 1, 0};
+    if (tid == 0)
+        for (int s = 0; s < STAGES; ++s)
+            issue_unit<S>(cu, bc, mode, smem + size_t(s) * B::STAGE_BYTES, &full[s], &meta[s]);
+
+    float acc[NSTAT];
+    double acc64[NGRP];
+    float prod = 1.0f;
+    int ex = 0;
+#pragma unroll
+    for (int i = 0; i < NSTAT; ++i) acc[i] = 0.0f;
+#pragma unroll
+    for (int g = 0; g < NGRP; ++g) acc64[g] = 0.0;
+    float L[C::NGA], kap[C::MA], erho = 0.0f;
+    int cur_ds = -1;
+    int ftile = 0;
+
+    long long kbreak = 0;
+    for (long long k = 0;; ++k) {
+        const int s = int(k % STAGES);
+        const bool ok = mbar_wait_bounded(&full[s], uint32_t((k / STAGES) & 1), 2000000000ull);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) s_bad = 1;
+            kbreak = k;
+            break;
+        }
+        const StageMeta m = meta[s];
+        if (m.chunk < 0) break;
+        if (m.ds != cur_ds) {                               // a new data set: its FP32 globals
+            __syncthreads();
+            if (tid == 0) {
+                const DevState *st = bc.states + m.ds;
+                for (int i = 0; i < NG; ++i) s_glob[i] = st->sw.L[i];
+                for (int i = 0; i < M; ++i) s_glob[C::NGA + i] = st->sw.kappa[i];
+                s_glob[C::NGA + C::MA] = (mode == MODE_INIT) ? 0.0f : st->sw.erho;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int i = 0; i < NG; ++i) L[i] = s_glob[i];
+#pragma unroll
+            for (int i = 0; i < M; ++i) kap[i] = s_glob[C::NGA + i];
+            if constexpr (NG == 0) L[0] = 0.0f;
+            if constexpr (M == 0) kap[0] = 0.0f;
+            erho = s_glob[C::NGA + C::MA];
+            cur_ds = m.ds;
+        }
+        if (!(m.flags & UNIT_TAIL)) {
+            const float *rt = reinterpret_cast<const float *>(smem + size_t(s) * B::STAGE_BYTES);
+            const float *dt = rt + T;
+#pragma unroll
+            for (int u = 0; u < B::OPT; ++u) {
+                const int j = tid + u * THREADS;
+                float x[S];
+                load_row<S>(dt, j, x);
+                observe<S>(x, rt[j], L, kap, erho, acc, prod);
+                peel_exponent(prod, ex);
+            }
+            if (++ftile == 16) {
+                flush_warp<S>(acc, acc64, prod, ex, lane);
+                ftile = 0;
+            }
+        } else {
+            const float *rg = bc.r[m.ds];
+            const float *dg = bc.d[m.ds];
+            const long long hi = bc.chunk_hi[m.chunk];
+            for (long long i = m.obs0 + tid; i < hi; i += THREADS) {
+                float x[S];
+#pragma unroll
+                for (int q = 0; q < S; ++q) x[q] = __ldg(dg + i * S + q);
+                observe<S>(x, __ldg(rg + i), L, kap, erho, acc, prod);
+                peel_exponent(prod, ex);
+            }
+        }
+        if (m.flags & UNIT_LAST) {                          // chunk done: its FP64 partial
+            flush_warp<S>(acc, acc64, prod, ex, lane);
+            ftile = 0;
+#pragma unroll
+            for (int g = 0; g < NGRP; ++g) {
+                s_red[warp][g * 32 + lane] = acc64[g];
+                acc64[g] = 0.0;
+            }
+            __syncthreads();
+            for (int j = tid; j < NSTAT; j += THREADS) {
+                double t = 0.0;
+#pragma unroll
+                for (int w = 0; w < THREADS / 32; ++w) t += s_red[w][j];
+                bc.partials[size_t(m.chunk) * NSTAT + j] = t;
+            }
+        }
+        __syncthreads();                                    // stage s and s_red are free again
+        if (tid == 0) issue_unit<S>(cu, bc, mode, smem + size_t(s) * B::STAGE_BYTES, &full[s], &meta[s]);
+    }
+    if (s_bad && tid == 0) {
+        // a wait ran out: record it, then let the copies this block issued and
+        // did not consume land before the block exits (bounded)
+        atomicCAS(&bc.ctl->status, ST_OK, ST_ETIMEOUT);
+        for (long long kk = kbreak; kk < kbreak + STAGES; ++kk)
+            (void)mbar_wait_bounded(&full[kk % STAGES], uint32_t((kk / STAGES) & 1), 100000000ull);
+    }
+}
+
+template <int M>
+__global__ void __launch_bounds__(256) batched_update_kernel(BatchClass bc, BatchControl *ctl)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int b = bc.ds_list[blockIdx.x];
+    DevState *st = bc.states + b;
+    const int mode = bc.mode;
+    if (mode == MODE_ITER && !ds_running(st)) return;      // retired: chunks were skipped too
+    SweepArgs a{};
+    a.mode = mode;
+    a.use_cond = 0;
+    using C = SweepCfg<M + 1>;
+    global_update<M>(st, bc.partials + size_t(bc.ds_first_chunk[b]) * C::NSTAT, bc.ds_nchunks[b], a,
+                     reinterpret_cast<double *>(smem));
+    if (threadIdx.x == 0 && ds_running(st)) atomicAdd(&ctl->active, 1u);
+}
+
+// Set-up of every data set of a class (one warp per data set).
+template <int M>
+__global__ void batched_setup_kernel(BatchClass bc, int init)
+{
+    constexpr int MM = M > 0 ? M * M : 1;
+    __shared__ double A[MM], Lc[MM];
+    if (threadIdx.x >= 32) return;
+    setup_state<M>(bc.states + bc.ds_list[blockIdx.x], init, threadIdx.x, A, Lc);
+}
+
+} // namespace vbh

@@ -14,11 +14,26 @@ struct KernelInfo {
     int nstat;             // statistics per block partial
 };
 
+// Kernels of the batched form for one S class.
+struct BatchKernelInfo {
+    const void *pass;      // batched_pass_kernel<S>
+    const void *update;    // batched_update_kernel<S - 1>
+    const void *setup;     // batched_setup_kernel<S - 1>
+    size_t pass_smem;
+    size_t update_smem;
+    int threads;
+    int tile;              // observations per tile of the pass
+    int nstat;
+};
+
 // Each translation unit that instantiates sweep kernels fills the entries of
 // its S range and returns false for the others.
 bool kernel_info_s1_4(int S, KernelInfo *out);
 bool kernel_info_s5_8(int S, KernelInfo *out);
 bool kernel_info_s9_11(int S, KernelInfo *out);
+bool batch_kernel_info_s1_4(int S, BatchKernelInfo *out);
+bool batch_kernel_info_s5_8(int S, BatchKernelInfo *out);
+bool batch_kernel_info_s9_11(int S, BatchKernelInfo *out);
 
 } // namespace vbh
 
@@ -32,5 +47,19 @@ bool kernel_info_s9_11(int S, KernelInfo *out);
         out->threads = C::THREADS;                                                                                     \
         out->tile = C::T;                                                                                              \
         out->nstat = C::NSTAT;                                                                                         \
+        return true;                                                                                                   \
+    }
+
+#define VBH_BATCH_KERNEL_INFO_CASE(SV)                                                                                 \
+    case SV: {                                                                                                         \
+        using BC = ::vbh::BatchCfg<SV>;                                                                                \
+        out->pass = reinterpret_cast<const void *>(&::vbh::batched_pass_kernel<SV>);                                   \
+        out->update = reinterpret_cast<const void *>(&::vbh::batched_update_kernel<SV - 1>);                           \
+        out->setup = reinterpret_cast<const void *>(&::vbh::batched_setup_kernel<SV - 1>);                             \
+        out->pass_smem = BC::SMEM_BYTES;                                                                               \
+        out->update_smem = size_t(::vbh::gu_ws_doubles<SV - 1>()) * 8;                                                 \
+        out->threads = BC::THREADS;                                                                                    \
+        out->tile = BC::T;                                                                                             \
+        out->nstat = ::vbh::SweepCfg<SV>::NSTAT;                                                                       \
         return true;                                                                                                   \
     }

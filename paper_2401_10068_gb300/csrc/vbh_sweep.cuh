@@ -665,16 +665,14 @@ __device__ inline void elbo_const(ElboConst *k, int M, double a_rho, double nu, 
     }
 }
 
+// The set-up body for one state, run by one warp (lane = 0..31); A and Lc
+// are shared-memory scratch of M*M doubles each.
 template <int M>
-__global__ void setup_kernel(DevState *st, int init)
+__device__ void setup_state(DevState *st, int init, int lane, double *A, double *Lc)
 {
-    constexpr int MM = M > 0 ? M * M : 1;
     constexpr double LN2PI = 1.8378770664093454836;
     constexpr double LN2 = 0.69314718055994530942;
     constexpr double LNPI = 1.1447298858494002;
-    __shared__ double A[MM], Lc[MM];
-    const int lane = threadIdx.x;
-    if (threadIdx.x >= 32) return;
     for (int i = lane; i < M * M; i += 32) A[i] = st->L0inv[i];
     __syncwarp();
     int fail = warp_cholesky<M>(A, Lc, lane);
@@ -712,6 +710,15 @@ __global__ void setup_kernel(DevState *st, int init)
         st->ticket = 0u;
         if (fail) st->status = ST_ENONFINITE;
     }
+}
+
+template <int M>
+__global__ void setup_kernel(DevState *st, int init)
+{
+    constexpr int MM = M > 0 ? M * M : 1;
+    __shared__ double A[MM], Lc[MM];
+    if (threadIdx.x >= 32) return;
+    setup_state<M>(st, init, threadIdx.x, A, Lc);
 }
 
 } // namespace vbh

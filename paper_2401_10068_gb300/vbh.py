@@ -78,6 +78,8 @@ def _lib():
             "vbh_fit_result": (ci, [vp, R]),
             "vbh_elbo": (ci, [vp, vp, vp, i64, ci, P, R, _dp]),
             "vbh_fit_static": (ci, [vp, vp, i64, ci, P, O, R, ci, vp]),
+            "vbh_fit_batched": (ci, [vp, ci, ctypes.POINTER(i64), ctypes.POINTER(ci), ctypes.POINTER(vp),
+                                     ctypes.POINTER(vp), P, O, R]),
         }
         for name, (res, args) in sigs.items():
             f = getattr(lib, name)
@@ -131,8 +133,8 @@ class _PriorArgs:
 
 
 def result_to_dict(res: Result) -> dict:
-    S = res.S
-    M = S - 1
+    S = max(int(res.S), 0)
+    M = max(S - 1, 0)
     return {"S": S, "iters": res.iters, "converged": bool(res.converged), "status": res.status,
             "const_dropped": bool(res.elbo_const_dropped), "kappa": np.array(res.kappa[:M]),
             "weights": np.array(res.weights[:S]), "Winv": np.array(res.W_inv[:M * M]).reshape(M, M),
@@ -247,6 +249,54 @@ class Handle:
         if self._trace is not None:
             out["trace"] = self._trace[:res.iters + 1].copy()
         return out
+
+    def fit_batched(self, rs, ds, Ss, priors=None, tol: float = 1e-8, max_iter: int = 200, init_states=None,
+                    trace: bool = False) -> list:
+        """``vbh_fit_batched``: B independent fits (lists of inputs, one S per
+        data set; priors and init_states are lists of dicts or None)."""
+        B = len(rs)
+        if not (len(ds) == len(Ss) == B):
+            raise ValueError("rs, ds and Ss must have the same length")
+        Vs = (ctypes.c_int64 * B)(*[int(r.shape[0]) if r is not None else 0 for r in rs])
+        Sa = (ctypes.c_int * B)(*[int(x) for x in Ss])
+        rp = (ctypes.c_void_p * B)(*[(_ptr(r).value if r is not None else None) for r in rs])
+        dp = (ctypes.c_void_p * B)(*[(_ptr(d).value if d is not None else None) for d in ds])
+        keep = []
+        pa = None
+        if priors is not None:
+            pa = (Prior * B)()
+            for b in range(B):
+                pb = _PriorArgs(priors[b], int(Ss[b]))
+                keep.append(pb)
+                pa[b] = pb.c
+        o = Opts()
+        _lib().vbh_opts_default(ctypes.byref(o))
+        o.tol = float(tol)
+        o.max_iter = int(max_iter)
+        if init_states is not None:
+            ia = (Result * B)()
+            for b in range(B):
+                ia[b] = dict_to_result(init_states[b], int(Ss[b])) if isinstance(init_states[b], dict) else init_states[b]
+            keep.append(ia)
+            o.init = INIT_GIVEN
+            o.init_state = ctypes.cast(ia, ctypes.POINTER(Result))
+        buf = None
+        if trace:
+            buf = np.zeros((B, int(max_iter) + 1))
+            o.elbo_trace = buf.ctypes.data_as(_dp)
+        out = (Result * B)()
+        rc = _lib().vbh_fit_batched(self._h, B, Vs, Sa, rp, dp,
+                                    ctypes.cast(pa, ctypes.POINTER(Prior)) if pa is not None else None,
+                                    ctypes.byref(o), out)
+        res = [result_to_dict(out[b]) for b in range(B)]
+        if buf is not None:
+            for b in range(B):
+                res[b]["trace"] = buf[b, :res[b]["iters"] + 1].copy()
+        if rc != 0:
+            err = VBHError(rc, "vbh_fit_batched")
+            err.results = res
+            raise err
+        return res
 
     def elbo(self, r, d, S: int, state: dict, prior: dict | None = None, V: int | None = None) -> float:
         V = int(V if V is not None else (r.shape[0] if r is not None else 0))
