@@ -305,6 +305,85 @@ def ctypes_result_bytes():
     return 3 * vbh.state_bytes()
 
 
+BATCH = {"name": "batched: 4,096 independent data sets", "datasets": 4096, "n_lo": 200, "n_hi": 50000,
+         "genes": (48, 96), "S_lo": 2, "S_hi": 10, "alpha": 0.5, "seed0": 1000, "tol": 1e-8, "cap": 1000}
+
+
+def batch_specs(B):
+    """Data set shapes of the batched workload: N ~ log-uniform[200, 50000]
+    cells, G uniform on {48, 96} genes (V = N G), S uniform on 2..10."""
+    rng = np.random.default_rng(7)
+    N = np.floor(np.exp(rng.uniform(np.log(BATCH["n_lo"]), np.log(BATCH["n_hi"]), size=B))).astype(np.int64)
+    G = rng.choice(np.array(BATCH["genes"]), size=B)
+    S = rng.integers(BATCH["S_lo"], BATCH["S_hi"] + 1, size=B)
+    return N * G, S
+
+
+def run_batched(args):
+    """Converged data sets per second of the batched form, with the plain
+    single-data-set form timed on a sample of the same data sets."""
+    import torch
+    from paper_2401_10068_gb300 import _build
+    _build.build_all()
+    from paper_2401_10068_gb300 import synth, vbh
+    dev = torch.device("cuda", 0)
+    B = args.datasets
+    V, S = batch_specs(B)
+    stream = torch.cuda.Stream(dev)
+    rs, ds = [], []
+    with torch.cuda.stream(stream):
+        for b in range(B):
+            r, d, _ = synth.generate_device(int(V[b]), int(S[b]), seed=BATCH["seed0"] + b, alpha=BATCH["alpha"],
+                                            device=dev)
+            rs.append(r)
+            ds.append(d)
+    stream.synchronize()
+    h = vbh.Handle(0, stream)
+    Ss = [int(x) for x in S]
+    h.fit_batched(rs[:64], ds[:64], Ss[:64], None, tol=0.0, max_iter=args.warmup)       # warm-up
+    clocks = Clocks(0)
+    time.sleep(0.3)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    ev0.record(stream)
+    res = h.fit_batched(rs, ds, Ss, None, tol=BATCH["tol"], max_iter=BATCH["cap"])
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    sec = ev0.elapsed_time(ev1) * 1e-3
+    clk = clocks.stop()
+    iters = np.array([x["iters"] for x in res])
+    conv = np.array([x["converged"] for x in res])
+    upd = float(np.sum(V.astype(np.float64) * S * (iters + 1)))
+    byts = float(np.sum(V.astype(np.float64) * (S + 1) * 4 * (iters + 1)))
+    # the plain form on a sample, same tolerance and cap
+    sample = list(range(0, B, max(1, B // args.plain_sample)))[:args.plain_sample]
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    plain = [h.fit(rs[b], ds[b], Ss[b], None, tol=BATCH["tol"], max_iter=BATCH["cap"]) for b in sample]
+    torch.cuda.synchronize(dev)
+    sec_plain = time.perf_counter() - t0
+    gap = max(abs(res[b]["elbo"] - p["elbo"]) / abs(p["elbo"]) for b, p in zip(sample, plain))
+    # the same data sets by the plain form for exactly the batched form's sweep counts
+    same = [h.fit(rs[b], ds[b], Ss[b], None, tol=0.0, max_iter=res[b]["iters"]) for b in sample]
+    gap_same = max(abs(res[b]["elbo"] - p["elbo"]) / abs(p["elbo"]) for b, p in zip(sample, same))
+    stop_spread = [res[b]["iters"] - p["iters"] for b, p in zip(sample, plain)]
+    h.close()
+    line = {"metric": "converged datasets/s (batched form)", "value": float(conv.sum()) / sec, "unit": "datasets/s",
+            "n_gpus": 1, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": BATCH["name"], "datasets": B, "V_total": int(V.sum()),
+                       "bytes_resident": float(np.sum(V.astype(np.float64) * (S + 1) * 4)),
+                       "tol": BATCH["tol"], "cap": BATCH["cap"], "chunk_tiles": None},
+            "seconds": sec, "converged": int(conv.sum()), "iters_mean": float(iters.mean()),
+            "iters_max": int(iters.max()), "datasets_per_s_all": B / sec,
+            "updates_per_s": upd / sec, "achieved_gbs_data_pass": byts / sec / 1e9,
+            "plain": {"sample": len(sample), "seconds": sec_plain, "datasets_per_s": len(sample) / sec_plain,
+                      "max_rel_elbo_gap_vs_batched": gap, "max_rel_elbo_gap_same_sweeps": gap_same,
+                      "stop_sweep_difference_min_max": [int(min(stop_spread)), int(max(stop_spread))]},
+            "speedup_vs_plain": (B / sec) / (len(sample) / sec_plain), "clocks": clk}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -315,7 +394,13 @@ def main():
                     help="N cells (x 96 genes); smaller values give the small case used for ncu captures")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
+    ap.add_argument("--workload", default="at-scale", choices=["at-scale", "batched"],
+                    help="batched: the 4,096-data-set form (a separate measurement, not the default step)")
+    ap.add_argument("--datasets", type=int, default=BATCH["datasets"])
+    ap.add_argument("--plain-sample", type=int, default=32)
     args = ap.parse_args()
+    if args.workload == "batched":
+        return run_batched(args)
     global V_FULL
     if args.cells != WORKLOAD["cells"]:
         WORKLOAD["cells"] = args.cells
