@@ -28,6 +28,17 @@
  *     are contiguous).  Device pointers must be 16-byte aligned.
  *   - The sweep is FP32 per observation with FP64 accumulation across blocks
  *     and FP64 global updates; non-finite results return VBH_ENONFINITE.
+ *   - For 12 <= S <= 32 the two contractions per observation that grow with
+ *     M^2 (q_i = D_i^T Sigma0 D_i of Eq. 20-21 and the sum of
+ *     (w_i^2 - c_i) D_i D_i^T that enters Eq. 25) run on the tensor cores:
+ *     the profiles are converted once per fit to BF16 (a device buffer of
+ *     V x 64 bytes owned by the handle) and every FP32 operand is split into
+ *     BF16 parts, three for VBH_FP32 (the FP32 values) and two for VBH_BF16
+ *     (16 significant bits).  VBH_FP32 then needs profiles that BF16 holds
+ *     exactly (binary profiles, as in the paper, do) and returns
+ *     VBH_EUNSUPPORTED otherwise; VBH_BF16 rounds any profile to BF16.
+ *     Accumulation is FP32 over 16 tiles of 128 observations, compensated FP32
+ *     across tiles, FP64 across blocks.  These fits need V < 2^31.
  */
 #ifndef VBH_H
 #define VBH_H
@@ -53,7 +64,9 @@ extern "C" {
 #define VBH_EUNSUPPORTED (-7)    /* valid request this build does not implement (e.g. S above the FP32 sweep limit) */
 
 /* precision of the per-observation sweep */
-#define VBH_FP32 0
+#define VBH_FP32 0               /* FP32 products and sums per observation */
+#define VBH_BF16 1               /* 12 <= S <= 32: 16-bit tensor-core operands for all but the last
+                                    vbh_opts.refine_iters sweeps, which run as VBH_FP32; S <= 11 runs VBH_FP32 */
 
 /* initial state of a fit */
 #define VBH_INIT_PAPER 0         /* Q(beta_i) = N(K0, Lambda_0^{-1}) before sweep 0 (Section 3.5) */
@@ -87,8 +100,11 @@ typedef struct {
 typedef struct {
     double tol;                  /* stop after sweep t >= 1 when |L_t - L_{t-1}| < tol |L_t|; 0 runs max_iter sweeps */
     int max_iter;                /* sweeps after sweep 0, >= 0 */
-    int precision;               /* VBH_FP32 */
+    int precision;               /* VBH_FP32 or VBH_BF16 */
     int init;                    /* VBH_INIT_PAPER or VBH_INIT_GIVEN */
+    int refine_iters;            /* VBH_BF16 only: the last sweeps (>= 0, of max_iter) run as VBH_FP32;
+                                    after the 16-bit sweeps stop (tolerance or count) the FP32 sweeps
+                                    continue with the same tolerance test */
     const vbh_result *init_state;/* global factors to start from when init == VBH_INIT_GIVEN */
     double *elbo_trace;          /* optional host array of max_iter + 1 doubles: L_0 .. L_iters */
 } vbh_opts;
@@ -96,7 +112,7 @@ typedef struct {
 /* Fill *p with the paper's prior for S subpopulations (Section 3.5). */
 void vbh_prior_default(int S, vbh_prior *p);
 
-/* Fill *o with tol = 1e-8, max_iter = 200, VBH_FP32, VBH_INIT_PAPER, no trace. */
+/* Fill *o with tol = 1e-8, max_iter = 200, VBH_FP32, VBH_INIT_PAPER, refine_iters = 10, no trace. */
 void vbh_opts_default(vbh_opts *o);
 
 /* Create a handle on CUDA device `device` that issues all work on `stream`
@@ -113,6 +129,12 @@ void vbh_destroy(vbh_handle *h);
 
 /* Name of a status code (static string). */
 const char *vbh_strerror(int status);
+
+/* Detail of the last failed CUDA call behind a VBH_ECUDA or VBH_ENOMEM status
+ * returned to the calling host thread ("<call> at <file>:<line>: <error>"),
+ * or "" if there was none.  Thread-local static storage: valid until the
+ * thread's next failing call. */
+const char *vbh_last_error_detail(void);
 
 /* Bytes of the device-resident fit state that each vbh_fit_begin,
  * vbh_fit_step and vbh_fit_result call copies back to the host (a vbh_fit

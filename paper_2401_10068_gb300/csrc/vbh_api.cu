@@ -1,9 +1,11 @@
 // vbh_api.cu -- the C ABI declared in include/vbh.h: handle, argument
 // checks, input staging, the CUDA-graph sweep loop and result read-back.
 // All arithmetic of the method runs in the kernels of vbh_sweep.cuh.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -12,9 +14,31 @@
 #include "vbh_batched_host.h"
 #include "vbh_dispatch.cuh"
 #include "vbh_internal.cuh"
+#include "vbh_error.h"
+#include "vbh_tc_host.h"
 
 using vbh::DevState;
 using vbh::KernelInfo;
+
+// How the sweeps of a fit are launched: the CUDA-core kernel (S <= 11) or the
+// tensor-core kernel (12 <= S <= 32, which reads BF16 profiles through
+// tensor maps).
+struct Launch {
+    bool tc = false;
+    int S = 0;
+    int grid = 0;
+    int nsplit = 3;
+    int binary = 1;
+    KernelInfo ki{};
+    vbh::TcKernelInfo tki{};
+    CUtensorMap tmap_d;
+    const float *r_pad = nullptr;
+    const void *func() const { return tc ? tki.sweep : ki.sweep; }
+    const void *setup() const { return tc ? tki.setup : ki.setup; }
+    int threads() const { return tc ? tki.threads : ki.threads; }
+    size_t smem() const { return tc ? tki.smem : ki.smem; }
+    int tile() const { return tc ? tki.tile : ki.tile; }
+};
 
 struct vbh_handle {
     int device = 0;
@@ -24,7 +48,7 @@ struct vbh_handle {
     DevState *st_aux = nullptr;        // device state used by vbh_elbo
     DevState *mirror = nullptr;        // pinned host copy of a DevState
     double *partials = nullptr;
-    size_t partials_cap = 0;           // doubles
+    size_t partials_cap = 0;           // bytes
     double *trace = nullptr;
     int trace_cap = 0;
     float *stage_r = nullptr, *stage_d = nullptr;
@@ -36,14 +60,22 @@ struct vbh_handle {
     const float *r = nullptr, *d = nullptr;    // device pointers used by the kernels
     int max_iter = 0;
     double *user_trace = nullptr;
-    KernelInfo ki{};
-    int grid = 0;
+    Launch L;
+    bool bf16_phase = false;       // VBH_BF16 fit still in its 16-bit sweeps
+    int bf16_limit = 0;            // last sweep index of the 16-bit sweeps
+    int refine = 0;                // FP32 sweeps after them
+    // BF16 profiles of the tensor-core path
+    void *d16 = nullptr;
+    size_t d16_cap = 0;
+    unsigned long long *counts = nullptr;       // [inexact, non-binary] profile values (device)
+    const void *g_d16 = nullptr;
     // cached graph of the sweep loop
     cudaGraphExec_t gexec = nullptr;
     int g_S = -1, g_grid = -1;
     long long g_V = -1;
     const float *g_r = nullptr, *g_d = nullptr;
     const double *g_partials = nullptr;
+    const void *g_func = nullptr;
     bool attr_set[vbh::SMAX + 1] = {};
     bool direct = false;               // VBH_LAUNCH=direct: one stream launch per sweep, no graph
     vbh::BatchedHost batched;          // buffers of vbh_fit_batched
@@ -59,6 +91,19 @@ __global__ void set_target_kernel(DevState *st, int nsweeps)
         st->target = t > st->max_iter ? st->max_iter : int(t);
     }
 }
+
+namespace {
+thread_local char g_error_detail[512] = "";
+} // namespace
+
+void record_error(const char *what, const char *file, int line, const char *detail)
+{
+    const char *base = std::strrchr(file, '/');
+    std::snprintf(g_error_detail, sizeof(g_error_detail), "%s at %s:%d: %s", what, base ? base + 1 : file, line,
+                  detail ? detail : "");
+}
+
+const char *last_error_buf() { return g_error_detail; }
 
 } // namespace vbh
 
@@ -78,14 +123,7 @@ struct DeviceGuard {
     }
 };
 
-#define VBH_CK(call)                                                                                                   \
-    do {                                                                                                               \
-        cudaError_t e_ = (call);                                                                                       \
-        if (e_ != cudaSuccess) {                                                                                       \
-            (void)cudaGetLastError();                                                                                  \
-            return e_ == cudaErrorMemoryAllocation ? VBH_ENOMEM : VBH_ECUDA;                                           \
-        }                                                                                                              \
-    } while (0)
+#define VBH_CK(call) VBH_CHECK_CUDA(call)
 
 bool kernel_info(int S, KernelInfo *ki)
 {
@@ -230,28 +268,72 @@ void fill_prior(DevState *s, const vbh_prior *p, int S, long long V)
         default_L0inv(M, s->L0inv);
 }
 
-int prepare_kernel(vbh_handle *h, int S, long long V, KernelInfo *ki, int *grid)
+// Kernel choice, launch shape and partials buffer of a fit of (V, S).  For the
+// tensor-core path the BF16 profiles and the tensor maps are prepared too.
+int prepare_launch(vbh_handle *h, int S, long long V, int precision, const float *rd, const float *dd, Launch *L)
 {
-    if (!kernel_info(S, ki)) return VBH_EUNSUPPORTED;
-    if (!h->attr_set[S]) {
-        VBH_CK(cudaFuncSetAttribute(ki->sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, int(ki->smem)));
-        h->attr_set[S] = true;
+    L->S = S;
+    const int M = S - 1;
+    const size_t nstat = size_t(M * (M + 1) / 2 + M + 3);
+    if (S <= vbh::S_FP32_MAX) {
+        L->tc = false;
+        if (!kernel_info(S, &L->ki)) return VBH_EUNSUPPORTED;
+        if (!h->attr_set[S]) {
+            VBH_CK(cudaFuncSetAttribute(L->ki.sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, int(L->ki.smem)));
+            h->attr_set[S] = true;
+        }
+    } else {
+        if (V >= (1LL << 31)) return VBH_EUNSUPPORTED;
+        L->tc = true;
+        L->nsplit = (precision == VBH_BF16) ? 2 : 3;
+        if (!vbh::tc_kernel_info(L->nsplit, &L->tki)) return VBH_EUNSUPPORTED;
+        VBH_CK(cudaFuncSetAttribute(L->tki.sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, int(L->tki.smem)));
     }
     int per_sm = 0;
-    VBH_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ki->sweep, ki->threads, ki->smem));
-    if (per_sm < 1) return VBH_ECUDA;
-    long long tiles = (V + ki->tile - 1) / ki->tile;
+    VBH_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, L->func(), L->threads(), L->smem()));
+    if (per_sm < 1) {
+        vbh::record_error("occupancy of the sweep kernel", __FILE__, __LINE__, "no block fits on an SM");
+        return VBH_ECUDA;
+    }
+    if (L->tc) per_sm = 1;                                   // one CTA per SM owns all 512 TMEM columns
+    long long tiles = (V + L->tile() - 1) / L->tile();
     long long g = (long long)h->nsm * per_sm;
     if (tiles < g) g = tiles;
     if (g < 1) g = 1;
-    *grid = int(g);
-    int rc = ensure(reinterpret_cast<void **>(&h->partials), &h->partials_cap,
-                    size_t(g) * size_t(ki->nstat) * sizeof(double));
-    return rc;
+    L->grid = int(g);
+    int rc = ensure(reinterpret_cast<void **>(&h->partials), &h->partials_cap, size_t(g) * nstat * sizeof(double));
+    if (rc) return rc;
+    if (L->tc && V > 0) {
+        if ((rc = ensure(&h->d16, &h->d16_cap, vbh::tc_input_bytes(V)))) return rc;
+        if (!h->counts) {
+            size_t cap = 0;
+            if ((rc = ensure(reinterpret_cast<void **>(&h->counts), &cap, 2 * sizeof(unsigned long long)))) return rc;
+        }
+        VBH_CK(cudaMemsetAsync(h->counts, 0, 2 * sizeof(unsigned long long), h->stream));
+        if ((rc = vbh::tc_convert_inputs(dd, rd, V, S, h->d16, h->counts, h->stream, h->nsm))) return rc;
+        unsigned long long cnt[2] = {0, 0};
+        VBH_CK(cudaMemcpyAsync(cnt, h->counts, sizeof(cnt), cudaMemcpyDeviceToHost, h->stream));
+        VBH_CK(cudaStreamSynchronize(h->stream));
+        // the FP32 form needs profiles that BF16 holds exactly (binary ones do)
+        if (cnt[0] != 0 && precision != VBH_BF16) return VBH_EUNSUPPORTED;
+        L->binary = cnt[1] == 0 ? 1 : 0;
+        L->r_pad = vbh::tc_r_pad(h->d16, V);
+        if ((rc = vbh::tc_encode_tensor_map(h->d16, V, &L->tmap_d))) return rc;
+    }
+    return VBH_OK;
 }
 
-int launch_sweep(vbh_handle *h, DevState *st, int mode, const KernelInfo &ki, int grid, const float *r,
-                 const float *d, long long V)
+// Switch of a VBH_BF16 fit to its FP32 sweeps: clear the convergence flag of
+// the 16-bit sweeps and cap the FP32 ones.
+__global__ void refine_phase_kernel(DevState *st, int max_iter)
+{
+    if (threadIdx.x == 0) {
+        st->converged = 0;
+        st->max_iter = max_iter;
+    }
+}
+
+int launch_sweep(vbh_handle *h, DevState *st, int mode, Launch &L, const float *r, const float *d, long long V)
 {
     vbh::SweepArgs a{};
     a.r = r;
@@ -261,22 +343,30 @@ int launch_sweep(vbh_handle *h, DevState *st, int mode, const KernelInfo &ki, in
     a.partials = h->partials;
     a.use_cond = 0;
     a.mode = mode;
-    void *args[] = {&a};
-    VBH_CK(cudaLaunchKernel(ki.sweep, dim3(grid), dim3(ki.threads), args, ki.smem, h->stream));
+    if (L.tc) {
+        a.r = L.r_pad;
+        vbh::TcArgs ta{a, L.S, L.binary};
+        void *args[] = {&L.tmap_d, &ta};
+        VBH_CK(cudaLaunchKernel(L.tki.sweep, dim3(L.grid), dim3(L.tki.threads), args, L.tki.smem, h->stream));
+    } else {
+        void *args[] = {&a};
+        VBH_CK(cudaLaunchKernel(L.ki.sweep, dim3(L.grid), dim3(L.ki.threads), args, L.ki.smem, h->stream));
+    }
     return VBH_OK;
 }
 
-int launch_setup(vbh_handle *h, DevState *st, const KernelInfo &ki, int init)
+int launch_setup(vbh_handle *h, DevState *st, const Launch &L, int init)
 {
     void *args[] = {&st, &init};
-    VBH_CK(cudaLaunchKernel(ki.setup, dim3(1), dim3(32), args, 0, h->stream));
+    VBH_CK(cudaLaunchKernel(L.setup(), dim3(1), dim3(32), args, 0, h->stream));
     return VBH_OK;
 }
 
 int build_graph(vbh_handle *h)
 {
-    if (h->gexec && h->g_S == h->S && h->g_grid == h->grid && h->g_V == h->V && h->g_r == h->r && h->g_d == h->d &&
-        h->g_partials == h->partials)
+    Launch &L = h->L;
+    if (h->gexec && h->g_S == h->S && h->g_grid == L.grid && h->g_V == h->V && h->g_r == h->r && h->g_d == h->d &&
+        h->g_partials == h->partials && h->g_func == L.func() && h->g_d16 == (L.tc ? h->d16 : nullptr))
         return VBH_OK;
     if (h->gexec) {
         cudaGraphExecDestroy(h->gexec);
@@ -290,8 +380,11 @@ int build_graph(vbh_handle *h)
     cudaGraphNode_t wnode, knode;
     cudaGraphNodeParams kp{};
     vbh::SweepArgs a{};
+    vbh::TcArgs ta{};
     void *args[] = {&a};
+    void *targs[] = {&L.tmap_d, &ta};
     if (cudaGraphConditionalHandleCreate(&cond, g, 1u, cudaGraphCondAssignDefault) != cudaSuccess) {
+        vbh::record_error("cudaGraphConditionalHandleCreate", __FILE__, __LINE__, cudaGetErrorName(cudaGetLastError()));
         rc = VBH_ECUDA;
         goto out;
     }
@@ -300,6 +393,7 @@ int build_graph(vbh_handle *h)
     cp.conditional.type = cudaGraphCondTypeWhile;
     cp.conditional.size = 1;
     if (cudaGraphAddNode(&wnode, g, nullptr, nullptr, 0, &cp) != cudaSuccess) {
+        vbh::record_error("cudaGraphAddNode(while)", __FILE__, __LINE__, cudaGetErrorName(cudaGetLastError()));
         rc = VBH_ECUDA;
         goto out;
     }
@@ -311,27 +405,35 @@ int build_graph(vbh_handle *h)
     a.cond = cond;
     a.use_cond = 1;
     a.mode = vbh::MODE_ITER;
+    ta.sa = a;
+    ta.sa.r = L.r_pad;
+    ta.S = L.S;
+    ta.binary = L.binary;
     kp.type = cudaGraphNodeTypeKernel;
-    kp.kernel.func = const_cast<void *>(h->ki.sweep);
-    kp.kernel.gridDim = dim3(h->grid);
-    kp.kernel.blockDim = dim3(h->ki.threads);
-    kp.kernel.sharedMemBytes = (unsigned)h->ki.smem;
-    kp.kernel.kernelParams = args;
+    kp.kernel.func = const_cast<void *>(L.func());
+    kp.kernel.gridDim = dim3(L.grid);
+    kp.kernel.blockDim = dim3(L.threads());
+    kp.kernel.sharedMemBytes = (unsigned)L.smem();
+    kp.kernel.kernelParams = L.tc ? targs : args;
     if (cudaGraphAddNode(&knode, cp.conditional.phGraph_out[0], nullptr, nullptr, 0, &kp) != cudaSuccess) {
+        vbh::record_error("cudaGraphAddNode(sweep)", __FILE__, __LINE__, cudaGetErrorName(cudaGetLastError()));
         rc = VBH_ECUDA;
         goto out;
     }
     if (cudaGraphInstantiate(&h->gexec, g, 0) != cudaSuccess) {
+        vbh::record_error("cudaGraphInstantiate", __FILE__, __LINE__, cudaGetErrorName(cudaGetLastError()));
         h->gexec = nullptr;
         rc = VBH_ECUDA;
         goto out;
     }
     h->g_S = h->S;
-    h->g_grid = h->grid;
+    h->g_grid = L.grid;
     h->g_V = h->V;
     h->g_r = h->r;
     h->g_d = h->d;
     h->g_partials = h->partials;
+    h->g_func = L.func();
+    h->g_d16 = L.tc ? h->d16 : nullptr;
 out:
     if (rc) (void)cudaGetLastError();
     cudaGraphDestroy(g);
@@ -402,6 +504,7 @@ void vbh_opts_default(vbh_opts *o)
     o->tol = 1e-8;
     o->max_iter = 200;
     o->precision = VBH_FP32;
+    o->refine_iters = 10;
     o->init = VBH_INIT_PAPER;
     o->init_state = nullptr;
     o->elbo_trace = nullptr;
@@ -423,6 +526,8 @@ const char *vbh_strerror(int status)
 }
 
 size_t vbh_state_bytes(void) { return sizeof(DevState); }
+
+const char *vbh_last_error_detail(void) { return vbh::last_error_buf(); }
 
 int vbh_create(vbh_handle **hp, int device, void *stream)
 {
@@ -468,6 +573,8 @@ void vbh_destroy(vbh_handle *h)
     cudaFree(h->trace);
     cudaFree(h->stage_r);
     cudaFree(h->stage_d);
+    cudaFree(h->d16);
+    cudaFree(h->counts);
     if (h->mirror) cudaFreeHost(h->mirror);
     cudaFree(h->batched.arena);
     if (h->batched.host_states) cudaFreeHost(h->batched.host_states);
@@ -481,18 +588,19 @@ int vbh_fit_begin(vbh_handle *h, const float *r, const float *d, int64_t V, int 
     int rc = check_common(h, r, d, V, S);
     if (rc) return rc;
     if ((rc = check_prior(p, S))) return rc;
-    if (!o || o->max_iter < 0 || !(o->tol >= 0.0) || !std::isfinite(o->tol) || o->precision != VBH_FP32)
+    if (!o || o->max_iter < 0 || !(o->tol >= 0.0) || !std::isfinite(o->tol) ||
+        (o->precision != VBH_FP32 && o->precision != VBH_BF16))
         return VBH_EINVAL;
+    if (o->precision == VBH_BF16 && o->refine_iters < 0) return VBH_EINVAL;
     if (o->init != VBH_INIT_PAPER && o->init != VBH_INIT_GIVEN) return VBH_EINVAL;
     if (o->init == VBH_INIT_GIVEN && (!o->init_state || o->init_state->S != S)) return VBH_EINVAL;
     DeviceGuard g(h->device);
     if (!g.ok) return VBH_ECUDA;
     h->begun = false;
-    KernelInfo ki;
-    int grid = 0;
-    if ((rc = prepare_kernel(h, S, V, &ki, &grid))) return rc;
     const float *rd = nullptr, *dd = nullptr;
     if ((rc = stage_inputs(h, r, d, V, S, &rd, &dd))) return rc;
+    Launch L;
+    if ((rc = prepare_launch(h, S, V, o->precision, rd, dd, &L))) return rc;
     if (o->max_iter + 1 > h->trace_cap) {
         size_t cap = 0;
         cudaFree(h->trace);
@@ -523,15 +631,19 @@ int vbh_fit_begin(vbh_handle *h, const float *r, const float *d, int64_t V, int 
         for (int j = 0; j < M; ++j) s->kappa[j] = q->kappa[j];
         symmetrize(M, q->W_inv, s->Winv);
     }
+    // the 16-bit sweeps of a VBH_BF16 fit, then its FP32 ones
+    const bool bf16 = L.tc && L.nsplit == 2;
+    const int refine = bf16 ? (o->refine_iters < o->max_iter ? o->refine_iters : o->max_iter) : 0;
+    if (bf16) s->max_iter = o->max_iter - refine;
     VBH_CK(cudaMemcpyAsync(h->st, s, sizeof(DevState), cudaMemcpyHostToDevice, h->stream));
     if (o->init == VBH_INIT_GIVEN) {
         // sweep 0 = the ELBO of the given factors (Q(beta) from them); the
         // sweeps that follow update all factors
-        if ((rc = launch_setup(h, h->st, ki, 0))) return rc;
-        if ((rc = launch_sweep(h, h->st, vbh::MODE_ELBO, ki, grid, rd, dd, V))) return rc;
+        if ((rc = launch_setup(h, h->st, L, 0))) return rc;
+        if ((rc = launch_sweep(h, h->st, vbh::MODE_ELBO, L, rd, dd, V))) return rc;
     } else {
-        if ((rc = launch_setup(h, h->st, ki, 1))) return rc;
-        if ((rc = launch_sweep(h, h->st, vbh::MODE_INIT, ki, grid, rd, dd, V))) return rc;
+        if ((rc = launch_setup(h, h->st, L, 1))) return rc;
+        if ((rc = launch_sweep(h, h->st, vbh::MODE_INIT, L, rd, dd, V))) return rc;
     }
     if ((rc = read_state(h, h->st))) return rc;
     if (h->mirror->status) return h->mirror->status;
@@ -540,12 +652,35 @@ int vbh_fit_begin(vbh_handle *h, const float *r, const float *d, int64_t V, int 
     h->V = V;
     h->r = rd;
     h->d = dd;
-    h->ki = ki;
-    h->grid = grid;
+    h->L = L;
+    h->bf16_phase = bf16;
+    h->bf16_limit = o->max_iter - refine;
+    h->refine = refine;
     h->max_iter = o->max_iter;
     h->user_trace = o->elbo_trace;
     return VBH_OK;
 }
+
+namespace {
+// Up to n sweeps of the current kernel (fewer on convergence or at the caps).
+int run_sweeps(vbh_handle *h, int n)
+{
+    int rc = VBH_OK;
+    vbh::set_target_kernel<<<1, 32, 0, h->stream>>>(h->st, n);
+    VBH_CK(cudaGetLastError());
+    if (h->direct) {
+        // each launch checks the control fields first and does nothing once the
+        // fit has converged or reached its target
+        const int m = n < h->max_iter ? n : h->max_iter;
+        for (int i = 0; i < m; ++i)
+            if ((rc = launch_sweep(h, h->st, vbh::MODE_ITER, h->L, h->r, h->d, h->V))) return rc;
+    } else {
+        if ((rc = build_graph(h))) return rc;
+        VBH_CK(cudaGraphLaunch(h->gexec, h->stream));
+    }
+    return read_state(h, h->st);
+}
+} // namespace
 
 int vbh_fit_step(vbh_handle *h, int nsweeps, int *converged)
 {
@@ -554,19 +689,26 @@ int vbh_fit_step(vbh_handle *h, int nsweeps, int *converged)
     DeviceGuard g(h->device);
     if (!g.ok) return VBH_ECUDA;
     int rc = VBH_OK;
-    vbh::set_target_kernel<<<1, 32, 0, h->stream>>>(h->st, nsweeps);
-    VBH_CK(cudaGetLastError());
-    if (h->direct) {
-        // each launch checks the control fields first and does nothing once the
-        // fit has converged or reached its target
-        const int n = nsweeps < h->max_iter ? nsweeps : h->max_iter;
-        for (int i = 0; i < n; ++i)
-            if ((rc = launch_sweep(h, h->st, vbh::MODE_ITER, h->ki, h->grid, h->r, h->d, h->V))) return rc;
-    } else {
-        if ((rc = build_graph(h))) return rc;
-        VBH_CK(cudaGraphLaunch(h->gexec, h->stream));
+    int left = nsweeps;
+    if (h->bf16_phase) {
+        const int it0 = h->mirror->iter;
+        if (left > 0 && (rc = run_sweeps(h, left))) return rc;
+        left -= h->mirror->iter - it0;
+        if (h->mirror->status) return h->mirror->status;
+        if (h->mirror->converged || h->mirror->iter >= h->bf16_limit) {
+            // switch to the FP32 sweeps: same BF16 profiles and tensor maps, three-part operands
+            Launch &L = h->L;
+            L.nsplit = 3;
+            if (!vbh::tc_kernel_info(3, &L.tki)) return VBH_EUNSUPPORTED;
+            VBH_CK(cudaFuncSetAttribute(L.tki.sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, int(L.tki.smem)));
+            const int cap = h->mirror->iter + h->refine < h->max_iter ? h->mirror->iter + h->refine : h->max_iter;
+            refine_phase_kernel<<<1, 32, 0, h->stream>>>(h->st, cap);
+            VBH_CK(cudaGetLastError());
+            h->bf16_phase = false;
+            if ((rc = read_state(h, h->st))) return rc;
+        }
     }
-    if ((rc = read_state(h, h->st))) return rc;
+    if (!h->bf16_phase && left > 0 && (rc = run_sweeps(h, left))) return rc;
     if (converged) *converged = h->mirror->converged;
     return h->mirror->status;
 }
@@ -628,12 +770,13 @@ int vbh_elbo(vbh_handle *h, const float *r, const float *d, int64_t V, int S, co
     if (!host_spd(M, q->W_inv)) return VBH_EINVAL;
     DeviceGuard g(h->device);
     if (!g.ok) return VBH_ECUDA;
-    KernelInfo ki;
-    int grid = 0;
-    if ((rc = prepare_kernel(h, S, V, &ki, &grid))) return rc;
     const float *rd = nullptr, *dd = nullptr;
     if ((rc = stage_inputs(h, r, d, V, S, &rd, &dd))) return rc;
-    if (h->begun && (rd != h->r || dd != h->d)) h->begun = false;   // staging buffers were reused
+    // a fit in progress loses its inputs when the staging buffers, the BF16
+    // profiles or the partials buffer are reused here
+    if (h->begun && (rd != h->r || dd != h->d || S > vbh::S_FP32_MAX || h->L.tc)) h->begun = false;
+    Launch L;
+    if ((rc = prepare_launch(h, S, V, VBH_FP32, rd, dd, &L))) return rc;
     DevState *s = h->mirror;
     VBH_CK(cudaStreamSynchronize(h->stream));
     std::memset(s, 0, sizeof(DevState));
@@ -645,8 +788,8 @@ int vbh_elbo(vbh_handle *h, const float *r, const float *d, int64_t V, int S, co
     for (int j = 0; j < M; ++j) s->kappa[j] = q->kappa[j];
     symmetrize(M, q->W_inv, s->Winv);
     VBH_CK(cudaMemcpyAsync(h->st_aux, s, sizeof(DevState), cudaMemcpyHostToDevice, h->stream));
-    if ((rc = launch_setup(h, h->st_aux, ki, 0))) return rc;
-    if ((rc = launch_sweep(h, h->st_aux, vbh::MODE_ELBO, ki, grid, rd, dd, V))) return rc;
+    if ((rc = launch_setup(h, h->st_aux, L, 0))) return rc;
+    if ((rc = launch_sweep(h, h->st_aux, vbh::MODE_ELBO, L, rd, dd, V))) return rc;
     if ((rc = read_state(h, h->st_aux))) return rc;
     *elbo = h->mirror->elbo;
     return h->mirror->status;

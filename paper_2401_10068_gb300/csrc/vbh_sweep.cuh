@@ -184,8 +184,7 @@ __device__ __forceinline__ void flush_warp(float (&acc)[SweepCfg<S>::NSTAT], dou
 // matrix A in shared memory, column by column, by one warp.  Returns nonzero
 // in every lane when A is not positive definite (a unit pivot is used then).
 // ---------------------------------------------------------------------------
-template <int M>
-__device__ int warp_cholesky(const double *A, double *L, int lane)
+__device__ inline int warp_cholesky_rt(int M, const double *A, double *L, int lane)
 {
     int fail = 0;
     for (int i = lane; i < M * M; i += 32) L[i] = 0.0;
@@ -212,6 +211,12 @@ __device__ int warp_cholesky(const double *A, double *L, int lane)
     return __shfl_sync(0xffffffffu, fail, 0);
 }
 
+template <int M>
+__device__ __forceinline__ int warp_cholesky(const double *A, double *L, int lane)
+{
+    return warp_cholesky_rt(M, A, L, lane);
+}
+
 // Sum over the lanes of a warp (fixed order).
 __device__ __forceinline__ double warp_sum(double v)
 {
@@ -226,10 +231,10 @@ __device__ __forceinline__ double warp_sum(double v)
 // warp; Lw receives chol(W^{-1}); returns ln|W^{-1}| in every lane.  The
 // global update and the set-up kernel both use this function, so a fit
 // resumed from saved factors continues bit for bit.
-template <int M>
-__device__ double derive_pass_globals(DevState *st, const double *Wn, double nu, double *Lw, int lane, int *fail)
+__device__ inline double derive_pass_globals_rt(int M, DevState *st, const double *Wn, double nu, double *Lw,
+                                                int lane, int *fail)
 {
-    *fail = warp_cholesky<M>(Wn, Lw, lane);
+    *fail = warp_cholesky_rt(M, Wn, Lw, lane);
     const double rs = rsqrt(nu);
     for (int i = lane; i < M; i += 32)
         for (int k = 0; k <= i; ++k) st->sw.L[i * (i + 1) / 2 + k] = static_cast<float>(Lw[i * M + k] * rs);
@@ -239,25 +244,39 @@ __device__ double derive_pass_globals(DevState *st, const double *Wn, double nu,
     return ld;
 }
 
+template <int M>
+__device__ __forceinline__ double derive_pass_globals(DevState *st, const double *Wn, double nu, double *Lw, int lane,
+                                                     int *fail)
+{
+    return derive_pass_globals_rt(M, st, Wn, nu, Lw, lane, fail);
+}
+
 // ---------------------------------------------------------------------------
 // (d)+(e): FP64 global update, ELBO and control, run by the whole last block.
-// ws: shared-memory workspace of at least gu_ws_doubles<M>() doubles.
+// ws: shared-memory workspace of at least gu_ws_doubles(M) doubles.  The
+// statistics of the partials are laid out as in SweepCfg: packed lower G,
+// g, T3, T4 (ln of mantissas), E4 (binary exponents).
 // ---------------------------------------------------------------------------
-template <int M>
-constexpr int gu_ws_doubles()
+__host__ __device__ constexpr int gu_ws_doubles_rt(int M)
 {
     return ((M * (M + 1) / 2 + M + 3 + 31) / 32) * 32 + 9 * (M > 0 ? M * M : 1) + 6 * (M > 0 ? M : 1) + 32;
 }
 
 template <int M>
-__device__ void global_update(DevState *st, const double *__restrict__ part, int nblk, const SweepArgs &a,
-                              double *ws)
+constexpr int gu_ws_doubles()
 {
-    using C = SweepCfg<M + 1>;
-    constexpr int NSTAT = C::NSTAT;
-    constexpr int MM = M > 0 ? M * M : 1;
-    constexpr int MV = M > 0 ? M : 1;
-    constexpr int MD = M > 0 ? M : 1;               // divisor (loops over M*M entries are empty at M = 0)
+    return gu_ws_doubles_rt(M);
+}
+
+__device__ inline void global_update_rt(int M, DevState *st, const double *__restrict__ part, int nblk,
+                                        const SweepArgs &a, double *ws)
+{
+    const int NG = M * (M + 1) / 2;
+    const int NSTAT = NG + M + 3;
+    const int I_g = NG, I_T3 = NG + M, I_T4 = NG + M + 1, I_E4 = NG + M + 2;
+    const int MM = M > 0 ? M * M : 1;
+    const int MV = M > 0 ? M : 1;
+    const int MD = M > 0 ? M : 1;                   // divisor (loops over M*M entries are empty at M = 0)
     constexpr double LN2PI = 1.8378770664093454836;
     constexpr double LN2 = 0.69314718055994530942;
     constexpr double LNPI = 1.1447298858494002;
@@ -320,8 +339,8 @@ __device__ void global_update(DevState *st, const double *__restrict__ part, int
 
     const ElboConst kc = (mode == MODE_ELBO) ? st->kc_given : st->kc_upd;
     const double V = st->V;
-    const double T3 = stat[C::I_T3];
-    const double T4 = stat[C::I_T4] + LN2 * stat[C::I_E4];
+    const double T3 = stat[I_T3];
+    const double T4 = stat[I_T4] + LN2 * stat[I_E4];
     const double q0 = st->q0, n0 = st->n0, b0 = st->b0, a0 = st->a0;
     const double lam = kc.lam, nu = kc.nu;
 
@@ -330,7 +349,7 @@ __device__ void global_update(DevState *st, const double *__restrict__ part, int
         const int r = i / MD, c = i % MD;
         G[i] = (r >= c) ? stat[r * (r + 1) / 2 + c] : stat[c * (c + 1) / 2 + r];
     }
-    for (int i = tid; i < M; i += nth) gv[i] = stat[C::I_g + i];
+    for (int i = tid; i < M; i += nth) gv[i] = stat[I_g + i];
     __syncthreads();
     for (int i = tid; i < M * M; i += nth) {
         const int r = i / MD, c = i % MD;
@@ -380,10 +399,10 @@ __device__ void global_update(DevState *st, const double *__restrict__ part, int
         int fail;
         double lndetWn;
         if (mode == MODE_ELBO) {
-            fail = warp_cholesky<M>(Wn, Lw, lane);
+            fail = warp_cholesky_rt(M, Wn, Lw, lane);
             lndetWn = warp_sum(lane < M ? 2.0 * log(Lw[lane * M + lane]) : 0.0);
         } else {
-            lndetWn = derive_pass_globals<M>(st, Wn, nu, Lw, lane, &fail);
+            lndetWn = derive_pass_globals_rt(M, st, Wn, nu, Lw, lane, &fail);
         }
         if (lane == 0) {
             if (fail) s_fail = 1;
@@ -484,6 +503,13 @@ __device__ void global_update(DevState *st, const double *__restrict__ part, int
                          st->iter < st->target && st->iter < st->max_iter;
         if (a.use_cond) cudaGraphSetConditional(a.cond, keep ? 1u : 0u);
     }
+}
+
+template <int M>
+__device__ __forceinline__ void global_update(DevState *st, const double *__restrict__ part, int nblk,
+                                              const SweepArgs &a, double *ws)
+{
+    global_update_rt(M, st, part, nblk, a, ws);
 }
 
 // ---------------------------------------------------------------------------
@@ -667,15 +693,14 @@ __device__ inline void elbo_const(ElboConst *k, int M, double a_rho, double nu, 
 
 // The set-up body for one state, run by one warp (lane = 0..31); A and Lc
 // are shared-memory scratch of M*M doubles each.
-template <int M>
-__device__ void setup_state(DevState *st, int init, int lane, double *A, double *Lc)
+__device__ inline void setup_state_rt(int M, DevState *st, int init, int lane, double *A, double *Lc)
 {
     constexpr double LN2PI = 1.8378770664093454836;
     constexpr double LN2 = 0.69314718055994530942;
     constexpr double LNPI = 1.1447298858494002;
     for (int i = lane; i < M * M; i += 32) A[i] = st->L0inv[i];
     __syncwarp();
-    int fail = warp_cholesky<M>(A, Lc, lane);
+    int fail = warp_cholesky_rt(M, A, Lc, lane);
     const double l0 = warp_sum(lane < M ? 2.0 * log(Lc[lane * M + lane]) : 0.0);
     // prior-only terms: M/2 (ln q0 - ln 2 pi) + a0 ln b0 - lnGamma(a0) + ln B(Lambda_0, n0)
     const double n0 = st->n0;
@@ -697,7 +722,7 @@ __device__ void setup_state(DevState *st, int init, int lane, double *A, double 
         for (int i = lane; i < M * M; i += 32) A[i] = st->Winv[i];
     __syncwarp();
     int fail2 = 0;
-    (void)derive_pass_globals<M>(st, A, init ? 1.0 : st->nu, Lc, lane, &fail2);
+    (void)derive_pass_globals_rt(M, st, A, init ? 1.0 : st->nu, Lc, lane, &fail2);
     fail |= fail2;
     for (int i = lane; i < M; i += 32) {
         const double kv = init ? st->K0[i] : st->kappa[i];
@@ -710,6 +735,12 @@ __device__ void setup_state(DevState *st, int init, int lane, double *A, double 
         st->ticket = 0u;
         if (fail) st->status = ST_ENONFINITE;
     }
+}
+
+template <int M>
+__device__ __forceinline__ void setup_state(DevState *st, int init, int lane, double *A, double *Lc)
+{
+    setup_state_rt(M, st, init, lane, A, Lc);
 }
 
 template <int M>

@@ -18,6 +18,7 @@ from . import _build
 SMAX = 32
 MMAX = 31
 FP32 = 0
+BF16 = 1
 INIT_PAPER = 0
 INIT_GIVEN = 1
 
@@ -28,7 +29,12 @@ STATUS = {0: "VBH_OK", -1: "VBH_EINVAL", -2: "VBH_ENOMEM", -3: "VBH_ECUDA", -4: 
 class VBHError(RuntimeError):
     def __init__(self, status: int, what: str):
         self.status = status
-        super().__init__(f"{what}: {STATUS.get(status, status)} ({_lib().vbh_strerror(status).decode()})")
+        msg = f"{what}: {STATUS.get(status, status)} ({_lib().vbh_strerror(status).decode()})"
+        if status in (-2, -3):
+            detail = _lib().vbh_last_error_detail().decode()
+            if detail:
+                msg += f" [{detail}]"
+        super().__init__(msg)
 
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -50,7 +56,8 @@ class Result(ctypes.Structure):
 
 class Opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("precision", ctypes.c_int),
-                ("init", ctypes.c_int), ("init_state", ctypes.POINTER(Result)), ("elbo_trace", _dp)]
+                ("init", ctypes.c_int), ("refine_iters", ctypes.c_int), ("init_state", ctypes.POINTER(Result)),
+                ("elbo_trace", _dp)]
 
 
 _LIB = None
@@ -72,6 +79,7 @@ def _lib():
             "vbh_destroy": (None, [vp]),
             "vbh_strerror": (ctypes.c_char_p, [ci]),
             "vbh_state_bytes": (ctypes.c_size_t, []),
+            "vbh_last_error_detail": (ctypes.c_char_p, []),
             "vbh_fit": (ci, [vp, vp, vp, i64, ci, P, O, R]),
             "vbh_fit_begin": (ci, [vp, vp, vp, i64, ci, P, O]),
             "vbh_fit_step": (ci, [vp, ci, ctypes.POINTER(ci)]),
@@ -190,11 +198,13 @@ class Handle:
         self.close()
 
     @staticmethod
-    def _opts(tol, max_iter, init_state, S, trace):
+    def _opts(tol, max_iter, init_state, S, trace, precision=FP32, refine_iters=10):
         o = Opts()
         _lib().vbh_opts_default(ctypes.byref(o))
         o.tol = float(tol)
         o.max_iter = int(max_iter)
+        o.precision = int(precision)
+        o.refine_iters = int(refine_iters)
         keep = []
         if init_state is not None:
             st = dict_to_result(init_state, S) if isinstance(init_state, dict) else init_state
@@ -208,10 +218,11 @@ class Handle:
         return o, keep, buf
 
     def fit(self, r, d, S: int, prior: dict | None = None, tol: float = 1e-8, max_iter: int = 200,
-            init_state=None, trace: bool = False, V: int | None = None) -> dict:
+            init_state=None, trace: bool = False, V: int | None = None, precision: int = FP32,
+            refine_iters: int = 10) -> dict:
         V = int(V if V is not None else (r.shape[0] if r is not None else 0))
         pa = _PriorArgs(prior, S)
-        o, keep, buf = self._opts(tol, max_iter, init_state, S, trace)
+        o, keep, buf = self._opts(tol, max_iter, init_state, S, trace, precision, refine_iters)
         res = Result()
         rc = _lib().vbh_fit(self._h, _ptr(r), _ptr(d), V, int(S), ctypes.byref(pa.c), ctypes.byref(o),
                             ctypes.byref(res))
@@ -223,10 +234,11 @@ class Handle:
         return out
 
     def fit_begin(self, r, d, S: int, prior: dict | None = None, tol: float = 1e-8, max_iter: int = 200,
-                  init_state=None, trace: bool = False, V: int | None = None):
+                  init_state=None, trace: bool = False, V: int | None = None, precision: int = FP32,
+                  refine_iters: int = 10):
         V = int(V if V is not None else (r.shape[0] if r is not None else 0))
         pa = _PriorArgs(prior, S)
-        o, keep, buf = self._opts(tol, max_iter, init_state, S, trace)
+        o, keep, buf = self._opts(tol, max_iter, init_state, S, trace, precision, refine_iters)
         rc = _lib().vbh_fit_begin(self._h, _ptr(r), _ptr(d), V, int(S), ctypes.byref(pa.c), ctypes.byref(o))
         if rc != 0:
             raise VBHError(rc, "vbh_fit_begin")
