@@ -384,6 +384,100 @@ def run_batched(args):
     return 0
 
 
+PREC = {"name": "precision form: N=1,048,576 cells x G=512 genes, S=32", "cells": 1 << 20, "genes": 512, "S": 32,
+        "p_const": 0.05, "alpha": 0.5, "seed": 3, "refine": 10}
+
+
+def run_precision(args):
+    """The precision form on one data set of V = N G = 536,870,912 observations
+    and S = 32: the tensor-core sweep with 16-bit operands (VBH_BF16) for all
+    but the last `refine` sweeps, which run with FP32 operands; the same number
+    of sweeps of the FP32 form alone for the speedup and the error of the
+    BF16 schedule against it."""
+    import torch
+    from paper_2401_10068_gb300 import _build
+    _build.build_all()
+    from paper_2401_10068_gb300 import synth, vbh
+    dev = torch.device("cuda", 0)
+    S, V = PREC["S"], PREC["cells"] * PREC["genes"]
+    refine = PREC["refine"]
+    if args.steps <= refine:
+        raise SystemExit(f"--steps must exceed the {refine} refinement sweeps")
+    stream = torch.cuda.Stream(dev)
+    with torch.cuda.stream(stream):
+        r, d, _ = synth.generate_device(V, S, seed=PREC["seed"], alpha=PREC["alpha"], p_const=PREC["p_const"],
+                                        device=dev)
+    stream.synchronize()
+    h = vbh.Handle(0, stream)
+    total = args.warmup + args.steps
+    clocks = Clocks(0)
+    time.sleep(0.3)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+
+    h.fit_begin(r, d, S, None, tol=0.0, max_iter=total, precision=vbh.BF16, refine_iters=refine)
+    h.fit_step(args.warmup)
+    torch.cuda.synchronize(dev)
+    ev[0].record(stream)
+    h.fit_step(args.steps - refine)
+    ev[1].record(stream)
+    h.fit_step(refine)
+    ev[2].record(stream)
+    torch.cuda.synchronize(dev)
+    res_bf16 = h.fit_result()
+    assert res_bf16["iters"] == total, res_bf16["iters"]
+    ms_bf16 = ev[0].elapsed_time(ev[1]) / (args.steps - refine)
+    ms_ref = ev[1].elapsed_time(ev[2]) / refine
+    ms_sched = ev[0].elapsed_time(ev[2]) / args.steps
+
+    h.fit_begin(r, d, S, None, tol=0.0, max_iter=total, precision=vbh.FP32)
+    h.fit_step(args.warmup)
+    torch.cuda.synchronize(dev)
+    ev[0].record(stream)
+    h.fit_step(args.steps)
+    ev[3].record(stream)
+    torch.cuda.synchronize(dev)
+    res_fp32 = h.fit_result()
+    ms_fp32 = ev[0].elapsed_time(ev[3]) / args.steps
+    clk = clocks.stop()
+    h.close()
+
+    def relerr(a, b):
+        a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
+        return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+    err = {k: relerr(res_bf16[k], res_fp32[k]) for k in ("kappa", "Winv", "b_rho")}
+    err["elbo"] = abs(res_bf16["elbo"] - res_fp32["elbo"]) / abs(res_fp32["elbo"])
+    peak, peak_kind = _peaks()
+    bytes_obs = 68.0                     # BF16 profile row (32 x 2 B) + r (4 B)
+    # MMA work per tile of 128 observations: U = d (128 x 32) . B1 (32 x N1) and
+    # G' = A2 (128 x 128) . d (128 x 32)
+    flops_tile = lambda n1: 2 * 128 * n1 * 32 + 2 * 128 * 32 * 128
+    tiles = (V + 127) // 128
+    upd = float(V) * S
+    line = {"metric": "cell.gene.K CAVI updates/s (precision form, S = 32)", "unit": UNIT,
+            "value": upd / (ms_sched * 1e-3), "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_sched, "higher_is_better": True, "dtype": "bf16 operands, f32 accumulation",
+            "data": "synthetic",
+            "config": {"workload": PREC["name"], "V": V, "S": S, "p_const": PREC["p_const"], "seed": PREC["seed"],
+                       "schedule": f"{args.steps - refine} BF16-form sweeps + {refine} FP32-form sweeps",
+                       "l2": "inputs larger than L2 (129 MB), no flush"},
+            "bf16_form": {"ms_per_sweep": ms_bf16, "updates_per_s": upd / (ms_bf16 * 1e-3),
+                          "hbm_gbs": V * bytes_obs / (ms_bf16 * 1e-3) / 1e9,
+                          "tensor_tflops": tiles * flops_tile(80) / (ms_bf16 * 1e-3) / 1e12},
+            "fp32_form": {"ms_per_sweep": ms_fp32, "updates_per_s": upd / (ms_fp32 * 1e-3),
+                          "hbm_gbs": V * bytes_obs / (ms_fp32 * 1e-3) / 1e9,
+                          "tensor_tflops": tiles * flops_tile(112) / (ms_fp32 * 1e-3) / 1e12,
+                          "ms_per_sweep_in_schedule": ms_ref},
+            "speedup_schedule_vs_fp32_form": ms_fp32 / ms_sched,
+            "rel_error_bf16_schedule_vs_fp32_form": err,
+            "roofline": {"bound": "hbm", "achieved": V * bytes_obs / (ms_bf16 * 1e-3) / 1e9, "peak": peak,
+                         "unit": "GB/s", "frac": V * bytes_obs / (ms_bf16 * 1e-3) / 1e9 / peak,
+                         "kernel": "tc_sweep_kernel<2>", "peak_kind": peak_kind, "bytes_per_obs": bytes_obs},
+            "clocks": clk}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -394,13 +488,19 @@ def main():
                     help="N cells (x 96 genes); smaller values give the small case used for ncu captures")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
-    ap.add_argument("--workload", default="at-scale", choices=["at-scale", "batched"],
-                    help="batched: the 4,096-data-set form (a separate measurement, not the default step)")
+    ap.add_argument("--workload", default="at-scale", choices=["at-scale", "batched", "precision"],
+                    help="batched: the 4,096-data-set form; precision: the S = 32 tensor-core form "
+                         "(separate measurements, not the default step)")
     ap.add_argument("--datasets", type=int, default=BATCH["datasets"])
     ap.add_argument("--plain-sample", type=int, default=32)
     args = ap.parse_args()
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "precision":
+        if args.cells != WORKLOAD["cells"]:
+            PREC["cells"] = args.cells
+            PREC["name"] = "precision recipe, reduced N (profiling case)"
+        return run_precision(args)
     global V_FULL
     if args.cells != WORKLOAD["cells"]:
         WORKLOAD["cells"] = args.cells

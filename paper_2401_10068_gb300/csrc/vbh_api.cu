@@ -1,7 +1,6 @@
 // vbh_api.cu -- the C ABI declared in include/vbh.h: handle, argument
 // checks, input staging, the CUDA-graph sweep loop and result read-back.
 // All arithmetic of the method runs in the kernels of vbh_sweep.cuh.
-#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -31,8 +30,7 @@ struct Launch {
     int binary = 1;
     KernelInfo ki{};
     vbh::TcKernelInfo tki{};
-    CUtensorMap tmap_d;
-    const float *r_pad = nullptr;
+    const unsigned char *tiles = nullptr;   // repacked inputs of the tensor-core sweep
     const void *func() const { return tc ? tki.sweep : ki.sweep; }
     const void *setup() const { return tc ? tki.setup : ki.setup; }
     int threads() const { return tc ? tki.threads : ki.threads; }
@@ -64,11 +62,11 @@ struct vbh_handle {
     bool bf16_phase = false;       // VBH_BF16 fit still in its 16-bit sweeps
     int bf16_limit = 0;            // last sweep index of the 16-bit sweeps
     int refine = 0;                // FP32 sweeps after them
-    // BF16 profiles of the tensor-core path
-    void *d16 = nullptr;
-    size_t d16_cap = 0;
+    // repacked inputs of the tensor-core path
+    void *tc_tiles = nullptr;
+    size_t tc_cap = 0;
     unsigned long long *counts = nullptr;       // [inexact, non-binary] profile values (device)
-    const void *g_d16 = nullptr;
+    const void *g_tiles = nullptr;
     // cached graph of the sweep loop
     cudaGraphExec_t gexec = nullptr;
     int g_S = -1, g_grid = -1;
@@ -304,21 +302,20 @@ int prepare_launch(vbh_handle *h, int S, long long V, int precision, const float
     int rc = ensure(reinterpret_cast<void **>(&h->partials), &h->partials_cap, size_t(g) * nstat * sizeof(double));
     if (rc) return rc;
     if (L->tc && V > 0) {
-        if ((rc = ensure(&h->d16, &h->d16_cap, vbh::tc_input_bytes(V)))) return rc;
+        if ((rc = ensure(&h->tc_tiles, &h->tc_cap, vbh::tc_input_bytes(V)))) return rc;
         if (!h->counts) {
             size_t cap = 0;
             if ((rc = ensure(reinterpret_cast<void **>(&h->counts), &cap, 2 * sizeof(unsigned long long)))) return rc;
         }
         VBH_CK(cudaMemsetAsync(h->counts, 0, 2 * sizeof(unsigned long long), h->stream));
-        if ((rc = vbh::tc_convert_inputs(dd, rd, V, S, h->d16, h->counts, h->stream, h->nsm))) return rc;
+        if ((rc = vbh::tc_convert_inputs(dd, rd, V, S, h->tc_tiles, h->counts, h->stream, h->nsm))) return rc;
         unsigned long long cnt[2] = {0, 0};
         VBH_CK(cudaMemcpyAsync(cnt, h->counts, sizeof(cnt), cudaMemcpyDeviceToHost, h->stream));
         VBH_CK(cudaStreamSynchronize(h->stream));
         // the FP32 form needs profiles that BF16 holds exactly (binary ones do)
         if (cnt[0] != 0 && precision != VBH_BF16) return VBH_EUNSUPPORTED;
         L->binary = cnt[1] == 0 ? 1 : 0;
-        L->r_pad = vbh::tc_r_pad(h->d16, V);
-        if ((rc = vbh::tc_encode_tensor_map(h->d16, V, &L->tmap_d))) return rc;
+        L->tiles = static_cast<const unsigned char *>(h->tc_tiles);
     }
     return VBH_OK;
 }
@@ -344,9 +341,8 @@ int launch_sweep(vbh_handle *h, DevState *st, int mode, Launch &L, const float *
     a.use_cond = 0;
     a.mode = mode;
     if (L.tc) {
-        a.r = L.r_pad;
-        vbh::TcArgs ta{a, L.S, L.binary};
-        void *args[] = {&L.tmap_d, &ta};
+        vbh::TcArgs ta{a, L.tiles, L.S, L.binary};
+        void *args[] = {&ta};
         VBH_CK(cudaLaunchKernel(L.tki.sweep, dim3(L.grid), dim3(L.tki.threads), args, L.tki.smem, h->stream));
     } else {
         void *args[] = {&a};
@@ -366,7 +362,7 @@ int build_graph(vbh_handle *h)
 {
     Launch &L = h->L;
     if (h->gexec && h->g_S == h->S && h->g_grid == L.grid && h->g_V == h->V && h->g_r == h->r && h->g_d == h->d &&
-        h->g_partials == h->partials && h->g_func == L.func() && h->g_d16 == (L.tc ? h->d16 : nullptr))
+        h->g_partials == h->partials && h->g_func == L.func() && h->g_tiles == (L.tc ? h->tc_tiles : nullptr))
         return VBH_OK;
     if (h->gexec) {
         cudaGraphExecDestroy(h->gexec);
@@ -382,7 +378,7 @@ int build_graph(vbh_handle *h)
     vbh::SweepArgs a{};
     vbh::TcArgs ta{};
     void *args[] = {&a};
-    void *targs[] = {&L.tmap_d, &ta};
+    void *targs[] = {&ta};
     if (cudaGraphConditionalHandleCreate(&cond, g, 1u, cudaGraphCondAssignDefault) != cudaSuccess) {
         vbh::record_error("cudaGraphConditionalHandleCreate", __FILE__, __LINE__, cudaGetErrorName(cudaGetLastError()));
         rc = VBH_ECUDA;
@@ -406,7 +402,7 @@ int build_graph(vbh_handle *h)
     a.use_cond = 1;
     a.mode = vbh::MODE_ITER;
     ta.sa = a;
-    ta.sa.r = L.r_pad;
+    ta.tiles = L.tiles;
     ta.S = L.S;
     ta.binary = L.binary;
     kp.type = cudaGraphNodeTypeKernel;
@@ -433,7 +429,7 @@ int build_graph(vbh_handle *h)
     h->g_d = h->d;
     h->g_partials = h->partials;
     h->g_func = L.func();
-    h->g_d16 = L.tc ? h->d16 : nullptr;
+    h->g_tiles = L.tc ? h->tc_tiles : nullptr;
 out:
     if (rc) (void)cudaGetLastError();
     cudaGraphDestroy(g);
@@ -573,7 +569,7 @@ void vbh_destroy(vbh_handle *h)
     cudaFree(h->trace);
     cudaFree(h->stage_r);
     cudaFree(h->stage_d);
-    cudaFree(h->d16);
+    cudaFree(h->tc_tiles);
     cudaFree(h->counts);
     if (h->mirror) cudaFreeHost(h->mirror);
     cudaFree(h->batched.arena);

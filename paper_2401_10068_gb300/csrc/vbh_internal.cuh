@@ -159,7 +159,7 @@ __device__ __forceinline__ void bulk_load(void *dst_smem, const void *src_gmem, 
 }
 
 // ---------------------------------------------------------------------------
-// Tensor-memory (tcgen05) and tensor-map bulk-copy helpers.
+// Tensor-memory (tcgen05) helpers.
 // ---------------------------------------------------------------------------
 // Shared-memory matrix descriptor of tcgen05.mma: start address, leading and
 // stride byte offsets (16-byte units), descriptor version 1, layout (0 none,
@@ -250,17 +250,26 @@ __device__ __forceinline__ void tmem_ld4(uint32_t taddr, float (&v)[4])
     for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-
-// Tensor-map bulk copy global -> shared (2-D tile mode), completing on an mbarrier.
-__device__ __forceinline__ void tma_load_2d(void *dst, const void *tmap, int x, int y, uint64_t *bar)
+// 32 consecutive FP32 columns at taddr and one column at taddr1, one wait for both.
+__device__ __forceinline__ void tmem_ld32_1(uint32_t taddr, float (&v)[32], uint32_t taddr1, float &x)
 {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
-            "r"(smem_addr(dst)),
-        "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(smem_addr(bar))
-        : "memory");
+    uint32_t r[32], r1;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%33];\n\t"
+                 "tcgen05.ld.sync.aligned.32x32b.x1.b32 {%32}, [%34];\n\t"
+                 "tcgen05.wait::ld.sync.aligned;"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                   "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                   "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                   "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r1)
+                 : "r"(taddr), "r"(taddr1));
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+    x = __uint_as_float(r1);
 }
+
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 {

@@ -1,10 +1,7 @@
 // vbh_tc.cu -- instantiations and host helpers of the tensor-core sweep
-// (12 <= S <= 32): the runtime-S set-up kernel, the BF16 conversion of the
-// profiles (with a padded copy of r) and the tensor map of the profiles.
-#include <cuda.h>
+// (12 <= S <= 32): the runtime-S set-up kernel and the repacking of the
+// inputs into BF16 tiles.
 #include <cuda_runtime.h>
-
-#include <cstdio>
 
 #include "vbh.h"
 #include "vbh_error.h"
@@ -46,62 +43,11 @@ int tc_convert_inputs(const float *d, const float *r, long long V, int S, void *
                       cudaStream_t stream, int nsm)
 {
     if (V == 0) return VBH_OK;
-    const long long Vp = tc_padded(V);
-    long long blocks = (Vp * 32 + 255) / 256;
+    const long long work = (V + 127) / 128 * 128 * 4;
+    long long blocks = (work + 255) / 256;
     if (blocks > 16LL * nsm) blocks = 16LL * nsm;
-    tc_inputs_kernel<<<int(blocks), 256, 0, stream>>>(d, r, V, Vp, S, static_cast<__nv_bfloat16 *>(buf),
-                                                      const_cast<float *>(tc_r_pad(buf, V)), counts_dev);
+    tc_inputs_kernel<<<int(blocks), 256, 0, stream>>>(d, r, V, S, static_cast<unsigned char *>(buf), counts_dev);
     VBH_CHECK_CUDA(cudaGetLastError());
-    return VBH_OK;
-}
-
-namespace {
-typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
-                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn encode_fn()
-{
-    static EncodeTiledFn fn = nullptr;
-    if (!fn) {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        const cudaError_t e =
-            cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q);
-        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess) {
-            char buf[96];
-            std::snprintf(buf, sizeof(buf), "%s, query result %d", cudaGetErrorName(e), int(q));
-            record_error("cudaGetDriverEntryPointByVersion(cuTensorMapEncodeTiled)", __FILE__, __LINE__, buf);
-            (void)cudaGetLastError();
-            return nullptr;
-        }
-        fn = reinterpret_cast<EncodeTiledFn>(p);
-    }
-    return fn;
-}
-} // namespace
-
-// Profiles: BF16 [Vp rows x 32 components], box 32 x 128 rows, 64-byte
-// swizzle (the layout the kernel's MMAs read).
-int tc_encode_tensor_map(const void *buf, long long V, void *tmap_d)
-{
-    EncodeTiledFn fn = encode_fn();
-    if (!fn) return VBH_ECUDA;
-    if (V <= 0 || V >= (1LL << 31)) return VBH_EINVAL;
-    const cuuint64_t dimd[2] = {32, cuuint64_t(tc_padded(V))};
-    const cuuint64_t strd[1] = {64};
-    const cuuint32_t boxd[2] = {32, 128};
-    const cuuint32_t es[2] = {1, 1};
-    const CUresult cr = fn(static_cast<CUtensorMap *>(tmap_d), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
-                           const_cast<void *>(buf), dimd, strd, boxd, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                           CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (cr != CUDA_SUCCESS) {
-        char msg[32];
-        std::snprintf(msg, sizeof(msg), "CUresult %d", int(cr));
-        record_error("cuTensorMapEncodeTiled(profiles)", __FILE__, __LINE__, msg);
-        return VBH_ECUDA;
-    }
     return VBH_OK;
 }
 

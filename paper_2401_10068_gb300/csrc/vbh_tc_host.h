@@ -9,11 +9,16 @@
 
 namespace vbh {
 
-// Kernel arguments of the tensor-core sweep (the tensor maps are passed beside them).
+// Bytes of one input tile of the tensor-core sweep: 128 observations, BF16
+// profiles (128 x 64 bytes, in the kernel's shared-memory order) then r (128 x 4).
+constexpr unsigned TC_TILE_BYTES = 128 * 64 + 128 * 4;
+
+// Kernel arguments of the tensor-core sweep.
 struct TcArgs {
-    SweepArgs sa;          // r = the padded r copy; V, st, partials, cond, use_cond, mode (d unused: tensor map)
+    SweepArgs sa;                  // V, st, partials, cond, use_cond, mode (r and d unused)
+    const unsigned char *tiles;    // the repacked inputs (tc_convert_inputs)
     int S;
-    int binary;            // 1: every profile value is 0 or 1
+    int binary;                    // 1: every profile value is 0 or 1
 };
 
 struct TcKernelInfo {
@@ -28,27 +33,14 @@ struct TcKernelInfo {
 // or 3 (FP32-exact globals).
 bool tc_kernel_info(int nsplit, TcKernelInfo *out);
 
-// Observations padded to whole tiles of 128.
-inline long long tc_padded(long long V) { return (V + 127) / 128 * 128; }
-
-// Device bytes of the converted inputs of V observations: BF16 profiles
-// (tc_padded(V) x 64 bytes) followed by the padded r (tc_padded(V) floats).
-inline size_t tc_input_bytes(long long V) { return size_t(tc_padded(V)) * 68; }
+// Device bytes of the repacked inputs of V observations.
+inline size_t tc_input_bytes(long long V) { return size_t((V + 127) / 128) * TC_TILE_BYTES; }
 
 // d (V x S FP32) and r (V FP32), device -> buf (tc_input_bytes(V) bytes,
-// device).  counts_dev[0] (device) gains the number of profile values BF16
-// does not represent exactly, counts_dev[1] the number other than 0 and 1.
+// device), in tiles of 128 observations.  counts_dev[0] (device) gains the
+// number of profile values BF16 does not represent exactly, counts_dev[1] the
+// number other than 0 and 1.
 int tc_convert_inputs(const float *d, const float *r, long long V, int S, void *buf, unsigned long long *counts_dev,
                       cudaStream_t stream, int nsm);
-
-// The padded r inside buf.
-inline const float *tc_r_pad(const void *buf, long long V)
-{
-    return reinterpret_cast<const float *>(static_cast<const unsigned char *>(buf) + size_t(tc_padded(V)) * 64);
-}
-
-// Tensor map (CUtensorMap, 128 bytes) of the BF16 profiles in buf.
-int tc_encode_tensor_map(const void *buf, long long V, void *tmap_d);
-
 
 } // namespace vbh
