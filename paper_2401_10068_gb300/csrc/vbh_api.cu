@@ -312,7 +312,7 @@ int prepare_launch(vbh_handle *h, int S, long long V, int precision, const float
         unsigned long long cnt[2] = {0, 0};
         VBH_CK(cudaMemcpyAsync(cnt, h->counts, sizeof(cnt), cudaMemcpyDeviceToHost, h->stream));
         VBH_CK(cudaStreamSynchronize(h->stream));
-        // the FP32 form needs profiles that BF16 holds exactly (binary ones do)
+        // the FP32 form needs differences d_j - d_S that BF16 holds exactly (binary profiles give -1, 0, 1)
         if (cnt[0] != 0 && precision != VBH_BF16) return VBH_EUNSUPPORTED;
         L->binary = cnt[1] == 0 ? 1 : 0;
         L->tiles = static_cast<const unsigned char *>(h->tc_tiles);

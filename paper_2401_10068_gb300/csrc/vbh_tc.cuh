@@ -2,36 +2,38 @@
 // cores (one persistent CTA per SM).
 //
 // Same sweep as vbh_sweep.cuh (steps (a)-(e), Eq. 16-31); the two contractions
-// that grow with M^2 run as BF16 MMAs with FP32 accumulation in tensor memory:
-//   MMA1  U = d_tile (128 x 32) . B1 (32 x 48): per observation the vector
-//         v = L~^T D_i (columns 0..31, so q_i = |v|^2) and t_i = kappa~^T D_i
-//         (column 32).  The profile column d_S is folded into B1 (row S-1
-//         holds minus the column sums), so the MMA reads the raw profiles.  L~
-//         and kappa~ (the FP32 globals of the pass) are split into NSPLIT BF16
-//         parts, one B1 operand each, and the NSPLIT MMAs accumulate into the
-//         same columns.  With binary profiles every product is exact: NSPLIT = 3
-//         carries the FP32 values (24 bits), NSPLIT = 2 keeps 16 bits (the BF16
-//         form).
-//   MMA2  G' = A2 (128 x 128 obs) . d_tile (128 obs x 32): the rows of A2 are
-//         the NSPLIT BF16 parts of gamma_i d_i (gamma_i = w_i^2 - c_i) and of
-//         w_i, so G' holds sum gamma d d^T and sum w d in the raw-profile basis;
-//         G and g of the sweep follow in FP64 by removing the d_S column
-//         (G_jk = G'_jk - G'_jS - G'_Sk + G'_SS, g_j = g'_j - g'_S).  G'
-//         accumulates in FP32 in tensor memory over an epoch of 16 tiles and is
-//         then added into compensated FP32 sums (sum and lost low part).
+// that grow with M^2 run as BF16 MMAs with FP32 accumulation in tensor memory.
+// The inputs are repacked once per fit into tiles of 128 observations in the
+// basis of Eq. 3: per observation the M differences D_ij = d_ij - d_iS as BF16
+// in slots 0..M-1 of a 32-slot row, the constant 1 in slot 31 (free for
+// S <= 32 because D has M <= 31 entries), and y_i = r_i - d_iS in FP32.
+//   MMA1  U = D~_tile (128 x 32) . B1 (32 x N1): per observation the NSPLIT
+//         BF16 parts of v = L~^T D_i (q_i = |v|^2) and of t_i = kappa~^T D_i,
+//         side by side in N; L~ and kappa~ (the FP32 globals of the pass) are
+//         split into NSPLIT BF16 parts.  With D in {-1, 0, 1} every product is
+//         exact: NSPLIT = 3 carries the FP32 values (24 bits), NSPLIT = 2 keeps
+//         16 bits (the BF16 form).
+//   MMA2  G'' = A2^T . D~_tile: row (p, j) of A2 holds part p of
+//         gamma_i D_ij (gamma_i = w_i^2 - c_i) for j < 31 and part p of w_i in
+//         slot 31; against the D~ columns this gives sum gamma D D^T and, in
+//         row (p, 31), sum w D (slot 31 of D~ is 1).  In the BF16 form two sets
+//         of 64 observations share one MMA: A2 rows 0-63 hold the parts for
+//         observations 0-63, rows 64-127 for 64-127, and B is the 64-column
+//         pair of their D~ rows, so each MMA covers 32 observations (the cross
+//         blocks of the output are not read).  G'' accumulates in FP32 in tensor
+//         memory over an epoch of 16 tiles and is then added into compensated
+//         FP32 sums (sum and lost low part).
 // The scalar per-observation work (c_i, w_i, S_i, ln(1 + E[rho] q_i)) stays
-// on the CUDA cores.  The inputs are repacked once per fit into tiles of 128
-// observations, each 8,704 contiguous bytes: the BF16 profiles as the
-// 64-byte-swizzled shared-memory image the MMAs read (64-byte rows), then the
-// 128 r values.  One bulk copy per tile lands it in a pipeline stage (a
-// tensor-map load of the same box moved only ~11 GB/s per SM); the profile tile
-// is MMA1's K-major A operand and MMA2's MN-major B operand.
+// on the CUDA cores.  A tile is 8,704 contiguous bytes (the BF16 rows in the
+// 64-byte-swizzled order of the kernel's shared memory, then y), landed by one
+// bulk copy per pipeline stage; it is MMA1's K-major A operand and MMA2's
+// MN-major B operand.
 //
 // Roles (14 warps): warps 0-7 are two groups of four consumer warps that take
 // alternate tiles, each warp owning one quarter of the tensor-memory lanes (32
-// observations); warps 8-11 flush the G' epochs (one lane quarter each); warp
+// observations); warps 8-11 flush the G'' epochs (one lane quarter each); warp
 // 12 lane 0 issues the loads and warp 13 lane 0 the MMAs.  MMA1 runs two tiles
-// ahead of MMA2 (four U buffers in tensor memory, four A2 buffers in shared
+// ahead of MMA2 (three U buffers in tensor memory, four A2 buffers in shared
 // memory), so a consumer group never waits for the MMA of its own previous
 // tile.  Every wait is bounded: on a timeout the kernel records VBH_ETIMEOUT,
 // lets its copies and MMAs drain, frees its tensor memory and returns.
@@ -47,32 +49,34 @@ namespace vbh {
 template <int NSPLIT>
 struct TcCfg {
     static constexpr int TILE = 128;                                   // observations per tile
-    static constexpr int N1 = 48;                                      // MMA1 N: v (32 columns), t (column 32)
-    static constexpr int STAGES = 10;                                  // input tiles in flight
-    static constexpr int NBUF = 4;                                     // U and A2 buffers (tile k uses k & 3)
-    static constexpr uint32_t D_BYTES = TILE * 64;                     // swizzled BF16 profiles
-    static constexpr uint32_t STAGE_BYTES = TC_TILE_BYTES;             // + 128 r values
-    static constexpr uint32_t B1_PART = N1 * 64;                       // one split of the MMA1 B operand
-    static constexpr uint32_t A2_ATOM = TILE * 128;                    // one 64-row atom column
+    static constexpr int SETS = (NSPLIT == 2) ? 2 : 1;                 // observation sets per MMA2
+    static constexpr int N1 = ((33 * NSPLIT + 15) / 16) * 16;          // MMA1 N: parts of v, then of t (80, 112)
+    static constexpr int N2 = 32 * SETS;                               // MMA2 N
+    static constexpr int NK2 = 8 / SETS;                               // MMA2 instructions per tile (K = 16)
+    static constexpr int STAGES = (NSPLIT == 2) ? 14 : 10;             // input tiles in flight
+    static constexpr int NUBUF = 3;                                    // U buffers (tile k uses k % 3)
+    static constexpr int NBUF = 4;                                     // A2 buffers (tile k uses k & 3)
+    static constexpr uint32_t D_BYTES = TILE * 64;                     // swizzled BF16 rows
+    static constexpr uint32_t STAGE_BYTES = TC_TILE_BYTES;             // + 128 y values
+    static constexpr uint32_t B1_BYTES = N1 * 64;
+    static constexpr uint32_t A2_ATOM = (TILE / SETS) * 128;           // 64 rows of A2 x the K of one set
     static constexpr uint32_t A2_BYTES = 2 * A2_ATOM;
-    static constexpr int EPOCH = 16;                                   // tiles per G' epoch
+    static constexpr int EPOCH = 16;                                   // tiles per G'' epoch
     static constexpr int NCW = 8;                                      // consumer warps
     static constexpr int FLUSH_WARP0 = NCW;                            // warps 8..11
     static constexpr int PRODUCER_WARP = NCW + 4;
     static constexpr int MMA_WARP = NCW + 5;
     static constexpr int THREADS = 32 * (NCW + 6);
     static constexpr int TMEM_COLS = 512;
-    static constexpr uint32_t COL_U = 0, COL_U_STRIDE = 64;           // U[u] at column 64 u
-    static constexpr uint32_t COL_G = 256, COL_G_STRIDE = 32;          // G'[e & 1] at column 256 + 32 (e & 1)
-    // rows of G': part p of gamma d in rows 32 p .. 32 p + 31, part p of w in row 32 NSPLIT + p
-    static constexpr int GROWS = 33 * NSPLIT;
+    static constexpr uint32_t COL_U = 0, COL_U_STRIDE = 128;          // U[u] at column 128 u
+    static constexpr uint32_t COL_G = 384, COL_G_STRIDE = N2;          // G''[e & 1] at column 384 + N2 (e & 1)
     static constexpr uint32_t OFF_D = 0;                                // stage s at s * STAGE_BYTES (512-byte aligned)
     static constexpr uint32_t OFF_A2 = ((OFF_D + STAGES * STAGE_BYTES + 1023) / 1024) * 1024;
     static constexpr uint32_t OFF_B1 = OFF_A2 + NBUF * A2_BYTES;
-    static constexpr uint32_t OFF_BAR = OFF_B1 + ((NSPLIT * B1_PART + 1023) / 1024) * 1024;
+    static constexpr uint32_t OFF_BAR = OFF_B1 + ((B1_BYTES + 1023) / 1024) * 1024;
     // mbarrier slots (8 bytes each) from OFF_BAR
     static constexpr int BAR_FULL = 0, BAR_EMPTY = BAR_FULL + STAGES, BAR_UFULL = BAR_EMPTY + STAGES;
-    static constexpr int BAR_UEMPTY = BAR_UFULL + NBUF, BAR_A2FULL = BAR_UEMPTY + NBUF;
+    static constexpr int BAR_UEMPTY = BAR_UFULL + NUBUF, BAR_A2FULL = BAR_UEMPTY + NUBUF;
     static constexpr int BAR_A2EMPTY = BAR_A2FULL + NBUF, BAR_GFULL = BAR_A2EMPTY + NBUF;
     static constexpr int BAR_GEMPTY = BAR_GFULL + 2, BAR_DRAIN = BAR_GEMPTY + 2, NBARS = BAR_DRAIN + 1;
     static constexpr uint32_t OFF_MISC = OFF_BAR + 64 * 8;
@@ -81,8 +85,10 @@ struct TcCfg {
     // end-of-kernel scratch, once the pipeline is idle
     static constexpr uint32_t OFF_GACC = OFF_D;                        // [sum, comp][32 columns][128 rows] FP32
     static constexpr uint32_t OFF_RED = OFF_A2;                        // 3 doubles per thread
-    static_assert(GROWS <= 128, "rows of the MMA2 accumulator");
-    static_assert(2 * 32 * 128 * 4 <= STAGES * STAGE_BYTES, "G' totals scratch");
+    static_assert(SETS * 32 * NSPLIT <= 128 && (SETS == 1 || 32 * NSPLIT <= 64), "rows of the MMA2 accumulator");
+    static_assert(COL_U + NUBUF * COL_U_STRIDE <= COL_G && COL_G + 2 * COL_G_STRIDE <= TMEM_COLS, "tensor memory");
+    static_assert(N1 <= COL_U_STRIDE && N1 * 64 <= 8192, "MMA1 shape");
+    static_assert(2 * 32 * 128 * 4 <= STAGES * STAGE_BYTES, "G'' totals scratch");
     static_assert(STAGE_BYTES % 512 == 0 && D_BYTES + TILE * 4 == STAGE_BYTES, "stage layout");
     static_assert(3 * THREADS * 8 <= NBUF * A2_BYTES, "reduction scratch");
     static_assert(SMEM_BYTES <= 227 * 1024, "shared memory per block");
@@ -176,9 +182,11 @@ __global__ void __launch_bounds__(TcCfg<NSPLIT>::THREADS, 1)
                 mbar_init(&full[i], 1);
                 mbar_init(&empty[i], 1);
             }
-            for (int i = 0; i < C::NBUF; ++i) {
+            for (int i = 0; i < C::NUBUF; ++i) {
                 mbar_init(&ufull[i], 1);
                 mbar_init(&uempty[i], 4);
+            }
+            for (int i = 0; i < C::NBUF; ++i) {
                 mbar_init(&a2full[i], 4);
                 mbar_init(&a2empty[i], 1);
             }
@@ -192,30 +200,23 @@ __global__ void __launch_bounds__(TcCfg<NSPLIT>::THREADS, 1)
         }
         for (int i = tid; i < int(C::NBUF * C::A2_BYTES / 16); i += nth)
             reinterpret_cast<uint4 *>(a2)[i] = make_uint4(0, 0, 0, 0);
-        // B1 part p (48 rows x 32 components, K-major, 64-byte swizzle): row c < 32 holds split p
-        // of L'(k, c), row 32 split p of kappa'(k); L' and kappa' fold in -d_S.
+        // B1 (N1 rows x 32 slots, K-major, 64-byte swizzle): row 32 p + c holds part p of column c
+        // of L~ (L~(k, c) at slot k), row 32 NSPLIT + p part p of kappa~; slot 31 (the constant 1
+        // of the tile rows) meets zeros.
         const float erho_f = (a.mode == MODE_INIT) ? 0.0f : st->sw.erho;
-        for (int idx = tid; idx < NSPLIT * C::N1 * 32; idx += nth) {
-            const int p = idx / (C::N1 * 32), n = (idx >> 5) % C::N1, k = idx & 31;
+        for (int idx = tid; idx < C::N1 * 32; idx += nth) {
+            const int n = idx >> 5, k = idx & 31;
             double x = 0.0;
-            if (n < M) {
-                if (k < M) {
-                    x = (k >= n) ? static_cast<double>(st->sw.L[k * (k + 1) / 2 + n]) : 0.0;
-                } else if (k == M) {
-                    double cs = 0.0;
-                    for (int kk = n; kk < M; ++kk) cs += static_cast<double>(st->sw.L[kk * (kk + 1) / 2 + n]);
-                    x = -cs;
-                }
-            } else if (n == 32) {
-                if (k < M) {
-                    x = static_cast<double>(st->sw.kappa[k]);
-                } else if (k == M) {
-                    double cs = 0.0;
-                    for (int kk = 0; kk < M; ++kk) cs += static_cast<double>(st->sw.kappa[kk]);
-                    x = -cs;
-                }
+            int p = 0;
+            if (n < 32 * NSPLIT) {
+                p = n >> 5;
+                const int c = n & 31;
+                if (c < M && k < M && k >= c) x = static_cast<double>(st->sw.L[k * (k + 1) / 2 + c]);
+            } else if (n < 32 * NSPLIT + NSPLIT) {
+                p = n - 32 * NSPLIT;
+                if (k < M) x = static_cast<double>(st->sw.kappa[k]);
             }
-            *reinterpret_cast<__nv_bfloat16 *>(b1 + p * C::B1_PART + sw64(n, k >> 3) + (k & 7) * 2) = bf16_part(x, p);
+            *reinterpret_cast<__nv_bfloat16 *>(b1 + sw64(n, k >> 3) + (k & 7) * 2) = bf16_part(x, p);
         }
         if (warp == 0) tmem_alloc<C::TMEM_COLS>(const_cast<uint32_t *>(tslot));
         fence_proxy_async_smem();
@@ -252,26 +253,24 @@ __global__ void __launch_bounds__(TcCfg<NSPLIT>::THREADS, 1)
             // ---------------- MMA issuer: MMA1 of tile k, then MMA2 of tile k - 2 ----------------
             if (lane == 0) {
                 constexpr uint32_t IDESC1 = umma_idesc_bf16(128, C::N1, 0, 0);
-                constexpr uint32_t IDESC2 = umma_idesc_bf16(128, 32, 1, 1);
+                constexpr uint32_t IDESC2 = umma_idesc_bf16(128, C::N2, 1, 1);
                 const uint32_t b1a = smem_addr(b1), a2a = smem_addr(a2), da = smem_addr(dtile);
                 for (int k = 0; k < nk + 2; ++k) {
                     if (*s_abort) break;
                     if (k < nk) {
-                        const int s = k % C::STAGES, u = k & 3;
+                        const int s = k % C::STAGES, u = k % C::NUBUF;
                         if (!mbar_wait_bounded(&full[s], uint32_t((k / C::STAGES) & 1), BUDGET) ||
-                            (k >= 4 && !mbar_wait_bounded(&uempty[u], uint32_t(((k >> 2) - 1) & 1), BUDGET))) {
+                            (k >= C::NUBUF &&
+                             !mbar_wait_bounded(&uempty[u], uint32_t(((k / C::NUBUF) - 1) & 1), BUDGET))) {
                             *s_abort = 1;
                             break;
                         }
                         tc_fence_after();
                         const uint32_t d0 = da + s * C::STAGE_BYTES;
 #pragma unroll
-                        for (int p = 0; p < NSPLIT; ++p)
-#pragma unroll
-                            for (int kk = 0; kk < 2; ++kk)
-                                umma_bf16(tbase + C::COL_U + u * C::COL_U_STRIDE, umma_desc(d0 + kk * 32, 16, 512, 4),
-                                          umma_desc(b1a + p * C::B1_PART + kk * 32, 16, 512, 4), IDESC1,
-                                          (p | kk) ? 1u : 0u);
+                        for (int kk = 0; kk < 2; ++kk)
+                            umma_bf16(tbase + C::COL_U + u * C::COL_U_STRIDE, umma_desc(d0 + kk * 32, 16, 512, 4),
+                                      umma_desc(b1a + kk * 32, 16, 512, 4), IDESC1, kk ? 1u : 0u);
                         umma_commit(&ufull[u]);
                     }
                     if (k >= 2) {
@@ -285,11 +284,14 @@ __global__ void __launch_bounds__(TcCfg<NSPLIT>::THREADS, 1)
                         }
                         tc_fence_after();
                         const uint32_t a0 = a2a + b * C::A2_BYTES, d0 = da + s * C::STAGE_BYTES;
+                        // K step: 16 rows of A2 (128-byte rows) and of the tile (64-byte rows); the
+                        // second atom of A2 (rows 64..127) is A2_ATOM further, that of the tile
+                        // (observations 64..127, used with two sets) 4 KiB further
 #pragma unroll
-                        for (int kk = 0; kk < 8; ++kk)
+                        for (int kk = 0; kk < C::NK2; ++kk)
                             umma_bf16(tbase + C::COL_G + eb * C::COL_G_STRIDE,
                                       umma_desc(a0 + kk * 16 * 128, C::A2_ATOM, 1024, 2),
-                                      umma_desc(d0 + kk * 16 * 64, 1024, 512, 4), IDESC2,
+                                      umma_desc(d0 + kk * 16 * 64, C::SETS == 2 ? 4096 : 1024, 512, 4), IDESC2,
                                       (first && kk == 0) ? 0u : 1u);
                         umma_commit(&a2empty[b]);
                         umma_commit(&empty[s]);
@@ -321,7 +323,9 @@ __global__ void __launch_bounds__(TcCfg<NSPLIT>::THREADS, 1)
                 }
                 tc_fence_after();
                 float v[32];
-                tmem_ld32(tbase + (uint32_t(32 * q) << 16) + C::COL_G + eb * C::COL_G_STRIDE, v);
+                // rows 0..63 read the first 32 columns; with two sets rows 64..127 read the next 32
+                const uint32_t colset = (C::SETS == 2 && q >= 2) ? 32u : 0u;
+                tmem_ld32(tbase + (uint32_t(32 * q) << 16) + C::COL_G + eb * C::COL_G_STRIDE + colset, v);
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&gempty[eb]);
@@ -344,31 +348,37 @@ __global__ void __launch_bounds__(TcCfg<NSPLIT>::THREADS, 1)
             }
         } else {
             // ---------------- consumers ----------------
-            // group g takes tiles k = g (mod 2); tile k uses U and A2 buffer k & 3
+            // group g takes tiles k = g (mod 2); tile k uses U buffer k % 3 and A2 buffer k & 3
             const int g = warp >> 2, q = warp & 3;
             const int row = 32 * q + lane;
             const uint32_t lanebase = uint32_t(32 * q) << 16;
-            const uint32_t ds_off = sw64(row, uint32_t(M) >> 3) + (M & 7) * 2;
             float t3 = 0.0f, prod = 1.0f;
             int ex = 0, cnt = 0;
             const float erho = erho_f;
             const bool binary = args.binary != 0;
-            constexpr int WATOM = (32 * NSPLIT) / 64, WCHUNK = ((32 * NSPLIT) % 64) / 8;
             for (int k = g; k < nk; k += 2) {
                 if (__any_sync(0xffffffffu, *s_abort)) break;
-                const int s = k % C::STAGES, u = k & 3;
+                const int s = k % C::STAGES, u = k % C::NUBUF, b = k & 3;
                 const long long obs = (bid + (long long)k * nb) * C::TILE + row;
                 const bool valid = obs < V;
                 const bool okw = mbar_wait_bounded(&full[s], uint32_t((k / C::STAGES) & 1), BUDGET) &&
-                                 mbar_wait_bounded(&ufull[u], uint32_t((k >> 2) & 1), BUDGET);
+                                 mbar_wait_bounded(&ufull[u], uint32_t((k / C::NUBUF) & 1), BUDGET);
                 if (__any_sync(0xffffffffu, !okw)) {
                     *s_abort = 1;
                     break;
                 }
                 tc_fence_after();
-                float v[32], t;
+                // v = L~^T D and t = kappa~^T D: sums of the NSPLIT parts
+                float v[32], w32[32], tv[4];
                 const uint32_t tu = tbase + lanebase + C::COL_U + u * C::COL_U_STRIDE;
-                tmem_ld32_1(tu, v, tu + 32, t);
+                tmem_ld32(tu, v);
+#pragma unroll
+                for (int p = 1; p < NSPLIT; ++p) {
+                    tmem_ld32(tu + 32 * p, w32);
+#pragma unroll
+                    for (int c = 0; c < 32; ++c) v[c] += w32[c];
+                }
+                tmem_ld4(tu + 32 * NSPLIT, tv);
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&uempty[u]);
@@ -381,14 +391,16 @@ __global__ void __launch_bounds__(TcCfg<NSPLIT>::THREADS, 1)
                     q3 = fmaf(v[c + 3], v[c + 3], q3);
                 }
                 const float qv = (q0 + q1) + (q2 + q3);
-                // the observation: r and the profile row from the stage
+                float t = tv[0];
+#pragma unroll
+                for (int p = 1; p < NSPLIT; ++p) t += tv[p];
+                // the observation: y and the D~ row from the stage
                 const unsigned char *drow = dtile + s * C::STAGE_BYTES;
                 uint4 ch[4];
 #pragma unroll
                 for (int c = 0; c < 4; ++c) ch[c] = *reinterpret_cast<const uint4 *>(drow + sw64(row, c));
-                const float dS = __bfloat162float(*reinterpret_cast<const __nv_bfloat16 *>(drow + ds_off));
-                const float rr = reinterpret_cast<const float *>(drow + C::D_BYTES)[row];
-                const float e = (rr - dS) - t;
+                const float yv = reinterpret_cast<const float *>(drow + C::D_BYTES)[row];
+                const float e = yv - t;
                 const float den = fmaf(erho, qv, 1.0f);
                 float inv = rcp_approx(den);
                 inv = fmaf(inv, fmaf(-den, inv, 1.0f), inv);
@@ -408,16 +420,25 @@ __global__ void __launch_bounds__(TcCfg<NSPLIT>::THREADS, 1)
                     ex = 0;
                     cnt = 0;
                 }
-                // A2 row of this observation (MN-major, 128-byte swizzle): the NSPLIT parts of
-                // gamma d, then the NSPLIT parts of w
-                const bool oka = (k < 4) || mbar_wait_bounded(&a2empty[u], uint32_t(((k >> 2) - 1) & 1), BUDGET);
+                // A2 row of this observation (MN-major, 128-byte swizzle): part p of gamma D~ with
+                // part p of w in slot 31
+                const bool oka = (k < 4) || mbar_wait_bounded(&a2empty[b], uint32_t(((k >> 2) - 1) & 1), BUDGET);
                 if (__any_sync(0xffffffffu, !oka)) {
                     *s_abort = 1;
                     break;
                 }
-                unsigned char *arow = a2 + u * C::A2_BYTES;
+                unsigned char *abuf = a2 + b * C::A2_BYTES;
+                __nv_bfloat16 wp[NSPLIT];
+                f32_split<NSPLIT>(w, wp);
+                // with two sets: row (row & 63) of atom (row >> 6), part p in chunks 4 p .. 4 p + 3;
+                // with one set: row `row`, part p in atom p >> 1, chunks 4 (p & 1) .. 4 (p & 1) + 3
+                auto chunk_addr = [&](int p, int c) -> unsigned char * {
+                    if (C::SETS == 2)
+                        return abuf + (uint32_t(row) >> 6) * C::A2_ATOM + sw128(uint32_t(row) & 63u, uint32_t(4 * p + c));
+                    return abuf + (p >> 1) * C::A2_ATOM + sw128(uint32_t(row), uint32_t(4 * (p & 1) + c));
+                };
                 if (binary) {
-                    // d in {0, 1}: each part of gamma times d is exact in BF16
+                    // D in {-1, 0, 1}: each part of gamma times D is exact in BF16
                     __nv_bfloat16 gp[NSPLIT];
                     f32_split<NSPLIT>(gam, gp);
 #pragma unroll
@@ -430,11 +451,12 @@ __global__ void __launch_bounds__(TcCfg<NSPLIT>::THREADS, 1)
                             __nv_bfloat162 *op = reinterpret_cast<__nv_bfloat162 *>(&o);
 #pragma unroll
                             for (int h = 0; h < 4; ++h) op[h] = __hmul2(g2, dp[h]);
-                            *reinterpret_cast<uint4 *>(arow + (p >> 1) * C::A2_ATOM + sw128(row, 4 * (p & 1) + c)) = o;
+                            if (c == 3) op[3].y = wp[p];
+                            *reinterpret_cast<uint4 *>(chunk_addr(p, c)) = o;
                         }
                     }
                 } else {
-                    // general d (exact in BF16): gamma d_x in FP32, then its parts
+                    // general D (exact in BF16): gamma D_j in FP32, then its parts
 #pragma unroll
                     for (int c = 0; c < 4; ++c) {
                         const __nv_bfloat162 *dp = reinterpret_cast<const __nv_bfloat162 *>(&ch[c]);
@@ -448,22 +470,15 @@ __global__ void __launch_bounds__(TcCfg<NSPLIT>::THREADS, 1)
                             for (int p = 0; p < NSPLIT; ++p) reinterpret_cast<__nv_bfloat162 *>(&o[p])[h] = pp[p];
                         }
 #pragma unroll
-                        for (int p = 0; p < NSPLIT; ++p)
-                            *reinterpret_cast<uint4 *>(arow + (p >> 1) * C::A2_ATOM + sw128(row, 4 * (p & 1) + c)) = o[p];
+                        for (int p = 0; p < NSPLIT; ++p) {
+                            if (c == 3) reinterpret_cast<__nv_bfloat162 *>(&o[p])[3].y = wp[p];
+                            *reinterpret_cast<uint4 *>(chunk_addr(p, c)) = o[p];
+                        }
                     }
-                }
-                {
-                    __nv_bfloat16 wp[NSPLIT];
-                    f32_split<NSPLIT>(w, wp);
-                    uint4 wv = make_uint4(0, 0, 0, 0);
-                    __nv_bfloat16 *wq = reinterpret_cast<__nv_bfloat16 *>(&wv);
-#pragma unroll
-                    for (int p = 0; p < NSPLIT; ++p) wq[p] = wp[p];
-                    *reinterpret_cast<uint4 *>(arow + WATOM * C::A2_ATOM + sw128(row, WCHUNK)) = wv;
                 }
                 fence_proxy_async_smem();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&a2full[u]);
+                if (lane == 0) mbar_arrive(&a2full[b]);
             }
             t3_64 += static_cast<double>(t3);
             t4_64 += static_cast<double>(logf(prod));
@@ -486,20 +501,16 @@ __global__ void __launch_bounds__(TcCfg<NSPLIT>::THREADS, 1)
     red[3 * tid + 1] = t4_64;
     red[3 * tid + 2] = e4_64;
     __syncthreads();
-    // G'(x, y) as sum - comp; summed over the NSPLIT parts
-    auto gval = [&](int x, int y) {
-        return static_cast<double>(gsum[y * 128 + x]) - static_cast<double>(gcmp[y * 128 + x]);
+    // G''(m, y) as sum - comp; G(x, y) sums rows (set, part, x), g(y) rows (set, part, 31)
+    auto gval = [&](int m, int y) {
+        return static_cast<double>(gsum[y * 128 + m]) - static_cast<double>(gcmp[y * 128 + m]);
     };
-    auto Graw = [&](int x, int y) {
+    auto Gsum = [&](int x, int y) {
         double v = 0.0;
 #pragma unroll
-        for (int p = 0; p < NSPLIT; ++p) v += gval(32 * p + x, y);
-        return v;
-    };
-    auto graw = [&](int y) {
-        double v = 0.0;
+        for (int set = 0; set < C::SETS; ++set)
 #pragma unroll
-        for (int p = 0; p < NSPLIT; ++p) v += gval(32 * NSPLIT + p, y);
+            for (int p = 0; p < NSPLIT; ++p) v += gval(64 * set + 32 * p + x, y);
         return v;
     };
     double *part = a.partials + size_t(blockIdx.x) * NSTAT;
@@ -512,9 +523,9 @@ __global__ void __launch_bounds__(TcCfg<NSPLIT>::THREADS, 1)
             int r = 0;
             while ((r + 1) * (r + 2) / 2 <= j) ++r;
             const int c = j - r * (r + 1) / 2;
-            v = Graw(r, c) - Graw(r, M) - Graw(M, c) + Graw(M, M);
+            v = Gsum(r, c);
         } else if (j < NG + M) {
-            v = graw(j - NG) - graw(M);
+            v = Gsum(31, j - NG);
         } else {
             const int which = j - NG - M;                                  // T3, T4, E4
             for (int t = 0; t < 32 * C::NCW; ++t) v += red[3 * t + which];
@@ -536,39 +547,47 @@ __global__ void __launch_bounds__(TcCfg<NSPLIT>::THREADS, 1)
 }
 
 // Inputs of the tensor-core sweep, repacked into tiles of 128 observations
-// (TC_TILE_BYTES each): the profiles (V x S FP32, row-major) as BF16 rows of 32
-// components (zero padded) in the 64-byte-swizzled order of the kernel's shared
-// memory (16-byte chunk c of row j at j * 64 + ((c ^ ((j >> 1) & 3)) << 4)),
-// then the tile's r values (FP32); rows past V are zero.  counts[0] += profile
-// values that BF16 does not represent exactly, counts[1] += values other than
-// 0 and 1.
+// (TC_TILE_BYTES each) in the basis of Eq. 3: per observation a row of 32 BF16
+// slots, D_ij = d_ij - d_iS in slots j < M, 0 in slots M..30 and 1 in slot 31,
+// stored in the 64-byte-swizzled order of the kernel's shared memory (16-byte
+// chunk c of row i at i * 64 + ((c ^ ((i >> 1) & 3)) << 4)); then the tile's
+// y_i = r_i - d_iS (FP32).  Rows past V are zero.  counts[0] += D values that
+// BF16 does not represent exactly, counts[1] += D values other than -1, 0, 1.
 __global__ void tc_inputs_kernel(const float *__restrict__ d, const float *__restrict__ r, long long V, int S,
                                  unsigned char *__restrict__ out, unsigned long long *counts)
 {
-    unsigned long long bad = 0, nonbin = 0;
+    unsigned long long bad = 0, nonunit = 0;
+    const int M = S - 1;
     const long long ntiles = (V + 127) / 128;
     const long long stride = (long long)gridDim.x * blockDim.x;
-    // one thread per (observation, 8-component chunk)
+    // one thread per (observation, 8-slot chunk)
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ntiles * 128 * 4; i += stride) {
         const long long o = i >> 2;
         const int c = int(i & 3);
         const uint32_t j = uint32_t(o & 127);
+        const bool in = o < V;
+        const float dS = in ? d[o * S + M] : 0.0f;
         __align__(16) __nv_bfloat16 b[8];
 #pragma unroll
         for (int h = 0; h < 8; ++h) {
             const int col = 8 * c + h;
-            const float x = (col < S && o < V) ? d[o * S + col] : 0.0f;
+            float x = 0.0f;
+            if (in && col < M) {
+                x = d[o * S + col] - dS;
+                if (x != 0.0f && x != 1.0f && x != -1.0f) ++nonunit;
+            } else if (in && col == 31) {
+                x = 1.0f;
+            }
             b[h] = __float2bfloat16_rn(x);
             if (__bfloat162float(b[h]) != x) ++bad;
-            if (x != 0.0f && x != 1.0f) ++nonbin;
         }
         unsigned char *tile = out + (o >> 7) * (long long)TC_TILE_BYTES;
         *reinterpret_cast<uint4 *>(tile + j * 64 + ((uint32_t(c) ^ ((j >> 1) & 3)) << 4)) =
             *reinterpret_cast<const uint4 *>(b);
-        if (c == 0) reinterpret_cast<float *>(tile + 128 * 64)[j] = (o < V) ? r[o] : 0.0f;
+        if (c == 0) reinterpret_cast<float *>(tile + 128 * 64)[j] = in ? r[o] - dS : 0.0f;
     }
     if (bad) atomicAdd(&counts[0], bad);
-    if (nonbin) atomicAdd(&counts[1], nonbin);
+    if (nonunit) atomicAdd(&counts[1], nonunit);
 }
 
 } // namespace vbh

@@ -10,7 +10,8 @@
 namespace vbh {
 
 // Bytes of one input tile of the tensor-core sweep: 128 observations, BF16
-// profiles (128 x 64 bytes, in the kernel's shared-memory order) then r (128 x 4).
+// rows of D = d_{1:M} - d_S (128 x 64 bytes, in the kernel's shared-memory
+// order) then y = r - d_S (128 x 4).
 constexpr unsigned TC_TILE_BYTES = 128 * 64 + 128 * 4;
 
 // Kernel arguments of the tensor-core sweep.
@@ -18,7 +19,7 @@ struct TcArgs {
     SweepArgs sa;                  // V, st, partials, cond, use_cond, mode (r and d unused)
     const unsigned char *tiles;    // the repacked inputs (tc_convert_inputs)
     int S;
-    int binary;                    // 1: every profile value is 0 or 1
+    int binary;                    // 1: every D value is -1, 0 or 1
 };
 
 struct TcKernelInfo {
@@ -38,8 +39,8 @@ inline size_t tc_input_bytes(long long V) { return size_t((V + 127) / 128) * TC_
 
 // d (V x S FP32) and r (V FP32), device -> buf (tc_input_bytes(V) bytes,
 // device), in tiles of 128 observations.  counts_dev[0] (device) gains the
-// number of profile values BF16 does not represent exactly, counts_dev[1] the
-// number other than 0 and 1.
+// number of D = d_j - d_S values BF16 does not represent exactly, counts_dev[1]
+// the number other than -1, 0 and 1.
 int tc_convert_inputs(const float *d, const float *r, long long V, int S, void *buf, unsigned long long *counts_dev,
                       cudaStream_t stream, int nsm);
 

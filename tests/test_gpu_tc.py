@@ -118,7 +118,8 @@ def test_non_binary_profiles_exact_in_bf16(handle):
 
 
 def test_profiles_inexact_in_bf16(handle):
-    """VBH_FP32 refuses profiles that BF16 cannot hold; VBH_BF16 rounds them."""
+    """VBH_FP32 refuses profiles whose differences d_j - d_S BF16 cannot hold;
+    VBH_BF16 rounds those differences."""
     S, V = 12, 20000
     r, d, _ = synth.generate(V, S, seed=42, alpha=0.5)
     d = (d * np.float32(0.3)).astype(np.float32)
@@ -126,7 +127,12 @@ def test_profiles_inexact_in_bf16(handle):
     with pytest.raises(vbh.VBHError) as ei:
         handle.fit(_dev(r), _dev(d), S, prior, tol=0.0, max_iter=2)
     assert ei.value.status == -7
-    d16 = torch.from_numpy(d).to(torch.bfloat16).to(torch.float32).numpy()
+    # the BF16 form rounds D_j = d_j - d_S to BF16 and keeps y = r - d_S in FP32: the oracle
+    # gets the profiles d_S + bf16(d_j - d_S), which reproduce exactly those values
+    dS = d[:, S - 1:]
+    D16 = torch.from_numpy((d[:, :S - 1] - dS).astype(np.float32)).to(torch.bfloat16).to(torch.float32).numpy()
+    d16 = np.concatenate([(dS + D16).astype(np.float32), dS], axis=1)
+    assert np.array_equal((d16[:, :S - 1] - dS).astype(np.float32), D16)
     ref = O.fit(r, d16, prior, tol=0.0, max_iter=4)
     got = handle.fit(_dev(r), _dev(d), S, prior, tol=0.0, max_iter=4, precision=vbh.BF16, refine_iters=0)
     e = errors(got, ref)
