@@ -35,7 +35,7 @@ bool tc_kernel_info(int nsplit, TcKernelInfo *out)
         return false;
     }
     out->setup = reinterpret_cast<const void *>(&setup_kernel_rt);
-    out->tile = TcCfg<2>::TILE;
+    out->tile = 2 * TcCfg<2>::TILE;                 // a block takes pairs of tiles
     return true;
 }
 
@@ -43,10 +43,12 @@ int tc_convert_inputs(const float *d, const float *r, long long V, int S, void *
                       cudaStream_t stream, int nsm)
 {
     if (V == 0) return VBH_OK;
-    const long long work = (V + 127) / 128 * 128 * 4;
+    const long long ntiles = tc_tiles(V);
+    const long long work = ntiles * 16 * 32;
     long long blocks = (work + 255) / 256;
     if (blocks > 16LL * nsm) blocks = 16LL * nsm;
-    tc_inputs_kernel<<<int(blocks), 256, 0, stream>>>(d, r, V, S, static_cast<unsigned char *>(buf), counts_dev);
+    tc_inputs_kernel<<<int(blocks), 256, 0, stream>>>(d, r, V, S, ntiles, static_cast<unsigned char *>(buf),
+                                                      counts_dev);
     VBH_CHECK_CUDA(cudaGetLastError());
     return VBH_OK;
 }

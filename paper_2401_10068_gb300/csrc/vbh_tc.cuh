@@ -5,37 +5,38 @@
 // that grow with M^2 run as BF16 MMAs with FP32 accumulation in tensor memory.
 // The inputs are repacked once per fit into tiles of 128 observations in the
 // basis of Eq. 3: per observation the M differences D_ij = d_ij - d_iS as BF16
-// in slots 0..M-1 of a 32-slot row, the constant 1 in slot 31 (free for
-// S <= 32 because D has M <= 31 entries), and y_i = r_i - d_iS in FP32.
+// in slots 0..M-1 of 32 slots, the constant 1 in slot 31 (free for S <= 32,
+// since D has M <= 31 entries) and y_i = r_i - d_iS in FP32.  The BF16 part of
+// a tile is slot-major ("comp-major"): for each slot, the tile's observations
+// are contiguous, so that both operands of MMA2 are K-major.
 //   MMA1  U = D~_tile (128 x 32) . B1 (32 x N1): per observation the NSPLIT
 //         BF16 parts of v = L~^T D_i (q_i = |v|^2) and of t_i = kappa~^T D_i,
 //         side by side in N; L~ and kappa~ (the FP32 globals of the pass) are
 //         split into NSPLIT BF16 parts.  With D in {-1, 0, 1} every product is
 //         exact: NSPLIT = 3 carries the FP32 values (24 bits), NSPLIT = 2 keeps
 //         16 bits (the BF16 form).
-//   MMA2  G'' = A2^T . D~_tile: row (p, j) of A2 holds part p of
+//   MMA2  G'' = A2 . D~_tile^T: row (p, j) of A2 holds part p of
 //         gamma_i D_ij (gamma_i = w_i^2 - c_i) for j < 31 and part p of w_i in
-//         slot 31; against the D~ columns this gives sum gamma D D^T and, in
-//         row (p, 31), sum w D (slot 31 of D~ is 1).  In the BF16 form two sets
-//         of 64 observations share one MMA: A2 rows 0-63 hold the parts for
-//         observations 0-63, rows 64-127 for 64-127, and B is the 64-column
-//         pair of their D~ rows, so each MMA covers 32 observations (the cross
-//         blocks of the output are not read).  G'' accumulates in FP32 in tensor
-//         memory over an epoch of 16 tiles and is then added into compensated
-//         FP32 sums (sum and lost low part).
+//         slot 31, with the observations along K; against the D~ rows this
+//         gives sum gamma D D^T and, in row (p, 31), sum w D (slot 31 of D~ is
+//         1).  In the BF16 form two sets of 64 observations share one MMA: A2
+//         rows 0-63 belong to observations 0-63 and rows 64-127 to 64-127, B is
+//         the 64 slot rows of both sets, so each MMA covers 32 observations (the
+//         cross blocks of the output are not read).  G'' accumulates in FP32 in
+//         tensor memory over an epoch of 16 tiles and is then added into
+//         compensated FP32 sums (sum and lost low part).
 // The scalar per-observation work (c_i, w_i, S_i, ln(1 + E[rho] q_i)) stays
-// on the CUDA cores.  A tile is 8,704 contiguous bytes (the BF16 rows in the
-// 64-byte-swizzled order of the kernel's shared memory, then y), landed by one
-// bulk copy per pipeline stage; it is MMA1's K-major A operand and MMA2's
-// MN-major B operand.
+// on the CUDA cores; the consumer threads then build A2 from staged BF16 parts
+// of gamma in chunks of 8 observations.  Two tiles (17,408 contiguous bytes)
+// land in a pipeline stage by one bulk copy.
 //
-// Roles (14 warps): warps 0-7 are two groups of four consumer warps that take
+// Roles (15 warps): warps 0-7 are two groups of four consumer warps that take
 // alternate tiles, each warp owning one quarter of the tensor-memory lanes (32
-// observations); warps 8-11 flush the G'' epochs (one lane quarter each); warp
-// 12 lane 0 issues the loads and warp 13 lane 0 the MMAs.  MMA1 runs two tiles
-// ahead of MMA2 (three U buffers in tensor memory, four A2 buffers in shared
-// memory), so a consumer group never waits for the MMA of its own previous
-// tile.  Every wait is bounded: on a timeout the kernel records VBH_ETIMEOUT,
+// observations); warps 8-11 flush the G'' epochs (one lane quarter each); lane
+// 0 of warp 12 issues the loads, of warp 13 the MMA1s and of warp 14 the
+// MMA2s.  MMA1 runs ahead of the consumers on its own (three U buffers in
+// tensor memory), and four A2 buffers in shared memory decouple the consumers
+// from MMA2.  Every wait is bounded: on a timeout the kernel records VBH_ETIMEOUT,
 // lets its copies and MMAs drain, frees its tensor memory and returns.
 #pragma once
 
@@ -46,6 +47,15 @@
 
 namespace vbh {
 
+// Layout of the BF16 part of a tile (8 KiB, two 4 KiB blocks j of 64 rows x 64
+// bytes, 64-byte swizzle): observation o of slot x sits in block (o >> 5) & 1,
+// row 32 (o >> 6) + x, element o & 31.
+__host__ __device__ constexpr uint32_t tc_slot_byte(uint32_t o, uint32_t x)
+{
+    return ((o >> 5) & 1u) * 4096u + (32u * (o >> 6) + x) * 64u +
+           ((((o & 31u) >> 3) ^ (((32u * (o >> 6) + x) >> 1) & 3u)) << 4) + (o & 7u) * 2u;
+}
+
 template <int NSPLIT>
 struct TcCfg {
     static constexpr int TILE = 128;                                   // observations per tile
@@ -53,55 +63,55 @@ struct TcCfg {
     static constexpr int N1 = ((33 * NSPLIT + 15) / 16) * 16;          // MMA1 N: parts of v, then of t (80, 112)
     static constexpr int N2 = 32 * SETS;                               // MMA2 N
     static constexpr int NK2 = 8 / SETS;                               // MMA2 instructions per tile (K = 16)
-    static constexpr int STAGES = (NSPLIT == 2) ? 14 : 10;             // input tiles in flight
+    static constexpr int STAGES = (NSPLIT == 2) ? 8 : 4;               // pipeline stages of two tiles
     static constexpr int NUBUF = 3;                                    // U buffers (tile k uses k % 3)
     static constexpr int NBUF = 4;                                     // A2 buffers (tile k uses k & 3)
-    static constexpr uint32_t D_BYTES = TILE * 64;                     // swizzled BF16 rows
-    static constexpr uint32_t STAGE_BYTES = TC_TILE_BYTES;             // + 128 y values
+    static constexpr uint32_t D_BYTES = TILE * 64;                     // BF16 slots of a tile
+    static constexpr uint32_t TILE_BYTES = TC_TILE_BYTES;              // + 128 y values
+    static constexpr uint32_t STAGE_BYTES = 2 * TILE_BYTES;
     static constexpr uint32_t B1_BYTES = N1 * 64;
-    static constexpr uint32_t A2_ATOM = (TILE / SETS) * 128;           // 64 rows of A2 x the K of one set
-    static constexpr uint32_t A2_BYTES = 2 * A2_ATOM;
+    static constexpr uint32_t A2_BLOCK = 128 * 64;                     // 128 rows x 32 observations (or pairs)
+    static constexpr uint32_t A2_BYTES = (TILE / SETS / 32) * A2_BLOCK;
+    static constexpr uint32_t GAM_BYTES = NSPLIT * TILE * 2;           // staged BF16 parts of gamma
     static constexpr int EPOCH = 16;                                   // tiles per G'' epoch
     static constexpr int NCW = 8;                                      // consumer warps
     static constexpr int FLUSH_WARP0 = NCW;                            // warps 8..11
     static constexpr int PRODUCER_WARP = NCW + 4;
-    static constexpr int MMA_WARP = NCW + 5;
-    static constexpr int THREADS = 32 * (NCW + 6);
+    static constexpr int MMA1_WARP = NCW + 5;                          // issues MMA1 (runs ahead)
+    static constexpr int MMA2_WARP = NCW + 6;                          // issues MMA2
+    static constexpr int THREADS = 32 * (NCW + 7);
     static constexpr int TMEM_COLS = 512;
     static constexpr uint32_t COL_U = 0, COL_U_STRIDE = 128;          // U[u] at column 128 u
     static constexpr uint32_t COL_G = 384, COL_G_STRIDE = N2;          // G''[e & 1] at column 384 + N2 (e & 1)
+    static constexpr int NTASK = 31 * (TILE / 8);                     // A2 chunks (8 observations) per part
     static constexpr uint32_t OFF_D = 0;                                // stage s at s * STAGE_BYTES (512-byte aligned)
     static constexpr uint32_t OFF_A2 = ((OFF_D + STAGES * STAGE_BYTES + 1023) / 1024) * 1024;
     static constexpr uint32_t OFF_B1 = OFF_A2 + NBUF * A2_BYTES;
-    static constexpr uint32_t OFF_BAR = OFF_B1 + ((B1_BYTES + 1023) / 1024) * 1024;
+    static constexpr uint32_t OFF_GAM = OFF_B1 + ((B1_BYTES + 1023) / 1024) * 1024;
+    static constexpr uint32_t OFF_BAR = OFF_GAM + ((NBUF * GAM_BYTES + 1023) / 1024) * 1024;
     // mbarrier slots (8 bytes each) from OFF_BAR
     static constexpr int BAR_FULL = 0, BAR_EMPTY = BAR_FULL + STAGES, BAR_UFULL = BAR_EMPTY + STAGES;
     static constexpr int BAR_UEMPTY = BAR_UFULL + NUBUF, BAR_A2FULL = BAR_UEMPTY + NUBUF;
-    static constexpr int BAR_A2EMPTY = BAR_A2FULL + NBUF, BAR_GFULL = BAR_A2EMPTY + NBUF;
-    static constexpr int BAR_GEMPTY = BAR_GFULL + 2, BAR_DRAIN = BAR_GEMPTY + 2, NBARS = BAR_DRAIN + 1;
+    static constexpr int BAR_A2EMPTY = BAR_A2FULL + NBUF, BAR_STAGED = BAR_A2EMPTY + NBUF;
+    static constexpr int BAR_GFULL = BAR_STAGED + NBUF, BAR_GEMPTY = BAR_GFULL + 2, BAR_DRAIN = BAR_GEMPTY + 2;
+    static constexpr int NBARS = BAR_DRAIN + 2;                        // one drain barrier per MMA issuer
     static constexpr uint32_t OFF_MISC = OFF_BAR + 64 * 8;
-    static_assert(NBARS <= 64, "mbarrier slots");
     static constexpr uint32_t SMEM_BYTES = OFF_MISC + 64 + 1024;       // + slack to align the base to 1 KiB
     // end-of-kernel scratch, once the pipeline is idle
     static constexpr uint32_t OFF_GACC = OFF_D;                        // [sum, comp][32 columns][128 rows] FP32
     static constexpr uint32_t OFF_RED = OFF_A2;                        // 3 doubles per thread
+    static_assert(NBARS <= 64, "mbarrier slots");
     static_assert(SETS * 32 * NSPLIT <= 128 && (SETS == 1 || 32 * NSPLIT <= 64), "rows of the MMA2 accumulator");
     static_assert(COL_U + NUBUF * COL_U_STRIDE <= COL_G && COL_G + 2 * COL_G_STRIDE <= TMEM_COLS, "tensor memory");
     static_assert(N1 <= COL_U_STRIDE && N1 * 64 <= 8192, "MMA1 shape");
     static_assert(2 * 32 * 128 * 4 <= STAGES * STAGE_BYTES, "G'' totals scratch");
-    static_assert(STAGE_BYTES % 512 == 0 && D_BYTES + TILE * 4 == STAGE_BYTES, "stage layout");
+    static_assert(TILE_BYTES % 512 == 0 && D_BYTES + TILE * 4 == TILE_BYTES, "tile layout");
     static_assert(3 * THREADS * 8 <= NBUF * A2_BYTES, "reduction scratch");
     static_assert(SMEM_BYTES <= 227 * 1024, "shared memory per block");
 };
 
-// 16-byte chunk c of row `row` in a tile with 64-byte rows and 64-byte swizzle
+// 16-byte chunk c of row `row` in a region with 64-byte rows and 64-byte swizzle
 __device__ __forceinline__ uint32_t sw64(uint32_t row, uint32_t c) { return row * 64 + ((c ^ ((row >> 1) & 3)) << 4); }
-// 16-byte chunk c (0..7) of row `row` in a 128-byte-row atom with 128-byte swizzle,
-// rows grouped by 8 (1 KiB per group)
-__device__ __forceinline__ uint32_t sw128(uint32_t row, uint32_t c)
-{
-    return (row >> 3) * 1024 + (row & 7) * 128 + ((c ^ (row & 7)) << 4);
-}
 
 // Part `part` of the split of x into BF16 parts (x ~ part 0 + part 1 + ...).
 __device__ __forceinline__ __nv_bfloat16 bf16_part(double x, int part)
@@ -140,6 +150,16 @@ __device__ __forceinline__ void f32x2_split(float x, float y, __nv_bfloat162 (&o
     }
 }
 
+// Byte offset in an A2 buffer of element (row m, observation o) for the given
+// number of sets: K-major, 64-byte swizzle, blocks of 32 observations (pairs)
+// of 128 rows x 64 bytes.
+template <int SETS>
+__device__ __forceinline__ uint32_t a2_byte(uint32_t m, uint32_t o)
+{
+    const uint32_t k = (SETS == 2) ? (o & 63u) : o;                    // K index: pair or observation
+    return (k >> 5) * 8192u + sw64(m, (k & 31u) >> 3) + (k & 7u) * 2u;
+}
+
 template <int NSPLIT>
 __global__ void __launch_bounds__(TcCfg<NSPLIT>::THREADS, 1)
     tc_sweep_kernel(TcArgs args)
@@ -151,10 +171,12 @@ __global__ void __launch_bounds__(TcCfg<NSPLIT>::THREADS, 1)
     unsigned char *dtile = base + C::OFF_D;
     unsigned char *a2 = base + C::OFF_A2;
     unsigned char *b1 = base + C::OFF_B1;
+    __nv_bfloat16 *gam = reinterpret_cast<__nv_bfloat16 *>(base + C::OFF_GAM);
     uint64_t *bars = reinterpret_cast<uint64_t *>(base + C::OFF_BAR);
     uint64_t *full = bars + C::BAR_FULL, *empty = bars + C::BAR_EMPTY, *ufull = bars + C::BAR_UFULL;
     uint64_t *uempty = bars + C::BAR_UEMPTY, *a2full = bars + C::BAR_A2FULL, *a2empty = bars + C::BAR_A2EMPTY;
-    uint64_t *gfull = bars + C::BAR_GFULL, *gempty = bars + C::BAR_GEMPTY, *drain = bars + C::BAR_DRAIN;
+    uint64_t *staged = bars + C::BAR_STAGED, *gfull = bars + C::BAR_GFULL, *gempty = bars + C::BAR_GEMPTY;
+    uint64_t *drain = bars + C::BAR_DRAIN;
     volatile uint32_t *tslot = reinterpret_cast<volatile uint32_t *>(base + C::OFF_MISC);
     volatile int *s_abort = reinterpret_cast<volatile int *>(base + C::OFF_MISC + 4);
     volatile int *s_last = reinterpret_cast<volatile int *>(base + C::OFF_MISC + 8);
@@ -166,9 +188,11 @@ __global__ void __launch_bounds__(TcCfg<NSPLIT>::THREADS, 1)
     const int S = args.S, M = S - 1;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nth = blockDim.x;
     const long long V = a.V;
-    const long long ntiles = (V + C::TILE - 1) / C::TILE;
+    // this block's tiles: pairs of consecutive tiles (one stage each) taken round robin
+    const long long npairs = ((V + C::TILE - 1) / C::TILE + 1) / 2;
     const long long bid = blockIdx.x, nb = gridDim.x;
-    const int nk = (ntiles > bid) ? int((ntiles - bid + nb - 1) / nb) : 0;
+    const int npb = (npairs > bid) ? int((npairs - bid + nb - 1) / nb) : 0;
+    const int nk = 2 * npb;
     constexpr uint64_t BUDGET = 2000000000ull;
 
     const bool run = (a.mode != MODE_ITER) ||
@@ -180,7 +204,7 @@ __global__ void __launch_bounds__(TcCfg<NSPLIT>::THREADS, 1)
         if (tid == 0) {
             for (int i = 0; i < C::STAGES; ++i) {
                 mbar_init(&full[i], 1);
-                mbar_init(&empty[i], 1);
+                mbar_init(&empty[i], 2);                        // both tiles' MMA2
             }
             for (int i = 0; i < C::NUBUF; ++i) {
                 mbar_init(&ufull[i], 1);
@@ -189,12 +213,14 @@ __global__ void __launch_bounds__(TcCfg<NSPLIT>::THREADS, 1)
             for (int i = 0; i < C::NBUF; ++i) {
                 mbar_init(&a2full[i], 4);
                 mbar_init(&a2empty[i], 1);
+                mbar_init(&staged[i], 4);
             }
             for (int i = 0; i < 2; ++i) {
                 mbar_init(&gfull[i], 1);
                 mbar_init(&gempty[i], 4);
             }
-            mbar_init(drain, 1);
+            mbar_init(&drain[0], 1);
+            mbar_init(&drain[1], 1);
             *s_abort = 0;
             fence_mbar_init();
         }
@@ -226,83 +252,93 @@ __global__ void __launch_bounds__(TcCfg<NSPLIT>::THREADS, 1)
         const uint32_t tbase = *tslot;
 
         if (warp == C::PRODUCER_WARP) {
-            // ---------------- producer: profile tiles (tensor map) and r tiles (bulk copies) ----------------
+            // ---------------- producer: one bulk copy of two tiles per stage ----------------
             if (lane == 0) {
                 int issued = 0;
-                for (int k = 0; k < nk; ++k) {
+                for (int i = 0; i < npb; ++i) {
                     if (*s_abort) break;
-                    const int s = k % C::STAGES;
-                    if (k >= C::STAGES &&
-                        !mbar_wait_bounded(&empty[s], uint32_t(((k / C::STAGES) - 1) & 1), BUDGET)) {
+                    const int s = i % C::STAGES;
+                    if (i >= C::STAGES &&
+                        !mbar_wait_bounded(&empty[s], uint32_t(((i / C::STAGES) - 1) & 1), BUDGET)) {
                         *s_abort = 1;
                         break;
                     }
-                    const int tile = int(bid + (long long)k * nb);
                     mbar_arrive_expect_tx(&full[s], C::STAGE_BYTES);
-                    bulk_load(dtile + s * C::STAGE_BYTES, args.tiles + (long long)tile * C::STAGE_BYTES, C::STAGE_BYTES,
-                              &full[s]);
-                    issued = k + 1;
+                    bulk_load(dtile + s * C::STAGE_BYTES, args.tiles + (bid + (long long)i * nb) * C::STAGE_BYTES,
+                              C::STAGE_BYTES, &full[s]);
+                    issued = i + 1;
                 }
                 if (*s_abort) {
                     // the last copy of each stage may not have been consumed: let it land (bounded)
-                    for (int k = (issued > C::STAGES ? issued - C::STAGES : 0); k < issued; ++k)
-                        (void)mbar_wait_bounded(&full[k % C::STAGES], uint32_t((k / C::STAGES) & 1), BUDGET);
+                    for (int i = (issued > C::STAGES ? issued - C::STAGES : 0); i < issued; ++i)
+                        (void)mbar_wait_bounded(&full[i % C::STAGES], uint32_t((i / C::STAGES) & 1), BUDGET);
                 }
             }
-        } else if (warp == C::MMA_WARP) {
-            // ---------------- MMA issuer: MMA1 of tile k, then MMA2 of tile k - 2 ----------------
+        } else if (warp == C::MMA1_WARP) {
+            // ---------------- MMA1 issuer: U of tile k as soon as its inputs and a U buffer are there ----------------
             if (lane == 0) {
-                constexpr uint32_t IDESC1 = umma_idesc_bf16(128, C::N1, 0, 0);
-                constexpr uint32_t IDESC2 = umma_idesc_bf16(128, C::N2, 1, 1);
-                const uint32_t b1a = smem_addr(b1), a2a = smem_addr(a2), da = smem_addr(dtile);
-                for (int k = 0; k < nk + 2; ++k) {
+                constexpr uint32_t IDESC1 = umma_idesc_bf16(128, C::N1, 1, 0);
+                const uint32_t b1a = smem_addr(b1), da = smem_addr(dtile);
+                for (int k = 0; k < nk; ++k) {
                     if (*s_abort) break;
-                    if (k < nk) {
-                        const int s = k % C::STAGES, u = k % C::NUBUF;
-                        if (!mbar_wait_bounded(&full[s], uint32_t((k / C::STAGES) & 1), BUDGET) ||
-                            (k >= C::NUBUF &&
-                             !mbar_wait_bounded(&uempty[u], uint32_t(((k / C::NUBUF) - 1) & 1), BUDGET))) {
-                            *s_abort = 1;
-                            break;
-                        }
-                        tc_fence_after();
-                        const uint32_t d0 = da + s * C::STAGE_BYTES;
-#pragma unroll
-                        for (int kk = 0; kk < 2; ++kk)
-                            umma_bf16(tbase + C::COL_U + u * C::COL_U_STRIDE, umma_desc(d0 + kk * 32, 16, 512, 4),
-                                      umma_desc(b1a + kk * 32, 16, 512, 4), IDESC1, kk ? 1u : 0u);
-                        umma_commit(&ufull[u]);
+                    const int i = k >> 1, s = i % C::STAGES, u = k % C::NUBUF;
+                    if (!mbar_wait_bounded(&full[s], uint32_t((i / C::STAGES) & 1), BUDGET) ||
+                        (k >= C::NUBUF &&
+                         !mbar_wait_bounded(&uempty[u], uint32_t(((k / C::NUBUF) - 1) & 1), BUDGET))) {
+                        *s_abort = 1;
+                        break;
                     }
-                    if (k >= 2) {
-                        const int j = k - 2, b = j & 3, s = j % C::STAGES, e = j / C::EPOCH, eb = e & 1;
-                        const bool first = (j % C::EPOCH) == 0;
-                        if (!mbar_wait_bounded(&a2full[b], uint32_t((j >> 2) & 1), BUDGET) ||
-                            (first && e >= 2 &&
-                             !mbar_wait_bounded(&gempty[eb], uint32_t(((e >> 1) - 1) & 1), BUDGET))) {
-                            *s_abort = 1;
-                            break;
-                        }
-                        tc_fence_after();
-                        const uint32_t a0 = a2a + b * C::A2_BYTES, d0 = da + s * C::STAGE_BYTES;
-                        // K step: 16 rows of A2 (128-byte rows) and of the tile (64-byte rows); the
-                        // second atom of A2 (rows 64..127) is A2_ATOM further, that of the tile
-                        // (observations 64..127, used with two sets) 4 KiB further
+                    tc_fence_after();
+                    const uint32_t d0 = da + s * C::STAGE_BYTES + (k & 1) * C::TILE_BYTES;
+                    // A = the tile's slots as an MN-major operand: four atoms of 32 observations
+                    // (2 KiB apart), K step 16 slots = 1 KiB
 #pragma unroll
-                        for (int kk = 0; kk < C::NK2; ++kk)
-                            umma_bf16(tbase + C::COL_G + eb * C::COL_G_STRIDE,
-                                      umma_desc(a0 + kk * 16 * 128, C::A2_ATOM, 1024, 2),
-                                      umma_desc(d0 + kk * 16 * 64, C::SETS == 2 ? 4096 : 1024, 512, 4), IDESC2,
-                                      (first && kk == 0) ? 0u : 1u);
-                        umma_commit(&a2empty[b]);
-                        umma_commit(&empty[s]);
-                        if ((j % C::EPOCH) == C::EPOCH - 1 || j == nk - 1) umma_commit(&gfull[eb]);
-                    }
+                    for (int kk = 0; kk < 2; ++kk)
+                        umma_bf16(tbase + C::COL_U + u * C::COL_U_STRIDE, umma_desc(d0 + kk * 1024, 2048, 512, 4),
+                                  umma_desc(b1a + kk * 32, 16, 512, 4), IDESC1, kk ? 1u : 0u);
+                    umma_commit(&ufull[u]);
                 }
-                umma_commit(drain);             // arrives once every MMA issued above has completed
-                if (!mbar_wait_bounded(drain, 0u, BUDGET)) *s_abort = 1;
+                umma_commit(&drain[0]);         // arrives once every MMA issued above has completed
+                if (!mbar_wait_bounded(&drain[0], 0u, BUDGET)) *s_abort = 1;
             }
-        } else if (warp >= C::FLUSH_WARP0) {
-            // ---------------- flushers: G' epochs -> compensated FP32 sums (one row per lane) ----------------
+        } else if (warp == C::MMA2_WARP) {
+            // ---------------- MMA2 issuer: G'' += A2 . D~ of tile j once its A2 is built ----------------
+            if (lane == 0) {
+                constexpr uint32_t IDESC2 = umma_idesc_bf16(128, C::N2, 0, 0);
+                const uint32_t a2a = smem_addr(a2), da = smem_addr(dtile);
+                for (int j = 0; j < nk; ++j) {
+                    if (*s_abort) break;
+                    const int b = j & 3, i = j >> 1, s = i % C::STAGES;
+                    const int e = j / C::EPOCH, eb = e & 1;
+                    const bool first = (j % C::EPOCH) == 0;
+                    if (!mbar_wait_bounded(&full[s], uint32_t((i / C::STAGES) & 1), BUDGET) ||
+                        !mbar_wait_bounded(&a2full[b], uint32_t((j >> 2) & 1), BUDGET) ||
+                        (first && e >= 2 &&
+                         !mbar_wait_bounded(&gempty[eb], uint32_t(((e >> 1) - 1) & 1), BUDGET))) {
+                        *s_abort = 1;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t a0 = a2a + b * C::A2_BYTES;
+                    const uint32_t d0 = da + s * C::STAGE_BYTES + (j & 1) * C::TILE_BYTES;
+#pragma unroll
+                    for (int kk = 0; kk < C::NK2; ++kk) {
+                        // K step kk: 16 observations (pairs) = half of a 32-wide block
+                        const uint32_t blk = uint32_t(kk >> 1), half = uint32_t(kk & 1) * 32;
+                        const uint32_t boff = (C::SETS == 2) ? blk * 4096 + half
+                                                             : (blk & 1) * 4096 + (blk >> 1) * 2048 + half;
+                        umma_bf16(tbase + C::COL_G + eb * C::COL_G_STRIDE, umma_desc(a0 + blk * 8192 + half, 16, 512, 4),
+                                  umma_desc(d0 + boff, 16, 512, 4), IDESC2, (first && kk == 0) ? 0u : 1u);
+                    }
+                    umma_commit(&a2empty[b]);
+                    umma_commit(&empty[s]);
+                    if ((j % C::EPOCH) == C::EPOCH - 1 || j == nk - 1) umma_commit(&gfull[eb]);
+                }
+                umma_commit(&drain[1]);
+                if (!mbar_wait_bounded(&drain[1], 0u, BUDGET)) *s_abort = 1;
+            }
+        } else if (warp >= C::FLUSH_WARP0 && warp < C::FLUSH_WARP0 + 4) {
+            // ---------------- flushers: G'' epochs -> compensated FP32 sums (one row per lane) ----------------
             const int q = warp - C::FLUSH_WARP0;
             const int row = 32 * q + lane;
             float gs[32], gc[32];
@@ -315,7 +351,7 @@ __global__ void __launch_bounds__(TcCfg<NSPLIT>::THREADS, 1)
                     break;
                 }
                 const int eb = e & 1;
-                const bool okg = mbar_wait_bounded(&gfull[eb], uint32_t((e >> 1) & 1), BUDGET);
+                const bool okg = mbar_wait_backoff(&gfull[eb], uint32_t((e >> 1) & 1), BUDGET);
                 if (__any_sync(0xffffffffu, !okg)) {
                     *s_abort = 1;
                     ok = false;
@@ -348,37 +384,52 @@ __global__ void __launch_bounds__(TcCfg<NSPLIT>::THREADS, 1)
             }
         } else {
             // ---------------- consumers ----------------
-            // group g takes tiles k = g (mod 2); tile k uses U buffer k % 3 and A2 buffer k & 3
+            // group g takes tiles k = g (mod 2); tile k uses U buffer k % 3, A2 buffer k & 3
             const int g = warp >> 2, q = warp & 3;
-            const int row = 32 * q + lane;
+            const int row = 32 * q + lane;                       // tensor-memory lane
+            // U row `row` belongs to observation obs_row of the tile: the MMA1 atoms are the
+            // 32-observation runs 0, 64, 32, 96 (bits 5 and 6 of the row swapped)
+            const uint32_t o_r = (uint32_t(row) & 31u) | ((uint32_t(row) & 32u) << 1) | ((uint32_t(row) & 64u) >> 1);
             const uint32_t lanebase = uint32_t(32 * q) << 16;
+            const int gt = tid & 127;                            // thread within the group
             float t3 = 0.0f, prod = 1.0f;
             int ex = 0, cnt = 0;
             const float erho = erho_f;
             const bool binary = args.binary != 0;
             for (int k = g; k < nk; k += 2) {
                 if (__any_sync(0xffffffffu, *s_abort)) break;
-                const int s = k % C::STAGES, u = k % C::NUBUF, b = k & 3;
-                const long long obs = (bid + (long long)k * nb) * C::TILE + row;
-                const bool valid = obs < V;
-                const bool okw = mbar_wait_bounded(&full[s], uint32_t((k / C::STAGES) & 1), BUDGET) &&
-                                 mbar_wait_bounded(&ufull[u], uint32_t((k / C::NUBUF) & 1), BUDGET);
+                const int i = k >> 1, s = i % C::STAGES, u = k % C::NUBUF, b = k & 3;
+                const long long tile = 2 * (bid + (long long)i * nb) + (k & 1);
+                const bool valid = tile * C::TILE + o_r < V;
+                const bool okw = mbar_wait_backoff(&full[s], uint32_t((i / C::STAGES) & 1), BUDGET) &&
+                                 mbar_wait_backoff(&ufull[u], uint32_t((k / C::NUBUF) & 1), BUDGET);
                 if (__any_sync(0xffffffffu, !okw)) {
                     *s_abort = 1;
                     break;
                 }
                 tc_fence_after();
-                // v = L~^T D and t = kappa~^T D: sums of the NSPLIT parts
-                float v[32], w32[32], tv[4];
+                // v = L~^T D and t = kappa~^T D: sums of the NSPLIT parts (all loads, then one wait)
+                uint32_t ur[NSPLIT][32], tr[4];
                 const uint32_t tu = tbase + lanebase + C::COL_U + u * C::COL_U_STRIDE;
-                tmem_ld32(tu, v);
 #pragma unroll
-                for (int p = 1; p < NSPLIT; ++p) {
-                    tmem_ld32(tu + 32 * p, w32);
+                for (int p = 0; p < NSPLIT; ++p) tmem_ld32_nowait(tu + 32 * p, ur[p]);
+                tmem_ld4_nowait(tu + 32 * NSPLIT, tr);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-                    for (int c = 0; c < 32; ++c) v[c] += w32[c];
+                for (int p = 0; p < NSPLIT; ++p)
+#pragma unroll
+                    for (int c = 0; c < 32; ++c) asm volatile("" : "+r"(ur[p][c]));
+#pragma unroll
+                for (int c = 0; c < 4; ++c) asm volatile("" : "+r"(tr[c]));
+                float v[32], tv[4];
+#pragma unroll
+                for (int c = 0; c < 32; ++c) {
+                    v[c] = __uint_as_float(ur[0][c]);
+#pragma unroll
+                    for (int p = 1; p < NSPLIT; ++p) v[c] += __uint_as_float(ur[p][c]);
                 }
-                tmem_ld4(tu + 32 * NSPLIT, tv);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) tv[c] = __uint_as_float(tr[c]);
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&uempty[u]);
@@ -394,12 +445,8 @@ __global__ void __launch_bounds__(TcCfg<NSPLIT>::THREADS, 1)
                 float t = tv[0];
 #pragma unroll
                 for (int p = 1; p < NSPLIT; ++p) t += tv[p];
-                // the observation: y and the D~ row from the stage
-                const unsigned char *drow = dtile + s * C::STAGE_BYTES;
-                uint4 ch[4];
-#pragma unroll
-                for (int c = 0; c < 4; ++c) ch[c] = *reinterpret_cast<const uint4 *>(drow + sw64(row, c));
-                const float yv = reinterpret_cast<const float *>(drow + C::D_BYTES)[row];
+                const unsigned char *dt = dtile + s * C::STAGE_BYTES + (k & 1) * C::TILE_BYTES;
+                const float yv = reinterpret_cast<const float *>(dt + C::D_BYTES)[o_r];
                 const float e = yv - t;
                 const float den = fmaf(erho, qv, 1.0f);
                 float inv = rcp_approx(den);
@@ -407,7 +454,7 @@ __global__ void __launch_bounds__(TcCfg<NSPLIT>::THREADS, 1)
                 const float c_ = erho * inv;
                 const float ei = e * inv;
                 const float w = valid ? c_ * e : 0.0f;
-                const float gam = valid ? fmaf(c_ * e, c_ * e, -c_) : 0.0f;
+                const float gm = valid ? fmaf(c_ * e, c_ * e, -c_) : 0.0f;
                 t3 += valid ? fmaf(ei, ei, qv * inv) : 0.0f;
                 prod *= valid ? den : 1.0f;
                 peel_exponent(prod, ex);
@@ -420,60 +467,98 @@ __global__ void __launch_bounds__(TcCfg<NSPLIT>::THREADS, 1)
                     ex = 0;
                     cnt = 0;
                 }
-                // A2 row of this observation (MN-major, 128-byte swizzle): part p of gamma D~ with
-                // part p of w in slot 31
-                const bool oka = (k < 4) || mbar_wait_bounded(&a2empty[b], uint32_t(((k >> 2) - 1) & 1), BUDGET);
+                // stage this observation's parts: gamma for the chunk builders, w straight into
+                // A2 row (set, p, 31)
+                const bool oka = (k < 4) || mbar_wait_backoff(&a2empty[b], uint32_t(((k >> 2) - 1) & 1), BUDGET);
                 if (__any_sync(0xffffffffu, !oka)) {
                     *s_abort = 1;
                     break;
                 }
                 unsigned char *abuf = a2 + b * C::A2_BYTES;
-                __nv_bfloat16 wp[NSPLIT];
-                f32_split<NSPLIT>(w, wp);
-                // with two sets: row (row & 63) of atom (row >> 6), part p in chunks 4 p .. 4 p + 3;
-                // with one set: row `row`, part p in atom p >> 1, chunks 4 (p & 1) .. 4 (p & 1) + 3
-                auto chunk_addr = [&](int p, int c) -> unsigned char * {
-                    if (C::SETS == 2)
-                        return abuf + (uint32_t(row) >> 6) * C::A2_ATOM + sw128(uint32_t(row) & 63u, uint32_t(4 * p + c));
-                    return abuf + (p >> 1) * C::A2_ATOM + sw128(uint32_t(row), uint32_t(4 * (p & 1) + c));
-                };
-                if (binary) {
-                    // D in {-1, 0, 1}: each part of gamma times D is exact in BF16
-                    __nv_bfloat16 gp[NSPLIT];
-                    f32_split<NSPLIT>(gam, gp);
+                __nv_bfloat16 *gb = gam + b * (NSPLIT * C::TILE);
+                {
+                    __nv_bfloat16 gp[NSPLIT], wp[NSPLIT];
+                    f32_split<NSPLIT>(gm, gp);
+                    f32_split<NSPLIT>(w, wp);
+                    const uint32_t set = (C::SETS == 2) ? (o_r >> 6) : 0u;
 #pragma unroll
                     for (int p = 0; p < NSPLIT; ++p) {
-                        const __nv_bfloat162 g2 = __halves2bfloat162(gp[p], gp[p]);
+                        gb[p * C::TILE + o_r] = gp[p];
+                        *reinterpret_cast<__nv_bfloat16 *>(abuf + a2_byte<C::SETS>(64 * set + 32 * p + 31, o_r)) = wp[p];
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&staged[b]);
+                const bool oks = mbar_wait_backoff(&staged[b], uint32_t((k >> 2) & 1), BUDGET);
+                if (__any_sync(0xffffffffu, !oks)) {
+                    *s_abort = 1;
+                    break;
+                }
+                // A2 chunks: slot x < 31 of 8 observations (pairs) -> part p of gamma D_x; each
+                // thread takes up to TPT chunks, loading all operands before the products
+                constexpr int TPT = (C::NTASK + 127) / 128;
+                if (binary) {
+                    uint4 dch[TPT], gch[TPT][NSPLIT];
 #pragma unroll
-                        for (int c = 0; c < 4; ++c) {
-                            const __nv_bfloat162 *dp = reinterpret_cast<const __nv_bfloat162 *>(&ch[c]);
-                            uint4 o;
-                            __nv_bfloat162 *op = reinterpret_cast<__nv_bfloat162 *>(&o);
+                    for (int i = 0; i < TPT; ++i) {
+                        const int task = gt + 128 * i;
+                        if (task < C::NTASK) {
+                            const uint32_t x = uint32_t(task % 31), o0 = 8 * uint32_t(task / 31);
+                            dch[i] = *reinterpret_cast<const uint4 *>(dt + tc_slot_byte(o0, x));
 #pragma unroll
-                            for (int h = 0; h < 4; ++h) op[h] = __hmul2(g2, dp[h]);
-                            if (c == 3) op[3].y = wp[p];
-                            *reinterpret_cast<uint4 *>(chunk_addr(p, c)) = o;
+                            for (int p = 0; p < NSPLIT; ++p)
+                                gch[i][p] = *reinterpret_cast<const uint4 *>(gb + p * C::TILE + o0);
+                        }
+                    }
+#pragma unroll
+                    for (int i = 0; i < TPT; ++i) {
+                        const int task = gt + 128 * i;
+                        if (task < C::NTASK) {
+                            const uint32_t x = uint32_t(task % 31), o0 = 8 * uint32_t(task / 31);
+                            const uint32_t set = (C::SETS == 2) ? (o0 >> 6) : 0u;
+                            const __nv_bfloat162 *dp = reinterpret_cast<const __nv_bfloat162 *>(&dch[i]);
+#pragma unroll
+                            for (int p = 0; p < NSPLIT; ++p) {
+                                // D in {-1, 0, 1}: each part of gamma times D is exact in BF16
+                                const __nv_bfloat162 *gq = reinterpret_cast<const __nv_bfloat162 *>(&gch[i][p]);
+                                uint4 o;
+                                __nv_bfloat162 *op = reinterpret_cast<__nv_bfloat162 *>(&o);
+#pragma unroll
+                                for (int h = 0; h < 4; ++h) op[h] = __hmul2(gq[h], dp[h]);
+                                *reinterpret_cast<uint4 *>(abuf + a2_byte<C::SETS>(64 * set + 32 * p + x, o0)) = o;
+                            }
                         }
                     }
                 } else {
-                    // general D (exact in BF16): gamma D_j in FP32, then its parts
+                    for (int task = gt; task < C::NTASK; task += 128) {
+                        const uint32_t x = uint32_t(task % 31), o0 = 8 * uint32_t(task / 31);
+                        const uint32_t set = (C::SETS == 2) ? (o0 >> 6) : 0u;
+                        const uint4 dch = *reinterpret_cast<const uint4 *>(dt + tc_slot_byte(o0, x));
+                        const __nv_bfloat162 *dp = reinterpret_cast<const __nv_bfloat162 *>(&dch);
+                        // general D (exact in BF16): gamma (the sum of its parts) times D_x in FP32,
+                        // then the parts of the product
+                        float gsum8[8];
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        const __nv_bfloat162 *dp = reinterpret_cast<const __nv_bfloat162 *>(&ch[c]);
+                        for (int h = 0; h < 8; ++h) gsum8[h] = 0.0f;
+#pragma unroll
+                        for (int p = 0; p < NSPLIT; ++p) {
+                            const uint4 gch = *reinterpret_cast<const uint4 *>(gb + p * C::TILE + o0);
+                            const __nv_bfloat16 *gq = reinterpret_cast<const __nv_bfloat16 *>(&gch);
+#pragma unroll
+                            for (int h = 0; h < 8; ++h) gsum8[h] += __bfloat162float(gq[h]);
+                        }
                         uint4 o[NSPLIT];
 #pragma unroll
                         for (int h = 0; h < 4; ++h) {
                             const float2 df = __bfloat1622float2(dp[h]);
                             __nv_bfloat162 pp[NSPLIT];
-                            f32x2_split<NSPLIT>(gam * df.x, gam * df.y, pp);
+                            f32x2_split<NSPLIT>(gsum8[2 * h] * df.x, gsum8[2 * h + 1] * df.y, pp);
 #pragma unroll
                             for (int p = 0; p < NSPLIT; ++p) reinterpret_cast<__nv_bfloat162 *>(&o[p])[h] = pp[p];
                         }
 #pragma unroll
-                        for (int p = 0; p < NSPLIT; ++p) {
-                            if (c == 3) reinterpret_cast<__nv_bfloat162 *>(&o[p])[3].y = wp[p];
-                            *reinterpret_cast<uint4 *>(chunk_addr(p, c)) = o[p];
-                        }
+                        for (int p = 0; p < NSPLIT; ++p)
+                            *reinterpret_cast<uint4 *>(abuf + a2_byte<C::SETS>(64 * set + 32 * p + x, o0)) = o[p];
                     }
                 }
                 fence_proxy_async_smem();
@@ -547,44 +632,45 @@ __global__ void __launch_bounds__(TcCfg<NSPLIT>::THREADS, 1)
 }
 
 // Inputs of the tensor-core sweep, repacked into tiles of 128 observations
-// (TC_TILE_BYTES each) in the basis of Eq. 3: per observation a row of 32 BF16
-// slots, D_ij = d_ij - d_iS in slots j < M, 0 in slots M..30 and 1 in slot 31,
-// stored in the 64-byte-swizzled order of the kernel's shared memory (16-byte
-// chunk c of row i at i * 64 + ((c ^ ((i >> 1) & 3)) << 4)); then the tile's
-// y_i = r_i - d_iS (FP32).  Rows past V are zero.  counts[0] += D values that
-// BF16 does not represent exactly, counts[1] += D values other than -1, 0, 1.
+// (TC_TILE_BYTES each; an even number of tiles) in the basis of Eq. 3: the
+// BF16 slots D_ij = d_ij - d_iS (j < M), 0 (M <= j < 31) and 1 (j = 31) in the
+// slot-major layout of tc_slot_byte, then y_i = r_i - d_iS (FP32).  Rows past V
+// are zero.  counts[0] += D values that BF16 does not represent exactly,
+// counts[1] += D values other than -1, 0, 1.  One thread per (8 observations,
+// slot).
 __global__ void tc_inputs_kernel(const float *__restrict__ d, const float *__restrict__ r, long long V, int S,
-                                 unsigned char *__restrict__ out, unsigned long long *counts)
+                                 long long ntiles, unsigned char *__restrict__ out, unsigned long long *counts)
 {
     unsigned long long bad = 0, nonunit = 0;
     const int M = S - 1;
-    const long long ntiles = (V + 127) / 128;
     const long long stride = (long long)gridDim.x * blockDim.x;
-    // one thread per (observation, 8-slot chunk)
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ntiles * 128 * 4; i += stride) {
-        const long long o = i >> 2;
-        const int c = int(i & 3);
-        const uint32_t j = uint32_t(o & 127);
-        const bool in = o < V;
-        const float dS = in ? d[o * S + M] : 0.0f;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ntiles * 16 * 32; i += stride) {
+        const int x = int(i & 31);
+        const long long oct = i >> 5;                                  // global octet of observations
+        const long long o0 = oct * 8;
+        unsigned char *tile = out + (o0 >> 7) * (long long)TC_TILE_BYTES;
+        const uint32_t ot = uint32_t(o0 & 127);
         __align__(16) __nv_bfloat16 b[8];
 #pragma unroll
         for (int h = 0; h < 8; ++h) {
-            const int col = 8 * c + h;
-            float x = 0.0f;
-            if (in && col < M) {
-                x = d[o * S + col] - dS;
-                if (x != 0.0f && x != 1.0f && x != -1.0f) ++nonunit;
-            } else if (in && col == 31) {
-                x = 1.0f;
+            const long long o = o0 + h;
+            float v = 0.0f;
+            if (o < V) {
+                const float dS = d[o * S + M];
+                if (x < M) {
+                    v = d[o * S + x] - dS;
+                    if (v != 0.0f && v != 1.0f && v != -1.0f) ++nonunit;
+                } else if (x == 31) {
+                    v = 1.0f;
+                }
+                if (x == 0) reinterpret_cast<float *>(tile + 128 * 64)[ot + h] = r[o] - dS;
+            } else if (x == 0) {
+                reinterpret_cast<float *>(tile + 128 * 64)[ot + h] = 0.0f;
             }
-            b[h] = __float2bfloat16_rn(x);
-            if (__bfloat162float(b[h]) != x) ++bad;
+            b[h] = __float2bfloat16_rn(v);
+            if (__bfloat162float(b[h]) != v) ++bad;
         }
-        unsigned char *tile = out + (o >> 7) * (long long)TC_TILE_BYTES;
-        *reinterpret_cast<uint4 *>(tile + j * 64 + ((uint32_t(c) ^ ((j >> 1) & 3)) << 4)) =
-            *reinterpret_cast<const uint4 *>(b);
-        if (c == 0) reinterpret_cast<float *>(tile + 128 * 64)[j] = in ? r[o] - dS : 0.0f;
+        *reinterpret_cast<uint4 *>(tile + tc_slot_byte(ot, uint32_t(x))) = *reinterpret_cast<const uint4 *>(b);
     }
     if (bad) atomicAdd(&counts[0], bad);
     if (nonunit) atomicAdd(&counts[1], nonunit);

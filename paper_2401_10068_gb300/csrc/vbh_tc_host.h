@@ -9,9 +9,9 @@
 
 namespace vbh {
 
-// Bytes of one input tile of the tensor-core sweep: 128 observations, BF16
-// rows of D = d_{1:M} - d_S (128 x 64 bytes, in the kernel's shared-memory
-// order) then y = r - d_S (128 x 4).
+// Bytes of one input tile of the tensor-core sweep: 128 observations, the
+// BF16 slots of D = d_{1:M} - d_S (32 slots x 128 observations, in the kernel's
+// shared-memory order) then y = r - d_S (128 x 4).
 constexpr unsigned TC_TILE_BYTES = 128 * 64 + 128 * 4;
 
 // Kernel arguments of the tensor-core sweep.
@@ -34,8 +34,11 @@ struct TcKernelInfo {
 // or 3 (FP32-exact globals).
 bool tc_kernel_info(int nsplit, TcKernelInfo *out);
 
+// Tiles of the repacked inputs of V observations (an even number).
+inline long long tc_tiles(long long V) { return ((V + 127) / 128 + 1) / 2 * 2; }
+
 // Device bytes of the repacked inputs of V observations.
-inline size_t tc_input_bytes(long long V) { return size_t((V + 127) / 128) * TC_TILE_BYTES; }
+inline size_t tc_input_bytes(long long V) { return size_t(tc_tiles(V)) * TC_TILE_BYTES; }
 
 // d (V x S FP32) and r (V FP32), device -> buf (tc_input_bytes(V) bytes,
 // device), in tiles of 128 observations.  counts_dev[0] (device) gains the
