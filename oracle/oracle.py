@@ -52,6 +52,10 @@ class _Glob(ctypes.Structure):
                 ("Winv", ctypes.c_double * (MMAX * MMAX))]
 
 
+class _EM(ctypes.Structure):
+    _fields_ = [("rho", ctypes.c_double), ("K", ctypes.c_double * MMAX), ("Linv", ctypes.c_double * (MMAX * MMAX))]
+
+
 class _Sums(ctypes.Structure):
     _fields_ = [("V", ctypes.c_double), ("sum_S", ctypes.c_double), ("sum_mu", ctypes.c_double * MMAX),
                 ("sum_Ebb", ctypes.c_double * (MMAX * MMAX)), ("sum_logdet", ctypes.c_double)]
@@ -81,6 +85,9 @@ def _load():
             "vbo_fit_grouped": (ci, [_P(_Prior), ci, _dp, _dp, _dp, _dp, ctypes.c_double, ci, _P(_Glob), _dp,
                                      _P(ci), _P(ci), _dp, _P(ci)]),
             "vbo_elbo_at": (ci, [_P(_Prior), i64, _fp, _fp, _P(_Glob), _dp, _P(ci)]),
+            "vbo_em_loglik": (ci, [ci, i64, _fp, _fp, _P(_EM), _dp]),
+            "vbo_em_step": (ci, [ci, i64, _fp, _fp, _P(_EM), _P(_EM)]),
+            "vbo_em_fit": (ci, [ci, i64, _fp, _fp, _P(_EM), ctypes.c_double, ci, _P(_EM), _dp, _P(ci), _P(ci)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -347,3 +354,71 @@ def group_profiles(r, d, S: int) -> dict:
     codes = np.nonzero(keep)[0]
     dprof = ((codes[:, None] >> np.arange(S)[None, :]) & 1).astype(np.float64)
     return {"dprof": dprof, "n": n[keep], "sy": sy[keep], "syy": syy[keep]}
+
+
+# --------------------------------------------------------------------------- #
+# Expectation maximisation (Section 4.2, Eq. 42-47).                          #
+# --------------------------------------------------------------------------- #
+def em_init(prior: dict) -> dict:
+    """theta^(0) from the prior constants: K = K0, Lambda^{-1} = Lambda_0^{-1},
+    rho = a0 / b0 (the paper gives no starting point; this is the reading the
+    CUDA path uses too)."""
+    M = int(prior["S"]) - 1
+    return {"rho": float(prior["a0"]) / float(prior["b0"]), "K": np.array(prior["K0"], dtype=np.float64).reshape(M),
+            "Linv": np.array(prior["L0inv"], dtype=np.float64).reshape(M, M)}
+
+
+def _em_to_c(t: dict, M: int) -> _EM:
+    c = _EM()
+    c.rho = float(t["rho"])
+    K = np.asarray(t["K"], dtype=np.float64).reshape(M)
+    L = np.asarray(t["Linv"], dtype=np.float64).reshape(M * M)
+    for j in range(M):
+        c.K[j] = K[j]
+    for j in range(M * M):
+        c.Linv[j] = L[j]
+    return c
+
+
+def _em_from_c(c: _EM, M: int) -> dict:
+    return {"rho": c.rho, "K": np.array(c.K[:M]), "Linv": np.array(c.Linv[:M * M]).reshape(M, M)}
+
+
+def em_loglik(r, d, S: int, theta: dict) -> float:
+    """ln p(r | theta): the marginal of Eq. 3 under Eq. 4."""
+    lib = _load()
+    r, rp = _f32(r)
+    d, dp = _f32(d)
+    out = ctypes.c_double()
+    _check(lib.vbo_em_loglik(int(S), r.shape[0], rp, dp, ctypes.byref(_em_to_c(theta, S - 1)), ctypes.byref(out)),
+           "em_loglik")
+    return out.value
+
+
+def em_step(r, d, S: int, theta: dict) -> dict:
+    """One EM iteration (Eq. 42-47)."""
+    lib = _load()
+    r, rp = _f32(r)
+    d, dp = _f32(d)
+    o = _EM()
+    _check(lib.vbo_em_step(int(S), r.shape[0], rp, dp, ctypes.byref(_em_to_c(theta, S - 1)), ctypes.byref(o)),
+           "em_step")
+    return _em_from_c(o, S - 1)
+
+
+def em_fit(r, d, S: int, theta0: dict, tol: float = 1e-8, max_iter: int = 200) -> dict:
+    """EM from theta0: trace[n] = ln p(r | theta^(n)), n = 0..iters; the result
+    holds theta^(iters + 1)."""
+    lib = _load()
+    r, rp = _f32(r)
+    d, dp = _f32(d)
+    o = _EM()
+    trace = np.zeros(max_iter + 1)
+    iters, conv = ctypes.c_int(), ctypes.c_int()
+    rc = lib.vbo_em_fit(int(S), r.shape[0], rp, dp, ctypes.byref(_em_to_c(theta0, S - 1)), float(tol), int(max_iter),
+                        ctypes.byref(o), trace.ctypes.data_as(_dp), ctypes.byref(iters), ctypes.byref(conv))
+    _check(rc, "em_fit")
+    out = _em_from_c(o, S - 1)
+    out.update(iters=iters.value, converged=bool(conv.value), trace=trace[:iters.value + 1].copy(),
+               loglik=float(trace[iters.value]))
+    return out

@@ -1,7 +1,8 @@
 /*
  * vbh_oracle.c -- plain FP64 CPU oracle of the mean-field variational-Bayes
  * (CAVI) iteration for the conjugate-exponential cancer-tissue model of
- * Sections 3.3-3.5 (Eq. 2-31).
+ * Sections 3.3-3.5 (Eq. 2-31), and of its expectation-maximisation variant
+ * (Section 4.2, Eq. 42-47).
  *
  * TEST INFRASTRUCTURE.  Only the test suite, __graft_entry__.smoke() and the
  * cpu_baseline / reference legs of bench.py may load or call this library.
@@ -527,4 +528,129 @@ done:
     free(mu);
     free(Sig);
     return rc;
+}
+
+/* ======================================================================== */
+/* Expectation maximisation (Section 4.2, Eq. 42-47).                        */
+/* ======================================================================== */
+/*
+ * Point estimates theta = (K, Lambda^{-1}, rho) of the same model (Eq. 3-4),
+ * beta_i integrated out.  Readings taken here:
+ *   - Eq. 45-47 carry no prior terms: the iteration maximises the marginal
+ *     likelihood p(r | theta) (maximum-likelihood EM).
+ *   - The paper gives no starting point; theta^(0) is passed in (the CUDA
+ *     path's default is the prior's K0, Lambda_0^{-1} and a0 / b0).
+ *   - Iteration n evaluates ln p(r | theta^(n)) and then forms theta^(n+1); it
+ *     stops after iteration n >= 1 when |L_n - L_{n-1}| < tol |L_n|.
+ */
+typedef struct {
+    double rho;                         /* noise precision */
+    double K[VBO_MMAX];                 /* mean of beta_i */
+    double Linv[VBO_MMAX * VBO_MMAX];   /* Lambda^{-1}, row-major M x M */
+} vbo_em;
+
+/* ln p(r | theta) = sum_i ln N(r_i; D_i^T K + mu_i, 1/rho + D_i^T Lambda^{-1} D_i)
+ * (the marginal of Eq. 3 under Eq. 4), summed in observation order. */
+int vbo_em_loglik(int S, int64_t V, const float *r, const float *d, const vbo_em *t, double *ll)
+{
+    const int M = S - 1;
+    if (!(t->rho > 0.0)) return -1;
+    double sum = 0.0;
+    for (int64_t i = 0; i < V; ++i) {
+        const float *di = d + (size_t)i * (size_t)S;
+        const double dS = (double)di[M];
+        double D[VBO_MMAX];
+        for (int j = 0; j < M; ++j) D[j] = (double)di[j] - dS;
+        double mean = dS, var = 1.0 / t->rho;
+        for (int j = 0; j < M; ++j) {
+            mean += D[j] * t->K[j];
+            for (int k = 0; k < M; ++k) var += D[j] * t->Linv[j * M + k] * D[k];
+        }
+        const double e = (double)r[i] - mean;
+        sum += -0.5 * (VBO_LN2PI + log(var) + e * e / var);
+    }
+    *ll = sum;
+    return 0;
+}
+
+/* One EM iteration from theta_in: for every i, Sigma_i = [Lambda + rho D_i D_i^T]^{-1}
+ * by an explicit inverse (Eq. 42), M_i (Eq. 43) and S_i (Eq. 44); then rho
+ * (Eq. 45), K (Eq. 46) and Lambda^{-1} (Eq. 47). */
+int vbo_em_step(int S, int64_t V, const float *r, const float *d, const vbo_em *in, vbo_em *out)
+{
+    const int M = S - 1;
+    double Lam[VBO_MMAX * VBO_MMAX], LamK[VBO_MMAX];
+    if (M > 0 && spd_inverse(M, in->Linv, Lam, NULL)) return -1;
+    for (int j = 0; j < M; ++j) {
+        double s = 0.0;
+        for (int k = 0; k < M; ++k) s += Lam[j * M + k] * in->K[k];
+        LamK[j] = s;
+    }
+    double sumS = 0.0, sumM[VBO_MMAX], sumMM[VBO_MMAX * VBO_MMAX];
+    for (int j = 0; j < M; ++j) sumM[j] = 0.0;
+    for (int j = 0; j < M * M; ++j) sumMM[j] = 0.0;
+    for (int64_t i = 0; i < V; ++i) {
+        const float *di = d + (size_t)i * (size_t)S;
+        const double dS = (double)di[M];
+        const double y = (double)r[i] - dS;                     /* r_i - mu_i */
+        double D[VBO_MMAX], P[VBO_MMAX * VBO_MMAX], Sig[VBO_MMAX * VBO_MMAX], rhs[VBO_MMAX], Mi[VBO_MMAX];
+        for (int j = 0; j < M; ++j) D[j] = (double)di[j] - dS;
+        for (int j = 0; j < M; ++j)                              /* Lambda + rho D D^T */
+            for (int k = 0; k < M; ++k) P[j * M + k] = Lam[j * M + k] + in->rho * D[j] * D[k];
+        if (M > 0 && spd_inverse(M, P, Sig, NULL)) return -1;   /* Eq. 42 */
+        for (int j = 0; j < M; ++j) rhs[j] = LamK[j] + in->rho * D[j] * y;
+        for (int j = 0; j < M; ++j) {                            /* Eq. 43 */
+            double s = 0.0;
+            for (int k = 0; k < M; ++k) s += Sig[j * M + k] * rhs[k];
+            Mi[j] = s;
+        }
+        double DM = 0.0, DQD = 0.0;                              /* Eq. 44 */
+        for (int j = 0; j < M; ++j) {
+            DM += D[j] * Mi[j];
+            for (int k = 0; k < M; ++k) DQD += D[j] * (Mi[j] * Mi[k] + Sig[j * M + k]) * D[k];
+        }
+        sumS += y * y - 2.0 * y * DM + DQD;
+        for (int j = 0; j < M; ++j) {
+            sumM[j] += Mi[j];
+            for (int k = 0; k < M; ++k) sumMM[j * M + k] += Mi[j] * Mi[k] + Sig[j * M + k];
+        }
+    }
+    if (!(sumS > 0.0)) return -1;
+    const double Vd = (double)V;
+    out->rho = Vd / sumS;                                        /* Eq. 45 */
+    for (int j = 0; j < M; ++j) out->K[j] = sumM[j] / Vd;        /* Eq. 46 */
+    for (int j = 0; j < M; ++j)                                  /* Eq. 47 */
+        for (int k = 0; k < M; ++k) out->Linv[j * M + k] = sumMM[j * M + k] / Vd - out->K[j] * out->K[k];
+    for (int j = 0; j < M; ++j)
+        for (int k = 0; k < j; ++k) {
+            const double a = 0.5 * (out->Linv[j * M + k] + out->Linv[k * M + j]);
+            out->Linv[j * M + k] = a;
+            out->Linv[k * M + j] = a;
+        }
+    return 0;
+}
+
+/* EM from theta0: trace[n] = ln p(r | theta^(n)) for n = 0..*iters; *out =
+ * theta^(*iters + 1). */
+int vbo_em_fit(int S, int64_t V, const float *r, const float *d, const vbo_em *theta0, double tol, int max_iter,
+               vbo_em *out, double *trace, int *iters, int *converged)
+{
+    vbo_em cur = *theta0, nxt;
+    double L = 0.0, Lprev = 0.0;
+    *iters = 0;
+    *converged = 0;
+    for (int n = 0; n <= max_iter; ++n) {
+        if (vbo_em_loglik(S, V, r, d, &cur, &L)) return -1;
+        if (trace) trace[n] = L;
+        if (vbo_em_step(S, V, r, d, &cur, &nxt)) return -1;
+        cur = nxt;
+        *iters = n;
+        if (n >= 1 && fabs(L - Lprev) < tol * fabs(L)) {
+            *converged = 1;
+            break;
+        }
+        Lprev = L;
+    }
+    *out = cur;
+    return 0;
 }
