@@ -68,6 +68,11 @@ extern "C" {
 #define VBH_BF16 1               /* 12 <= S <= 32: 16-bit tensor-core operands for all but the last
                                     vbh_opts.refine_iters sweeps, which run as VBH_FP32; S <= 11 runs VBH_FP32 */
 
+/* method of a fit */
+#define VBH_CAVI 0               /* variational Bayes: Q(rho) Q(beta) Q(K, Lambda) by coordinate ascent (Section 3.5) */
+#define VBH_EM 1                 /* expectation maximisation: point estimates of K, Lambda, rho (Section 4.2,
+                                    Eq. 42-47); see vbh_opts.method */
+
 /* initial state of a fit */
 #define VBH_INIT_PAPER 0         /* Q(beta_i) = N(K0, Lambda_0^{-1}) before sweep 0 (Section 3.5) */
 #define VBH_INIT_GIVEN 1         /* start from the global factors in vbh_opts.init_state (warm start / resume) */
@@ -107,12 +112,21 @@ typedef struct {
                                     continue with the same tolerance test */
     const vbh_result *init_state;/* global factors to start from when init == VBH_INIT_GIVEN */
     double *elbo_trace;          /* optional host array of max_iter + 1 doubles: L_0 .. L_iters */
+    int method;                  /* VBH_CAVI or VBH_EM.  EM maximises ln p(r | K, Lambda, rho) (beta_i
+                                    integrated out; Eq. 45-47 carry no prior terms).  Iteration n evaluates
+                                    ln p(r | theta^(n)) -- the "elbo" of the trace and result -- and forms
+                                    theta^(n+1), which the result holds: kappa = K, W_inv = Lambda^{-1},
+                                    a_rho = rho_mean = rho_mode = rho, b_rho = nu = 1, lambda = V.  Start:
+                                    VBH_INIT_PAPER takes K0, Lambda_0^{-1} and rho = a0 / b0 from the prior;
+                                    VBH_INIT_GIVEN takes kappa, W_inv and a_rho / b_rho of init_state.
+                                    vbh_fit_batched and vbh_fit_static run VBH_CAVI only. */
 } vbh_opts;
 
 /* Fill *p with the paper's prior for S subpopulations (Section 3.5). */
 void vbh_prior_default(int S, vbh_prior *p);
 
-/* Fill *o with tol = 1e-8, max_iter = 200, VBH_FP32, VBH_INIT_PAPER, refine_iters = 10, no trace. */
+/* Fill *o with tol = 1e-8, max_iter = 200, VBH_FP32, VBH_INIT_PAPER, refine_iters = 10, no trace,
+ * VBH_CAVI. */
 void vbh_opts_default(vbh_opts *o);
 
 /* Create a handle on CUDA device `device` that issues all work on `stream`

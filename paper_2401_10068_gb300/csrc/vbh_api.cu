@@ -465,7 +465,7 @@ void to_result(const DevState &s, vbh_result *out)
     out->a_rho = s.a_rho;
     out->b_rho = s.b_rho;
     out->rho_mean = s.a_rho / s.b_rho;
-    out->rho_mode = (s.a_rho - 1.0) / s.b_rho;
+    out->rho_mode = s.em ? out->rho_mean : (s.a_rho - 1.0) / s.b_rho;   // EM: the point estimate
     out->elbo = s.elbo;
 }
 
@@ -501,6 +501,7 @@ void vbh_opts_default(vbh_opts *o)
     o->max_iter = 200;
     o->precision = VBH_FP32;
     o->refine_iters = 10;
+    o->method = VBH_CAVI;
     o->init = VBH_INIT_PAPER;
     o->init_state = nullptr;
     o->elbo_trace = nullptr;
@@ -588,6 +589,8 @@ int vbh_fit_begin(vbh_handle *h, const float *r, const float *d, int64_t V, int 
         (o->precision != VBH_FP32 && o->precision != VBH_BF16))
         return VBH_EINVAL;
     if (o->precision == VBH_BF16 && o->refine_iters < 0) return VBH_EINVAL;
+    if (o->method != VBH_CAVI && o->method != VBH_EM) return VBH_EINVAL;
+    const bool em = o->method == VBH_EM;
     if (o->init != VBH_INIT_PAPER && o->init != VBH_INIT_GIVEN) return VBH_EINVAL;
     if (o->init == VBH_INIT_GIVEN && (!o->init_state || o->init_state->S != S)) return VBH_EINVAL;
     DeviceGuard g(h->device);
@@ -614,16 +617,25 @@ int vbh_fit_begin(vbh_handle *h, const float *r, const float *d, int64_t V, int 
     s->max_iter = o->max_iter;
     s->target = 0;
     s->trace = h->trace;
+    s->em = em ? 1 : 0;
     const int M = S - 1;
-    if (o->init == VBH_INIT_GIVEN) {
+    if (em && o->init == VBH_INIT_PAPER) {
+        // theta^(0) from the prior: K0, Lambda_0^{-1}, rho = a0 / b0 (as (a_rho, b_rho) = (rho, 1), nu = 1)
+        for (int j = 0; j < M; ++j) s->kappa[j] = s->K0[j];
+        for (int j = 0; j < M * M; ++j) s->Winv[j] = s->L0inv[j];
+        s->a_rho = p->a0 / p->b0;
+        s->b_rho = 1.0;
+        s->nu = 1.0;
+        s->lam = double(V);
+    } else if (o->init == VBH_INIT_GIVEN) {
         const vbh_result *q = o->init_state;
-        if (!pos_finite(q->a_rho) || !pos_finite(q->b_rho) || !(q->nu > M - 1.0) || !pos_finite(q->lambda))
-            return VBH_EINVAL;
+        if (!pos_finite(q->a_rho) || !pos_finite(q->b_rho)) return VBH_EINVAL;
+        if (!em && (!(q->nu > M - 1.0) || !pos_finite(q->lambda))) return VBH_EINVAL;
         if (!host_spd(M, q->W_inv)) return VBH_EINVAL;
-        s->a_rho = q->a_rho;
-        s->b_rho = q->b_rho;
-        s->nu = q->nu;
-        s->lam = q->lambda;
+        s->a_rho = em ? q->a_rho / q->b_rho : q->a_rho;
+        s->b_rho = em ? 1.0 : q->b_rho;
+        s->nu = em ? 1.0 : q->nu;
+        s->lam = em ? double(V) : q->lambda;
         for (int j = 0; j < M; ++j) s->kappa[j] = q->kappa[j];
         symmetrize(M, q->W_inv, s->Winv);
     }
@@ -632,7 +644,11 @@ int vbh_fit_begin(vbh_handle *h, const float *r, const float *d, int64_t V, int 
     const int refine = bf16 ? (o->refine_iters < o->max_iter ? o->refine_iters : o->max_iter) : 0;
     if (bf16) s->max_iter = o->max_iter - refine;
     VBH_CK(cudaMemcpyAsync(h->st, s, sizeof(DevState), cudaMemcpyHostToDevice, h->stream));
-    if (o->init == VBH_INIT_GIVEN) {
+    if (em) {
+        // EM iteration 0 from theta^(0): ln p(r | theta^(0)), then theta^(1)
+        if ((rc = launch_setup(h, h->st, L, 0))) return rc;
+        if ((rc = launch_sweep(h, h->st, vbh::MODE_INIT, L, rd, dd, V))) return rc;
+    } else if (o->init == VBH_INIT_GIVEN) {
         // sweep 0 = the ELBO of the given factors (Q(beta) from them); the
         // sweeps that follow update all factors
         if ((rc = launch_setup(h, h->st, L, 0))) return rc;

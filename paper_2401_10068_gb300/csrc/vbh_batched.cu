@@ -132,6 +132,7 @@ int fit_batched_impl(BatchedHost &hb, cudaStream_t stream, int nsm, int B, const
     if (B == 0) return VBH_OK;
     if (o->max_iter < 0 || !(o->tol >= 0.0) || !std::isfinite(o->tol) || o->precision != VBH_FP32) return VBH_EINVAL;
     if (o->init != VBH_INIT_PAPER && o->init != VBH_INIT_GIVEN) return VBH_EINVAL;
+    if (o->method != VBH_CAVI) return VBH_EUNSUPPORTED;           // this entry point runs CAVI only
     if (o->init == VBH_INIT_GIVEN && !o->init_state) return VBH_EINVAL;
     for (int b = 0; b < B; ++b) {
         if (S[b] < 1 || S[b] > VBH_SMAX || V[b] < 0 || V[b] > (int64_t(1) << 40)) return VBH_EINVAL;

@@ -62,7 +62,7 @@ struct DevState {
     double elbo, elbo_prev, tol;
     int iter, target, max_iter, converged, status, const_dropped;
     unsigned int ticket;             // last-block-done counter of a sweep launch
-    int pad0;
+    int em;                          // 1: expectation maximisation (Eq. 42-47) instead of CAVI
     double *trace;                   // device array [max_iter + 1] (may be null)
     // per-fit constants: kc_upd for (a0 + V/2, n0 + V, q0 + V), kc_given for
     // the factors a fit or vbh_elbo starts from; prior_const collects the

@@ -134,6 +134,7 @@ extern "C" int vbh_fit_static(const float *r, const float *d, int64_t V, int S, 
     if (p->Lambda0_inv && !spd(M, p->Lambda0_inv)) return VBH_EINVAL;
     if (o->max_iter < 0 || !(o->tol >= 0.0) || !std::isfinite(o->tol) || o->precision != VBH_FP32) return VBH_EINVAL;
     if (o->init != VBH_INIT_PAPER && o->init != VBH_INIT_GIVEN) return VBH_EINVAL;
+    if (o->method != VBH_CAVI) return VBH_EUNSUPPORTED;           // this entry point runs CAVI only
     if (o->elbo_trace && o->max_iter + 1 > VBH_STATIC_TRACE_MAX) return VBH_EINVAL;   // trace beyond the scratch
     const vbh_result *q = o->init_state;
     if (o->init == VBH_INIT_GIVEN) {

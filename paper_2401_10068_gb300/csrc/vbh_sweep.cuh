@@ -338,6 +338,9 @@ __device__ inline void global_update_rt(int M, DevState *st, const double *__res
     __syncthreads();
 
     const ElboConst kc = (mode == MODE_ELBO) ? st->kc_given : st->kc_upd;
+    // EM (Eq. 42-47): the pass used the point estimates K~ = kappa~, Lambda^{-1}~ =
+    // Sigma0~ and rho~ = E[rho] of sw; the statistics of the pass are the same sums
+    const bool em = st->em != 0;
     const double V = st->V;
     const double T3 = stat[I_T3];
     const double T4 = stat[I_T4] + LN2 * stat[I_E4];
@@ -371,7 +374,10 @@ __device__ inline void global_update_rt(int M, DevState *st, const double *__res
         B[i] = s;
     }
     for (int i = tid; i < M; i += nth) {
-        if (mode == MODE_ELBO) {                    // kappa is given; kappa~ is its FP32 rounding
+        if (em) {                                   // Eq. 46: K' = (1/V) sum M_i = K~ + Sigma0~ g / V
+            dv[i] = sv[i] / V;
+            kn[i] = ko[i] + dv[i];
+        } else if (mode == MODE_ELBO) {             // kappa is given; kappa~ is its FP32 rounding
             kn[i] = st->kappa[i];
             dv[i] = kn[i] - ko[i];
         } else {
@@ -384,7 +390,10 @@ __device__ inline void global_update_rt(int M, DevState *st, const double *__res
     for (int i = tid; i < M * M; i += nth) {
         const int r = i / MD, c = i % MD;
         const double Bs = 0.5 * (B[r * M + c] + B[c * M + r]);
-        if (mode == MODE_ELBO) {
+        if (em) {
+            // Eq. 47: (1/V) sum (M_i M_i^T + Sigma_i) - K' K'^T = Sigma0~ + Sigma0~ G Sigma0~ / V - a a^T
+            Wn[i] = Sg[i] + Bs / V - dv[r] * dv[c];
+        } else if (mode == MODE_ELBO) {
             Wn[i] = st->Winv[i];
         } else {
             Wn[i] = st->L0inv[i] + V * Sg[i] + Bs + q0 * av[r] * av[c] - lam * dv[r] * dv[c];
@@ -398,11 +407,11 @@ __device__ inline void global_update_rt(int M, DevState *st, const double *__res
     if (warp == 0) {
         int fail;
         double lndetWn;
-        if (mode == MODE_ELBO) {
+        if (mode == MODE_ELBO && !em) {
             fail = warp_cholesky_rt(M, Wn, Lw, lane);
             lndetWn = warp_sum(lane < M ? 2.0 * log(Lw[lane * M + lane]) : 0.0);
         } else {
-            lndetWn = derive_pass_globals_rt(M, st, Wn, nu, Lw, lane, &fail);
+            lndetWn = derive_pass_globals_rt(M, st, Wn, em ? 1.0 : nu, Lw, lane, &fail);
         }
         if (lane == 0) {
             if (fail) s_fail = 1;
@@ -427,8 +436,40 @@ __device__ inline void global_update_rt(int M, DevState *st, const double *__res
         EL[i] = nu * s;
     }
     __syncthreads();
-    // 7. traces (warp 0), then the ELBO and control (thread 0)
-    if (warp == 0) {
+    // 7. traces (warp 0), then the ELBO (or, for EM, ln p(r | theta)) and control (thread 0)
+    if (em && warp == 0) {
+        // ln p(r | theta~) = sum_i ln N(y_i; D_i^T K~, 1/rho~ + q_i): with the pass's sums,
+        // V/2 (ln rho~ - ln 2 pi) - rho~/2 sum S_i - 1/2 sum ln(1 + rho~ q_i) - 1/2 tr(Sigma0~ G)
+        double t1 = 0.0;
+        for (int i = lane; i < M * M; i += 32) t1 = fma(Sg[i], G[i], t1);
+        const double trSG = warp_sum(t1);
+        if (lane == 0) {
+            const double rho_t = static_cast<double>(st->sw.erho);
+            const double L = 0.5 * V * (log(rho_t) - LN2PI) - 0.5 * rho_t * T3 - 0.5 * T4 - 0.5 * trSG;
+            const double rho_n = V / T3;                                             // Eq. 45
+            bool finite = isfinite(L) && isfinite(rho_n) && rho_n > 0.0 && !s_fail;
+            for (int j = 0; j < M; ++j) finite = finite && isfinite(kn[j]);
+            st->elbo = L;
+            st->const_dropped = 0;
+            st->a_rho = rho_n;                                                       // point estimate as (rho, 1)
+            st->b_rho = 1.0;
+            st->nu = 1.0;
+            st->lam = V;
+            st->erho = rho_n;
+            if (mode == MODE_INIT) {
+                st->iter = 0;
+                st->converged = 0;
+            } else {
+                st->iter += 1;
+                st->converged = (fabs(L - st->elbo_prev) < st->tol * fabs(L)) ? 1 : 0;
+            }
+            if (st->trace && st->iter <= st->max_iter) st->trace[st->iter] = L;
+            st->elbo_prev = L;
+            if (!finite && st->status == ST_OK) st->status = ST_ENONFINITE;
+            sc[0] = rho_n;
+        }
+    }
+    if (!em && warp == 0) {
         double t1 = 0.0, t2 = 0.0, t3 = 0.0;
         for (int i = lane; i < M * M; i += 32) {
             const int r = i / MD, c = i % MD;
@@ -488,7 +529,7 @@ __device__ inline void global_update_rt(int M, DevState *st, const double *__res
     }
     __syncthreads();
     // 8. write the new globals and the FP32 inputs of the next sweep
-    if (mode != MODE_ELBO) {
+    if (mode != MODE_ELBO || em) {
         for (int i = tid; i < M * M; i += nth) st->Winv[i] = Wn[i];
         for (int i = tid; i < M; i += nth) {
             st->kappa[i] = kn[i];
@@ -545,7 +586,7 @@ __global__ void __launch_bounds__(SweepCfg<S>::THREADS, SweepCfg<S>::MINB) sweep
 
     if (run) {
         float L[C::NGA], kap[C::MA];
-        const float erho = (a.mode == MODE_INIT) ? 0.0f : st->sw.erho;   // sweep 0: c_i = 0
+        const float erho = st->sw.erho;          // 0 in sweep 0 of a CAVI fit from the paper's start: c_i = 0
 #pragma unroll
         for (int i = 0; i < NG; ++i) L[i] = st->sw.L[i];
 #pragma unroll

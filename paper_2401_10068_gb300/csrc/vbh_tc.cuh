@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(TcCfg<NSPLIT>::THREADS, 1)
         // B1 (N1 rows x 32 slots, K-major, 64-byte swizzle): row 32 p + c holds part p of column c
         // of L~ (L~(k, c) at slot k), row 32 NSPLIT + p part p of kappa~; slot 31 (the constant 1
         // of the tile rows) meets zeros.
-        const float erho_f = (a.mode == MODE_INIT) ? 0.0f : st->sw.erho;
+        const float erho_f = st->sw.erho;       // 0 in sweep 0 of a CAVI fit from the paper's start
         for (int idx = tid; idx < C::N1 * 32; idx += nth) {
             const int n = idx >> 5, k = idx & 31;
             double x = 0.0;

@@ -19,6 +19,8 @@ SMAX = 32
 MMAX = 31
 FP32 = 0
 BF16 = 1
+CAVI = 0
+EM = 1
 INIT_PAPER = 0
 INIT_GIVEN = 1
 
@@ -57,7 +59,7 @@ class Result(ctypes.Structure):
 class Opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("precision", ctypes.c_int),
                 ("init", ctypes.c_int), ("refine_iters", ctypes.c_int), ("init_state", ctypes.POINTER(Result)),
-                ("elbo_trace", _dp)]
+                ("elbo_trace", _dp), ("method", ctypes.c_int)]
 
 
 _LIB = None
@@ -198,13 +200,14 @@ class Handle:
         self.close()
 
     @staticmethod
-    def _opts(tol, max_iter, init_state, S, trace, precision=FP32, refine_iters=10):
+    def _opts(tol, max_iter, init_state, S, trace, precision=FP32, refine_iters=10, method=CAVI):
         o = Opts()
         _lib().vbh_opts_default(ctypes.byref(o))
         o.tol = float(tol)
         o.max_iter = int(max_iter)
         o.precision = int(precision)
         o.refine_iters = int(refine_iters)
+        o.method = int(method)
         keep = []
         if init_state is not None:
             st = dict_to_result(init_state, S) if isinstance(init_state, dict) else init_state
@@ -219,10 +222,10 @@ class Handle:
 
     def fit(self, r, d, S: int, prior: dict | None = None, tol: float = 1e-8, max_iter: int = 200,
             init_state=None, trace: bool = False, V: int | None = None, precision: int = FP32,
-            refine_iters: int = 10) -> dict:
+            refine_iters: int = 10, method: int = CAVI) -> dict:
         V = int(V if V is not None else (r.shape[0] if r is not None else 0))
         pa = _PriorArgs(prior, S)
-        o, keep, buf = self._opts(tol, max_iter, init_state, S, trace, precision, refine_iters)
+        o, keep, buf = self._opts(tol, max_iter, init_state, S, trace, precision, refine_iters, method)
         res = Result()
         rc = _lib().vbh_fit(self._h, _ptr(r), _ptr(d), V, int(S), ctypes.byref(pa.c), ctypes.byref(o),
                             ctypes.byref(res))
@@ -235,10 +238,10 @@ class Handle:
 
     def fit_begin(self, r, d, S: int, prior: dict | None = None, tol: float = 1e-8, max_iter: int = 200,
                   init_state=None, trace: bool = False, V: int | None = None, precision: int = FP32,
-                  refine_iters: int = 10):
+                  refine_iters: int = 10, method: int = CAVI):
         V = int(V if V is not None else (r.shape[0] if r is not None else 0))
         pa = _PriorArgs(prior, S)
-        o, keep, buf = self._opts(tol, max_iter, init_state, S, trace, precision, refine_iters)
+        o, keep, buf = self._opts(tol, max_iter, init_state, S, trace, precision, refine_iters, method)
         rc = _lib().vbh_fit_begin(self._h, _ptr(r), _ptr(d), V, int(S), ctypes.byref(pa.c), ctypes.byref(o))
         if rc != 0:
             raise VBHError(rc, "vbh_fit_begin")
