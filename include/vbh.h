@@ -120,13 +120,20 @@ typedef struct {
                                     VBH_INIT_PAPER takes K0, Lambda_0^{-1} and rho = a0 / b0 from the prior;
                                     VBH_INIT_GIVEN takes kappa, W_inv and a_rho / b_rho of init_state.
                                     vbh_fit_batched and vbh_fit_static run VBH_CAVI only. */
+    int grouped;                 /* 1: exact profile-grouped sweeps for binary profiles (every d_ij 0 or 1;
+                                    otherwise VBH_EINVAL), S <= 16: one pass histograms (count, sum y,
+                                    sum y^2) per profile, y = r - d_S (FP64), and every sweep then runs over
+                                    the 2^S profiles in FP64 at a cost independent of V.  Same schedule,
+                                    methods and results as the per-observation sweeps (up to their FP32
+                                    rounding); the histogram's FP64 atomic sums make the last bits depend on
+                                    the order of the additions.  Ignores precision. */
 } vbh_opts;
 
 /* Fill *p with the paper's prior for S subpopulations (Section 3.5). */
 void vbh_prior_default(int S, vbh_prior *p);
 
 /* Fill *o with tol = 1e-8, max_iter = 200, VBH_FP32, VBH_INIT_PAPER, refine_iters = 10, no trace,
- * VBH_CAVI. */
+ * VBH_CAVI, not grouped. */
 void vbh_opts_default(vbh_opts *o);
 
 /* Create a handle on CUDA device `device` that issues all work on `stream`

@@ -14,6 +14,7 @@
 #include "vbh_dispatch.cuh"
 #include "vbh_internal.cuh"
 #include "vbh_error.h"
+#include "vbh_grouped_host.h"
 #include "vbh_tc_host.h"
 
 using vbh::DevState;
@@ -23,6 +24,9 @@ using vbh::KernelInfo;
 // tensor-core kernel (12 <= S <= 32, which reads BF16 profiles through
 // tensor maps).
 struct Launch {
+    bool grp = false;                       // profile-grouped sweep
+    int P = 0;                              // profile codes (2^S)
+    const double *gstats = nullptr;         // their (n, sum y, sum y^2)
     bool tc = false;
     int S = 0;
     int grid = 0;
@@ -31,10 +35,10 @@ struct Launch {
     KernelInfo ki{};
     vbh::TcKernelInfo tki{};
     const unsigned char *tiles = nullptr;   // repacked inputs of the tensor-core sweep
-    const void *func() const { return tc ? tki.sweep : ki.sweep; }
-    const void *setup() const { return tc ? tki.setup : ki.setup; }
-    int threads() const { return tc ? tki.threads : ki.threads; }
-    size_t smem() const { return tc ? tki.smem : ki.smem; }
+    const void *func() const { return grp ? vbh::grouped_sweep_func() : tc ? tki.sweep : ki.sweep; }
+    const void *setup() const { return (tc || grp) ? tki.setup : ki.setup; }
+    int threads() const { return grp ? vbh::GROUPED_THREADS : tc ? tki.threads : ki.threads; }
+    size_t smem() const { return grp ? vbh::grouped_smem_bytes() : tc ? tki.smem : ki.smem; }
     int tile() const { return tc ? tki.tile : ki.tile; }
 };
 
@@ -66,7 +70,10 @@ struct vbh_handle {
     void *tc_tiles = nullptr;
     size_t tc_cap = 0;
     unsigned long long *counts = nullptr;       // [inexact, non-binary] profile values (device)
+    double *gstats = nullptr;                    // profile histogram of the grouped sweep
+    size_t gstats_cap = 0;
     const void *g_tiles = nullptr;
+    const void *g_gstats = nullptr;
     // cached graph of the sweep loop
     cudaGraphExec_t gexec = nullptr;
     int g_S = -1, g_grid = -1;
@@ -268,11 +275,37 @@ void fill_prior(DevState *s, const vbh_prior *p, int S, long long V)
 
 // Kernel choice, launch shape and partials buffer of a fit of (V, S).  For the
 // tensor-core path the BF16 profiles and the tensor maps are prepared too.
-int prepare_launch(vbh_handle *h, int S, long long V, int precision, const float *rd, const float *dd, Launch *L)
+int prepare_launch(vbh_handle *h, int S, long long V, int precision, const float *rd, const float *dd, Launch *L,
+                   bool grouped = false)
 {
     L->S = S;
     const int M = S - 1;
     const size_t nstat = size_t(M * (M + 1) / 2 + M + 3);
+    if (grouped) {
+        // one histogram pass, then sweeps over the 2^S profile codes
+        if (S > vbh::GROUPED_SMAX) return VBH_EUNSUPPORTED;
+        L->grp = true;
+        L->P = 1 << S;
+        if (!vbh::tc_kernel_info(3, &L->tki)) return VBH_EUNSUPPORTED;          // the runtime-M set-up kernel
+        int rc = ensure(reinterpret_cast<void **>(&h->gstats), &h->gstats_cap, size_t(3) * L->P * sizeof(double));
+        if (rc) return rc;
+        if (!h->counts) {
+            size_t cap = 0;
+            if ((rc = ensure(reinterpret_cast<void **>(&h->counts), &cap, 2 * sizeof(unsigned long long)))) return rc;
+        }
+        VBH_CK(cudaMemsetAsync(h->gstats, 0, size_t(3) * L->P * sizeof(double), h->stream));
+        VBH_CK(cudaMemsetAsync(h->counts, 0, 2 * sizeof(unsigned long long), h->stream));
+        if ((rc = vbh::grouped_histogram(rd, dd, V, S, h->gstats, h->counts + 1, h->stream, h->nsm))) return rc;
+        unsigned long long nonbin = 0;
+        VBH_CK(cudaMemcpyAsync(&nonbin, h->counts + 1, sizeof(nonbin), cudaMemcpyDeviceToHost, h->stream));
+        VBH_CK(cudaStreamSynchronize(h->stream));
+        if (nonbin != 0) return VBH_EINVAL;                                      // the grouped form needs binary d
+        L->gstats = h->gstats;
+        long long g = (L->P + 7) / 8;                                            // 8 warps per block
+        if (g > h->nsm) g = h->nsm;
+        L->grid = int(g);
+        return ensure(reinterpret_cast<void **>(&h->partials), &h->partials_cap, size_t(g) * nstat * sizeof(double));
+    }
     if (S <= vbh::S_FP32_MAX) {
         L->tc = false;
         if (!kernel_info(S, &L->ki)) return VBH_EUNSUPPORTED;
@@ -340,7 +373,11 @@ int launch_sweep(vbh_handle *h, DevState *st, int mode, Launch &L, const float *
     a.partials = h->partials;
     a.use_cond = 0;
     a.mode = mode;
-    if (L.tc) {
+    if (L.grp) {
+        vbh::GroupArgs ga{a, L.gstats, L.P};
+        void *args[] = {&ga};
+        VBH_CK(cudaLaunchKernel(L.func(), dim3(L.grid), dim3(L.threads()), args, L.smem(), h->stream));
+    } else if (L.tc) {
         vbh::TcArgs ta{a, L.tiles, L.S, L.binary};
         void *args[] = {&ta};
         VBH_CK(cudaLaunchKernel(L.tki.sweep, dim3(L.grid), dim3(L.tki.threads), args, L.tki.smem, h->stream));
@@ -362,7 +399,8 @@ int build_graph(vbh_handle *h)
 {
     Launch &L = h->L;
     if (h->gexec && h->g_S == h->S && h->g_grid == L.grid && h->g_V == h->V && h->g_r == h->r && h->g_d == h->d &&
-        h->g_partials == h->partials && h->g_func == L.func() && h->g_tiles == (L.tc ? h->tc_tiles : nullptr))
+        h->g_partials == h->partials && h->g_func == L.func() && h->g_tiles == (L.tc ? h->tc_tiles : nullptr) &&
+        h->g_gstats == (L.grp ? L.gstats : nullptr))
         return VBH_OK;
     if (h->gexec) {
         cudaGraphExecDestroy(h->gexec);
@@ -377,8 +415,10 @@ int build_graph(vbh_handle *h)
     cudaGraphNodeParams kp{};
     vbh::SweepArgs a{};
     vbh::TcArgs ta{};
+    vbh::GroupArgs ga{};
     void *args[] = {&a};
     void *targs[] = {&ta};
+    void *gargs[] = {&ga};
     if (cudaGraphConditionalHandleCreate(&cond, g, 1u, cudaGraphCondAssignDefault) != cudaSuccess) {
         vbh::record_error("cudaGraphConditionalHandleCreate", __FILE__, __LINE__, cudaGetErrorName(cudaGetLastError()));
         rc = VBH_ECUDA;
@@ -401,6 +441,9 @@ int build_graph(vbh_handle *h)
     a.cond = cond;
     a.use_cond = 1;
     a.mode = vbh::MODE_ITER;
+    ga.sa = a;
+    ga.stats = L.gstats;
+    ga.P = L.P;
     ta.sa = a;
     ta.tiles = L.tiles;
     ta.S = L.S;
@@ -410,7 +453,7 @@ int build_graph(vbh_handle *h)
     kp.kernel.gridDim = dim3(L.grid);
     kp.kernel.blockDim = dim3(L.threads());
     kp.kernel.sharedMemBytes = (unsigned)L.smem();
-    kp.kernel.kernelParams = L.tc ? targs : args;
+    kp.kernel.kernelParams = L.grp ? gargs : L.tc ? targs : args;
     if (cudaGraphAddNode(&knode, cp.conditional.phGraph_out[0], nullptr, nullptr, 0, &kp) != cudaSuccess) {
         vbh::record_error("cudaGraphAddNode(sweep)", __FILE__, __LINE__, cudaGetErrorName(cudaGetLastError()));
         rc = VBH_ECUDA;
@@ -430,6 +473,7 @@ int build_graph(vbh_handle *h)
     h->g_partials = h->partials;
     h->g_func = L.func();
     h->g_tiles = L.tc ? h->tc_tiles : nullptr;
+    h->g_gstats = L.grp ? L.gstats : nullptr;
 out:
     if (rc) (void)cudaGetLastError();
     cudaGraphDestroy(g);
@@ -502,6 +546,7 @@ void vbh_opts_default(vbh_opts *o)
     o->precision = VBH_FP32;
     o->refine_iters = 10;
     o->method = VBH_CAVI;
+    o->grouped = 0;
     o->init = VBH_INIT_PAPER;
     o->init_state = nullptr;
     o->elbo_trace = nullptr;
@@ -571,6 +616,7 @@ void vbh_destroy(vbh_handle *h)
     cudaFree(h->stage_r);
     cudaFree(h->stage_d);
     cudaFree(h->tc_tiles);
+    cudaFree(h->gstats);
     cudaFree(h->counts);
     if (h->mirror) cudaFreeHost(h->mirror);
     cudaFree(h->batched.arena);
@@ -598,8 +644,9 @@ int vbh_fit_begin(vbh_handle *h, const float *r, const float *d, int64_t V, int 
     h->begun = false;
     const float *rd = nullptr, *dd = nullptr;
     if ((rc = stage_inputs(h, r, d, V, S, &rd, &dd))) return rc;
+    if (o->grouped != 0 && o->grouped != 1) return VBH_EINVAL;
     Launch L;
-    if ((rc = prepare_launch(h, S, V, o->precision, rd, dd, &L))) return rc;
+    if ((rc = prepare_launch(h, S, V, o->precision, rd, dd, &L, o->grouped == 1))) return rc;
     if (o->max_iter + 1 > h->trace_cap) {
         size_t cap = 0;
         cudaFree(h->trace);
@@ -640,7 +687,7 @@ int vbh_fit_begin(vbh_handle *h, const float *r, const float *d, int64_t V, int 
         symmetrize(M, q->W_inv, s->Winv);
     }
     // the 16-bit sweeps of a VBH_BF16 fit, then its FP32 ones
-    const bool bf16 = L.tc && L.nsplit == 2;
+    const bool bf16 = L.tc && !L.grp && L.nsplit == 2;
     const int refine = bf16 ? (o->refine_iters < o->max_iter ? o->refine_iters : o->max_iter) : 0;
     if (bf16) s->max_iter = o->max_iter - refine;
     VBH_CK(cudaMemcpyAsync(h->st, s, sizeof(DevState), cudaMemcpyHostToDevice, h->stream));

@@ -1,0 +1,180 @@
+// vbh_grouped.cu -- the exact profile-grouped form of the sweep for binary
+// profiles (d_ij in {0, 1}).
+//
+// Within a group of observations that share a profile, D_i, q_i, t_i, c_i and
+// ln(1 + E[rho] q_i) are the same, and every sum the sweep needs is a
+// polynomial of degree <= 2 in e_i = y_i - t: with n, sum y and sum y^2 of the
+// group,  sum e = sum y - n t,  sum e^2 = sum y^2 - 2 t sum y + n t^2,
+//   sum w D = c (sum e) D,  sum (w^2 - c) D D^T = (c^2 sum e^2 - n c) D D^T,
+//   sum S_i = inv^2 sum e^2 + n q inv,  sum ln(1 + E[rho] q) = n ln(1 + E[rho] q),
+// with c = E[rho] inv and inv = 1 / (1 + E[rho] q) (Eq. 19-21 in the rank-1
+// form of the per-observation sweep).  One histogram pass over the data gives
+// (n, sum y, sum y^2) per profile code; after it each sweep costs
+// O(2^S M^2), independent of V.  The sweep uses the FP32 globals of the pass
+// (as the per-observation sweep does) with FP64 arithmetic, writes the same
+// per-block partials and ends in the same global update.
+#include <cuda_runtime.h>
+
+#include "vbh.h"
+#include "vbh_error.h"
+#include "vbh_grouped_host.h"
+#include "vbh_sweep.cuh"
+
+namespace vbh {
+
+namespace {
+constexpr int GW = GROUPED_THREADS / 32;                        // warps per block
+constexpr int GMAX = GROUPED_SMAX - 1;                          // largest M
+constexpr int GNSTAT = GMAX * (GMAX + 1) / 2 + GMAX + 3;
+} // namespace
+
+__global__ void grouped_hist_kernel(const float *__restrict__ r, const float *__restrict__ d, long long V, int S,
+                                    double *__restrict__ stats, unsigned long long *nonbinary)
+{
+    extern __shared__ double sh[];
+    const int P = 1 << S;
+    const bool local = P <= 2048;                               // 48 KiB of block histogram
+    if (local) {
+        for (int i = threadIdx.x; i < 3 * P; i += blockDim.x) sh[i] = 0.0;
+        __syncthreads();
+    }
+    unsigned long long bad = 0;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < V; i += stride) {
+        const float *di = d + i * S;
+        int code = 0;
+        for (int j = 0; j < S; ++j) {
+            const float x = di[j];
+            if (x == 1.0f) code |= 1 << j;
+            else if (x != 0.0f) ++bad;
+        }
+        const double y = static_cast<double>(r[i]) - static_cast<double>(di[S - 1]);
+        double *dst = local ? sh + 3 * code : stats + 3 * code;
+        atomicAdd(dst, 1.0);
+        atomicAdd(dst + 1, y);
+        atomicAdd(dst + 2, y * y);
+    }
+    if (local) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < 3 * P; i += blockDim.x)
+            if (sh[i] != 0.0) atomicAdd(stats + i, sh[i]);
+    }
+    if (bad) atomicAdd(nonbinary, bad);
+}
+
+// One sweep over the profile groups: warp w of the grid takes codes w, w + W, ...;
+// lane j < M keeps row j of the packed G (columns k <= j) and g_j in registers.
+__global__ void __launch_bounds__(GROUPED_THREADS) grouped_sweep_kernel(GroupArgs ga)
+{
+    extern __shared__ double gsm[];
+    __shared__ int s_last;
+    const SweepArgs &a = ga.sa;
+    DevState *st = a.st;
+    const int S = st->S, M = S - 1;
+    const int NG = M * (M + 1) / 2, NSTAT = NG + M + 3;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool run = (a.mode != MODE_ITER) ||
+                     (st->status == ST_OK && !st->converged && st->iter < st->target && st->iter < st->max_iter);
+
+    double gacc[GMAX], gv = 0.0, t3 = 0.0, t4 = 0.0;
+#pragma unroll
+    for (int k = 0; k < GMAX; ++k) gacc[k] = 0.0;
+    if (run) {
+        // column `lane` of L~ and kappa~ of the pass (FP32 globals, as the per-observation sweep)
+        double lcol[GMAX];
+#pragma unroll
+        for (int k = 0; k < GMAX; ++k)
+            lcol[k] = (lane < M && k < M && k >= lane) ? static_cast<double>(st->sw.L[k * (k + 1) / 2 + lane]) : 0.0;
+        const double kap = lane < M ? static_cast<double>(st->sw.kappa[lane]) : 0.0;
+        const double erho = static_cast<double>(st->sw.erho);
+        const int nwarps = gridDim.x * GW;
+        for (int p = blockIdx.x * GW + warp; p < ga.P; p += nwarps) {
+            const double n = ga.stats[3 * p];
+            if (n == 0.0) continue;                             // warp-uniform
+            const double sy = ga.stats[3 * p + 1], syy = ga.stats[3 * p + 2];
+            const int bS = (p >> M) & 1;
+            auto Dk = [&](int k) { return static_cast<double>(((p >> k) & 1) - bS); };
+            double v = 0.0;
+#pragma unroll
+            for (int k = 0; k < GMAX; ++k) v = fma(lcol[k], (k < M) ? Dk(k) : 0.0, v);   // (L~^T D)_lane
+            const double Dj = lane < M ? Dk(lane) : 0.0;
+            const double q = warp_sum(v * v);
+            const double t = warp_sum(kap * Dj);
+            const double den = fma(erho, q, 1.0);
+            const double inv = 1.0 / den;
+            const double c = erho * inv;
+            const double se = sy - n * t;
+            const double see = syy - 2.0 * t * sy + n * t * t;
+            const double sw = c * se;
+            const double sgam = c * c * see - n * c;
+            if (lane < M) {
+#pragma unroll
+                for (int k = 0; k < GMAX; ++k)
+                    if (k <= lane) gacc[k] = fma(sgam * Dj, Dk(k), gacc[k]);
+                gv = fma(sw, Dj, gv);
+            }
+            if (lane == 0) {
+                t3 += inv * inv * see + n * q * inv;
+                t4 += n * log(den);
+            }
+        }
+    }
+    // per-warp partials -> shared memory [warp][NSTAT] -> this block's partials (fixed order)
+    double *red = gsm;
+    if (lane < M) {
+#pragma unroll
+        for (int k = 0; k < GMAX; ++k)
+            if (k <= lane) red[warp * GNSTAT + lane * (lane + 1) / 2 + k] = gacc[k];
+        red[warp * GNSTAT + NG + lane] = gv;
+    }
+    if (lane == 0) {
+        red[warp * GNSTAT + NG + M] = t3;
+        red[warp * GNSTAT + NG + M + 1] = t4;
+        red[warp * GNSTAT + NG + M + 2] = 0.0;
+    }
+    __syncthreads();
+    double *part = a.partials + size_t(blockIdx.x) * NSTAT;
+    for (int j = tid; j < NSTAT; j += blockDim.x) {
+        double s = 0.0;
+        for (int w = 0; w < GW; ++w) s += red[w * GNSTAT + j];
+        part[j] = s;
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = (atomicAdd(&st->ticket, 1u) == gridDim.x - 1) ? 1 : 0;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (run && st->status == ST_OK) {
+        global_update_rt(M, st, a.partials, gridDim.x, a, gsm);
+    } else if (tid == 0 && a.use_cond) {
+        cudaGraphSetConditional(a.cond, 0u);
+    }
+    if (tid == 0) st->ticket = 0u;
+}
+
+const void *grouped_sweep_func() { return reinterpret_cast<const void *>(&grouped_sweep_kernel); }
+
+size_t grouped_smem_bytes()
+{
+    const size_t red = size_t(GW) * GNSTAT * sizeof(double);
+    const size_t ws = size_t(gu_ws_doubles_rt(GMAX)) * sizeof(double);
+    return red > ws ? red : ws;
+}
+
+int grouped_histogram(const float *r, const float *d, long long V, int S, double *stats,
+                      unsigned long long *nonbinary_dev, cudaStream_t stream, int nsm)
+{
+    if (V == 0) return VBH_OK;
+    const int P = 1 << S;
+    const size_t smem = (P <= 2048) ? size_t(3) * P * sizeof(double) : 0;
+    long long blocks = (V + 255) / 256;
+    if (blocks > 4LL * nsm) blocks = 4LL * nsm;
+    if (smem > 48 * 1024) VBH_CHECK_CUDA(cudaFuncSetAttribute(grouped_hist_kernel,
+                                                             cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    grouped_hist_kernel<<<int(blocks), 256, smem, stream>>>(r, d, V, S, stats, nonbinary_dev);
+    VBH_CHECK_CUDA(cudaGetLastError());
+    return VBH_OK;
+}
+
+} // namespace vbh

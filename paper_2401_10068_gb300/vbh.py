@@ -59,7 +59,7 @@ class Result(ctypes.Structure):
 class Opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("precision", ctypes.c_int),
                 ("init", ctypes.c_int), ("refine_iters", ctypes.c_int), ("init_state", ctypes.POINTER(Result)),
-                ("elbo_trace", _dp), ("method", ctypes.c_int)]
+                ("elbo_trace", _dp), ("method", ctypes.c_int), ("grouped", ctypes.c_int)]
 
 
 _LIB = None
@@ -200,7 +200,7 @@ class Handle:
         self.close()
 
     @staticmethod
-    def _opts(tol, max_iter, init_state, S, trace, precision=FP32, refine_iters=10, method=CAVI):
+    def _opts(tol, max_iter, init_state, S, trace, precision=FP32, refine_iters=10, method=CAVI, grouped=False):
         o = Opts()
         _lib().vbh_opts_default(ctypes.byref(o))
         o.tol = float(tol)
@@ -208,6 +208,7 @@ class Handle:
         o.precision = int(precision)
         o.refine_iters = int(refine_iters)
         o.method = int(method)
+        o.grouped = 1 if grouped else 0
         keep = []
         if init_state is not None:
             st = dict_to_result(init_state, S) if isinstance(init_state, dict) else init_state
@@ -222,10 +223,10 @@ class Handle:
 
     def fit(self, r, d, S: int, prior: dict | None = None, tol: float = 1e-8, max_iter: int = 200,
             init_state=None, trace: bool = False, V: int | None = None, precision: int = FP32,
-            refine_iters: int = 10, method: int = CAVI) -> dict:
+            refine_iters: int = 10, method: int = CAVI, grouped: bool = False) -> dict:
         V = int(V if V is not None else (r.shape[0] if r is not None else 0))
         pa = _PriorArgs(prior, S)
-        o, keep, buf = self._opts(tol, max_iter, init_state, S, trace, precision, refine_iters, method)
+        o, keep, buf = self._opts(tol, max_iter, init_state, S, trace, precision, refine_iters, method, grouped)
         res = Result()
         rc = _lib().vbh_fit(self._h, _ptr(r), _ptr(d), V, int(S), ctypes.byref(pa.c), ctypes.byref(o),
                             ctypes.byref(res))
@@ -238,10 +239,10 @@ class Handle:
 
     def fit_begin(self, r, d, S: int, prior: dict | None = None, tol: float = 1e-8, max_iter: int = 200,
                   init_state=None, trace: bool = False, V: int | None = None, precision: int = FP32,
-                  refine_iters: int = 10, method: int = CAVI):
+                  refine_iters: int = 10, method: int = CAVI, grouped: bool = False):
         V = int(V if V is not None else (r.shape[0] if r is not None else 0))
         pa = _PriorArgs(prior, S)
-        o, keep, buf = self._opts(tol, max_iter, init_state, S, trace, precision, refine_iters, method)
+        o, keep, buf = self._opts(tol, max_iter, init_state, S, trace, precision, refine_iters, method, grouped)
         rc = _lib().vbh_fit_begin(self._h, _ptr(r), _ptr(d), V, int(S), ctypes.byref(pa.c), ctypes.byref(o))
         if rc != 0:
             raise VBHError(rc, "vbh_fit_begin")
