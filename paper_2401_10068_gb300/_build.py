@@ -34,8 +34,8 @@ def nvcc() -> str:
 LIBS = {
     "vbh": {
         "sources": lambda: sorted(glob.glob(os.path.join(PKG, "csrc", "*.cu"))),
-        "deps": lambda: sorted(glob.glob(os.path.join(PKG, "csrc", "*.cuh")) + glob.glob(os.path.join(PKG, "csrc", "*.h")))
-        + [os.path.join(INCLUDE, "vbh.h")],
+        "deps": lambda: sorted(glob.glob(os.path.join(PKG, "csrc", "*.cuh")) + glob.glob(os.path.join(PKG, "csrc", "*.h"))
+                               + glob.glob(os.path.join(INCLUDE, "vbh*.h"))),
         "out": os.path.join(PKG, "libvbh.so"),
     },
     "vbh_synth": {

@@ -90,6 +90,17 @@ def _lib():
             "vbh_fit_static": (ci, [vp, vp, i64, ci, P, O, R, ci, vp]),
             "vbh_fit_batched": (ci, [vp, ci, ctypes.POINTER(i64), ctypes.POINTER(ci), ctypes.POINTER(vp),
                                      ctypes.POINTER(vp), P, O, R]),
+            "vbh_ws_create": (ci, [ctypes.POINTER(vp), ci, ci, ctypes.c_uint64, ci, vp]),
+            "vbh_ws_destroy": (None, [vp]),
+            "vbh_ws_sizes": (ci, [vp, ctypes.POINTER(ci), ctypes.POINTER(ci), ctypes.POINTER(ctypes.c_size_t)]),
+            "vbh_ws_get_params": (ci, [vp, ctypes.POINTER(ctypes.c_float), ctypes.c_size_t]),
+            "vbh_ws_set_params": (ci, [vp, ctypes.POINTER(ctypes.c_float), ctypes.c_size_t]),
+            "vbh_ws_set_norm": (ci, [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]),
+            "vbh_ws_features": (ci, [vp, vp, vp, i64, ci, vp]),
+            "vbh_ws_forward": (ci, [vp, ci, ci, vp, vp]),
+            "vbh_ws_loss_grad": (ci, [vp, ci, ci, vp, vp, _dp, ctypes.POINTER(ctypes.c_float)]),
+            "vbh_ws_train_step": (ci, [vp, ci, ci, vp, vp, ctypes.c_float, _dp]),
+            "vbh_ws_predict": (ci, [vp, vp, vp, i64, P, ci, R]),
         }
         for name, (res, args) in sigs.items():
             f = getattr(lib, name)
@@ -348,3 +359,83 @@ def fit_static(r, d, S: int, prior: dict | None = None, tol: float = 1e-8, max_i
     if buf is not None:
         out["trace"] = buf[:res.iters + 1].copy()
     return out
+
+
+class WarmStart:
+    """The learned warm start (``include/vbh_ws.h``): a set encoder for one S.
+    Device buffers are torch tensors on the encoder's device."""
+
+    def __init__(self, S: int, hidden: int = 256, seed: int = 1, device: int = 0, stream=None):
+        lib = _lib()
+        self._m = ctypes.c_void_p()
+        st = getattr(stream, "cuda_stream", stream)
+        rc = lib.vbh_ws_create(ctypes.byref(self._m), int(S), int(hidden), ctypes.c_uint64(seed), int(device),
+                               ctypes.c_void_p(st) if st else None)
+        if rc != 0:
+            raise VBHError(rc, "vbh_ws_create")
+        F, P, n = ctypes.c_int(), ctypes.c_int(), ctypes.c_size_t()
+        lib.vbh_ws_sizes(self._m, ctypes.byref(F), ctypes.byref(P), ctypes.byref(n))
+        self.S, self.F, self.P, self.nparams = int(S), F.value, P.value, n.value
+
+    def close(self):
+        if self._m:
+            _lib().vbh_ws_destroy(self._m)
+            self._m = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(self.nparams, dtype=np.float32)
+        _check(_lib().vbh_ws_get_params(self._m, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), out.size),
+               "vbh_ws_get_params")
+        return out
+
+    def set_params(self, theta) -> None:
+        t = np.ascontiguousarray(theta, dtype=np.float32)
+        _check(_lib().vbh_ws_set_params(self._m, t.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), t.size),
+               "vbh_ws_set_params")
+
+    def set_norm(self, mean, std) -> None:
+        mu = np.ascontiguousarray(mean, dtype=np.float32)
+        sd = np.ascontiguousarray(std, dtype=np.float32)
+        fp = ctypes.POINTER(ctypes.c_float)
+        _check(_lib().vbh_ws_set_norm(self._m, mu.ctypes.data_as(fp), sd.ctypes.data_as(fp)), "vbh_ws_set_norm")
+        self.mean, self.std = mu.copy(), sd.copy()
+
+    def features(self, r, d, n: int, out):
+        _check(_lib().vbh_ws_features(self._m, _ptr(r), _ptr(d), int(r.shape[0]), int(n), _ptr(out)),
+               "vbh_ws_features")
+        return out
+
+    def forward(self, x, B: int, n: int, out):
+        _check(_lib().vbh_ws_forward(self._m, int(B), int(n), _ptr(x), _ptr(out)), "vbh_ws_forward")
+        return out
+
+    def loss_grad(self, x, target, B: int, n: int):
+        loss = ctypes.c_double()
+        g = np.empty(self.nparams, dtype=np.float32)
+        _check(_lib().vbh_ws_loss_grad(self._m, int(B), int(n), _ptr(x), _ptr(target), ctypes.byref(loss),
+                                       g.ctypes.data_as(ctypes.POINTER(ctypes.c_float))), "vbh_ws_loss_grad")
+        return loss.value, g
+
+    def train_step(self, x, target, B: int, n: int, lr: float) -> float:
+        loss = ctypes.c_double()
+        _check(_lib().vbh_ws_train_step(self._m, int(B), int(n), _ptr(x), _ptr(target), float(lr), ctypes.byref(loss)),
+               "vbh_ws_train_step")
+        return loss.value
+
+    def predict(self, r, d, prior: dict | None = None, n: int = 8192) -> dict:
+        pa = _PriorArgs(prior, self.S)
+        res = Result()
+        _check(_lib().vbh_ws_predict(self._m, _ptr(r), _ptr(d), int(r.shape[0]), ctypes.byref(pa.c), int(n),
+                                     ctypes.byref(res)), "vbh_ws_predict")
+        return result_to_dict(res)
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise VBHError(rc, what)
