@@ -303,8 +303,10 @@ int prepare_launch(vbh_handle *h, int S, long long V, int precision, const float
         L->gstats = h->gstats;
         long long g = (L->P + 7) / 8;                                            // 8 warps per block
         if (g > h->nsm) g = h->nsm;
+        if (g > vbh::GRID_MAX) g = vbh::GRID_MAX;
         L->grid = int(g);
-        return ensure(reinterpret_cast<void **>(&h->partials), &h->partials_cap, size_t(g) * nstat * sizeof(double));
+        return ensure(reinterpret_cast<void **>(&h->partials), &h->partials_cap,
+                      size_t(vbh::partial_rows(g)) * nstat * sizeof(double));
     }
     if (S <= vbh::S_FP32_MAX) {
         L->tc = false;
@@ -330,9 +332,11 @@ int prepare_launch(vbh_handle *h, int S, long long V, int precision, const float
     long long tiles = (V + L->tile() - 1) / L->tile();
     long long g = (long long)h->nsm * per_sm;
     if (tiles < g) g = tiles;
+    if (g > vbh::GRID_MAX) g = vbh::GRID_MAX;
     if (g < 1) g = 1;
     L->grid = int(g);
-    int rc = ensure(reinterpret_cast<void **>(&h->partials), &h->partials_cap, size_t(g) * nstat * sizeof(double));
+    int rc = ensure(reinterpret_cast<void **>(&h->partials), &h->partials_cap,
+                    size_t(vbh::partial_rows(g)) * nstat * sizeof(double));
     if (rc) return rc;
     if (L->tc && V > 0) {
         if ((rc = ensure(&h->tc_tiles, &h->tc_cap, vbh::tc_input_bytes(V)))) return rc;

@@ -289,6 +289,7 @@ __global__ void __launch_bounds__(256) batched_update_kernel(BatchClass bc, Batc
     using C = SweepCfg<M + 1>;
     global_update<M>(st, bc.partials + size_t(bc.ds_first_chunk[b]) * C::NSTAT, bc.ds_nchunks[b], a,
                      reinterpret_cast<double *>(smem));
+    __syncthreads();                                       // the control fields were written by another warp
     if (threadIdx.x == 0 && ds_running(st)) atomicAdd(&ctl->active, 1u);
 }
 

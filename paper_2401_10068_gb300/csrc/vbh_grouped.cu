@@ -139,18 +139,13 @@ __global__ void __launch_bounds__(GROUPED_THREADS) grouped_sweep_kernel(GroupArg
         for (int w = 0; w < GW; ++w) s += red[w * GNSTAT + j];
         part[j] = s;
     }
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) s_last = (atomicAdd(&st->ticket, 1u) == gridDim.x - 1) ? 1 : 0;
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
+    int row0, nrows;
+    if (!finish_ticket(st, a.partials, gridDim.x, NSTAT, &s_last, &row0, &nrows, gsm)) return;
     if (run && st->status == ST_OK) {
-        global_update_rt(M, st, a.partials, gridDim.x, a, gsm);
+        global_update_rt(M, st, a.partials + size_t(row0) * NSTAT, nrows, a, gsm);
     } else if (tid == 0 && a.use_cond) {
         cudaGraphSetConditional(a.cond, 0u);
     }
-    if (tid == 0) st->ticket = 0u;
 }
 
 const void *grouped_sweep_func() { return reinterpret_cast<const void *>(&grouped_sweep_kernel); }

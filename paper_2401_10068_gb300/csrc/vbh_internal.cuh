@@ -8,6 +8,19 @@
 namespace vbh {
 
 constexpr int MMAX = 31;             // largest M = S - 1
+// Block partials are reduced in one level up to TICKET_SINGLE_MAX blocks (the
+// block that finishes the launch sums all rows) and in two levels above: the
+// last block of each group of TICKET_GROUP consecutive blocks sums the group's
+// rows, the last group's reducer runs the global update over the group sums.
+constexpr int TICKET_SINGLE_MAX = 64;
+constexpr int TICKET_GROUP = 32;
+constexpr int TICKET_GROUPS_MAX = 40;
+constexpr int GRID_MAX = TICKET_GROUP * TICKET_GROUPS_MAX;  // largest sweep grid
+// rows of the partials buffer for a grid of nblk blocks: one per block, then one per group
+__host__ __device__ constexpr long long partial_rows(long long nblk)
+{
+    return nblk <= TICKET_SINGLE_MAX ? nblk : nblk + (nblk + TICKET_GROUP - 1) / TICKET_GROUP;
+}
 constexpr int SMAX = 32;
 constexpr int S_FP32_MAX = 11;       // largest S of the register-resident FP32 sweep
 
@@ -39,6 +52,13 @@ struct ElboConst {
     double sum_psi_nu;               // sum_{j=1..M} psi((nu + 1 - j)/2)
     double sum_lgamma_nu;            // sum_{j=1..M} lnGamma((nu + 1 - j)/2)
     double log_lam;
+    double log_nu, rs_nu;            // ln nu, 1/sqrt(nu)
+    double inv_lam, inv_V;           // 1/lambda, 1/V (0 when V = 0)
+    // the ELBO of Eq. 11 as an affine function of what a sweep changes:
+    //   L = e0 + e_logb ln b_rho - e_ldw ln|W^{-1}| - tr(E[Lambda] X)/2 - T4/2
+    //       + V ln|Sigma0~|/2 - E[rho] (b0 + T3/2)
+    // (X = C + Lambda_0^{-1} + q0 (kappa - K0)(kappa - K0)^T, C as in the update)
+    double e0, e_logb, e_ldw;
 };
 
 // FP64 state of one fit, resident in device memory.
@@ -62,6 +82,7 @@ struct DevState {
     double elbo, elbo_prev, tol;
     int iter, target, max_iter, converged, status, const_dropped;
     unsigned int ticket;             // last-block-done counter of a sweep launch
+    unsigned int gticket[TICKET_GROUPS_MAX];   // per-group counters of the two-level reduction
     int em;                          // 1: expectation maximisation (Eq. 42-47) instead of CAVI
     double *trace;                   // device array [max_iter + 1] (may be null)
     // per-fit constants: kc_upd for (a0 + V/2, n0 + V, q0 + V), kc_given for

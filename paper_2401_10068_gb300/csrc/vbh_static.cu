@@ -170,8 +170,8 @@ extern "C" int vbh_fit_static(const float *r, const float *d, int64_t V, int S, 
     long long grid = (long long)nsm * (per_sm > 0 ? per_sm : 1);
     const long long tiles = (V + ki.tile - 1) / ki.tile;
     if (tiles < grid) grid = tiles;
-    const long long cap = (long long)(PART_DOUBLES / size_t(ki.nstat));
-    if (grid > cap) grid = cap;
+    if (grid > vbh::GRID_MAX) grid = vbh::GRID_MAX;
+    while (grid > 1 && size_t(vbh::partial_rows(grid)) * size_t(ki.nstat) > PART_DOUBLES) --grid;
     if (grid < 1) grid = 1;
 
     // ---- the whole state is written by each call: nothing of an earlier call

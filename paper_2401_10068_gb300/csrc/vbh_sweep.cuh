@@ -180,41 +180,24 @@ __device__ __forceinline__ void flush_warp(float (&acc)[SweepCfg<S>::NSTAT], dou
 }
 
 // ---------------------------------------------------------------------------
-// Cholesky factor L (lower, row-major) of a symmetric positive-definite M x M
-// matrix A in shared memory, column by column, by one warp.  Returns nonzero
-// in every lane when A is not positive definite (a unit pivot is used then).
+// Named barriers of the global update (ids the sweep kernels leave unused).
+// The main warps (all but the last) synchronise on BAR_MAIN; the last warp,
+// the scalar warp, evaluates the logarithms and divisions of the update off
+// the matrix chain and waits on BAR_T3 for the reduced statistics and on
+// BAR_PIV for the Cholesky pivots.  FP64 divisions and logarithms are slow
+// next to FP64 multiply-adds, so keeping them off the chain is what sets the
+// latency of the update.
 // ---------------------------------------------------------------------------
-__device__ inline int warp_cholesky_rt(int M, const double *A, double *L, int lane)
+constexpr int BAR_MAIN = 1, BAR_T3 = 2, BAR_PIV = 3;
+
+__device__ __forceinline__ void named_sync(int id, int count)
 {
-    int fail = 0;
-    for (int i = lane; i < M * M; i += 32) L[i] = 0.0;
-    __syncwarp();
-    for (int j = 0; j < M; ++j) {
-        if (lane == 0) {
-            double s = A[j * M + j];
-            for (int k = 0; k < j; ++k) s -= L[j * M + k] * L[j * M + k];
-            if (!(s > 0.0) || !isfinite(s)) {
-                fail = 1;
-                s = 1.0;
-            }
-            L[j * M + j] = sqrt(s);
-        }
-        __syncwarp();
-        const double rjj = 1.0 / L[j * M + j];
-        for (int i = j + 1 + lane; i < M; i += 32) {
-            double s = A[i * M + j];
-            for (int k = 0; k < j; ++k) s -= L[i * M + k] * L[j * M + k];
-            L[i * M + j] = s * rjj;
-        }
-        __syncwarp();
-    }
-    return __shfl_sync(0xffffffffu, fail, 0);
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
-template <int M>
-__device__ __forceinline__ int warp_cholesky(const double *A, double *L, int lane)
+__device__ __forceinline__ void named_arrive(int id, int count)
 {
-    return warp_cholesky_rt(M, A, L, lane);
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
 // Sum over the lanes of a warp (fixed order).
@@ -225,41 +208,221 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
-// What the next data pass reads, from W^{-1} and nu (Eq. 28: E[Lambda] = nu W,
-// so Sigma0 = W^{-1}/nu): the FP32 Cholesky factor of Sigma0 (plus Sigma0 and
-// ln|Sigma0| for information).  Sweep 0 uses (Lambda_0^{-1}, nu = 1).  One
-// warp; Lw receives chol(W^{-1}); returns ln|W^{-1}| in every lane.  The
-// global update and the set-up kernel both use this function, so a fit
-// resumed from saved factors continues bit for bit.
-__device__ inline double derive_pass_globals_rt(int M, DevState *st, const double *Wn, double nu, double *Lw,
-                                                int lane, int *fail)
+// 1/sqrt(nu) as the pass factors use it (exactly 1 for nu = 1).
+__device__ __forceinline__ double rs_of(double nu) { return nu == 1.0 ? 1.0 : rsqrt(nu); }
+
+// ---------------------------------------------------------------------------
+// Cholesky factor L (lower, row-major, zero above the diagonal) of a symmetric
+// positive-definite M x M matrix A (M <= 32) in shared memory, by one warp,
+// right-looking: lane i owns row i; for column j every lane forms the
+// pivot's reciprocal square root r_j, the column below the pivot is scaled
+// by it and the trailing rows are updated in parallel.  rd[j] = 1/L_jj and
+// piv[j] = L_jj^2 (the pivots; their logarithms add up to ln|A|).  Returns
+// nonzero in every lane when A is not positive definite (a unit pivot is
+// used then).
+// ---------------------------------------------------------------------------
+__device__ inline int warp_cholesky_rt(int M, const double *A, double *L, double *rd, double *piv, int lane)
 {
-    *fail = warp_cholesky_rt(M, Wn, Lw, lane);
-    const double rs = rsqrt(nu);
-    for (int i = lane; i < M; i += 32)
-        for (int k = 0; k <= i; ++k) st->sw.L[i * (i + 1) / 2 + k] = static_cast<float>(Lw[i * M + k] * rs);
-    for (int i = lane; i < M * M; i += 32) st->Sigma0[i] = Wn[i] / nu;
-    const double ld = warp_sum(lane < M ? 2.0 * log(Lw[lane * M + lane]) : 0.0);
-    if (lane == 0) st->lndetSigma0 = ld - M * log(nu);
-    return ld;
+    const int MD = M > 0 ? M : 1;
+    for (int e = lane; e < M * M; e += 32) {
+        const int r = e / MD, c = e - (e / MD) * MD;
+        L[e] = (c <= r) ? A[e] : 0.0;
+    }
+    __syncwarp();
+    int fail = 0;
+    const int i = lane;
+    for (int j = 0; j < M; ++j) {
+        double p = L[j * M + j];
+        const bool bad = !(p > 0.0) || !isfinite(p);
+        if (bad) p = 1.0;
+        fail |= bad ? 1 : 0;
+        const double r = rsqrt(p);
+        __syncwarp();                               // the pivot is read before lane j overwrites it
+        if (i > j && i < M) {
+            L[i * M + j] *= r;
+        } else if (i == j) {
+            L[j * M + j] = p * r;
+            rd[j] = r;
+            piv[j] = p;
+        }
+        __syncwarp();
+        if (i > j && i < M) {
+            const double lij = L[i * M + j];
+            for (int k = j + 1; k <= i; ++k) L[i * M + k] = fma(-lij, L[k * M + j], L[i * M + k]);
+        }
+        __syncwarp();
+    }
+    return fail;
 }
 
-template <int M>
-__device__ __forceinline__ double derive_pass_globals(DevState *st, const double *Wn, double nu, double *Lw, int lane,
-                                                     int *fail)
+// Li = L^{-1} (lower) of a Cholesky factor L with reciprocal diagonal rd, by
+// one warp: lane c forms column c by forward substitution, subtracting each
+// finished row from the rows below it (lanes never wait on one another).
+__device__ inline void warp_tri_inverse_rt(int M, const double *L, const double *rd, double *Li, int lane)
 {
-    return derive_pass_globals_rt(M, st, Wn, nu, Lw, lane, fail);
+    const int c = lane;
+    if (c < M) {
+        for (int i = 0; i < M; ++i) Li[i * M + c] = (i == c) ? 1.0 : 0.0;
+        for (int i = 0; i < M; ++i) {
+            if (c <= i) {
+                const double x = Li[i * M + c] * rd[i];
+                Li[i * M + c] = x;
+                for (int l = i + 1; l < M; ++l) Li[l * M + c] = fma(-L[l * M + i], x, Li[l * M + c]);
+            }
+        }
+    }
+    __syncwarp();
+}
+
+// ln|A| from the pivots of its Cholesky factorisation (one warp, every lane).
+__device__ __forceinline__ double warp_logdet_rt(int M, const double *piv, int lane)
+{
+    return warp_sum(lane < M ? log(piv[lane]) : 0.0);
+}
+
+// What the next data pass reads, from W^{-1}, its Cholesky factor Lw and nu
+// (Eq. 28: E[Lambda] = nu W, so Sigma0 = W^{-1}/nu): the FP32 Cholesky
+// factor of Sigma0, and Sigma0 itself for information.  Threads t0, t0 + nt,
+// ... of the block.  The global update and the set-up kernel both use this
+// function and warp_cholesky_rt, so a fit resumed from saved factors
+// continues bit for bit.
+__device__ inline void write_pass_globals_rt(int M, DevState *st, const double *Wn, const double *Lw, double nu,
+                                             double rs, int t0, int nt)
+{
+    const int MD = M > 0 ? M : 1;
+    for (int e = t0; e < M * M; e += nt) {
+        const int r = e / MD, c = e - (e / MD) * MD;
+        st->Sigma0[e] = Wn[e] / nu;
+        if (c <= r) st->sw.L[r * (r + 1) / 2 + c] = static_cast<float>(Lw[e] * rs);
+    }
 }
 
 // ---------------------------------------------------------------------------
-// (d)+(e): FP64 global update, ELBO and control, run by the whole last block.
-// ws: shared-memory workspace of at least gu_ws_doubles(M) doubles.  The
-// statistics of the partials are laid out as in SweepCfg: packed lower G,
-// g, T3, T4 (ln of mantissas), E4 (binary exponents).
+// Column sums of rows [0, nrows) of a row-major [nrows][ns] FP64 array in
+// global memory, in a fixed order: thread t (t < R ns, of the first nt
+// threads) takes column t % ns and the t / ns-th of R chunks of consecutive
+// rows (four interleaved accumulators) and writes the chunk sum to red[t].
+// R = nt / ns clamped to [1, 8]; returns R.  FP64 additions are costly on
+// this hardware (one warp instruction every few dozen cycles), so the rows
+// are spread over as many threads as there are.
+// ---------------------------------------------------------------------------
+__device__ inline int chunk_sums(const double *__restrict__ part, int nrows, int ns, double *__restrict__ red,
+                                 int tid, int nt)
+{
+    int R = nt / ns;
+    R = R < 1 ? 1 : (R > 8 ? 8 : R);
+    const int len = (nrows + R - 1) / R;
+    for (int t = tid; t < R * ns; t += nt) {
+        const int c = t / ns, j = t - c * ns;
+        const int b0 = c * len, b1 = (b0 + len < nrows) ? b0 + len : nrows;
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        int b = b0;
+        for (; b + 3 < b1; b += 4) {
+            s0 += __ldcg(part + size_t(b) * ns + j);
+            s1 += __ldcg(part + size_t(b + 1) * ns + j);
+            s2 += __ldcg(part + size_t(b + 2) * ns + j);
+            s3 += __ldcg(part + size_t(b + 3) * ns + j);
+        }
+        for (; b < b1; ++b) s0 += __ldcg(part + size_t(b) * ns + j);
+        red[t] = (s0 + s1) + (s2 + s3);
+    }
+    return R;
+}
+
+// Total of column j from the R chunk sums of chunk_sums (chunk order).
+__device__ __forceinline__ double chunk_total(const double *red, int R, int ns, int j)
+{
+    double s0 = 0.0, s1 = 0.0;
+    int c = 0;
+    for (; c + 1 < R; c += 2) {
+        s0 += red[c * ns + j];
+        s1 += red[(c + 1) * ns + j];
+    }
+    if (c < R) s0 += red[c * ns + j];
+    return s0 + s1;
+}
+
+// ---------------------------------------------------------------------------
+// Completion of a sweep launch, called by every thread of every block after
+// the block wrote its row of `part` ([nblk][ns] FP64, then one row per
+// group).  Thread 0 publishes the block's writes (a CTA barrier, then a
+// device-scope fence before the counter) and takes a ticket.  Up to
+// TICKET_SINGLE_MAX blocks the last block to arrive finishes the launch and
+// reads every row.  Above, the last block of each group of TICKET_GROUP
+// blocks sums the group's rows (fixed order, scratch: >= 512 doubles of
+// shared memory) into the group's row and takes a second ticket; the last
+// group's reducer finishes the launch and reads the group rows.  Returns true
+// in the finishing block only, with the rows it reads in [*row0, *row0 +
+// *nrows).  Counters are reset by the block that read them.
+// ---------------------------------------------------------------------------
+__device__ inline bool finish_ticket(DevState *st, double *part, int nblk, int ns, volatile int *s_flag, int *row0,
+                                     int *nrows, double *scratch)
+{
+    const int tid = threadIdx.x, nth = blockDim.x;
+    __syncthreads();
+    if (nblk <= TICKET_SINGLE_MAX) {
+        if (tid == 0) {
+            __threadfence();
+            const int last = (atomicAdd(&st->ticket, 1u) == unsigned(nblk - 1)) ? 1 : 0;
+            if (last) {
+                __threadfence();
+                st->ticket = 0u;
+            }
+            *s_flag = last;
+        }
+        __syncthreads();
+        if (!*s_flag) return false;
+        *row0 = 0;
+        *nrows = nblk;
+        return true;
+    }
+    const int g = blockIdx.x / TICKET_GROUP, ng = (nblk + TICKET_GROUP - 1) / TICKET_GROUP;
+    const int b0 = g * TICKET_GROUP;
+    const int gsz = (nblk - b0 < TICKET_GROUP) ? nblk - b0 : TICKET_GROUP;
+    if (tid == 0) {
+        __threadfence();
+        const int last = (atomicAdd(&st->gticket[g], 1u) == unsigned(gsz - 1)) ? 1 : 0;
+        if (last) {
+            __threadfence();
+            st->gticket[g] = 0u;
+        }
+        *s_flag = last;
+    }
+    __syncthreads();
+    if (!*s_flag) return false;
+    const int R = chunk_sums(part + size_t(b0) * ns, gsz, ns, scratch, tid, nth);
+    __syncthreads();
+    double *out = part + size_t(nblk + g) * ns;
+    for (int j = tid; j < ns; j += nth) out[j] = chunk_total(scratch, R, ns, j);
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        const int last = (atomicAdd(&st->ticket, 1u) == unsigned(ng - 1)) ? 1 : 0;
+        if (last) {
+            __threadfence();
+            st->ticket = 0u;
+        }
+        *s_flag = last;
+    }
+    __syncthreads();
+    if (!*s_flag) return false;
+    *row0 = nblk;
+    *nrows = ng;
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// (d)+(e): FP64 global update, ELBO and control, run by the whole block that
+// finishes the launch (blockDim.x a multiple of 32, at least 96 threads).
+// part: nrows rows of per-block (or per-group) statistics, laid out as in
+// SweepCfg: packed lower G, g, T3, T4 (ln of mantissas), E4 (binary
+// exponents).  ws: shared-memory workspace of at least gu_ws_doubles(M)
+// doubles.
 // ---------------------------------------------------------------------------
 __host__ __device__ constexpr int gu_ws_doubles_rt(int M)
 {
-    return ((M * (M + 1) / 2 + M + 3 + 31) / 32) * 32 + 9 * (M > 0 ? M * M : 1) + 6 * (M > 0 ? M : 1) + 32;
+    // statistics (rounded up to 32), 10 M x M matrices, 9 M-vectors, 32 scalars, 512 of reduction scratch
+    return ((M * (M + 1) / 2 + M + 3 + 31) / 32) * 32 + 10 * (M > 0 ? M * M : 1) + 9 * (M > 0 ? M : 1) + 32 + 512;
 }
 
 template <int M>
@@ -268,20 +431,23 @@ constexpr int gu_ws_doubles()
     return gu_ws_doubles_rt(M);
 }
 
-__device__ inline void global_update_rt(int M, DevState *st, const double *__restrict__ part, int nblk,
-                                        const SweepArgs &a, double *ws)
+__device__ __forceinline__ void global_update_rt(int M, DevState *st, const double *__restrict__ part, int nrows,
+                                                 const SweepArgs &a, double *ws)
 {
     const int NG = M * (M + 1) / 2;
     const int NSTAT = NG + M + 3;
-    const int I_g = NG, I_T3 = NG + M, I_T4 = NG + M + 1, I_E4 = NG + M + 2;
+    const int I_T3 = NG + M, I_T4 = NG + M + 1, I_E4 = NG + M + 2;
     const int MM = M > 0 ? M * M : 1;
     const int MV = M > 0 ? M : 1;
     const int MD = M > 0 ? M : 1;                   // divisor (loops over M*M entries are empty at M = 0)
     constexpr double LN2PI = 1.8378770664093454836;
     constexpr double LN2 = 0.69314718055994530942;
-    constexpr double LNPI = 1.1447298858494002;
     const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
+    const int nthm = nth - 32;                      // threads of the main warps
     const int mode = a.mode;
+    const bool em = st->em != 0;
+    const bool elbo_only = (mode == MODE_ELBO) && !em;   // the ELBO of given factors: nothing is updated
+    const ElboConst *kc = (mode == MODE_ELBO) ? &st->kc_given : &st->kc_upd;
 
     double *stat = ws;
     double *Sg = stat + ((NSTAT + 31) / 32) * 32;   // Sigma0~ = L~ L~^T of this pass
@@ -291,266 +457,274 @@ __device__ inline void global_update_rt(int M, DevState *st, const double *__res
     double *Wn = B + MM;                            // new W^{-1}
     double *Lw = Wn + MM;                           // chol(W^{-1})
     double *Li = Lw + MM;                           // Lw^{-1}
-    double *EL = Li + MM;                           // E[Lambda] = nu W
-    double *Cm = EL + MM;                           // sum_i E[(beta_i - kappa')(beta_i - kappa')^T]
-    double *sv = Cm + MM;                           // Sigma0~ g
+    double *X = Li + MM;                            // C + Lambda_0^{-1} + q0 (kappa'-K0)(kappa'-K0)^T
+    double *Lf = X + MM;                            // L~ (packed) in FP64
+    double *L0s = Lf + MM;                          // Lambda_0^{-1}
+    double *sv = L0s + MM;                          // Sigma0~ g
     double *dv = sv + MV;                           // kappa' - kappa~
     double *ko = dv + MV;                           // kappa~ (this pass)
     double *kn = ko + MV;                           // kappa'
     double *av = kn + MV;                           // K0 - kappa~
     double *gv = av + MV;                           // g
-    double *sc = gv + MV;                           // scalars
+    double *rd = gv + MV;                           // 1 / diag(Lw)
+    double *piv = rd + MV;                          // Cholesky pivots of W'^{-1}
+    double *K0s = piv + MV;                         // K0
+    double *sc = K0s + MV;                          // scalars
+    double *red = sc + 32;                          // reduction scratch [R][NSTAT]
     __shared__ int s_fail;
 
-    // 1. partials -> totals (fixed order per statistic); Sigma0~, kappa~.
-    //    The data pass used the FP32 factor L~ and kappa~ of st->sw; its
-    //    Q(beta_i) is the exact Eq. 20-21 posterior for Sigma0~ = L~ L~^T and
-    //    kappa~, so every FP64 quantity below is taken with those values: each
-    //    sweep is an exact coordinate step from the rounded globals and the
-    //    ELBO sequence is smooth (FP32 rounding enters at second order only).
-    for (int j = warp; j < NSTAT; j += nwarp) {
-        double s = 0.0;
-#pragma unroll 4
-        for (int b = lane; b < nblk; b += 32) s += __ldcg(part + size_t(b) * NSTAT + j);
-        s = warp_sum(s);
-        if (lane == 0) stat[j] = s;
-    }
-    if (warp == nwarp - 1) {
-        const double ld = warp_sum(lane < M ? 2.0 * log(static_cast<double>(st->sw.L[lane * (lane + 1) / 2 + lane]))
-                                            : 0.0);
-        if (lane == 0) {
-            sc[1] = ld;                                  // ln|Sigma0~|
-            s_fail = 0;
+    if (warp < nwarp - 1) {
+        const double V = st->V, q0 = st->q0;
+        const double inv_V = kc->inv_V, inv_lam = kc->inv_lam, lam = kc->lam, nu = kc->nu, rs_nu = kc->rs_nu;
+        // 1. rows -> chunk sums; FP64 copies of the pass factors and of the
+        //    prior.  The data pass used the FP32 factor L~ and kappa~ of st->sw;
+        //    its Q(beta_i) is the exact Eq. 20-21 posterior for Sigma0~ = L~ L~^T
+        //    and kappa~, so every FP64 quantity below is taken with those
+        //    values: each sweep is an exact coordinate step from the rounded
+        //    globals and the ELBO sequence is smooth (FP32 rounding enters at
+        //    second order only).
+        const int R = chunk_sums(part, nrows, NSTAT, red, tid, nthm);
+        for (int e = tid; e < NG; e += nthm) Lf[e] = static_cast<double>(st->sw.L[e]);
+        for (int e = tid; e < M * M; e += nthm) {
+            L0s[e] = st->L0inv[e];
+            if (elbo_only) Wn[e] = st->Winv[e];
         }
-    }
-    for (int i = tid; i < M * M; i += nth) {
-        const int r = i / MD, c = i % MD;
-        const int kmax = r < c ? r : c;
-        double s = 0.0;
-        for (int k = 0; k <= kmax; ++k)
-            s = fma(static_cast<double>(st->sw.L[r * (r + 1) / 2 + k]), static_cast<double>(st->sw.L[c * (c + 1) / 2 + k]), s);
-        Sg[i] = s;
-    }
-    for (int i = tid; i < M; i += nth) {
-        ko[i] = static_cast<double>(st->sw.kappa[i]);
-        av[i] = st->K0[i] - ko[i];
-    }
-    __syncthreads();
-
-    const ElboConst kc = (mode == MODE_ELBO) ? st->kc_given : st->kc_upd;
-    // EM (Eq. 42-47): the pass used the point estimates K~ = kappa~, Lambda^{-1}~ =
-    // Sigma0~ and rho~ = E[rho] of sw; the statistics of the pass are the same sums
-    const bool em = st->em != 0;
-    const double V = st->V;
-    const double T3 = stat[I_T3];
-    const double T4 = stat[I_T4] + LN2 * stat[I_E4];
-    const double q0 = st->q0, n0 = st->n0, b0 = st->b0, a0 = st->a0;
-    const double lam = kc.lam, nu = kc.nu;
-
-    // 2. G (full), g, s = Sigma0~ g, A = Sigma0~ G
-    for (int i = tid; i < M * M; i += nth) {
-        const int r = i / MD, c = i % MD;
-        G[i] = (r >= c) ? stat[r * (r + 1) / 2 + c] : stat[c * (c + 1) / 2 + r];
-    }
-    for (int i = tid; i < M; i += nth) gv[i] = stat[I_g + i];
-    __syncthreads();
-    for (int i = tid; i < M * M; i += nth) {
-        const int r = i / MD, c = i % MD;
-        double s = 0.0;
-        for (int k = 0; k < M; ++k) s = fma(Sg[r * M + k], G[k * M + c], s);
-        A[i] = s;
-    }
-    for (int i = tid; i < M; i += nth) {
-        double s = 0.0;
-        for (int k = 0; k < M; ++k) s = fma(Sg[i * M + k], gv[k], s);
-        sv[i] = s;
-    }
-    __syncthreads();
-    // 3. B = Sigma0~ G Sigma0~, delta, kappa'
-    for (int i = tid; i < M * M; i += nth) {
-        const int r = i / MD, c = i % MD;
-        double s = 0.0;
-        for (int k = 0; k < M; ++k) s = fma(A[r * M + k], Sg[k * M + c], s);
-        B[i] = s;
-    }
-    for (int i = tid; i < M; i += nth) {
-        if (em) {                                   // Eq. 46: K' = (1/V) sum M_i = K~ + Sigma0~ g / V
-            dv[i] = sv[i] / V;
-            kn[i] = ko[i] + dv[i];
-        } else if (mode == MODE_ELBO) {             // kappa is given; kappa~ is its FP32 rounding
-            kn[i] = st->kappa[i];
-            dv[i] = kn[i] - ko[i];
-        } else {
-            dv[i] = (sv[i] + q0 * av[i]) / lam;     // Eq. 24, centred on kappa~
-            kn[i] = ko[i] + dv[i];
+        for (int i = tid; i < M; i += nthm) {
+            ko[i] = static_cast<double>(st->sw.kappa[i]);
+            K0s[i] = st->K0[i];
+            av[i] = K0s[i] - ko[i];
+            if (mode == MODE_ELBO && !em) kn[i] = st->kappa[i];
         }
-    }
-    __syncthreads();
-    // 4. W'^{-1} (Eq. 25, centred) and C
-    for (int i = tid; i < M * M; i += nth) {
-        const int r = i / MD, c = i % MD;
-        const double Bs = 0.5 * (B[r * M + c] + B[c * M + r]);
-        if (em) {
-            // Eq. 47: (1/V) sum (M_i M_i^T + Sigma_i) - K' K'^T = Sigma0~ + Sigma0~ G Sigma0~ / V - a a^T
-            Wn[i] = Sg[i] + Bs / V - dv[r] * dv[c];
-        } else if (mode == MODE_ELBO) {
-            Wn[i] = st->Winv[i];
-        } else {
-            Wn[i] = st->L0inv[i] + V * Sg[i] + Bs + q0 * av[r] * av[c] - lam * dv[r] * dv[c];
-        }
-        // C = V Sigma0~ + Sigma0~ G Sigma0~ - s delta^T - delta s^T + V delta delta^T
-        Cm[i] = V * Sg[i] + Bs - sv[r] * dv[c] - dv[r] * sv[c] + V * dv[r] * dv[c];
-    }
-    __syncthreads();
-    // 5. Cholesky of W'^{-1} (warp 0) and, unless only the ELBO is wanted,
-    //    the FP32 factor of the next data pass; Lw^{-1}
-    if (warp == 0) {
-        int fail;
-        double lndetWn;
-        if (mode == MODE_ELBO && !em) {
-            fail = warp_cholesky_rt(M, Wn, Lw, lane);
-            lndetWn = warp_sum(lane < M ? 2.0 * log(Lw[lane * M + lane]) : 0.0);
-        } else {
-            lndetWn = derive_pass_globals_rt(M, st, Wn, em ? 1.0 : nu, Lw, lane, &fail);
-        }
-        if (lane == 0) {
-            if (fail) s_fail = 1;
-            sc[2] = lndetWn;
-        }
-        __syncwarp();
-        for (int c = lane; c < M; c += 32) {        // lane c solves Lw x = e_c
-            for (int i = 0; i < c; ++i) Li[i * M + c] = 0.0;
-            for (int i = c; i < M; ++i) {
-                double s = (i == c) ? 1.0 : 0.0;
-                for (int k = c; k < i; ++k) s -= Lw[i * M + k] * Li[k * M + c];
-                Li[i * M + c] = s / Lw[i * M + i];
+        if (tid == 0) s_fail = 0;
+        named_sync(BAR_MAIN, nthm);
+        //    chunk sums -> totals, scattered into G (full) and g; Sigma0~
+        for (int j = tid; j < NSTAT; j += nthm) {
+            const double s = chunk_total(red, R, NSTAT, j);
+            stat[j] = s;
+            if (j < NG) {
+                int r = static_cast<int>((sqrtf(8.0f * j + 1.0f) - 1.0f) * 0.5f);
+                while (r * (r + 1) / 2 > j) --r;
+                while ((r + 1) * (r + 2) / 2 <= j) ++r;
+                const int cc = j - r * (r + 1) / 2;
+                G[r * M + cc] = s;
+                G[cc * M + r] = s;
+            } else if (j < NG + M) {
+                gv[j - NG] = s;
             }
         }
+        named_arrive(BAR_T3, nth);                  // the statistics are in place for the scalar warp
+        for (int e = tid; e < M * M; e += nthm) {
+            const int r = e / MD, c = e - r * MD;
+            const int kmax = r < c ? r : c;
+            double s = 0.0;
+            for (int k = 0; k <= kmax; ++k) s = fma(Lf[r * (r + 1) / 2 + k], Lf[c * (c + 1) / 2 + k], s);
+            Sg[e] = s;
+        }
+        named_sync(BAR_MAIN, nthm);
+
+        // 2. A = Sigma0~ G, s = Sigma0~ g
+        for (int e = tid; e < M * M; e += nthm) {
+            const int r = e / MD, c = e - r * MD;
+            double s0 = 0.0, s1 = 0.0;
+            int k = 0;
+            for (; k + 1 < M; k += 2) {
+                s0 = fma(Sg[r * M + k], G[k * M + c], s0);
+                s1 = fma(Sg[r * M + k + 1], G[(k + 1) * M + c], s1);
+            }
+            if (k < M) s0 = fma(Sg[r * M + k], G[k * M + c], s0);
+            A[e] = s0 + s1;
+        }
+        for (int i = tid; i < M; i += nthm) {
+            double s0 = 0.0, s1 = 0.0;
+            int k = 0;
+            for (; k + 1 < M; k += 2) {
+                s0 = fma(Sg[i * M + k], gv[k], s0);
+                s1 = fma(Sg[i * M + k + 1], gv[k + 1], s1);
+            }
+            if (k < M) s0 = fma(Sg[i * M + k], gv[k], s0);
+            sv[i] = s0 + s1;
+        }
+        named_sync(BAR_MAIN, nthm);
+        // 3. B = Sigma0~ G Sigma0~, delta, kappa'
+        for (int e = tid; e < M * M; e += nthm) {
+            const int r = e / MD, c = e - r * MD;
+            double s0 = 0.0, s1 = 0.0;
+            int k = 0;
+            for (; k + 1 < M; k += 2) {
+                s0 = fma(A[r * M + k], Sg[k * M + c], s0);
+                s1 = fma(A[r * M + k + 1], Sg[(k + 1) * M + c], s1);
+            }
+            if (k < M) s0 = fma(A[r * M + k], Sg[k * M + c], s0);
+            B[e] = s0 + s1;
+        }
+        for (int i = tid; i < M; i += nthm) {
+            if (em) {                               // Eq. 46: K' = (1/V) sum M_i = K~ + Sigma0~ g / V
+                dv[i] = sv[i] * inv_V;
+                kn[i] = ko[i] + dv[i];
+            } else if (mode == MODE_ELBO) {         // kappa is given; kappa~ is its FP32 rounding
+                dv[i] = kn[i] - ko[i];
+            } else {
+                dv[i] = fma(q0, av[i], sv[i]) * inv_lam;   // Eq. 24, centred on kappa~
+                kn[i] = ko[i] + dv[i];
+            }
+        }
+        named_sync(BAR_MAIN, nthm);
+        // 4. W'^{-1} (Eq. 25, centred) and X
+        for (int e = tid; e < M * M; e += nthm) {
+            const int r = e / MD, c = e - r * MD;
+            const double Bs = 0.5 * (B[r * M + c] + B[c * M + r]);
+            if (em) {
+                // Eq. 47: (1/V) sum (M_i M_i^T + Sigma_i) - K' K'^T = Sigma0~ + Sigma0~ G Sigma0~ / V - a a^T
+                Wn[e] = fma(Bs, inv_V, Sg[e]) - dv[r] * dv[c];
+            } else {
+                if (!elbo_only) Wn[e] = L0s[e] + V * Sg[e] + Bs + q0 * av[r] * av[c] - lam * dv[r] * dv[c];
+                // C = V Sigma0~ + Sigma0~ G Sigma0~ - s delta^T - delta s^T + V delta delta^T
+                const double Cm = V * Sg[e] + Bs - sv[r] * dv[c] - dv[r] * sv[c] + V * dv[r] * dv[c];
+                X[e] = Cm + L0s[e] + q0 * (kn[r] - K0s[r]) * (kn[c] - K0s[c]);
+            }
+        }
+        named_sync(BAR_MAIN, nthm);
+        // 5. Cholesky of W'^{-1} (warp 0); its pivots go to the scalar warp
+        if (warp == 0) {
+            const int fail = warp_cholesky_rt(M, Wn, Lw, rd, piv, lane);
+            if (lane == 0 && fail) s_fail = 1;
+            named_arrive(BAR_PIV, 64);
+        }
+        named_sync(BAR_MAIN, nthm);
+        // 6. warp 0: tr(E[Lambda] X) with E[Lambda] = nu Li^T Li (Eq. 28);
+        //    warp 1 (EM): tr(Sigma0~ G); the other main warps: the new globals
+        if (warp == 0) {
+            if (!em) {
+                warp_tri_inverse_rt(M, Lw, rd, Li, lane);
+                double t0 = 0.0;
+                for (int e = lane; e < M * M; e += 32) {
+                    const int r = e / MD, c = e - r * MD;
+                    double e0 = 0.0, e1 = 0.0;
+                    int k = r > c ? r : c;
+                    for (; k + 1 < M; k += 2) {
+                        e0 = fma(Li[k * M + r], Li[k * M + c], e0);
+                        e1 = fma(Li[(k + 1) * M + r], Li[(k + 1) * M + c], e1);
+                    }
+                    if (k < M) e0 = fma(Li[k * M + r], Li[k * M + c], e0);
+                    t0 = fma(X[e], e0 + e1, t0);
+                }
+                const double t = warp_sum(t0);
+                if (lane == 0) sc[6] = nu * t;
+            }
+        } else {
+            if (em && warp == 1) {
+                double t1 = 0.0;
+                for (int e = lane; e < M * M; e += 32) t1 = fma(Sg[e], G[e], t1);
+                const double t = warp_sum(t1);
+                if (lane == 0) sc[7] = t;
+            }
+            if (!elbo_only) {
+                write_pass_globals_rt(M, st, Wn, Lw, em ? 1.0 : nu, em ? 1.0 : rs_nu, tid - 32, nthm - 32);
+                for (int e = tid - 32; e < M * M; e += nthm - 32) st->Winv[e] = Wn[e];
+                for (int i = tid - 32; i < M; i += nthm - 32) {
+                    st->kappa[i] = kn[i];
+                    st->sw.kappa[i] = static_cast<float>(kn[i]);
+                }
+            }
+        }
+        __syncthreads();
+        return;
     }
-    __syncthreads();
-    // 6. E[Lambda] = nu Li^T Li (Eq. 28)
-    for (int i = tid; i < M * M; i += nth) {
-        const int r = i / MD, c = i % MD;
-        double s = 0.0;
-        for (int k = (r > c ? r : c); k < M; ++k) s = fma(Li[k * M + r], Li[k * M + c], s);
-        EL[i] = nu * s;
+
+    // the scalar warp: what the final step reads, loaded while the main warps
+    // reduce; ln|Sigma0~| of this pass (and, for EM, ln rho~); then E[rho]
+    // and ln b_rho (Eq. 16-17, 29) or rho' = V / T3 (Eq. 45); then ln|W'^{-1}|;
+    // then (lane 0) the ELBO, control and the scalar globals
+    const double V = st->V, b0 = st->b0, tol = st->tol, elbo_prev = st->elbo_prev, given_brho = st->b_rho;
+    const double a_rho = kc->a_rho, e0 = kc->e0, e_logb = kc->e_logb, e_ldw = kc->e_ldw, log_nu = kc->log_nu;
+    const double nu = kc->nu, lam = kc->lam;
+    const int iter = st->iter, target = st->target, max_iter = st->max_iter, status = st->status;
+    const int prior_dropped = st->prior_dropped;
+    double *trace = st->trace;
+    const float erho_f = st->sw.erho;
+    double x = 1.0;
+    if (lane < M) x = static_cast<double>(st->sw.L[lane * (lane + 1) / 2 + lane]);
+    else if (lane == 31 && em) x = static_cast<double>(erho_f);
+    const double lx = log(x);
+    const double lnS0 = warp_sum(lane < M ? 2.0 * lx : 0.0);
+    const double lr = __shfl_sync(0xffffffffu, lx, 31);
+    named_sync(BAR_T3, nth);
+    const double T3 = stat[I_T3];
+    const double T4 = fma(LN2, stat[I_E4], stat[I_T4]);
+    double q, lb = 0.0, brho = 0.0;
+    if (em) {
+        q = V / T3;                                 // rho' (Eq. 45)
+    } else {
+        brho = elbo_only ? given_brho : fma(0.5, T3, b0);
+        q = a_rho / brho;                           // E[rho]
+        lb = log(brho);
     }
+    named_sync(BAR_PIV, 64);
+    const double ldW = warp_logdet_rt(M, piv, lane);
     __syncthreads();
-    // 7. traces (warp 0), then the ELBO (or, for EM, ln p(r | theta)) and control (thread 0)
-    if (em && warp == 0) {
+    if (lane != 0) return;
+
+    double L;
+    bool finite;
+    if (em) {
         // ln p(r | theta~) = sum_i ln N(y_i; D_i^T K~, 1/rho~ + q_i): with the pass's sums,
         // V/2 (ln rho~ - ln 2 pi) - rho~/2 sum S_i - 1/2 sum ln(1 + rho~ q_i) - 1/2 tr(Sigma0~ G)
-        double t1 = 0.0;
-        for (int i = lane; i < M * M; i += 32) t1 = fma(Sg[i], G[i], t1);
-        const double trSG = warp_sum(t1);
-        if (lane == 0) {
-            const double rho_t = static_cast<double>(st->sw.erho);
-            const double L = 0.5 * V * (log(rho_t) - LN2PI) - 0.5 * rho_t * T3 - 0.5 * T4 - 0.5 * trSG;
-            const double rho_n = V / T3;                                             // Eq. 45
-            bool finite = isfinite(L) && isfinite(rho_n) && rho_n > 0.0 && !s_fail;
-            for (int j = 0; j < M; ++j) finite = finite && isfinite(kn[j]);
-            st->elbo = L;
-            st->const_dropped = 0;
-            st->a_rho = rho_n;                                                       // point estimate as (rho, 1)
-            st->b_rho = 1.0;
-            st->nu = 1.0;
-            st->lam = V;
-            st->erho = rho_n;
-            if (mode == MODE_INIT) {
-                st->iter = 0;
-                st->converged = 0;
-            } else {
-                st->iter += 1;
-                st->converged = (fabs(L - st->elbo_prev) < st->tol * fabs(L)) ? 1 : 0;
-            }
-            if (st->trace && st->iter <= st->max_iter) st->trace[st->iter] = L;
-            st->elbo_prev = L;
-            if (!finite && st->status == ST_OK) st->status = ST_ENONFINITE;
-            sc[0] = rho_n;
+        L = 0.5 * V * (lr - LN2PI) - 0.5 * (fma(static_cast<double>(erho_f), T3, T4) + sc[7]);
+        finite = isfinite(L) && isfinite(q) && q > 0.0 && !s_fail;
+        st->a_rho = q;                              // point estimate as (rho, 1)
+        st->b_rho = 1.0;
+        st->nu = 1.0;
+        st->lam = V;
+        st->const_dropped = 0;
+    } else {
+        const double erb = elbo_only ? q * fma(0.5, T3, b0) : a_rho;   // E[rho] (b0 + T3/2)
+        L = (fma(e_logb, lb, e0) - fma(e_ldw, ldW, 0.5 * sc[6])) + (fma(0.5 * V, lnS0, -0.5 * T4) - erb);
+        finite = isfinite(L) && isfinite(brho) && brho > 0.0 && !s_fail;
+        st->const_dropped = prior_dropped;
+        if (!elbo_only) {
+            st->a_rho = a_rho;
+            st->b_rho = brho;
+            st->nu = nu;
+            st->lam = lam;
         }
     }
-    if (!em && warp == 0) {
-        double t1 = 0.0, t2 = 0.0, t3 = 0.0;
-        for (int i = lane; i < M * M; i += 32) {
-            const int r = i / MD, c = i % MD;
-            t1 = fma(EL[i], Cm[i], t1);                                   // tr(E[Lambda] C), both symmetric
-            t2 = fma(st->L0inv[i], EL[i], t2);                            // tr(Lambda_0^{-1} E[Lambda])
-            t3 = fma((kn[r] - st->K0[r]) * EL[i], kn[c] - st->K0[c], t3);  // (kappa'-K0)^T E[Lambda] (kappa'-K0)
+    for (int j = 0; j < M; ++j) finite = finite && isfinite(kn[j]);
+    st->elbo = L;
+    int it = iter, conv = 0;
+    if (!elbo_only) {
+        st->erho = q;
+        st->sw.erho = static_cast<float>(q);
+        st->lndetSigma0 = em ? ldW : fma(-double(M), log_nu, ldW);
+        if (mode != MODE_INIT) {
+            it = iter + 1;
+            conv = (fabs(L - elbo_prev) < tol * fabs(L)) ? 1 : 0;
+        } else {
+            it = 0;
         }
-        const double trELC = warp_sum(t1), trL0EL = warp_sum(t2), quadK = warp_sum(t3);
-        if (lane == 0) {
-            const double lndetS0 = sc[1];
-            const double lndetW = -sc[2];
-            const double a_rho = kc.a_rho;                                           // Eq. 16
-            const double b_rho = (mode == MODE_ELBO) ? st->b_rho : b0 + 0.5 * T3;    // Eq. 17
-            const double Er = a_rho / b_rho;                                         // Eq. 29
-            const double logb = log(b_rho);
-            const double Elr = kc.psi_a - logb;
-            const double ElL = kc.sum_psi_nu + M * LN2 + lndetW;
-            const double lnBq = -0.5 * nu * lndetW - 0.5 * nu * M * LN2 - 0.25 * M * (M - 1) * LNPI - kc.sum_lgamma_nu;
-            double L = st->prior_const;
-            L += 0.5 * V * (Elr - LN2PI) - 0.5 * Er * T3;                            // E ln p(r | beta, rho)
-            L += 0.5 * V * (ElL - M * LN2PI) - 0.5 * trELC - 0.5 * V * M / lam;     // E ln p(beta | K, Lambda)
-            L += 0.5 * ElL - 0.5 * q0 * (quadK + M / lam);                           // E ln p(K | Lambda)
-            L += 0.5 * (n0 - M - 1.0) * ElL - 0.5 * trL0EL;                          // E ln p(Lambda)
-            L += (a0 - 1.0) * Elr - b0 * Er;                                         // E ln p(rho)
-            L += 0.5 * (V * lndetS0 - T4) + 0.5 * V * M * (1.0 + LN2PI);             // H[Q(beta)]
-            L += -0.5 * ElL - 0.5 * M * (kc.log_lam - LN2PI) + 0.5 * M;              // H[Q(K | Lambda)]
-            if (M > 0) L += -lnBq - 0.5 * (nu - M - 1.0) * ElL + 0.5 * nu * M;      // H[Q(Lambda)]
-            L += a_rho - logb + kc.lgamma_a + (1.0 - a_rho) * kc.psi_a;              // H[Q(rho)]
-
-            bool finite = isfinite(L) && isfinite(b_rho) && b_rho > 0.0 && !s_fail;
-            for (int j = 0; j < M; ++j) finite = finite && isfinite(kn[j]);
-            st->elbo = L;
-            st->const_dropped = st->prior_dropped;
-            if (mode != MODE_ELBO) {
-                st->a_rho = a_rho;
-                st->b_rho = b_rho;
-                st->nu = nu;
-                st->lam = lam;
-                st->erho = Er;
-                if (mode == MODE_INIT) {
-                    st->iter = 0;
-                    st->converged = 0;
-                } else {
-                    st->iter += 1;
-                    st->converged = (fabs(L - st->elbo_prev) < st->tol * fabs(L)) ? 1 : 0;
-                }
-                if (st->trace && st->iter <= st->max_iter) st->trace[st->iter] = L;
-                st->elbo_prev = L;
-            } else {
-                // sweep 0 of a fit started from given factors: L_0 of that state
-                st->elbo_prev = L;
-                if (st->trace) st->trace[0] = L;
-            }
-            if (!finite && st->status == ST_OK) st->status = ST_ENONFINITE;
-            sc[0] = Er;
-        }
+        st->iter = it;
+        st->converged = conv;
+        if (trace && it <= max_iter) trace[it] = L;
+    } else if (trace) {
+        trace[0] = L;                               // sweep 0 of a fit started from given factors: L_0 of that state
     }
-    __syncthreads();
-    // 8. write the new globals and the FP32 inputs of the next sweep
-    if (mode != MODE_ELBO || em) {
-        for (int i = tid; i < M * M; i += nth) st->Winv[i] = Wn[i];
-        for (int i = tid; i < M; i += nth) {
-            st->kappa[i] = kn[i];
-            st->sw.kappa[i] = static_cast<float>(kn[i]);
-        }
-        if (tid == 0) st->sw.erho = static_cast<float>(sc[0]);
+    st->elbo_prev = L;
+    int stat_now = status;
+    if (!finite && status == ST_OK) {
+        st->status = ST_ENONFINITE;
+        stat_now = ST_ENONFINITE;
     }
-    __syncthreads();
-    if (tid == 0) {
-        __threadfence();
-        const int keep = (mode == MODE_ITER || mode == MODE_INIT) && st->status == ST_OK && !st->converged &&
-                         st->iter < st->target && st->iter < st->max_iter;
-        if (a.use_cond) cudaGraphSetConditional(a.cond, keep ? 1u : 0u);
+    if (a.use_cond) {
+        const int keep = (mode == MODE_ITER || mode == MODE_INIT) && stat_now == ST_OK && !conv && it < target &&
+                         it < max_iter;
+        cudaGraphSetConditional(a.cond, keep ? 1u : 0u);
     }
 }
 
 template <int M>
-__device__ __forceinline__ void global_update(DevState *st, const double *__restrict__ part, int nblk,
+__device__ __forceinline__ void global_update(DevState *st, const double *__restrict__ part, int nrows,
                                               const SweepArgs &a, double *ws)
 {
-    global_update_rt(M, st, part, nblk, a, ws);
+    global_update_rt(M, st, part, nrows, a, ws);
 }
 
 // ---------------------------------------------------------------------------
@@ -685,20 +859,16 @@ __global__ void __launch_bounds__(SweepCfg<S>::THREADS, SweepCfg<S>::MINB) sweep
         for (int w = 0; w < THREADS / 32; ++w) s += s_red[w * (NGRP * 32) + j];
         a.partials[size_t(blockIdx.x) * NSTAT + j] = s;
     }
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) s_last = (atomicAdd(&st->ticket, 1u) == gridDim.x - 1) ? 1 : 0;
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
+    int row0, nrows;
+    if (!finish_ticket(st, a.partials, gridDim.x, NSTAT, &s_last, &row0, &nrows, reinterpret_cast<double *>(smem)))
+        return;
     if (run && !s_bad) {
         // every copy of this block has landed, so the ring's shared memory
         // serves as the workspace of the global update
-        global_update<M>(st, a.partials, gridDim.x, a, reinterpret_cast<double *>(smem));
+        global_update<M>(st, a.partials + size_t(row0) * NSTAT, nrows, a, reinterpret_cast<double *>(smem));
     } else if (tid == 0 && a.use_cond) {
         cudaGraphSetConditional(a.cond, 0u);
     }
-    if (tid == 0) st->ticket = 0u;
 }
 
 // ---------------------------------------------------------------------------
@@ -710,8 +880,12 @@ __global__ void __launch_bounds__(SweepCfg<S>::THREADS, SweepCfg<S>::MINB) sweep
 // terms, and the special functions of (a_rho, nu, lambda) for the updates of
 // this data set (Eq. 16, 22, 23) and for the given factors.
 // ---------------------------------------------------------------------------
-__device__ inline void elbo_const(ElboConst *k, int M, double a_rho, double nu, double lam, int lane)
+__device__ inline void elbo_const(ElboConst *k, int M, double a_rho, double nu, double lam, double V, double pc,
+                                  const DevState *st, int lane)
 {
+    constexpr double LN2PI = 1.8378770664093454836;
+    constexpr double LN2 = 0.69314718055994530942;
+    constexpr double LNPI = 1.1447298858494002;
     double sp = 0.0, sl = 0.0;
     for (int j = lane; j < M; j += 32) {
         const double x = 0.5 * (nu - j);                 // (nu + 1 - (j + 1)) / 2
@@ -721,14 +895,43 @@ __device__ inline void elbo_const(ElboConst *k, int M, double a_rho, double nu, 
     sp = warp_sum(sp);
     sl = warp_sum(sl);
     if (lane == 0) {
+        const double q0 = st->q0, n0 = st->n0, a0 = st->a0;
+        const double lgamma_a = lgamma(a_rho), psi_a = digamma_d(a_rho), log_lam = log(lam);
         k->a_rho = a_rho;
         k->nu = nu;
         k->lam = lam;
-        k->lgamma_a = lgamma(a_rho);
-        k->psi_a = digamma_d(a_rho);
+        k->lgamma_a = lgamma_a;
+        k->psi_a = psi_a;
         k->sum_psi_nu = sp;
         k->sum_lgamma_nu = sl;
-        k->log_lam = log(lam);
+        k->log_lam = log_lam;
+        k->log_nu = log(nu);
+        k->rs_nu = rs_of(nu);
+        k->inv_lam = 1.0 / lam;
+        k->inv_V = V > 0.0 ? 1.0 / V : 0.0;
+        // Eq. 11 term by term, with E[ln rho] = psi(a_rho) - ln b_rho and
+        // E[ln|Lambda|] = sum psi + M ln 2 - ln|W^{-1}|; what a sweep leaves
+        // unchanged is collected in e0:
+        //   E ln p(r | beta, rho)  V/2 (E ln rho - ln 2pi) - E[rho] T3/2
+        //   E ln p(beta | K, L)    V/2 (E ln|L| - M ln 2pi) - tr(E[L] C)/2 - V M/(2 lam)
+        //   E ln p(K | L)          E ln|L|/2 - q0 ((kappa-K0)^T E[L] (kappa-K0) + M/lam)/2
+        //   E ln p(L)              (n0-M-1)/2 E ln|L| - tr(Lambda_0^{-1} E[L])/2
+        //   E ln p(rho)            (a0-1) E ln rho - b0 E[rho]
+        //   H[Q(beta)]             (V ln|Sigma0~| - T4)/2 + V M (1 + ln 2pi)/2
+        //   H[Q(K | L)]            -E ln|L|/2 - M (ln lam - ln 2pi)/2 + M/2
+        //   H[Q(L)] (M > 0)        -ln B(W, nu) - (nu-M-1)/2 E ln|L| + nu M/2
+        //   H[Q(rho)]              a_rho - ln b_rho + lnGamma(a_rho) + (1 - a_rho) psi(a_rho)
+        // plus the prior-only constant pc.
+        const double cr = 0.5 * V + (a0 - 1.0);                                          // of E ln rho
+        const double cl = 0.5 * V + 0.5 * (n0 - M - 1.0) - (M > 0 ? 0.5 * (nu - M - 1.0) : 0.0);   // of E ln|L|
+        double e0 = pc + cr * psi_a + cl * (sp + M * LN2);
+        e0 += -0.5 * V * LN2PI - 0.5 * V * M * LN2PI - 0.5 * (V + q0) * M / lam + 0.5 * V * M * (1.0 + LN2PI);
+        e0 += -0.5 * M * (log_lam - LN2PI) + 0.5 * M;
+        if (M > 0) e0 += 0.5 * nu * M * LN2 + 0.25 * M * (M - 1) * LNPI + sl + 0.5 * nu * M;
+        e0 += a_rho + lgamma_a + (1.0 - a_rho) * psi_a;
+        k->e0 = e0;
+        k->e_logb = -(cr + 1.0);
+        k->e_ldw = cl + (M > 0 ? 0.5 * nu : 0.0);
     }
 }
 
@@ -739,38 +942,47 @@ __device__ inline void setup_state_rt(int M, DevState *st, int init, int lane, d
     constexpr double LN2PI = 1.8378770664093454836;
     constexpr double LN2 = 0.69314718055994530942;
     constexpr double LNPI = 1.1447298858494002;
+    __shared__ double s_rd[MMAX], s_piv[MMAX];
     for (int i = lane; i < M * M; i += 32) A[i] = st->L0inv[i];
     __syncwarp();
-    int fail = warp_cholesky_rt(M, A, Lc, lane);
-    const double l0 = warp_sum(lane < M ? 2.0 * log(Lc[lane * M + lane]) : 0.0);
+    int fail = warp_cholesky_rt(M, A, Lc, s_rd, s_piv, lane);
+    __syncwarp();
+    const double l0 = warp_logdet_rt(M, s_piv, lane);
     // prior-only terms: M/2 (ln q0 - ln 2 pi) + a0 ln b0 - lnGamma(a0) + ln B(Lambda_0, n0)
     const double n0 = st->n0;
     const bool proper = (M == 0) || (n0 > M - 1.0);
     const double lg0 = warp_sum((lane < M && proper) ? lgamma(0.5 * (n0 - lane)) : 0.0);
+    double pc = 0.0;
     if (lane == 0) {
         st->lndetL0inv = l0;
-        double pc = 0.5 * M * (log(st->q0) - LN2PI) + st->a0 * log(st->b0) - lgamma(st->a0);
+        pc = 0.5 * M * (log(st->q0) - LN2PI) + st->a0 * log(st->b0) - lgamma(st->a0);
         if (M > 0 && proper)                            // ln B(W0, n0), ln|W0| = -ln|Lambda_0^{-1}|
             pc += 0.5 * n0 * l0 - 0.5 * n0 * M * LN2 - 0.25 * M * (M - 1) * LNPI - lg0;
         st->prior_const = pc;
         st->prior_dropped = (M > 0 && !proper) ? 1 : 0;
     }
+    pc = __shfl_sync(0xffffffffu, pc, 0);
     const double V = st->V;
-    elbo_const(&st->kc_upd, M, st->a0 + 0.5 * V, n0 + V, st->q0 + V, lane);
-    if (!init) elbo_const(&st->kc_given, M, st->a_rho, st->nu, st->lam, lane);
+    elbo_const(&st->kc_upd, M, st->a0 + 0.5 * V, n0 + V, st->q0 + V, V, pc, st, lane);
+    if (!init) elbo_const(&st->kc_given, M, st->a_rho, st->nu, st->lam, V, pc, st, lane);
     __syncwarp();
     if (!init)
         for (int i = lane; i < M * M; i += 32) A[i] = st->Winv[i];
     __syncwarp();
-    int fail2 = 0;
-    (void)derive_pass_globals_rt(M, st, A, init ? 1.0 : st->nu, Lc, lane, &fail2);
-    fail |= fail2;
+    // the pass factors of sweep 0: from (Lambda_0^{-1}, nu = 1) or (W^{-1}, nu)
+    const double nu = init ? 1.0 : st->nu;
+    fail |= warp_cholesky_rt(M, A, Lc, s_rd, s_piv, lane);
+    __syncwarp();
+    write_pass_globals_rt(M, st, A, Lc, nu, rs_of(nu), lane, 32);
+    const double ld = warp_logdet_rt(M, s_piv, lane);
     for (int i = lane; i < M; i += 32) {
         const double kv = init ? st->K0[i] : st->kappa[i];
         st->sw.kappa[i] = static_cast<float>(kv);
         if (init) st->kappa[i] = kv;
     }
+    for (int g = lane; g < TICKET_GROUPS_MAX; g += 32) st->gticket[g] = 0u;
     if (lane == 0) {
+        st->lndetSigma0 = ld - M * log(nu);
         st->erho = init ? 0.0 : st->a_rho / st->b_rho;
         st->sw.erho = static_cast<float>(st->erho);
         st->ticket = 0u;

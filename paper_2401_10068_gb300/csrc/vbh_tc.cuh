@@ -108,6 +108,7 @@ struct TcCfg {
     static_assert(TILE_BYTES % 512 == 0 && D_BYTES + TILE * 4 == TILE_BYTES, "tile layout");
     static_assert(3 * THREADS * 8 <= NBUF * A2_BYTES, "reduction scratch");
     static_assert(SMEM_BYTES <= 227 * 1024, "shared memory per block");
+    static_assert(size_t(gu_ws_doubles_rt(MMAX)) * 8 <= OFF_MISC, "workspace of the global update");
 };
 
 // 16-byte chunk c of row `row` in a region with 64-byte rows and 64-byte swizzle
@@ -617,18 +618,14 @@ __global__ void __launch_bounds__(TcCfg<NSPLIT>::THREADS, 1)
         }
         part[j] = v;
     }
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) *s_last = (atomicAdd(&st->ticket, 1u) == gridDim.x - 1) ? 1 : 0;
-    __syncthreads();
-    if (!*s_last) return;
-    __threadfence();
+    int row0, nrows;
+    if (!finish_ticket(st, a.partials, gridDim.x, NSTAT, s_last, &row0, &nrows, reinterpret_cast<double *>(base)))
+        return;
     if (run && st->status == ST_OK) {
-        global_update_rt(M, st, a.partials, gridDim.x, a, reinterpret_cast<double *>(base));
+        global_update_rt(M, st, a.partials + size_t(row0) * NSTAT, nrows, a, reinterpret_cast<double *>(base));
     } else if (tid == 0 && a.use_cond) {
         cudaGraphSetConditional(a.cond, 0u);
     }
-    if (tid == 0) st->ticket = 0u;
 }
 
 // Inputs of the tensor-core sweep, repacked into tiles of 128 observations
