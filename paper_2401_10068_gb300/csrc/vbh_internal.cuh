@@ -12,7 +12,7 @@ constexpr int MMAX = 31;             // largest M = S - 1
 // block that finishes the launch sums all rows) and in two levels above: the
 // last block of each group of TICKET_GROUP consecutive blocks sums the group's
 // rows, the last group's reducer runs the global update over the group sums.
-constexpr int TICKET_SINGLE_MAX = 64;
+constexpr int TICKET_SINGLE_MAX = 128;
 constexpr int TICKET_GROUP = 32;
 constexpr int TICKET_GROUPS_MAX = 40;
 constexpr int GRID_MAX = TICKET_GROUP * TICKET_GROUPS_MAX;  // largest sweep grid

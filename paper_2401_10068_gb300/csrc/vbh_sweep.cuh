@@ -221,7 +221,9 @@ __device__ __forceinline__ double rs_of(double nu) { return nu == 1.0 ? 1.0 : rs
 // nonzero in every lane when A is not positive definite (a unit pivot is
 // used then).
 // ---------------------------------------------------------------------------
-__device__ inline int warp_cholesky_rt(int M, const double *A, double *L, double *rd, double *piv, int lane)
+__device__ inline int warp_cholesky_rt(int M, const double *__restrict__ A, double *__restrict__ L,
+                                       double *__restrict__ rd, double *__restrict__ piv, double *__restrict__ col,
+                                       int lane)
 {
     const int MD = M > 0 ? M : 1;
     for (int e = lane; e < M * M; e += 32) {
@@ -231,6 +233,7 @@ __device__ inline int warp_cholesky_rt(int M, const double *A, double *L, double
     __syncwarp();
     int fail = 0;
     const int i = lane;
+    double *row = L + i * M;                        // lane i's row (i < M)
     for (int j = 0; j < M; ++j) {
         double p = L[j * M + j];
         const bool bad = !(p > 0.0) || !isfinite(p);
@@ -238,18 +241,19 @@ __device__ inline int warp_cholesky_rt(int M, const double *A, double *L, double
         fail |= bad ? 1 : 0;
         const double r = rsqrt(p);
         __syncwarp();                               // the pivot is read before lane j overwrites it
+        double lij = 0.0;
         if (i > j && i < M) {
-            L[i * M + j] *= r;
+            lij = row[j] * r;
+            row[j] = lij;
+            col[i] = lij;                           // column j below the pivot, for the other lanes
         } else if (i == j) {
-            L[j * M + j] = p * r;
+            row[j] = p * r;
             rd[j] = r;
             piv[j] = p;
         }
         __syncwarp();
-        if (i > j && i < M) {
-            const double lij = L[i * M + j];
-            for (int k = j + 1; k <= i; ++k) L[i * M + k] = fma(-lij, L[k * M + j], L[i * M + k]);
-        }
+        if (i > j && i < M)
+            for (int k = j + 1; k <= i; ++k) row[k] = fma(-lij, col[k], row[k]);
         __syncwarp();
     }
     return fail;
@@ -258,7 +262,8 @@ __device__ inline int warp_cholesky_rt(int M, const double *A, double *L, double
 // Li = L^{-1} (lower) of a Cholesky factor L with reciprocal diagonal rd, by
 // one warp: lane c forms column c by forward substitution, subtracting each
 // finished row from the rows below it (lanes never wait on one another).
-__device__ inline void warp_tri_inverse_rt(int M, const double *L, const double *rd, double *Li, int lane)
+__device__ inline void warp_tri_inverse_rt(int M, const double *__restrict__ L, const double *__restrict__ rd,
+                                           double *__restrict__ Li, int lane)
 {
     const int c = lane;
     if (c < M) {
@@ -360,6 +365,11 @@ __device__ inline bool finish_ticket(DevState *st, double *part, int nblk, int n
 {
     const int tid = threadIdx.x, nth = blockDim.x;
     __syncthreads();
+    if (nblk == 1) {                                // the only block: its own writes are visible after the barrier
+        *row0 = 0;
+        *nrows = 1;
+        return true;
+    }
     if (nblk <= TICKET_SINGLE_MAX) {
         if (tid == 0) {
             __threadfence();
@@ -421,8 +431,8 @@ __device__ inline bool finish_ticket(DevState *st, double *part, int nblk, int n
 // ---------------------------------------------------------------------------
 __host__ __device__ constexpr int gu_ws_doubles_rt(int M)
 {
-    // statistics (rounded up to 32), 10 M x M matrices, 9 M-vectors, 32 scalars, 512 of reduction scratch
-    return ((M * (M + 1) / 2 + M + 3 + 31) / 32) * 32 + 10 * (M > 0 ? M * M : 1) + 9 * (M > 0 ? M : 1) + 32 + 512;
+    // statistics (rounded up to 32), 10 M x M matrices, 10 M-vectors, 32 scalars, 512 of reduction scratch
+    return ((M * (M + 1) / 2 + M + 3 + 31) / 32) * 32 + 10 * (M > 0 ? M * M : 1) + 10 * (M > 0 ? M : 1) + 32 + 512;
 }
 
 template <int M>
@@ -469,7 +479,7 @@ __device__ __forceinline__ void global_update_rt(int M, DevState *st, const doub
     double *rd = gv + MV;                           // 1 / diag(Lw)
     double *piv = rd + MV;                          // Cholesky pivots of W'^{-1}
     double *K0s = piv + MV;                         // K0
-    double *sc = K0s + MV;                          // scalars
+    double *sc = K0s + 2 * MV;                      // scalars (after K0 and the Cholesky column scratch)
     double *red = sc + 32;                          // reduction scratch [R][NSTAT]
     __shared__ int s_fail;
 
@@ -576,8 +586,9 @@ __device__ __forceinline__ void global_update_rt(int M, DevState *st, const doub
             if (em) {
                 // Eq. 47: (1/V) sum (M_i M_i^T + Sigma_i) - K' K'^T = Sigma0~ + Sigma0~ G Sigma0~ / V - a a^T
                 Wn[e] = fma(Bs, inv_V, Sg[e]) - dv[r] * dv[c];
+            } else if (!elbo_only) {
+                Wn[e] = L0s[e] + V * Sg[e] + Bs + q0 * av[r] * av[c] - lam * dv[r] * dv[c];
             } else {
-                if (!elbo_only) Wn[e] = L0s[e] + V * Sg[e] + Bs + q0 * av[r] * av[c] - lam * dv[r] * dv[c];
                 // C = V Sigma0~ + Sigma0~ G Sigma0~ - s delta^T - delta s^T + V delta delta^T
                 const double Cm = V * Sg[e] + Bs - sv[r] * dv[c] - dv[r] * sv[c] + V * dv[r] * dv[c];
                 X[e] = Cm + L0s[e] + q0 * (kn[r] - K0s[r]) * (kn[c] - K0s[c]);
@@ -586,15 +597,19 @@ __device__ __forceinline__ void global_update_rt(int M, DevState *st, const doub
         named_sync(BAR_MAIN, nthm);
         // 5. Cholesky of W'^{-1} (warp 0); its pivots go to the scalar warp
         if (warp == 0) {
-            const int fail = warp_cholesky_rt(M, Wn, Lw, rd, piv, lane);
+            const int fail = warp_cholesky_rt(M, Wn, Lw, rd, piv, K0s + MV, lane);
             if (lane == 0 && fail) s_fail = 1;
             named_arrive(BAR_PIV, 64);
         }
         named_sync(BAR_MAIN, nthm);
         // 6. warp 0: tr(E[Lambda] X) with E[Lambda] = nu Li^T Li (Eq. 28);
-        //    warp 1 (EM): tr(Sigma0~ G); the other main warps: the new globals
+        //    warp 1 (EM): tr(Sigma0~ G); the other main warps: the new globals.
+        //    After the CAVI update of Q(K, Lambda) X equals the new W'^{-1}: with
+        //    a = K0 - kappa~, X - W'^{-1} = -(s + q0 a) delta^T - delta (s + q0 a)^T
+        //    + 2 lam delta delta^T = 0 since lam delta = s + q0 a (Eq. 24-25), so
+        //    tr(E[Lambda] X) = nu M and only the ELBO of given factors forms it.
         if (warp == 0) {
-            if (!em) {
+            if (elbo_only) {
                 warp_tri_inverse_rt(M, Lw, rd, Li, lane);
                 double t0 = 0.0;
                 for (int e = lane; e < M * M; e += 32) {
@@ -610,6 +625,8 @@ __device__ __forceinline__ void global_update_rt(int M, DevState *st, const doub
                 }
                 const double t = warp_sum(t0);
                 if (lane == 0) sc[6] = nu * t;
+            } else if (lane == 0) {
+                sc[6] = nu * M;
             }
         } else {
             if (em && warp == 1) {
@@ -942,10 +959,10 @@ __device__ inline void setup_state_rt(int M, DevState *st, int init, int lane, d
     constexpr double LN2PI = 1.8378770664093454836;
     constexpr double LN2 = 0.69314718055994530942;
     constexpr double LNPI = 1.1447298858494002;
-    __shared__ double s_rd[MMAX], s_piv[MMAX];
+    __shared__ double s_rd[MMAX], s_piv[MMAX], s_col[MMAX];
     for (int i = lane; i < M * M; i += 32) A[i] = st->L0inv[i];
     __syncwarp();
-    int fail = warp_cholesky_rt(M, A, Lc, s_rd, s_piv, lane);
+    int fail = warp_cholesky_rt(M, A, Lc, s_rd, s_piv, s_col, lane);
     __syncwarp();
     const double l0 = warp_logdet_rt(M, s_piv, lane);
     // prior-only terms: M/2 (ln q0 - ln 2 pi) + a0 ln b0 - lnGamma(a0) + ln B(Lambda_0, n0)
@@ -971,7 +988,7 @@ __device__ inline void setup_state_rt(int M, DevState *st, int init, int lane, d
     __syncwarp();
     // the pass factors of sweep 0: from (Lambda_0^{-1}, nu = 1) or (W^{-1}, nu)
     const double nu = init ? 1.0 : st->nu;
-    fail |= warp_cholesky_rt(M, A, Lc, s_rd, s_piv, lane);
+    fail |= warp_cholesky_rt(M, A, Lc, s_rd, s_piv, s_col, lane);
     __syncwarp();
     write_pass_globals_rt(M, st, A, Lc, nu, rs_of(nu), lane, 32);
     const double ld = warp_logdet_rt(M, s_piv, lane);
