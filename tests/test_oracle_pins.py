@@ -236,6 +236,42 @@ def test_elbo_non_decreasing_at_every_coordinate_step(S, prior):
         prev = L
 
 
+def _trace_term(p, s, g):
+    """tr(E[Lambda] X) / nu with X = C + Lambda_0^{-1} + q0 (kappa - K0)(kappa - K0)^T and
+    C = sum_i E[(beta_i - kappa)(beta_i - kappa)^T], from the oracle's sums and factors."""
+    k = np.asarray(g["kappa"])
+    mu = np.asarray(s["sum_mu"])
+    C = np.asarray(s["sum_Ebb"]) - np.outer(mu, k) - np.outer(k, mu) + s["V"] * np.outer(k, k)
+    X = C + p["L0inv"] + p["q0"] * np.outer(k - p["K0"], k - p["K0"])
+    W = np.linalg.inv(np.asarray(g["Winv"]))
+    return float(np.trace(W @ X)), X
+
+
+@pytest.mark.parametrize("S,prior", [(3, "paper"), (4, "rich"), (6, "rich")])
+def test_trace_term_after_the_KLambda_update_is_M(S, prior):
+    """After the Eq. 22-25 update of Q(K, Lambda) the matrix X that the ELBO's
+    E ln p(beta | K, Lambda) + E ln p(K | Lambda) + E ln p(Lambda) terms
+    contract with E[Lambda] equals the new W^{-1}, so tr(E[Lambda] X) = nu M;
+    the sweep kernels use this closed form and form the trace only for the
+    ELBO of given factors.  Before the update (after the Q(beta) step) it
+    differs from M, so the identity is not vacuous."""
+    M = S - 1
+    r, d, _ = synth.generate(400, S, seed=40 + S)
+    p = O.paper_prior(S) if prior == "paper" else _rich_prior(S, seed=S)
+    states = list(_sweep_states(r, d, p, 3))
+    checked = 0
+    for i, (name, mu, Sig, g) in enumerate(states):
+        s = O.sums_from_beta(r, d, p, mu, Sig)
+        tr, X = _trace_term(p, s, g)
+        if name in ("KLambda", "init"):
+            assert tr == pytest.approx(M, rel=1e-11), (name, i, tr)
+            assert np.allclose(X, g["Winv"], rtol=1e-10, atol=0.0)
+            checked += 1
+        elif name == "beta":
+            assert abs(tr - M) > 1e-6, (name, i, tr)
+    assert checked == 4
+
+
 def _central(fun, x, h):
     return (fun(x + h) - fun(x - h)) / (2 * h)
 
