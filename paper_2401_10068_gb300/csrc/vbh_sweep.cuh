@@ -214,12 +214,15 @@ __device__ __forceinline__ double rs_of(double nu) { return nu == 1.0 ? 1.0 : rs
 // ---------------------------------------------------------------------------
 // Cholesky factor L (lower, row-major, zero above the diagonal) of a symmetric
 // positive-definite M x M matrix A (M <= 32) in shared memory, by one warp,
-// right-looking: lane i owns row i; for column j every lane forms the
-// pivot's reciprocal square root r_j, the column below the pivot is scaled
-// by it and the trailing rows are updated in parallel.  rd[j] = 1/L_jj and
-// piv[j] = L_jj^2 (the pivots; their logarithms add up to ln|A|).  Returns
-// nonzero in every lane when A is not positive definite (a unit pivot is
-// used then).
+// right-looking: for column j every lane forms the pivot's reciprocal square
+// root r_j, lanes i > j scale the column below the pivot, and the trailing
+// entries (i, k), j < k <= i, are updated in parallel, each lane owning the
+// entries e = lane, lane + 32, ... of the packed lower triangle (row by row).
+// One FP64 multiply-add per lane and column for M <= 7, so the chain per
+// column is the pivot's rsqrt, one multiply and one multiply-add.  rd[j] =
+// 1/L_jj and piv[j] = L_jj^2 (the pivots, whose logarithms add up to ln|A|).
+// Returns nonzero in every lane when A is not positive definite (a unit
+// pivot is used then).
 // ---------------------------------------------------------------------------
 __device__ inline int warp_cholesky_rt(int M, const double *__restrict__ A, double *__restrict__ L,
                                        double *__restrict__ rd, double *__restrict__ piv, double *__restrict__ col,
@@ -232,8 +235,7 @@ __device__ inline int warp_cholesky_rt(int M, const double *__restrict__ A, doub
     }
     __syncwarp();
     int fail = 0;
-    const int i = lane;
-    double *row = L + i * M;                        // lane i's row (i < M)
+    const int NG = M * (M + 1) / 2;
     for (int j = 0; j < M; ++j) {
         double p = L[j * M + j];
         const bool bad = !(p > 0.0) || !isfinite(p);
@@ -241,19 +243,30 @@ __device__ inline int warp_cholesky_rt(int M, const double *__restrict__ A, doub
         fail |= bad ? 1 : 0;
         const double r = rsqrt(p);
         __syncwarp();                               // the pivot is read before lane j overwrites it
-        double lij = 0.0;
-        if (i > j && i < M) {
-            lij = row[j] * r;
-            row[j] = lij;
-            col[i] = lij;                           // column j below the pivot, for the other lanes
-        } else if (i == j) {
-            row[j] = p * r;
+        if (lane > j && lane < M) {
+            const double lij = L[lane * M + j] * r;
+            L[lane * M + j] = lij;
+            col[lane] = lij;                        // column j below the pivot
+        } else if (lane == j) {
+            L[j * M + j] = p * r;
             rd[j] = r;
             piv[j] = p;
         }
         __syncwarp();
-        if (i > j && i < M)
-            for (int k = j + 1; k <= i; ++k) row[k] = fma(-lij, col[k], row[k]);
+        // trailing update: entries (i, k) with k > j of the packed lower triangle
+        int i = 0, k = lane;                        // packed entry e = lane -> (i, k)
+        while (k > i) {
+            k -= i + 1;
+            ++i;
+        }
+        for (int e = lane; e < NG; e += 32) {
+            if (k > j) L[i * M + k] = fma(-col[i], col[k], L[i * M + k]);
+            k += 32;                                // next entry of this lane
+            while (k > i) {
+                k -= i + 1;
+                ++i;
+            }
+        }
         __syncwarp();
     }
     return fail;
@@ -350,8 +363,8 @@ __device__ __forceinline__ double chunk_total(const double *red, int R, int ns, 
 // ---------------------------------------------------------------------------
 // Completion of a sweep launch, called by every thread of every block after
 // the block wrote its row of `part` ([nblk][ns] FP64, then one row per
-// group).  Thread 0 publishes the block's writes (a CTA barrier, then a
-// device-scope fence before the counter) and takes a ticket.  Up to
+// group).  Thread 0 publishes the block's writes (a CTA barrier, then an
+// acquire-release fetch-and-add on the counter) and takes a ticket.  Up to
 // TICKET_SINGLE_MAX blocks the last block to arrive finishes the launch and
 // reads every row.  Above, the last block of each group of TICKET_GROUP
 // blocks sums the group's rows (fixed order, scratch: >= 512 doubles of
@@ -360,6 +373,15 @@ __device__ __forceinline__ double chunk_total(const double *red, int R, int ns, 
 // in the finishing block only, with the rows it reads in [*row0, *row0 +
 // *nrows).  Counters are reset by the block that read them.
 // ---------------------------------------------------------------------------
+// Device-scope acquire-release fetch-and-add: publishes the block's writes
+// (ordered before it by a CTA barrier) and acquires the other blocks'.
+__device__ __forceinline__ unsigned atomic_add_acq_rel(unsigned *p, unsigned v)
+{
+    unsigned old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
 __device__ inline bool finish_ticket(DevState *st, double *part, int nblk, int ns, volatile int *s_flag, int *row0,
                                      int *nrows, double *scratch)
 {
@@ -372,12 +394,8 @@ __device__ inline bool finish_ticket(DevState *st, double *part, int nblk, int n
     }
     if (nblk <= TICKET_SINGLE_MAX) {
         if (tid == 0) {
-            __threadfence();
-            const int last = (atomicAdd(&st->ticket, 1u) == unsigned(nblk - 1)) ? 1 : 0;
-            if (last) {
-                __threadfence();
-                st->ticket = 0u;
-            }
+            const int last = (atomic_add_acq_rel(&st->ticket, 1u) == unsigned(nblk - 1)) ? 1 : 0;
+            if (last) st->ticket = 0u;
             *s_flag = last;
         }
         __syncthreads();
@@ -390,12 +408,8 @@ __device__ inline bool finish_ticket(DevState *st, double *part, int nblk, int n
     const int b0 = g * TICKET_GROUP;
     const int gsz = (nblk - b0 < TICKET_GROUP) ? nblk - b0 : TICKET_GROUP;
     if (tid == 0) {
-        __threadfence();
-        const int last = (atomicAdd(&st->gticket[g], 1u) == unsigned(gsz - 1)) ? 1 : 0;
-        if (last) {
-            __threadfence();
-            st->gticket[g] = 0u;
-        }
+        const int last = (atomic_add_acq_rel(&st->gticket[g], 1u) == unsigned(gsz - 1)) ? 1 : 0;
+        if (last) st->gticket[g] = 0u;
         *s_flag = last;
     }
     __syncthreads();
@@ -406,12 +420,8 @@ __device__ inline bool finish_ticket(DevState *st, double *part, int nblk, int n
     for (int j = tid; j < ns; j += nth) out[j] = chunk_total(scratch, R, ns, j);
     __syncthreads();
     if (tid == 0) {
-        __threadfence();
-        const int last = (atomicAdd(&st->ticket, 1u) == unsigned(ng - 1)) ? 1 : 0;
-        if (last) {
-            __threadfence();
-            st->ticket = 0u;
-        }
+        const int last = (atomic_add_acq_rel(&st->ticket, 1u) == unsigned(ng - 1)) ? 1 : 0;
+        if (last) st->ticket = 0u;
         *s_flag = last;
     }
     __syncthreads();
