@@ -46,6 +46,18 @@ def _dist():
     return rank, world, local
 
 
+def whole_job(seconds_rank, units_rank, dist, world, device):
+    """Whole-job timing of N replicas: the maximum of the per-rank times over
+    the ranks (all-reduce MAX; every rank receives it) and the units of all
+    ranks divided by that time.  Returns (max seconds, units/s)."""
+    import torch
+    t = torch.tensor([float(seconds_rank)], device=device, dtype=torch.float64)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    t_max = float(t.item())
+    return t_max, float(units_rank) * world / t_max
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -220,12 +232,8 @@ def run_ours(args):
     clk = clocks.stop()
     res = h.fit_result()
     assert res["iters"] == total, res["iters"]
-    t = torch.tensor([ms], device=dev, dtype=torch.float64)
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    units = float(V) * S * args.steps * world
-    value = units / (ms_max * 1e-3)
+    t_max, value = whole_job(ms * 1e-3, float(V) * S * args.steps, dist, world, dev)
+    ms_max = t_max * 1e3
     ms_step = ms_max / args.steps
 
     # roofline of the dominant kernel (the fused sweep: one launch per step)
@@ -289,10 +297,7 @@ def _e2e(h, r, d, V, S, e2e_steps, dev, dist, world):
         out = h.fit(rh, dh, S, None, tol=0.0, max_iter=e2e_steps)
     t_e2e = (time.perf_counter() - t0) / reps
     assert out["iters"] == e2e_steps
-    te = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
-    if dist:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = float(V) * S * e2e_steps * world / float(te.item())
+    _, e2e_value = whole_job(t_e2e, float(V) * S * e2e_steps, dist, world, dev)
     h2d = V * 4 + V * S * 4
     d2h = ctypes_result_bytes()
     return {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d / e2e_steps,

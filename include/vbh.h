@@ -157,6 +157,18 @@ const char *vbh_strerror(int status);
  * thread's next failing call. */
 const char *vbh_last_error_detail(void);
 
+/* Diagnostic of the bounded device waits.  Every kernel of the library waits
+ * on mbarriers through waits that give up after a wall-time budget, after
+ * which the kernel records VBH_ETIMEOUT, lets its own copies land and returns
+ * (no trap, the CUDA context stays usable).  This runs those waits in one
+ * block on `stream` of `device`: on a barrier phase that nothing completes
+ * (status[0]: polling wait, status[1]: wait with a sleep between polls; both
+ * must be VBH_ETIMEOUT after budget_ns, 0 < budget_ns <= 1e9) and on a phase
+ * that a 1 KiB bulk copy completes (status[2]: VBH_OK; status[3]: VBH_OK when
+ * the copied bytes are right).  *waited_ns receives the time the first wait
+ * took.  Allocates and frees about 1 KiB of device memory; synchronous. */
+int vbh_selftest_wait(int device, void *stream, uint64_t budget_ns, int *status, uint64_t *waited_ns);
+
 /* Bytes of the device-resident fit state that each vbh_fit_begin,
  * vbh_fit_step and vbh_fit_result call copies back to the host (a vbh_fit
  * call copies it three times); for accounting of host<->device traffic. */

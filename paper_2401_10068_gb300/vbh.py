@@ -28,6 +28,20 @@ STATUS = {0: "VBH_OK", -1: "VBH_EINVAL", -2: "VBH_ENOMEM", -3: "VBH_ECUDA", -4: 
           -5: "VBH_ETIMEOUT", -6: "VBH_ESTATE", -7: "VBH_EUNSUPPORTED"}
 
 
+def selftest_wait(budget_ns: int, device: int = 0, stream=None):
+    """``vbh_selftest_wait``: statuses of the bounded waits (expired, expired,
+    completed, bytes) and the nanoseconds the first wait took."""
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    st = (ctypes.c_int * 4)()
+    waited = ctypes.c_uint64()
+    rc = _lib().vbh_selftest_wait(int(device), ctypes.c_void_p(stream) if stream else None, int(budget_ns), st,
+                                  ctypes.byref(waited))
+    if rc != 0:
+        raise VBHError(rc, "vbh_selftest_wait")
+    return list(st), int(waited.value)
+
+
 class VBHError(RuntimeError):
     def __init__(self, status: int, what: str):
         self.status = status
@@ -82,6 +96,8 @@ def _lib():
             "vbh_strerror": (ctypes.c_char_p, [ci]),
             "vbh_state_bytes": (ctypes.c_size_t, []),
             "vbh_last_error_detail": (ctypes.c_char_p, []),
+            "vbh_selftest_wait": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_uint64,
+                                                 ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_uint64)]),
             "vbh_fit": (ci, [vp, vp, vp, i64, ci, P, O, R]),
             "vbh_fit_begin": (ci, [vp, vp, vp, i64, ci, P, O]),
             "vbh_fit_step": (ci, [vp, ci, ctypes.POINTER(ci)]),
