@@ -108,6 +108,7 @@ struct TcCfg {
     static_assert(TILE_BYTES % 512 == 0 && D_BYTES + TILE * 4 == TILE_BYTES, "tile layout");
     static_assert(3 * THREADS * 8 <= NBUF * A2_BYTES, "reduction scratch");
     static_assert(SMEM_BYTES <= 227 * 1024, "shared memory per block");
+    static_assert(D_BYTES <= 8192 && A2_BYTES <= 32768 && TILE / 8 <= 16, "packed chunk offsets (13 + 15 + 4 bits)");
     static_assert(size_t(gu_ws_doubles_rt(MMAX)) * 8 <= OFF_MISC, "workspace of the global update");
 };
 
@@ -393,6 +394,18 @@ __global__ void __launch_bounds__(TcCfg<NSPLIT>::THREADS, 1)
             const uint32_t o_r = (uint32_t(row) & 31u) | ((uint32_t(row) & 32u) << 1) | ((uint32_t(row) & 64u) >> 1);
             const uint32_t lanebase = uint32_t(32 * q) << 16;
             const int gt = tid & 127;                            // thread within the group
+            // this thread's A2 chunk tasks (slot x < 31 of 8 observations), the same in every
+            // tile: source byte in the tile's BF16 part (13 bits), destination byte of part 0 in
+            // an A2 buffer (15 bits; part p is 2048 p further) and the chunk (4 bits), packed
+            constexpr int TPT = (C::NTASK + 127) / 128;
+            uint32_t tpk[TPT];
+#pragma unroll
+            for (int i = 0; i < TPT; ++i) {
+                const int task = gt + 128 * i;
+                const uint32_t x = uint32_t(task % 31), ch = uint32_t(task / 31) & 15u, o0 = 8u * ch;
+                const uint32_t set = (C::SETS == 2) ? (o0 >> 6) : 0u;
+                tpk[i] = tc_slot_byte(o0, x) | (a2_byte<C::SETS>(64 * set + x, o0) << 13) | (ch << 28);
+            }
             float t3 = 0.0f, prod = 1.0f;
             int ex = 0, cnt = 0;
             const float erho = erho_f;
@@ -497,15 +510,13 @@ __global__ void __launch_bounds__(TcCfg<NSPLIT>::THREADS, 1)
                 }
                 // A2 chunks: slot x < 31 of 8 observations (pairs) -> part p of gamma D_x; each
                 // thread takes up to TPT chunks, loading all operands before the products
-                constexpr int TPT = (C::NTASK + 127) / 128;
                 if (binary) {
                     uint4 dch[TPT], gch[TPT][NSPLIT];
 #pragma unroll
                     for (int i = 0; i < TPT; ++i) {
-                        const int task = gt + 128 * i;
-                        if (task < C::NTASK) {
-                            const uint32_t x = uint32_t(task % 31), o0 = 8 * uint32_t(task / 31);
-                            dch[i] = *reinterpret_cast<const uint4 *>(dt + tc_slot_byte(o0, x));
+                        if (gt + 128 * i < C::NTASK) {
+                            const uint32_t pk = tpk[i], o0 = (pk >> 28) << 3;
+                            dch[i] = *reinterpret_cast<const uint4 *>(dt + (pk & 0x1FFFu));
 #pragma unroll
                             for (int p = 0; p < NSPLIT; ++p)
                                 gch[i][p] = *reinterpret_cast<const uint4 *>(gb + p * C::TILE + o0);
@@ -513,10 +524,8 @@ __global__ void __launch_bounds__(TcCfg<NSPLIT>::THREADS, 1)
                     }
 #pragma unroll
                     for (int i = 0; i < TPT; ++i) {
-                        const int task = gt + 128 * i;
-                        if (task < C::NTASK) {
-                            const uint32_t x = uint32_t(task % 31), o0 = 8 * uint32_t(task / 31);
-                            const uint32_t set = (C::SETS == 2) ? (o0 >> 6) : 0u;
+                        if (gt + 128 * i < C::NTASK) {
+                            unsigned char *dst = abuf + ((tpk[i] >> 13) & 0x7FFFu);
                             const __nv_bfloat162 *dp = reinterpret_cast<const __nv_bfloat162 *>(&dch[i]);
 #pragma unroll
                             for (int p = 0; p < NSPLIT; ++p) {
@@ -526,15 +535,17 @@ __global__ void __launch_bounds__(TcCfg<NSPLIT>::THREADS, 1)
                                 __nv_bfloat162 *op = reinterpret_cast<__nv_bfloat162 *>(&o);
 #pragma unroll
                                 for (int h = 0; h < 4; ++h) op[h] = __hmul2(gq[h], dp[h]);
-                                *reinterpret_cast<uint4 *>(abuf + a2_byte<C::SETS>(64 * set + 32 * p + x, o0)) = o;
+                                *reinterpret_cast<uint4 *>(dst + 2048 * p) = o;
                             }
                         }
                     }
                 } else {
-                    for (int task = gt; task < C::NTASK; task += 128) {
-                        const uint32_t x = uint32_t(task % 31), o0 = 8 * uint32_t(task / 31);
-                        const uint32_t set = (C::SETS == 2) ? (o0 >> 6) : 0u;
-                        const uint4 dch = *reinterpret_cast<const uint4 *>(dt + tc_slot_byte(o0, x));
+#pragma unroll
+                    for (int i = 0; i < TPT; ++i) {
+                        if (gt + 128 * i >= C::NTASK) continue;
+                        const uint32_t pk = tpk[i], o0 = (pk >> 28) << 3;
+                        unsigned char *dst = abuf + ((pk >> 13) & 0x7FFFu);
+                        const uint4 dch = *reinterpret_cast<const uint4 *>(dt + (pk & 0x1FFFu));
                         const __nv_bfloat162 *dp = reinterpret_cast<const __nv_bfloat162 *>(&dch);
                         // general D (exact in BF16): gamma (the sum of its parts) times D_x in FP32,
                         // then the parts of the product
@@ -558,8 +569,7 @@ __global__ void __launch_bounds__(TcCfg<NSPLIT>::THREADS, 1)
                             for (int p = 0; p < NSPLIT; ++p) reinterpret_cast<__nv_bfloat162 *>(&o[p])[h] = pp[p];
                         }
 #pragma unroll
-                        for (int p = 0; p < NSPLIT; ++p)
-                            *reinterpret_cast<uint4 *>(abuf + a2_byte<C::SETS>(64 * set + 32 * p + x, o0)) = o[p];
+                        for (int p = 0; p < NSPLIT; ++p) *reinterpret_cast<uint4 *>(dst + 2048 * p) = o[p];
                     }
                 }
                 fence_proxy_async_smem();
