@@ -72,7 +72,8 @@ struct TcCfg {
     static constexpr uint32_t B1_BYTES = N1 * 64;
     static constexpr uint32_t A2_BLOCK = 128 * 64;                     // 128 rows x 32 observations (or pairs)
     static constexpr uint32_t A2_BYTES = (TILE / SETS / 32) * A2_BLOCK;
-    static constexpr uint32_t GAM_BYTES = NSPLIT * TILE * 2;           // staged BF16 parts of gamma
+    static constexpr bool TMEM_A2 = (NSPLIT == 2);                     // A2 in tensor memory (BF16 form)
+    static constexpr uint32_t GAM_BYTES = (TMEM_A2 ? 2 : 1) * NSPLIT * TILE * 2;   // staged BF16 parts of gamma (and w)
     static constexpr int EPOCH = 16;                                   // tiles per G'' epoch
     static constexpr int NCW = 8;                                      // consumer warps
     static constexpr int FLUSH_WARP0 = NCW;                            // warps 8..11
@@ -81,7 +82,8 @@ struct TcCfg {
     static constexpr int MMA2_WARP = NCW + 6;                          // issues MMA2
     static constexpr int THREADS = 32 * (NCW + 7);
     static constexpr int TMEM_COLS = 512;
-    static constexpr uint32_t COL_U = 0, COL_U_STRIDE = 128;          // U[u] at column 128 u
+    static constexpr uint32_t COL_U = 0, COL_U_STRIDE = TMEM_A2 ? N1 : 128;   // U[u] at column COL_U_STRIDE u
+    static constexpr uint32_t COL_A2 = NUBUF * COL_U_STRIDE, A2_COLS = 32;      // TMEM A2[b] at COL_A2 + 32 b
     static constexpr uint32_t COL_G = 384, COL_G_STRIDE = N2;          // G''[e & 1] at column 384 + N2 (e & 1)
     static constexpr int NTASK = 31 * (TILE / 8);                     // A2 chunks (8 observations) per part
     static constexpr uint32_t OFF_D = 0;                                // stage s at s * STAGE_BYTES (512-byte aligned)
@@ -108,6 +110,8 @@ struct TcCfg {
     static_assert(TILE_BYTES % 512 == 0 && D_BYTES + TILE * 4 == TILE_BYTES, "tile layout");
     static_assert(3 * THREADS * 8 <= NBUF * A2_BYTES, "reduction scratch");
     static_assert(SMEM_BYTES <= 227 * 1024, "shared memory per block");
+    static_assert(!TMEM_A2 || (SETS == 2 && COL_A2 % 16 == 0 && COL_A2 + NBUF * A2_COLS <= COL_G),
+                  "tensor memory of the A2 buffers");
     static_assert(D_BYTES <= 8192 && A2_BYTES <= 32768 && TILE / 8 <= 16, "packed chunk offsets (13 + 15 + 4 bits)");
     static_assert(size_t(gu_ws_doubles_rt(MMAX)) * 8 <= OFF_MISC, "workspace of the global update");
 };
@@ -329,8 +333,14 @@ __global__ void __launch_bounds__(TcCfg<NSPLIT>::THREADS, 1)
                         const uint32_t blk = uint32_t(kk >> 1), half = uint32_t(kk & 1) * 32;
                         const uint32_t boff = (C::SETS == 2) ? blk * 4096 + half
                                                              : (blk & 1) * 4096 + (blk >> 1) * 2048 + half;
-                        umma_bf16(tbase + C::COL_G + eb * C::COL_G_STRIDE, umma_desc(a0 + blk * 8192 + half, 16, 512, 4),
-                                  umma_desc(d0 + boff, 16, 512, 4), IDESC2, (first && kk == 0) ? 0u : 1u);
+                        if constexpr (C::TMEM_A2)
+                            umma_bf16_ts(tbase + C::COL_G + eb * C::COL_G_STRIDE,
+                                         tbase + C::COL_A2 + C::A2_COLS * uint32_t(b) + 8 * uint32_t(kk),
+                                         umma_desc(d0 + boff, 16, 512, 4), IDESC2, (first && kk == 0) ? 0u : 1u);
+                        else
+                            umma_bf16(tbase + C::COL_G + eb * C::COL_G_STRIDE,
+                                      umma_desc(a0 + blk * 8192 + half, 16, 512, 4), umma_desc(d0 + boff, 16, 512, 4),
+                                      IDESC2, (first && kk == 0) ? 0u : 1u);
                     }
                     umma_commit(&a2empty[b]);
                     umma_commit(&empty[s]);
@@ -481,6 +491,87 @@ __global__ void __launch_bounds__(TcCfg<NSPLIT>::THREADS, 1)
                     ex = 0;
                     cnt = 0;
                 }
+                if constexpr (C::TMEM_A2) {
+                    // stage this observation's parts of gamma and w for the A2 row builders
+                    const bool oka = (k < 4) || mbar_wait_backoff(&a2empty[b], uint32_t(((k >> 2) - 1) & 1), BUDGET);
+                    if (__any_sync(0xffffffffu, !oka)) {
+                        *s_abort = 1;
+                        break;
+                    }
+                    __nv_bfloat16 *gb = gam + b * (2 * NSPLIT * C::TILE);
+                    {
+                        __nv_bfloat16 gp[NSPLIT], wp[NSPLIT];
+                        f32_split<NSPLIT>(gm, gp);
+                        f32_split<NSPLIT>(w, wp);
+#pragma unroll
+                        for (int p = 0; p < NSPLIT; ++p) {
+                            gb[p * C::TILE + o_r] = gp[p];
+                            gb[(NSPLIT + p) * C::TILE + o_r] = wp[p];
+                        }
+                    }
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&staged[b]);
+                    const bool oks = mbar_wait_backoff(&staged[b], uint32_t((k >> 2) & 1), BUDGET);
+                    if (__any_sync(0xffffffffu, !oks)) {
+                        *s_abort = 1;
+                        break;
+                    }
+                    tc_fence_after();                   // after MMA2's reads of A2[b] (a2empty) and the staging
+                    // this thread's A2 row: tensor-memory lane 32 q + lane = (set q >> 1, part q & 1,
+                    // slot lane); K = the set's 64 observations, two per column.  Slot 31 of the tile
+                    // rows is 1, and row (set, part, 31) holds part `part` of w.
+                    const uint32_t set = uint32_t(q >> 1), part = uint32_t(q & 1), x = uint32_t(lane);
+                    uint32_t row[32];
+                    if (binary || x == 31) {
+                        const __nv_bfloat16 *src = gb + ((x == 31 ? NSPLIT : 0) + part) * C::TILE + 64 * set;
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            // 8 observations 64 set + 8 j ..: D in {-1, 0, 1} (or the constant 1), so each
+                            // product is exact in BF16
+                            const uint4 dv = *reinterpret_cast<const uint4 *>(dt + tc_slot_byte(64 * set + 8 * j, x));
+                            const uint4 gv = *reinterpret_cast<const uint4 *>(src + 8 * j);
+                            const __nv_bfloat162 *dp = reinterpret_cast<const __nv_bfloat162 *>(&dv);
+                            const __nv_bfloat162 *gq = reinterpret_cast<const __nv_bfloat162 *>(&gv);
+#pragma unroll
+                            for (int h = 0; h < 4; ++h)
+                                reinterpret_cast<__nv_bfloat162 *>(&row[4 * j + h])[0] = __hmul2(gq[h], dp[h]);
+                        }
+                    } else {
+                        // general D (exact in BF16): gamma (the sum of its parts) times D_x in FP32,
+                        // then part `part` of the product
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const uint4 dv = *reinterpret_cast<const uint4 *>(dt + tc_slot_byte(64 * set + 8 * j, x));
+                            const __nv_bfloat162 *dp = reinterpret_cast<const __nv_bfloat162 *>(&dv);
+                            float g8[8];
+#pragma unroll
+                            for (int h = 0; h < 8; ++h) g8[h] = 0.0f;
+#pragma unroll
+                            for (int p = 0; p < NSPLIT; ++p) {
+                                const uint4 gv = *reinterpret_cast<const uint4 *>(gb + p * C::TILE + 64 * set + 8 * j);
+                                const __nv_bfloat16 *gq = reinterpret_cast<const __nv_bfloat16 *>(&gv);
+#pragma unroll
+                                for (int h = 0; h < 8; ++h) g8[h] += __bfloat162float(gq[h]);
+                            }
+#pragma unroll
+                            for (int h = 0; h < 4; ++h) {
+                                const float2 df = __bfloat1622float2(dp[h]);
+                                __nv_bfloat162 pp[NSPLIT];
+                                f32x2_split<NSPLIT>(g8[2 * h] * df.x, g8[2 * h + 1] * df.y, pp);
+                                uint32_t u0, u1;
+                                memcpy(&u0, &pp[0], 4);
+                                memcpy(&u1, &pp[1], 4);
+                                row[4 * j + h] = part ? u1 : u0;
+                            }
+                        }
+                    }
+                    tmem_st32(tbase + lanebase + C::COL_A2 + C::A2_COLS * uint32_t(b), row);
+                    tmem_wait_st();
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&a2full[b]);
+                    continue;
+                } else {
                 // stage this observation's parts: gamma for the chunk builders, w straight into
                 // A2 row (set, p, 31)
                 const bool oka = (k < 4) || mbar_wait_backoff(&a2empty[b], uint32_t(((k >> 2) - 1) & 1), BUDGET);
@@ -575,6 +666,7 @@ __global__ void __launch_bounds__(TcCfg<NSPLIT>::THREADS, 1)
                 fence_proxy_async_smem();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&a2full[b]);
+                }
             }
             t3_64 += static_cast<double>(t3);
             t4_64 += static_cast<double>(logf(prod));
