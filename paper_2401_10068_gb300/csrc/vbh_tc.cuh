@@ -522,12 +522,15 @@ __global__ void __launch_bounds__(TcCfg<NSPLIT>::THREADS, 1)
                     // rows is 1, and row (set, part, 31) holds part `part` of w.
                     const uint32_t set = uint32_t(q >> 1), part = uint32_t(q & 1), x = uint32_t(lane);
                     uint32_t row[32];
-                    if (binary || x == 31) {
-                        const __nv_bfloat16 *src = gb + ((x == 31 ? NSPLIT : 0) + part) * C::TILE + 64 * set;
+                    const uint32_t ta2 = tbase + lanebase + C::COL_A2 + C::A2_COLS * uint32_t(b);
+                    const __nv_bfloat16 *wsrc = gb + (NSPLIT + part) * C::TILE + 64 * set;
+                    if (binary) {                       // warp-uniform: every tensor-memory store below is converged
+                        const __nv_bfloat16 *src = (x == 31) ? wsrc : gb + part * C::TILE + 64 * set;
 #pragma unroll
                         for (int j = 0; j < 8; ++j) {
-                            // 8 observations 64 set + 8 j ..: D in {-1, 0, 1} (or the constant 1), so each
-                            // product is exact in BF16
+                            if (j == 4) tmem_st16(ta2, row);          // first half on its way
+                            // 8 observations 64 set + 8 j ..: D in {-1, 0, 1} (or the constant 1 of slot
+                            // 31), so each product is exact in BF16
                             const uint4 dv = *reinterpret_cast<const uint4 *>(dt + tc_slot_byte(64 * set + 8 * j, x));
                             const uint4 gv = *reinterpret_cast<const uint4 *>(src + 8 * j);
                             const __nv_bfloat162 *dp = reinterpret_cast<const __nv_bfloat162 *>(&dv);
@@ -536,13 +539,16 @@ __global__ void __launch_bounds__(TcCfg<NSPLIT>::THREADS, 1)
                             for (int h = 0; h < 4; ++h)
                                 reinterpret_cast<__nv_bfloat162 *>(&row[4 * j + h])[0] = __hmul2(gq[h], dp[h]);
                         }
+                        tmem_st16(ta2 + 16, row + 16);
                     } else {
                         // general D (exact in BF16): gamma (the sum of its parts) times D_x in FP32,
-                        // then part `part` of the product
+                        // then part `part` of the product; slot 31 takes part `part` of w as staged
 #pragma unroll
                         for (int j = 0; j < 8; ++j) {
                             const uint4 dv = *reinterpret_cast<const uint4 *>(dt + tc_slot_byte(64 * set + 8 * j, x));
+                            const uint4 wv = *reinterpret_cast<const uint4 *>(wsrc + 8 * j);
                             const __nv_bfloat162 *dp = reinterpret_cast<const __nv_bfloat162 *>(&dv);
+                            const uint32_t *wq = reinterpret_cast<const uint32_t *>(&wv);
                             float g8[8];
 #pragma unroll
                             for (int h = 0; h < 8; ++h) g8[h] = 0.0f;
@@ -561,11 +567,11 @@ __global__ void __launch_bounds__(TcCfg<NSPLIT>::THREADS, 1)
                                 uint32_t u0, u1;
                                 memcpy(&u0, &pp[0], 4);
                                 memcpy(&u1, &pp[1], 4);
-                                row[4 * j + h] = part ? u1 : u0;
+                                row[4 * j + h] = (x == 31) ? wq[h] : (part ? u1 : u0);
                             }
                         }
+                        tmem_st32(ta2, row);
                     }
-                    tmem_st32(tbase + lanebase + C::COL_A2 + C::A2_COLS * uint32_t(b), row);
                     tmem_wait_st();
                     tc_fence_before();
                     __syncwarp();
