@@ -55,6 +55,11 @@ struct vbh_handle {
     int trace_cap = 0;
     float *stage_r = nullptr, *stage_d = nullptr;
     size_t stage_cap_r = 0, stage_cap_d = 0;   // bytes
+    // copy streams for host inputs: large copies are split over them so that several
+    // copy engines move the data; events join them with the handle's stream
+    static constexpr int NCOPY = 4;
+    cudaStream_t copy_stream[NCOPY] = {};
+    cudaEvent_t copy_event[NCOPY + 1] = {};
     // current fit
     bool begun = false;
     int S = 0;
@@ -224,8 +229,38 @@ int ensure(void **buf, size_t *cap, size_t bytes)
     return VBH_OK;
 }
 
+// Host -> device copy ordered on the handle's stream.  Copies of 256 MiB or
+// more are split into chunks issued round robin on the handle's copy streams
+// (after the work queued so far on the handle's stream), whose completion the
+// handle's stream then waits for.
+int copy_h2d(vbh_handle *h, void *dst, const void *src, size_t bytes)
+{
+    constexpr size_t SPLIT_MIN = size_t(256) << 20;
+    if (bytes < SPLIT_MIN || !h->copy_stream[0]) {
+        VBH_CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, h->stream));
+        return VBH_OK;
+    }
+    constexpr int NC = vbh_handle::NCOPY;
+    VBH_CK(cudaEventRecord(h->copy_event[NC], h->stream));
+    for (int i = 0; i < NC; ++i) VBH_CK(cudaStreamWaitEvent(h->copy_stream[i], h->copy_event[NC], 0));
+    const size_t nchunk = 4 * NC;
+    const size_t chunk = ((bytes + nchunk - 1) / nchunk + 4095) & ~size_t(4095);
+    size_t off = 0;
+    for (size_t c = 0; off < bytes; ++c) {
+        const size_t len = (bytes - off < chunk) ? bytes - off : chunk;
+        VBH_CK(cudaMemcpyAsync(static_cast<char *>(dst) + off, static_cast<const char *>(src) + off, len,
+                               cudaMemcpyHostToDevice, h->copy_stream[c % NC]));
+        off += len;
+    }
+    for (int i = 0; i < NC; ++i) {
+        VBH_CK(cudaEventRecord(h->copy_event[i], h->copy_stream[i]));
+        VBH_CK(cudaStreamWaitEvent(h->stream, h->copy_event[i], 0));
+    }
+    return VBH_OK;
+}
+
 // Resolve (r, d) to device pointers, copying host inputs into the handle's
-// staging buffers on the handle's stream.
+// staging buffers, ordered on the handle's stream.
 int stage_inputs(vbh_handle *h, const float *r, const float *d, long long V, int S, const float **rd,
                  const float **dd)
 {
@@ -240,7 +275,7 @@ int stage_inputs(vbh_handle *h, const float *r, const float *d, long long V, int
     if (kr == PTR_HOST) {
         int rc = ensure(reinterpret_cast<void **>(&h->stage_r), &h->stage_cap_r, br);
         if (rc) return rc;
-        VBH_CK(cudaMemcpyAsync(h->stage_r, r, br, cudaMemcpyHostToDevice, h->stream));
+        if ((rc = copy_h2d(h, h->stage_r, r, br))) return rc;
         *rd = h->stage_r;
     } else {
         *rd = r;
@@ -248,7 +283,7 @@ int stage_inputs(vbh_handle *h, const float *r, const float *d, long long V, int
     if (kd == PTR_HOST) {
         int rc = ensure(reinterpret_cast<void **>(&h->stage_d), &h->stage_cap_d, bd);
         if (rc) return rc;
-        VBH_CK(cudaMemcpyAsync(h->stage_d, d, bd, cudaMemcpyHostToDevice, h->stream));
+        if ((rc = copy_h2d(h, h->stage_d, d, bd))) return rc;
         *dd = h->stage_d;
     } else {
         *dd = d;
@@ -598,6 +633,10 @@ int vbh_create(vbh_handle **hp, int device, void *stream)
     if (!rc && cudaMalloc(&h->st, sizeof(DevState)) != cudaSuccess) rc = VBH_ENOMEM;
     if (!rc && cudaMalloc(&h->st_aux, sizeof(DevState)) != cudaSuccess) rc = VBH_ENOMEM;
     if (!rc && cudaMallocHost(&h->mirror, sizeof(DevState)) != cudaSuccess) rc = VBH_ENOMEM;
+    for (int i = 0; !rc && i < vbh_handle::NCOPY; ++i)
+        if (cudaStreamCreateWithFlags(&h->copy_stream[i], cudaStreamNonBlocking) != cudaSuccess) rc = VBH_ECUDA;
+    for (int i = 0; !rc && i <= vbh_handle::NCOPY; ++i)
+        if (cudaEventCreateWithFlags(&h->copy_event[i], cudaEventDisableTiming) != cudaSuccess) rc = VBH_ECUDA;
     if (rc) {
         (void)cudaGetLastError();
         vbh_destroy(h);
@@ -623,6 +662,13 @@ void vbh_destroy(vbh_handle *h)
     cudaFree(h->gstats);
     cudaFree(h->counts);
     if (h->mirror) cudaFreeHost(h->mirror);
+    for (int i = 0; i < vbh_handle::NCOPY; ++i)
+        if (h->copy_stream[i]) {
+            cudaStreamSynchronize(h->copy_stream[i]);
+            cudaStreamDestroy(h->copy_stream[i]);
+        }
+    for (int i = 0; i <= vbh_handle::NCOPY; ++i)
+        if (h->copy_event[i]) cudaEventDestroy(h->copy_event[i]);
     cudaFree(h->batched.arena);
     if (h->batched.host_states) cudaFreeHost(h->batched.host_states);
     (void)cudaGetLastError();
