@@ -273,7 +273,9 @@ def run_ours(args):
                              "bytes_per_launch": bytes_alg},
                 "cpu_baseline": cpu,
                 "e2e": e2e,
-                "gpu_launches": args.steps + 1,
+                # the sweeps, the budget kernel of fit_step and, for an odd step count, the
+                # second (idle) sweep launch of the graph's last loop iteration
+                "gpu_launches": args.steps + 1 + (args.steps % 2),
                 "clocks": clk}
         print(json.dumps(line), flush=True)
     if dist:

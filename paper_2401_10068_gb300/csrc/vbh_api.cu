@@ -450,7 +450,7 @@ int build_graph(vbh_handle *h)
     int rc = VBH_OK;
     cudaGraphConditionalHandle cond;
     cudaGraphNodeParams cp{};
-    cudaGraphNode_t wnode, knode;
+    cudaGraphNode_t wnode, knode, knode2;
     cudaGraphNodeParams kp{};
     vbh::SweepArgs a{};
     vbh::TcArgs ta{};
@@ -493,7 +493,11 @@ int build_graph(vbh_handle *h)
     kp.kernel.blockDim = dim3(L.threads());
     kp.kernel.sharedMemBytes = (unsigned)L.smem();
     kp.kernel.kernelParams = L.grp ? gargs : L.tc ? targs : args;
-    if (cudaGraphAddNode(&knode, cp.conditional.phGraph_out[0], nullptr, nullptr, 0, &kp) != cudaSuccess) {
+    // two sweeps per iteration of the while node: the second launch does no pass when the
+    // first converged or used up the sweep budget (the kernel checks the state first), and
+    // the conditional is evaluated half as often
+    if (cudaGraphAddNode(&knode, cp.conditional.phGraph_out[0], nullptr, nullptr, 0, &kp) != cudaSuccess ||
+        cudaGraphAddNode(&knode2, cp.conditional.phGraph_out[0], &knode, nullptr, 1, &kp) != cudaSuccess) {
         vbh::record_error("cudaGraphAddNode(sweep)", __FILE__, __LINE__, cudaGetErrorName(cudaGetLastError()));
         rc = VBH_ECUDA;
         goto out;
