@@ -35,7 +35,7 @@ struct Launch {
     KernelInfo ki{};
     vbh::TcKernelInfo tki{};
     const unsigned char *tiles = nullptr;   // repacked inputs of the tensor-core sweep
-    const void *func() const { return grp ? vbh::grouped_sweep_func() : tc ? tki.sweep : ki.sweep; }
+    const void *func() const { return grp ? vbh::grouped_sweep_func(S) : tc ? tki.sweep : ki.sweep; }
     const void *setup() const { return (tc || grp) ? tki.setup : ki.setup; }
     int threads() const { return grp ? vbh::GROUPED_THREADS : tc ? tki.threads : ki.threads; }
     size_t smem() const { return grp ? vbh::grouped_smem_bytes() : tc ? tki.smem : ki.smem; }
@@ -336,8 +336,7 @@ int prepare_launch(vbh_handle *h, int S, long long V, int precision, const float
         VBH_CK(cudaStreamSynchronize(h->stream));
         if (nonbin != 0) return VBH_EINVAL;                                      // the grouped form needs binary d
         L->gstats = h->gstats;
-        long long g = (L->P + 7) / 8;                                            // 8 warps per block
-        if (g > h->nsm) g = h->nsm;
+        long long g = vbh::grouped_grid(S, h->nsm);
         if (g > vbh::GRID_MAX) g = vbh::GRID_MAX;
         L->grid = int(g);
         return ensure(reinterpret_cast<void **>(&h->partials), &h->partials_cap,

@@ -148,13 +148,161 @@ __global__ void __launch_bounds__(GROUPED_THREADS) grouped_sweep_kernel(GroupArg
     }
 }
 
-const void *grouped_sweep_func() { return reinterpret_cast<const void *>(&grouped_sweep_kernel); }
+// The same sweep for many profile codes (S >= GROUPED_WIDE_S): lane = code.
+// Warp w of the grid takes batches of 32 codes w, w + W, ...; each lane forms
+// v = L~^T D, q, t and the scalar sums of its code in FP64 (D in {-1, 0, 1} by
+// selection, no conversions), then the lanes switch roles: lane l owns the
+// packed entries l, l + 32, ... of G and entry l of g and adds the batch's 32
+// codes in order.  About a tenth of the FP64 instructions per code of the
+// row-per-lane form, whose cost is one warp's chain per code.
+namespace {
+constexpr int GNG = GMAX * (GMAX + 1) / 2;                       // packed entries of G at the largest M
+constexpr int WIDE_GPL = (GNG + 31) / 32;                        // G entries per lane
+constexpr size_t WIDE_PASS_DOUBLES = GNG + 16 + 3 * GW * 32;    // L~, kappa~, per-warp (gamma sum, w sum, code)
+} // namespace
+
+__global__ void __launch_bounds__(GROUPED_THREADS) grouped_sweep_wide_kernel(GroupArgs ga)
+{
+    extern __shared__ double gsm[];
+    __shared__ int s_last;
+    const SweepArgs &a = ga.sa;
+    DevState *st = a.st;
+    const int S = st->S, M = S - 1;
+    const int NG = M * (M + 1) / 2, NSTAT = NG + M + 3;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool run = (a.mode != MODE_ITER) ||
+                     (st->status == ST_OK && !st->converged && st->iter < st->target && st->iter < st->max_iter);
+
+    double *Lf = gsm;                                            // L~ (packed lower, row i at i(i+1)/2), FP64
+    double *kf = Lf + GNG;                                       // kappa~
+    double *wsg = kf + 16;                                       // per warp: sum (w^2 - c) of each code
+    double *wsw = wsg + GW * 32;                                 // per warp: sum w of each code
+    int *wcode = reinterpret_cast<int *>(wsw + GW * 32);         // per warp: the codes
+    double *red = gsm + WIDE_PASS_DOUBLES;                       // [warp][NSTAT] partials
+
+    double gacc[WIDE_GPL], gvl = 0.0, t3 = 0.0, t4 = 0.0;
+#pragma unroll
+    for (int i = 0; i < WIDE_GPL; ++i) gacc[i] = 0.0;
+    int er[WIDE_GPL], ec[WIDE_GPL];                              // this lane's G entries as (row, column)
+#pragma unroll
+    for (int i = 0; i < WIDE_GPL; ++i) {
+        const int e = lane + 32 * i;
+        int r = 0;
+        while ((r + 1) * (r + 2) / 2 <= e) ++r;
+        er[i] = (e < NG) ? r : -1;
+        ec[i] = e - r * (r + 1) / 2;
+    }
+    if (run) {
+        for (int e = tid; e < NG; e += blockDim.x) Lf[e] = static_cast<double>(st->sw.L[e]);
+        for (int i = tid; i < M; i += blockDim.x) kf[i] = static_cast<double>(st->sw.kappa[i]);
+        __syncthreads();
+        const double erho = static_cast<double>(st->sw.erho);
+        const int nbatch = (ga.P + 31) / 32, nw = gridDim.x * GW;
+        for (int bt = blockIdx.x * GW + warp; bt < nbatch; bt += nw) {
+            const int p = bt * 32 + lane;
+            const bool valid = p < ga.P;
+            const double n = valid ? ga.stats[3 * p] : 0.0;
+            const double sy = valid ? ga.stats[3 * p + 1] : 0.0, syy = valid ? ga.stats[3 * p + 2] : 0.0;
+            const int bS = (p >> M) & 1;
+            auto Dk = [&](int k) -> double {                     // D_k = d_k - d_S in {-1, 0, 1}
+                const int b = (p >> k) & 1;
+                return b == bS ? 0.0 : (b ? 1.0 : -1.0);
+            };
+            double q = 0.0, t = 0.0;
+#pragma unroll
+            for (int j = 0; j < GMAX; ++j) {
+                if (j < M) {
+                    double v = 0.0;                              // (L~^T D)_j = sum_{k >= j} L~(k, j) D_k
+#pragma unroll
+                    for (int k = j; k < GMAX; ++k)
+                        if (k < M) {
+                            const double dk = Dk(k);
+                            if (dk != 0.0) v = fma(Lf[k * (k + 1) / 2 + j], dk, v);
+                        }
+                    q = fma(v, v, q);
+                    const double dj = Dk(j);
+                    if (dj != 0.0) t = fma(kf[j], dj, t);
+                }
+            }
+            const double den = fma(erho, q, 1.0);
+            const double inv = 1.0 / den;
+            const double c = erho * inv;
+            const double se = sy - n * t;
+            const double see = syy - 2.0 * t * sy + n * t * t;
+            t3 += inv * inv * see + n * q * inv;
+            t4 += n * log(den);
+            wsg[warp * 32 + lane] = c * c * see - n * c;
+            wsw[warp * 32 + lane] = c * se;
+            wcode[warp * 32 + lane] = p;
+            __syncwarp();
+            for (int cc = 0; cc < 32; ++cc) {
+                const int pc = wcode[warp * 32 + cc];
+                const int bc = (pc >> M) & 1;
+                const double sg = wsg[warp * 32 + cc], sw = wsw[warp * 32 + cc];
+#pragma unroll
+                for (int i = 0; i < WIDE_GPL; ++i)
+                    if (er[i] >= 0) {
+                        const int dr = ((pc >> er[i]) & 1) - bc, dc = ((pc >> ec[i]) & 1) - bc;
+                        const int pr = dr * dc;                  // D_r D_c in {-1, 0, 1}
+                        if (pr != 0) gacc[i] += (pr > 0) ? sg : -sg;
+                    }
+                if (lane < M) {
+                    const int dj = ((pc >> lane) & 1) - bc;
+                    if (dj != 0) gvl += (dj > 0) ? sw : -sw;
+                }
+            }
+            __syncwarp();
+        }
+    }
+    // per-warp partials -> shared memory [warp][NSTAT] -> this block's partials (fixed order)
+    const double t3w = warp_sum(t3), t4w = warp_sum(t4);
+#pragma unroll
+    for (int i = 0; i < WIDE_GPL; ++i)
+        if (er[i] >= 0) red[warp * GNSTAT + lane + 32 * i] = gacc[i];
+    if (lane < M) red[warp * GNSTAT + NG + lane] = gvl;
+    if (lane == 0) {
+        red[warp * GNSTAT + NG + M] = t3w;
+        red[warp * GNSTAT + NG + M + 1] = t4w;
+        red[warp * GNSTAT + NG + M + 2] = 0.0;
+    }
+    __syncthreads();
+    double *part = a.partials + size_t(blockIdx.x) * NSTAT;
+    for (int j = tid; j < NSTAT; j += blockDim.x) {
+        double sum = 0.0;
+        for (int w = 0; w < GW; ++w) sum += red[w * GNSTAT + j];
+        part[j] = sum;
+    }
+    int row0, nrows;
+    if (!finish_ticket(st, a.partials, gridDim.x, NSTAT, &s_last, &row0, &nrows, gsm)) return;
+    if (run && st->status == ST_OK) {
+        global_update_rt(M, st, a.partials + size_t(row0) * NSTAT, nrows, a, gsm);
+    } else if (tid == 0 && a.use_cond) {
+        cudaGraphSetConditional(a.cond, 0u);
+    }
+}
+
+const void *grouped_sweep_func(int S)
+{
+    return S >= GROUPED_WIDE_S ? reinterpret_cast<const void *>(&grouped_sweep_wide_kernel)
+                               : reinterpret_cast<const void *>(&grouped_sweep_kernel);
+}
+
+int grouped_grid(int S, int nsm)
+{
+    const long long P = 1LL << S;
+    long long g = (S >= GROUPED_WIDE_S) ? ((P + 31) / 32 + GW - 1) / GW : (P + GW - 1) / GW;   // warps of 32 codes / one code
+    const long long cap = (S >= GROUPED_WIDE_S) ? 2LL * nsm : nsm;            // the wide form: two blocks per SM
+    if (g > cap) g = cap;
+    return int(g < 1 ? 1 : g);
+}
 
 size_t grouped_smem_bytes()
 {
     const size_t red = size_t(GW) * GNSTAT * sizeof(double);
+    const size_t wide = (WIDE_PASS_DOUBLES + size_t(GW) * GNSTAT) * sizeof(double);
     const size_t ws = size_t(gu_ws_doubles_rt(GMAX)) * sizeof(double);
-    return red > ws ? red : ws;
+    size_t m = red > ws ? red : ws;
+    return m > wide ? m : wide;
 }
 
 int grouped_histogram(const float *r, const float *d, long long V, int S, double *stats,

@@ -18,9 +18,14 @@ struct GroupArgs {
     int P;                                   // 2^S
 };
 
-// The grouped sweep kernel (its grid: up to one block per SM, 8 warps each) and
-// its dynamic shared memory.
-const void *grouped_sweep_func();
+// From this S on the sweep takes 32 codes per warp (lane = code).
+constexpr int GROUPED_WIDE_S = 12;
+
+// The grouped sweep kernel for S, its grid (8 warps per block; up to one block
+// per SM, two for the wide form) and its dynamic shared memory (the same for
+// every S).
+const void *grouped_sweep_func(int S);
+int grouped_grid(int S, int nsm);
 size_t grouped_smem_bytes();
 
 // stats (3 * 2^S doubles, device, zeroed by the caller) += per-code counts and
