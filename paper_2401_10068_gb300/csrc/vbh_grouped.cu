@@ -62,6 +62,59 @@ __global__ void grouped_hist_kernel(const float *__restrict__ r, const float *__
     if (bad) atomicAdd(nonbinary, bad);
 }
 
+// The per-code work of the sweep below for M <= GM (loops of GM terms): warp
+// w of the grid takes codes w, w + W, ...; lane j < M keeps row j of the
+// packed G (columns k <= j) and g_j; D_k = d_k - d_S in {-1, 0, 1} by
+// selection (no conversions).
+template <int GM>
+__device__ __forceinline__ void grouped_codes(const GroupArgs &ga, const DevState *st, int lane, int warp,
+                                              double (&gacc)[GMAX], double &gv, double &t3, double &t4)
+{
+    const int M = st->S - 1;
+    // column `lane` of L~ and kappa~ of the pass (FP32 globals, as the per-observation sweep)
+    double lcol[GM > 0 ? GM : 1];
+#pragma unroll
+    for (int k = 0; k < GM; ++k)
+        lcol[k] = (lane < M && k < M && k >= lane) ? static_cast<double>(st->sw.L[k * (k + 1) / 2 + lane]) : 0.0;
+    const double kap = lane < M ? static_cast<double>(st->sw.kappa[lane]) : 0.0;
+    const double erho = static_cast<double>(st->sw.erho);
+    const int nwarps = gridDim.x * GW;
+    for (int p = blockIdx.x * GW + warp; p < ga.P; p += nwarps) {
+        const double n = ga.stats[3 * p];
+        if (n == 0.0) continue;                                 // warp-uniform
+        const double sy = ga.stats[3 * p + 1], syy = ga.stats[3 * p + 2];
+        const int bS = (p >> M) & 1;
+        auto Dk = [&](int k) -> double {
+            const int b = (p >> k) & 1;
+            return b == bS ? 0.0 : (b ? 1.0 : -1.0);
+        };
+        double v = 0.0;
+#pragma unroll
+        for (int k = 0; k < GM; ++k) v = fma(lcol[k], (k < M) ? Dk(k) : 0.0, v);   // (L~^T D)_lane
+        const double Dj = lane < M ? Dk(lane) : 0.0;
+        const double q = warp_sum(v * v);
+        const double t = warp_sum(kap * Dj);
+        const double den = fma(erho, q, 1.0);
+        const double inv = 1.0 / den;
+        const double c = erho * inv;
+        const double se = sy - n * t;
+        const double see = syy - 2.0 * t * sy + n * t * t;
+        const double sw = c * se;
+        const double sgam = c * c * see - n * c;
+        if (lane < M) {
+            const double sd = sgam * Dj;
+#pragma unroll
+            for (int k = 0; k < GM; ++k)
+                if (k <= lane) gacc[k] = fma(sd, Dk(k), gacc[k]);
+            gv = fma(sw, Dj, gv);
+        }
+        if (lane == 0) {
+            t3 += inv * inv * see + n * q * inv;
+            t4 += n * log(den);
+        }
+    }
+}
+
 // One sweep over the profile groups: warp w of the grid takes codes w, w + W, ...;
 // lane j < M keeps row j of the packed G (columns k <= j) and g_j in registers.
 __global__ void __launch_bounds__(GROUPED_THREADS) grouped_sweep_kernel(GroupArgs ga)
@@ -80,43 +133,19 @@ __global__ void __launch_bounds__(GROUPED_THREADS) grouped_sweep_kernel(GroupArg
 #pragma unroll
     for (int k = 0; k < GMAX; ++k) gacc[k] = 0.0;
     if (run) {
-        // column `lane` of L~ and kappa~ of the pass (FP32 globals, as the per-observation sweep)
-        double lcol[GMAX];
-#pragma unroll
-        for (int k = 0; k < GMAX; ++k)
-            lcol[k] = (lane < M && k < M && k >= lane) ? static_cast<double>(st->sw.L[k * (k + 1) / 2 + lane]) : 0.0;
-        const double kap = lane < M ? static_cast<double>(st->sw.kappa[lane]) : 0.0;
-        const double erho = static_cast<double>(st->sw.erho);
-        const int nwarps = gridDim.x * GW;
-        for (int p = blockIdx.x * GW + warp; p < ga.P; p += nwarps) {
-            const double n = ga.stats[3 * p];
-            if (n == 0.0) continue;                             // warp-uniform
-            const double sy = ga.stats[3 * p + 1], syy = ga.stats[3 * p + 2];
-            const int bS = (p >> M) & 1;
-            auto Dk = [&](int k) { return static_cast<double>(((p >> k) & 1) - bS); };
-            double v = 0.0;
-#pragma unroll
-            for (int k = 0; k < GMAX; ++k) v = fma(lcol[k], (k < M) ? Dk(k) : 0.0, v);   // (L~^T D)_lane
-            const double Dj = lane < M ? Dk(lane) : 0.0;
-            const double q = warp_sum(v * v);
-            const double t = warp_sum(kap * Dj);
-            const double den = fma(erho, q, 1.0);
-            const double inv = 1.0 / den;
-            const double c = erho * inv;
-            const double se = sy - n * t;
-            const double see = syy - 2.0 * t * sy + n * t * t;
-            const double sw = c * se;
-            const double sgam = c * c * see - n * c;
-            if (lane < M) {
-#pragma unroll
-                for (int k = 0; k < GMAX; ++k)
-                    if (k <= lane) gacc[k] = fma(sgam * Dj, Dk(k), gacc[k]);
-                gv = fma(sw, Dj, gv);
-            }
-            if (lane == 0) {
-                t3 += inv * inv * see + n * q * inv;
-                t4 += n * log(den);
-            }
+        switch (M) {                                            // loops of exactly M terms
+        case 0: grouped_codes<0>(ga, st, lane, warp, gacc, gv, t3, t4); break;
+        case 1: grouped_codes<1>(ga, st, lane, warp, gacc, gv, t3, t4); break;
+        case 2: grouped_codes<2>(ga, st, lane, warp, gacc, gv, t3, t4); break;
+        case 3: grouped_codes<3>(ga, st, lane, warp, gacc, gv, t3, t4); break;
+        case 4: grouped_codes<4>(ga, st, lane, warp, gacc, gv, t3, t4); break;
+        case 5: grouped_codes<5>(ga, st, lane, warp, gacc, gv, t3, t4); break;
+        case 6: grouped_codes<6>(ga, st, lane, warp, gacc, gv, t3, t4); break;
+        case 7: grouped_codes<7>(ga, st, lane, warp, gacc, gv, t3, t4); break;
+        case 8: grouped_codes<8>(ga, st, lane, warp, gacc, gv, t3, t4); break;
+        case 9: grouped_codes<9>(ga, st, lane, warp, gacc, gv, t3, t4); break;
+        case 10: grouped_codes<10>(ga, st, lane, warp, gacc, gv, t3, t4); break;
+        default: grouped_codes<GMAX>(ga, st, lane, warp, gacc, gv, t3, t4); break;
         }
     }
     // per-warp partials -> shared memory [warp][NSTAT] -> this block's partials (fixed order)
