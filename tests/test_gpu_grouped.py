@@ -56,7 +56,9 @@ CASES = [
     (2, 20011, 2, 10, 0.0),
     (3, 96000, 3, 25, 0.05),
     (8, 1_000_003, 4, 10, 0.05),
-    (12, 300_007, 5, 6, 0.0),
+    (11, 150_001, 10, 5, 0.05),         # the last S of the warp-per-code form
+    (12, 300_007, 5, 6, 0.0),           # from here a lane per code
+    (14, 500_009, 11, 4, 0.0),
     (16, 200_003, 6, 4, 0.05),
 ]
 
@@ -93,6 +95,19 @@ def test_grouped_converged(handle):
 def test_grouped_em(handle):
     S, V, iters = 5, 200_003, 12
     r, d, _ = synth.generate(V, S, seed=8, alpha=0.5, p_const=0.05)
+    prior = O.paper_prior(S)
+    ref = O.em_fit(r, d, S, O.em_init(prior), tol=0.0, max_iter=iters)
+    got = handle.fit(_dev(r), _dev(d), S, prior, tol=0.0, max_iter=iters, trace=True, grouped=True, method=vbh.EM)
+    assert rel(got["kappa"], ref["K"]) < TOL_PARAM and rel(got["Winv"], ref["Linv"]) < TOL_PARAM
+    assert rel(got["rho_mean"], ref["rho"]) < TOL_PARAM
+    for t, (a, b) in enumerate(zip(got["trace"], ref["trace"])):
+        assert close(a, b, V), (t, a, b)
+
+
+def test_grouped_em_lane_per_code(handle):
+    """EM through the lane-per-code form of the grouped sweep (S = 13)."""
+    S, V, iters = 13, 300_007, 5
+    r, d, _ = synth.generate(V, S, seed=12, alpha=0.5)
     prior = O.paper_prior(S)
     ref = O.em_fit(r, d, S, O.em_init(prior), tol=0.0, max_iter=iters)
     got = handle.fit(_dev(r), _dev(d), S, prior, tol=0.0, max_iter=iters, trace=True, grouped=True, method=vbh.EM)
