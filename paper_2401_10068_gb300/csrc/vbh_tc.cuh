@@ -47,6 +47,17 @@
 
 namespace vbh {
 
+// 16 consecutive 32-bit columns of this thread's TMEM lane (32x32b shape, x16),
+// without the wait.
+__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t (&r)[16])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                   "=r"(r[15])
+                 : "r"(taddr));
+}
+
 // Layout of the BF16 part of a tile (8 KiB, two 4 KiB blocks j of 64 rows x 64
 // bytes, 64-byte swizzle): observation o of slot x sits in block (o >> 5) & 1,
 // row 32 (o >> 6) + x, element o & 31.
@@ -63,9 +74,10 @@ struct TcCfg {
     static constexpr int N1 = ((33 * NSPLIT + 15) / 16) * 16;          // MMA1 N: parts of v, then of t (80, 112)
     static constexpr int N2 = 32 * SETS;                               // MMA2 N
     static constexpr int NK2 = 8 / SETS;                               // MMA2 instructions per tile (K = 16)
+    static constexpr int NCG = 2;                                      // consumer groups (tile k: group k % NCG)
     static constexpr int STAGES = (NSPLIT == 2) ? 8 : 4;               // pipeline stages of two tiles
-    static constexpr int NUBUF = 3;                                    // U buffers (tile k uses k % 3)
-    static constexpr int NBUF = 4;                                     // A2 buffers (tile k uses k & 3)
+    static constexpr int NUBUF = NCG;                                  // U buffers (tile k uses k % NUBUF)
+    static constexpr int NBUF = 4;                                     // A2 buffers (tile k uses k % NBUF)
     static constexpr uint32_t D_BYTES = TILE * 64;                     // BF16 slots of a tile
     static constexpr uint32_t TILE_BYTES = TC_TILE_BYTES;              // + 128 y values
     static constexpr uint32_t STAGE_BYTES = 2 * TILE_BYTES;
@@ -75,8 +87,8 @@ struct TcCfg {
     static constexpr bool TMEM_A2 = (NSPLIT == 2);                     // A2 in tensor memory (BF16 form)
     static constexpr uint32_t GAM_BYTES = (TMEM_A2 ? 2 : 1) * NSPLIT * TILE * 2;   // staged BF16 parts of gamma (and w)
     static constexpr int EPOCH = 16;                                   // tiles per G'' epoch
-    static constexpr int NCW = 8;                                      // consumer warps
-    static constexpr int FLUSH_WARP0 = NCW;                            // warps 8..11
+    static constexpr int NCW = 4 * NCG;                                // consumer warps
+    static constexpr int FLUSH_WARP0 = NCW;                            // four flusher warps
     static constexpr int PRODUCER_WARP = NCW + 4;
     static constexpr int MMA1_WARP = NCW + 5;                          // issues MMA1 (runs ahead)
     static constexpr int MMA2_WARP = NCW + 6;                          // issues MMA2
@@ -88,9 +100,14 @@ struct TcCfg {
     static constexpr int NTASK = 31 * (TILE / 8);                     // A2 chunks (8 observations) per part
     static constexpr uint32_t OFF_D = 0;                                // stage s at s * STAGE_BYTES (512-byte aligned)
     static constexpr uint32_t OFF_A2 = ((OFF_D + STAGES * STAGE_BYTES + 1023) / 1024) * 1024;
-    static constexpr uint32_t OFF_B1 = OFF_A2 + NBUF * A2_BYTES;
+    // A2 in shared memory, or (A2 in tensor memory) only the end-of-kernel reduction scratch
+    static constexpr uint32_t A2_REGION = TMEM_A2 ? ((3 * THREADS * 8 + 1023) / 1024) * 1024 : NBUF * A2_BYTES;
+    static constexpr uint32_t OFF_B1 = OFF_A2 + A2_REGION;
     static constexpr uint32_t OFF_GAM = OFF_B1 + ((B1_BYTES + 1023) / 1024) * 1024;
-    static constexpr uint32_t OFF_BAR = OFF_GAM + ((NBUF * GAM_BYTES + 1023) / 1024) * 1024;
+    // the flushers' compensation terms (3-group form: kept out of registers) [32 columns][128 rows]
+    static constexpr uint32_t GC_BYTES = (NCG == 3) ? 32 * 128 * 4 : 0;
+    static constexpr uint32_t OFF_GC = OFF_GAM + ((NBUF * GAM_BYTES + 1023) / 1024) * 1024;
+    static constexpr uint32_t OFF_BAR = OFF_GC + GC_BYTES;
     // mbarrier slots (8 bytes each) from OFF_BAR
     static constexpr int BAR_FULL = 0, BAR_EMPTY = BAR_FULL + STAGES, BAR_UFULL = BAR_EMPTY + STAGES;
     static constexpr int BAR_UEMPTY = BAR_UFULL + NUBUF, BAR_A2FULL = BAR_UEMPTY + NUBUF;
@@ -108,7 +125,14 @@ struct TcCfg {
     static_assert(N1 <= COL_U_STRIDE && N1 * 64 <= 8192, "MMA1 shape");
     static_assert(2 * 32 * 128 * 4 <= STAGES * STAGE_BYTES, "G'' totals scratch");
     static_assert(TILE_BYTES % 512 == 0 && D_BYTES + TILE * 4 == TILE_BYTES, "tile layout");
-    static_assert(3 * THREADS * 8 <= NBUF * A2_BYTES, "reduction scratch");
+    static_assert(3 * THREADS * 8 <= A2_REGION, "reduction scratch");
+    // An mbarrier parity wait is only sound when the waiter has waited for the barrier's previous
+    // phase too (a wait for parity 1 passes while phase 0 is still open).  So every buffer is
+    // used by one consumer group only: the tiles sharing a U buffer, an A2 buffer or a stage
+    // (k and k + NUBUF, k + NBUF, k + 2 STAGES) belong to the same group, and each group waits
+    // the phases of its buffers in order.
+    static_assert(NUBUF % NCG == 0 && NBUF % NCG == 0 && (2 * STAGES) % NCG == 0,
+                  "buffers shared across consumer groups");
     static_assert(SMEM_BYTES <= 227 * 1024, "shared memory per block");
     static_assert(!TMEM_A2 || (SETS == 2 && COL_A2 % 16 == 0 && COL_A2 + NBUF * A2_COLS <= COL_G),
                   "tensor memory of the A2 buffers");
@@ -230,7 +254,7 @@ __global__ void __launch_bounds__(TcCfg<NSPLIT>::THREADS, 1)
             *s_abort = 0;
             fence_mbar_init();
         }
-        for (int i = tid; i < int(C::NBUF * C::A2_BYTES / 16); i += nth)
+        for (int i = tid; i < int(C::A2_REGION / 16); i += nth)
             reinterpret_cast<uint4 *>(a2)[i] = make_uint4(0, 0, 0, 0);
         // B1 (N1 rows x 32 slots, K-major, 64-byte swizzle): row 32 p + c holds part p of column c
         // of L~ (L~(k, c) at slot k), row 32 NSPLIT + p part p of kappa~; slot 31 (the constant 1
@@ -314,11 +338,11 @@ __global__ void __launch_bounds__(TcCfg<NSPLIT>::THREADS, 1)
                 const uint32_t a2a = smem_addr(a2), da = smem_addr(dtile);
                 for (int j = 0; j < nk; ++j) {
                     if (*s_abort) break;
-                    const int b = j & 3, i = j >> 1, s = i % C::STAGES;
+                    const int b = j % C::NBUF, i = j >> 1, s = i % C::STAGES;
                     const int e = j / C::EPOCH, eb = e & 1;
                     const bool first = (j % C::EPOCH) == 0;
                     if (!mbar_wait_bounded(&full[s], uint32_t((i / C::STAGES) & 1), BUDGET) ||
-                        !mbar_wait_bounded(&a2full[b], uint32_t((j >> 2) & 1), BUDGET) ||
+                        !mbar_wait_bounded(&a2full[b], uint32_t((j / C::NBUF) & 1), BUDGET) ||
                         (first && e >= 2 &&
                          !mbar_wait_bounded(&gempty[eb], uint32_t(((e >> 1) - 1) & 1), BUDGET))) {
                         *s_abort = 1;
@@ -353,9 +377,18 @@ __global__ void __launch_bounds__(TcCfg<NSPLIT>::THREADS, 1)
             // ---------------- flushers: G'' epochs -> compensated FP32 sums (one row per lane) ----------------
             const int q = warp - C::FLUSH_WARP0;
             const int row = 32 * q + lane;
-            float gs[32], gc[32];
+            float gs[32], gc[(C::NCG == 3) ? 1 : 32];
+            float *gcs = reinterpret_cast<float *>(base + C::OFF_GC);   // used by the 3-group form
+            // compensation term of column c of this thread's row
+            auto gcr = [&](int c) -> float & {
+                if constexpr (C::NCG == 3) return gcs[c * 128 + row];
+                else return gc[c];
+            };
 #pragma unroll
-            for (int c = 0; c < 32; ++c) gs[c] = gc[c] = 0.0f;
+            for (int c = 0; c < 32; ++c) {
+                gs[c] = 0.0f;
+                gcr(c) = 0.0f;
+            }
             bool ok = true;
             for (int e = 0; e * C::EPOCH < nk; ++e) {
                 if (__any_sync(0xffffffffu, *s_abort)) {
@@ -370,20 +403,27 @@ __global__ void __launch_bounds__(TcCfg<NSPLIT>::THREADS, 1)
                     break;
                 }
                 tc_fence_after();
-                float v[32];
-                // rows 0..63 read the first 32 columns; with two sets rows 64..127 read the next 32
+                // rows 0..63 read the first 32 columns; with two sets rows 64..127 read the next 32;
+                // two halves of 16 columns (fewer live registers next to the 64 running sums)
                 const uint32_t colset = (C::SETS == 2 && q >= 2) ? 32u : 0u;
-                tmem_ld32(tbase + (uint32_t(32 * q) << 16) + C::COL_G + eb * C::COL_G_STRIDE + colset, v);
+                const uint32_t tg = tbase + (uint32_t(32 * q) << 16) + C::COL_G + eb * C::COL_G_STRIDE + colset;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    uint32_t vr[16];
+                    tmem_ld16_nowait(tg + 16 * h, vr);
+                    tmem_wait_regs(vr);
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) {
+                        float &cc = gcr(16 * h + c);
+                        const float y = __uint_as_float(vr[c]) - cc;
+                        const float t = gs[16 * h + c] + y;
+                        cc = (t - gs[16 * h + c]) - y;
+                        gs[16 * h + c] = t;
+                    }
+                }
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&gempty[eb]);
-#pragma unroll
-                for (int c = 0; c < 32; ++c) {
-                    const float y = v[c] - gc[c];
-                    const float t = gs[c] + y;
-                    gc[c] = (t - gs[c]) - y;
-                    gs[c] = t;
-                }
             }
             // after the last epoch every MMA has completed and every copy has been consumed, so the
             // stage buffers are free
@@ -391,12 +431,12 @@ __global__ void __launch_bounds__(TcCfg<NSPLIT>::THREADS, 1)
 #pragma unroll
                 for (int c = 0; c < 32; ++c) {
                     gsum[c * 128 + row] = gs[c];
-                    gcmp[c * 128 + row] = gc[c];
+                    gcmp[c * 128 + row] = gcr(c);
                 }
             }
         } else {
             // ---------------- consumers ----------------
-            // group g takes tiles k = g (mod 2); tile k uses U buffer k % 3, A2 buffer k & 3
+            // group g takes tiles k = g (mod NCG); tile k uses U buffer k % NUBUF, A2 buffer k % NBUF
             const int g = warp >> 2, q = warp & 3;
             const int row = 32 * q + lane;                       // tensor-memory lane
             // U row `row` belongs to observation obs_row of the tile: the MMA1 atoms are the
@@ -420,9 +460,9 @@ __global__ void __launch_bounds__(TcCfg<NSPLIT>::THREADS, 1)
             int ex = 0, cnt = 0;
             const float erho = erho_f;
             const bool binary = args.binary != 0;
-            for (int k = g; k < nk; k += 2) {
+            for (int k = g; k < nk; k += C::NCG) {
                 if (__any_sync(0xffffffffu, *s_abort)) break;
-                const int i = k >> 1, s = i % C::STAGES, u = k % C::NUBUF, b = k & 3;
+                const int i = k >> 1, s = i % C::STAGES, u = k % C::NUBUF, b = k % C::NBUF;
                 const long long tile = 2 * (bid + (long long)i * nb) + (k & 1);
                 const bool valid = tile * C::TILE + o_r < V;
                 const bool okw = mbar_wait_backoff(&full[s], uint32_t((i / C::STAGES) & 1), BUDGET) &&
@@ -432,39 +472,48 @@ __global__ void __launch_bounds__(TcCfg<NSPLIT>::THREADS, 1)
                     break;
                 }
                 tc_fence_after();
-                // v = L~^T D and t = kappa~^T D: sums of the NSPLIT parts (all loads, then one wait)
-                uint32_t ur[NSPLIT][32], tr[4];
+                // v = L~^T D (q = |v|^2) and t = kappa~^T D: sums of the NSPLIT parts, loaded in two
+                // halves of 16 columns (fewer live registers; q's accumulation order is unchanged)
                 const uint32_t tu = tbase + lanebase + C::COL_U + u * C::COL_U_STRIDE;
+                float q0 = 0.0f, q1 = 0.0f, q2 = 0.0f, q3 = 0.0f, tv[4];
 #pragma unroll
-                for (int p = 0; p < NSPLIT; ++p) tmem_ld32_nowait(tu + 32 * p, ur[p]);
-                tmem_ld4_nowait(tu + 32 * NSPLIT, tr);
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                for (int h = 0; h < 2; ++h) {
+                    uint32_t ur[NSPLIT][16], tr[4];
 #pragma unroll
-                for (int p = 0; p < NSPLIT; ++p)
+                    for (int p = 0; p < NSPLIT; ++p) tmem_ld16_nowait(tu + 32 * p + 16 * h, ur[p]);
+                    if (h == 0) tmem_ld4_nowait(tu + 32 * NSPLIT, tr);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-                    for (int c = 0; c < 32; ++c) asm volatile("" : "+r"(ur[p][c]));
+                    for (int p = 0; p < NSPLIT; ++p)
 #pragma unroll
-                for (int c = 0; c < 4; ++c) asm volatile("" : "+r"(tr[c]));
-                float v[32], tv[4];
+                        for (int c = 0; c < 16; ++c) asm volatile("" : "+r"(ur[p][c]));
+                    if (h == 0) {
 #pragma unroll
-                for (int c = 0; c < 32; ++c) {
-                    v[c] = __uint_as_float(ur[0][c]);
+                        for (int c = 0; c < 4; ++c) {
+                            asm volatile("" : "+r"(tr[c]));
+                            tv[c] = __uint_as_float(tr[c]);
+                        }
+                    }
 #pragma unroll
-                    for (int p = 1; p < NSPLIT; ++p) v[c] += __uint_as_float(ur[p][c]);
+                    for (int c = 0; c < 16; c += 4) {
+                        float v0 = __uint_as_float(ur[0][c]), v1 = __uint_as_float(ur[0][c + 1]);
+                        float v2 = __uint_as_float(ur[0][c + 2]), v3 = __uint_as_float(ur[0][c + 3]);
+#pragma unroll
+                        for (int p = 1; p < NSPLIT; ++p) {
+                            v0 += __uint_as_float(ur[p][c]);
+                            v1 += __uint_as_float(ur[p][c + 1]);
+                            v2 += __uint_as_float(ur[p][c + 2]);
+                            v3 += __uint_as_float(ur[p][c + 3]);
+                        }
+                        q0 = fmaf(v0, v0, q0);
+                        q1 = fmaf(v1, v1, q1);
+                        q2 = fmaf(v2, v2, q2);
+                        q3 = fmaf(v3, v3, q3);
+                    }
                 }
-#pragma unroll
-                for (int c = 0; c < 4; ++c) tv[c] = __uint_as_float(tr[c]);
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&uempty[u]);
-                float q0 = 0.0f, q1 = 0.0f, q2 = 0.0f, q3 = 0.0f;
-#pragma unroll
-                for (int c = 0; c < 32; c += 4) {
-                    q0 = fmaf(v[c], v[c], q0);
-                    q1 = fmaf(v[c + 1], v[c + 1], q1);
-                    q2 = fmaf(v[c + 2], v[c + 2], q2);
-                    q3 = fmaf(v[c + 3], v[c + 3], q3);
-                }
                 const float qv = (q0 + q1) + (q2 + q3);
                 float t = tv[0];
 #pragma unroll
@@ -493,7 +542,7 @@ __global__ void __launch_bounds__(TcCfg<NSPLIT>::THREADS, 1)
                 }
                 if constexpr (C::TMEM_A2) {
                     // stage this observation's parts of gamma and w for the A2 row builders
-                    const bool oka = (k < 4) || mbar_wait_backoff(&a2empty[b], uint32_t(((k >> 2) - 1) & 1), BUDGET);
+                    const bool oka = (k < C::NBUF) || mbar_wait_backoff(&a2empty[b], uint32_t(((k / C::NBUF) - 1) & 1), BUDGET);
                     if (__any_sync(0xffffffffu, !oka)) {
                         *s_abort = 1;
                         break;
@@ -511,7 +560,7 @@ __global__ void __launch_bounds__(TcCfg<NSPLIT>::THREADS, 1)
                     }
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&staged[b]);
-                    const bool oks = mbar_wait_backoff(&staged[b], uint32_t((k >> 2) & 1), BUDGET);
+                    const bool oks = mbar_wait_backoff(&staged[b], uint32_t((k / C::NBUF) & 1), BUDGET);
                     if (__any_sync(0xffffffffu, !oks)) {
                         *s_abort = 1;
                         break;
@@ -580,7 +629,7 @@ __global__ void __launch_bounds__(TcCfg<NSPLIT>::THREADS, 1)
                 } else {
                 // stage this observation's parts: gamma for the chunk builders, w straight into
                 // A2 row (set, p, 31)
-                const bool oka = (k < 4) || mbar_wait_backoff(&a2empty[b], uint32_t(((k >> 2) - 1) & 1), BUDGET);
+                const bool oka = (k < C::NBUF) || mbar_wait_backoff(&a2empty[b], uint32_t(((k / C::NBUF) - 1) & 1), BUDGET);
                 if (__any_sync(0xffffffffu, !oka)) {
                     *s_abort = 1;
                     break;
@@ -600,7 +649,7 @@ __global__ void __launch_bounds__(TcCfg<NSPLIT>::THREADS, 1)
                 }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&staged[b]);
-                const bool oks = mbar_wait_backoff(&staged[b], uint32_t((k >> 2) & 1), BUDGET);
+                const bool oks = mbar_wait_backoff(&staged[b], uint32_t((k / C::NBUF) & 1), BUDGET);
                 if (__any_sync(0xffffffffu, !oks)) {
                     *s_abort = 1;
                     break;
