@@ -16,9 +16,10 @@
 //       observations per thread, a warp butterfly, FP64 from there on.  T4 is
 //       carried as a running product of (1 + E[rho] q_i) whose binary exponent
 //       is peeled off every two observations; one log per chunk;
-//   (d) the last block to finish adds the per-block FP64 partials in block
-//       order (deterministic) and runs the closed-form updates of Eq. 16-18,
-//       22-25 and 28-31 in FP64, written in centred form:
+//   (d) the block that finishes the launch (a ticket; above 128 blocks the
+//       last block of each group of 32 first sums its group) adds the FP64
+//       partials in a fixed order (deterministic) and runs the closed-form
+//       updates of Eq. 16-18, 22-25 and 28-31 in FP64, written in centred form:
 //       s = Sigma0 g, delta = (s + q0 (K0 - kappa)) / (q0 + V), kappa' = kappa + delta
 //       W'^{-1} = Lambda_0^{-1} + V Sigma0 + Sigma0 G Sigma0 + q0 (K0-kappa)(K0-kappa)^T
 //                 - (q0 + V) delta delta^T        (= Eq. 25 exactly)
