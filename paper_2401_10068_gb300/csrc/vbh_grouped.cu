@@ -178,16 +178,24 @@ __global__ void __launch_bounds__(GROUPED_THREADS) grouped_sweep_kernel(GroupArg
 }
 
 // The same sweep for many profile codes (S >= GROUPED_WIDE_S): lane = code.
-// Warp w of the grid takes batches of 32 codes w, w + W, ...; each lane forms
-// v = L~^T D, q, t and the scalar sums of its code in FP64 (D in {-1, 0, 1} by
-// selection, no conversions), then the lanes switch roles: lane l owns the
-// packed entries l, l + 32, ... of G and entry l of g and adds the batch's 32
-// codes in order.  About a tenth of the FP64 instructions per code of the
-// row-per-lane form, whose cost is one warp's chain per code.
+// Warp w of the grid takes batches of 32 consecutive codes w, w + W, ...; in a
+// batch the low LB = 5 bits of the code (lane) vary and the others, d_S
+// included, are the warp's.  So with D_k = d_k - d_S in {-1, 0, 1}:
+//   v = L~^T D: the part over k >= LB is the same for the whole batch (lane j
+//     forms h_j = sum_{k >= max(j, LB)} L~(k, j) D_k once), the rest is LB
+//     terms per lane;  q = |v|^2,  t = kappa~^T D likewise;
+//   G = sum gamma D D^T and g = sum w D over the batch: entries (r, c) with
+//     r >= LB take D_r (D_c sum gamma or sum gamma D_c) from seven warp sums;
+//     the 15 entries with r < LB and g_{j < LB} are accumulated per lane and
+//     summed over the warp once at the end.
+// About half the FP64 instructions of forming every code's v and adding every
+// code into every G entry.
 namespace {
 constexpr int GNG = GMAX * (GMAX + 1) / 2;                       // packed entries of G at the largest M
-constexpr int WIDE_GPL = (GNG + 31) / 32;                        // G entries per lane
-constexpr size_t WIDE_PASS_DOUBLES = GNG + 16 + 3 * GW * 32;    // L~, kappa~, per-warp (gamma sum, w sum, code)
+constexpr int LB = 5;                                            // code bits that vary within a batch
+constexpr int NLL = LB * (LB + 1) / 2;                           // G entries with r < LB (first in the packed order)
+constexpr int WIDE_GPL = (GNG - NLL + 31) / 32;                  // entries with r >= LB per lane
+constexpr size_t WIDE_PASS_DOUBLES = GNG + 16;                   // L~, kappa~
 } // namespace
 
 __global__ void __launch_bounds__(GROUPED_THREADS) grouped_sweep_wide_kernel(GroupArgs ga)
@@ -196,7 +204,7 @@ __global__ void __launch_bounds__(GROUPED_THREADS) grouped_sweep_wide_kernel(Gro
     __shared__ int s_last;
     const SweepArgs &a = ga.sa;
     DevState *st = a.st;
-    const int S = st->S, M = S - 1;
+    const int S = st->S, M = S - 1;                              // M >= GROUPED_WIDE_S - 1 > LB
     const int NG = M * (M + 1) / 2, NSTAT = NG + M + 3;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const bool run = (a.mode != MODE_ITER) ||
@@ -204,18 +212,19 @@ __global__ void __launch_bounds__(GROUPED_THREADS) grouped_sweep_wide_kernel(Gro
 
     double *Lf = gsm;                                            // L~ (packed lower, row i at i(i+1)/2), FP64
     double *kf = Lf + GNG;                                       // kappa~
-    double *wsg = kf + 16;                                       // per warp: sum (w^2 - c) of each code
-    double *wsw = wsg + GW * 32;                                 // per warp: sum w of each code
-    int *wcode = reinterpret_cast<int *>(wsw + GW * 32);         // per warp: the codes
     double *red = gsm + WIDE_PASS_DOUBLES;                       // [warp][NSTAT] partials
 
-    double gacc[WIDE_GPL], gvl = 0.0, t3 = 0.0, t4 = 0.0;
+    double hacc[WIDE_GPL], llacc[NLL], glow[LB], ghigh = 0.0, t3 = 0.0, t4 = 0.0;
 #pragma unroll
-    for (int i = 0; i < WIDE_GPL; ++i) gacc[i] = 0.0;
-    int er[WIDE_GPL], ec[WIDE_GPL];                              // this lane's G entries as (row, column)
+    for (int i = 0; i < WIDE_GPL; ++i) hacc[i] = 0.0;
+#pragma unroll
+    for (int i = 0; i < NLL; ++i) llacc[i] = 0.0;
+#pragma unroll
+    for (int i = 0; i < LB; ++i) glow[i] = 0.0;
+    int er[WIDE_GPL], ec[WIDE_GPL];                              // this lane's entries with r >= LB
 #pragma unroll
     for (int i = 0; i < WIDE_GPL; ++i) {
-        const int e = lane + 32 * i;
+        const int e = NLL + lane + 32 * i;
         int r = 0;
         while ((r + 1) * (r + 2) / 2 <= e) ++r;
         er[i] = (e < NG) ? r : -1;
@@ -228,31 +237,42 @@ __global__ void __launch_bounds__(GROUPED_THREADS) grouped_sweep_wide_kernel(Gro
         const double erho = static_cast<double>(st->sw.erho);
         const int nbatch = (ga.P + 31) / 32, nw = gridDim.x * GW;
         for (int bt = blockIdx.x * GW + warp; bt < nbatch; bt += nw) {
-            const int p = bt * 32 + lane;
+            const int base = bt * 32, p = base + lane;
+            const int bS = (base >> M) & 1;
+            auto Dh = [&](int k) -> double {                     // D_k, k >= LB: the batch's
+                const int b = (base >> k) & 1;
+                return b == bS ? 0.0 : (b ? 1.0 : -1.0);
+            };
+            auto Dl = [&](int k) -> double {                     // D_k, k < LB: this lane's
+                const int b = (lane >> k) & 1;
+                return b == bS ? 0.0 : (b ? 1.0 : -1.0);
+            };
+            // the batch's parts: h_j (lane j), sum_{j >= LB} h_j^2 and sum_{k >= LB} kappa_k D_k
+            double hj = 0.0;
+            if (lane < M)
+                for (int k = (lane > LB ? lane : LB); k < M; ++k) {
+                    const double dk = Dh(k);
+                    if (dk != 0.0) hj = fma(Lf[k * (k + 1) / 2 + lane], dk, hj);
+                }
+            const double qh = warp_sum((lane >= LB && lane < M) ? hj * hj : 0.0);
+            const double th = warp_sum((lane >= LB && lane < M) ? kf[lane] * Dh(lane) : 0.0);
+            // this lane's code: the low parts
+            double q = qh, t = th;
+#pragma unroll
+            for (int j = 0; j < LB; ++j) {
+                double v = __shfl_sync(0xffffffffu, hj, j);
+#pragma unroll
+                for (int k = j; k < LB; ++k) {
+                    const double dk = Dl(k);
+                    if (dk != 0.0) v = fma(Lf[k * (k + 1) / 2 + j], dk, v);
+                }
+                q = fma(v, v, q);
+                const double dj = Dl(j);
+                if (dj != 0.0) t = fma(kf[j], dj, t);
+            }
             const bool valid = p < ga.P;
             const double n = valid ? ga.stats[3 * p] : 0.0;
             const double sy = valid ? ga.stats[3 * p + 1] : 0.0, syy = valid ? ga.stats[3 * p + 2] : 0.0;
-            const int bS = (p >> M) & 1;
-            auto Dk = [&](int k) -> double {                     // D_k = d_k - d_S in {-1, 0, 1}
-                const int b = (p >> k) & 1;
-                return b == bS ? 0.0 : (b ? 1.0 : -1.0);
-            };
-            double q = 0.0, t = 0.0;
-#pragma unroll
-            for (int j = 0; j < GMAX; ++j) {
-                if (j < M) {
-                    double v = 0.0;                              // (L~^T D)_j = sum_{k >= j} L~(k, j) D_k
-#pragma unroll
-                    for (int k = j; k < GMAX; ++k)
-                        if (k < M) {
-                            const double dk = Dk(k);
-                            if (dk != 0.0) v = fma(Lf[k * (k + 1) / 2 + j], dk, v);
-                        }
-                    q = fma(v, v, q);
-                    const double dj = Dk(j);
-                    if (dj != 0.0) t = fma(kf[j], dj, t);
-                }
-            }
             const double den = fma(erho, q, 1.0);
             const double inv = 1.0 / den;
             const double c = erho * inv;
@@ -260,35 +280,67 @@ __global__ void __launch_bounds__(GROUPED_THREADS) grouped_sweep_wide_kernel(Gro
             const double see = syy - 2.0 * t * sy + n * t * t;
             t3 += inv * inv * see + n * q * inv;
             t4 += n * log(den);
-            wsg[warp * 32 + lane] = c * c * see - n * c;
-            wsw[warp * 32 + lane] = c * se;
-            wcode[warp * 32 + lane] = p;
-            __syncwarp();
-            for (int cc = 0; cc < 32; ++cc) {
-                const int pc = wcode[warp * 32 + cc];
-                const int bc = (pc >> M) & 1;
-                const double sg = wsg[warp * 32 + cc], sw = wsw[warp * 32 + cc];
+            const double sg = c * c * see - n * c, sw = c * se;
+            // the batch's sums for the entries with r >= LB and for g_{j >= LB}
+            const double S0 = warp_sum(sg), W0 = warp_sum(sw);
+            auto sgd = [&](int k) {                               // sum over the batch of gamma D_k, k < LB
+                const double dk = Dl(k);
+                return warp_sum(dk == 0.0 ? 0.0 : (dk > 0.0 ? sg : -sg));
+            };
+            const double Sc0 = sgd(0), Sc1 = sgd(1), Sc2 = sgd(2), Sc3 = sgd(3), Sc4 = sgd(4);
+            static_assert(LB == 5, "five low bits");
 #pragma unroll
-                for (int i = 0; i < WIDE_GPL; ++i)
-                    if (er[i] >= 0) {
-                        const int dr = ((pc >> er[i]) & 1) - bc, dc = ((pc >> ec[i]) & 1) - bc;
-                        const int pr = dr * dc;                  // D_r D_c in {-1, 0, 1}
-                        if (pr != 0) gacc[i] += (pr > 0) ? sg : -sg;
+            for (int i = 0; i < WIDE_GPL; ++i)
+                if (er[i] >= 0) {
+                    const double dr = Dh(er[i]);
+                    if (dr != 0.0) {
+                        double x;
+                        if (ec[i] >= LB) {
+                            const double dc = Dh(ec[i]);
+                            x = dc * S0;
+                        } else {
+                            const int k = ec[i];
+                            x = k == 0 ? Sc0 : k == 1 ? Sc1 : k == 2 ? Sc2 : k == 3 ? Sc3 : Sc4;
+                        }
+                        hacc[i] = fma(dr, x, hacc[i]);
                     }
-                if (lane < M) {
-                    const int dj = ((pc >> lane) & 1) - bc;
-                    if (dj != 0) gvl += (dj > 0) ? sw : -sw;
+                }
+            if (lane >= LB && lane < M) {
+                const double dj = Dh(lane);
+                if (dj != 0.0) ghigh = fma(dj, W0, ghigh);
+            }
+            // this lane's code into the entries with r < LB and g_{j < LB}
+#pragma unroll
+            for (int r = 0; r < LB; ++r) {
+                const double dr = Dl(r);
+                if (dr != 0.0) {
+                    const double sgr = dr > 0.0 ? sg : -sg;
+#pragma unroll
+                    for (int cc = 0; cc <= r; ++cc) {
+                        const double dc = Dl(cc);
+                        if (dc != 0.0) llacc[r * (r + 1) / 2 + cc] += dc > 0.0 ? sgr : -sgr;
+                    }
+                    glow[r] += dr > 0.0 ? sw : -sw;
                 }
             }
-            __syncwarp();
         }
     }
     // per-warp partials -> shared memory [warp][NSTAT] -> this block's partials (fixed order)
     const double t3w = warp_sum(t3), t4w = warp_sum(t4);
 #pragma unroll
+    for (int i = 0; i < NLL; ++i) {
+        const double x = warp_sum(llacc[i]);
+        if (lane == 0) red[warp * GNSTAT + i] = x;
+    }
+#pragma unroll
+    for (int j = 0; j < LB; ++j) {
+        const double x = warp_sum(glow[j]);
+        if (lane == 0) red[warp * GNSTAT + NG + j] = x;
+    }
+#pragma unroll
     for (int i = 0; i < WIDE_GPL; ++i)
-        if (er[i] >= 0) red[warp * GNSTAT + lane + 32 * i] = gacc[i];
-    if (lane < M) red[warp * GNSTAT + NG + lane] = gvl;
+        if (er[i] >= 0) red[warp * GNSTAT + NLL + lane + 32 * i] = hacc[i];
+    if (lane >= LB && lane < M) red[warp * GNSTAT + NG + lane] = ghigh;
     if (lane == 0) {
         red[warp * GNSTAT + NG + M] = t3w;
         red[warp * GNSTAT + NG + M + 1] = t4w;
