@@ -152,6 +152,11 @@ __device__ __forceinline__ void issue_unit(Cursor &cu, const BatchClass &bc, int
     }
 }
 
+// One block barrier per unit: every thread waits for the stage, consumes it,
+// and meets the others at the end of the unit, after which thread 0 refills
+// the stage.  A chunk's FP64 partial is staged in one of two reduction buffers
+// before that barrier and summed after it, so the next chunk's partial (into
+// the other buffer) cannot overwrite it while it is read.
 template <int S>
 __global__ void __launch_bounds__(BatchCfg<S>::THREADS, SweepCfg<S>::MINB) batched_pass_kernel(BatchClass bc)
 {
@@ -162,8 +167,7 @@ __global__ void __launch_bounds__(BatchCfg<S>::THREADS, SweepCfg<S>::MINB) batch
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + B::RING_BYTES);
     __shared__ StageMeta meta[STAGES];
-    __shared__ double s_red[THREADS / 32][NGRP * 32];
-    __shared__ float s_glob[C::NGA + C::MA + 1];
+    __shared__ double s_red[2][THREADS / 32][NGRP * 32];
     __shared__ int s_bad;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int mode = bc.mode;
@@ -188,82 +192,83 @@ __global__ void __launch_bounds__(BatchCfg<S>::THREADS, SweepCfg<S>::MINB) batch
 #pragma unroll
     for (int g = 0; g < NGRP; ++g) acc64[g] = 0.0;
     float L[C::NGA], kap[C::MA], erho = 0.0f;
+    if constexpr (NG == 0) L[0] = 0.0f;
+    if constexpr (M == 0) kap[0] = 0.0f;
     int cur_ds = -1;
     int ftile = 0;
+    int rbuf = 0;                                           // reduction buffer of the next chunk partial
 
     long long kbreak = 0;
     for (long long k = 0;; ++k) {
         const int s = int(k % STAGES);
         const bool ok = mbar_wait_bounded(&full[s], uint32_t((k / STAGES) & 1), 2000000000ull);
-        if (__syncthreads_or(!ok)) {
+        StageMeta m;
+        m.chunk = -1;
+        m.flags = 0;
+        if (ok) m = meta[s];                                // the same for every thread once the stage is full
+        const bool work = ok && m.chunk >= 0;
+        if (work) {
+            if (m.ds != cur_ds) {                           // a new data set: its FP32 globals (cached reads)
+                const DevState *st = bc.states + m.ds;
+#pragma unroll
+                for (int i = 0; i < NG; ++i) L[i] = st->sw.L[i];
+#pragma unroll
+                for (int i = 0; i < M; ++i) kap[i] = st->sw.kappa[i];
+                erho = (mode == MODE_INIT) ? 0.0f : st->sw.erho;
+                cur_ds = m.ds;
+            }
+            if (!(m.flags & UNIT_TAIL)) {
+                const float *rt = reinterpret_cast<const float *>(smem + size_t(s) * B::STAGE_BYTES);
+                const float *dt = rt + T;
+#pragma unroll
+                for (int u = 0; u < B::OPT; ++u) {
+                    const int j = tid + u * THREADS;
+                    float x[S];
+                    load_row<S>(dt, j, x);
+                    observe<S>(x, rt[j], L, kap, erho, acc, prod);
+                    peel_exponent(prod, ex);
+                }
+                if (++ftile == 16) {
+                    flush_warp<S>(acc, acc64, prod, ex, lane);
+                    ftile = 0;
+                }
+            } else {
+                const float *rg = bc.r[m.ds];
+                const float *dg = bc.d[m.ds];
+                const long long hi = bc.chunk_hi[m.chunk];
+                for (long long i = m.obs0 + tid; i < hi; i += THREADS) {
+                    float x[S];
+#pragma unroll
+                    for (int q = 0; q < S; ++q) x[q] = __ldg(dg + i * S + q);
+                    observe<S>(x, __ldg(rg + i), L, kap, erho, acc, prod);
+                    peel_exponent(prod, ex);
+                }
+            }
+            if (m.flags & UNIT_LAST) {                      // chunk done: stage its FP64 partial
+                flush_warp<S>(acc, acc64, prod, ex, lane);
+                ftile = 0;
+#pragma unroll
+                for (int g = 0; g < NGRP; ++g) {
+                    s_red[rbuf][warp][g * 32 + lane] = acc64[g];
+                    acc64[g] = 0.0;
+                }
+            }
+        }
+        if (__syncthreads_or(!ok)) {                        // stage s is free again; s_red[rbuf] is complete
             if (tid == 0) s_bad = 1;
             kbreak = k;
             break;
         }
-        const StageMeta m = meta[s];
-        if (m.chunk < 0) break;
-        if (m.ds != cur_ds) {                               // a new data set: its FP32 globals
-            __syncthreads();
-            if (tid == 0) {
-                const DevState *st = bc.states + m.ds;
-                for (int i = 0; i < NG; ++i) s_glob[i] = st->sw.L[i];
-                for (int i = 0; i < M; ++i) s_glob[C::NGA + i] = st->sw.kappa[i];
-                s_glob[C::NGA + C::MA] = (mode == MODE_INIT) ? 0.0f : st->sw.erho;
-            }
-            __syncthreads();
-#pragma unroll
-            for (int i = 0; i < NG; ++i) L[i] = s_glob[i];
-#pragma unroll
-            for (int i = 0; i < M; ++i) kap[i] = s_glob[C::NGA + i];
-            if constexpr (NG == 0) L[0] = 0.0f;
-            if constexpr (M == 0) kap[0] = 0.0f;
-            erho = s_glob[C::NGA + C::MA];
-            cur_ds = m.ds;
-        }
-        if (!(m.flags & UNIT_TAIL)) {
-            const float *rt = reinterpret_cast<const float *>(smem + size_t(s) * B::STAGE_BYTES);
-            const float *dt = rt + T;
-#pragma unroll
-            for (int u = 0; u < B::OPT; ++u) {
-                const int j = tid + u * THREADS;
-                float x[S];
-                load_row<S>(dt, j, x);
-                observe<S>(x, rt[j], L, kap, erho, acc, prod);
-                peel_exponent(prod, ex);
-            }
-            if (++ftile == 16) {
-                flush_warp<S>(acc, acc64, prod, ex, lane);
-                ftile = 0;
-            }
-        } else {
-            const float *rg = bc.r[m.ds];
-            const float *dg = bc.d[m.ds];
-            const long long hi = bc.chunk_hi[m.chunk];
-            for (long long i = m.obs0 + tid; i < hi; i += THREADS) {
-                float x[S];
-#pragma unroll
-                for (int q = 0; q < S; ++q) x[q] = __ldg(dg + i * S + q);
-                observe<S>(x, __ldg(rg + i), L, kap, erho, acc, prod);
-                peel_exponent(prod, ex);
-            }
-        }
-        if (m.flags & UNIT_LAST) {                          // chunk done: its FP64 partial
-            flush_warp<S>(acc, acc64, prod, ex, lane);
-            ftile = 0;
-#pragma unroll
-            for (int g = 0; g < NGRP; ++g) {
-                s_red[warp][g * 32 + lane] = acc64[g];
-                acc64[g] = 0.0;
-            }
-            __syncthreads();
+        if (!work) break;                                   // the end mark (every thread read it)
+        if (m.flags & UNIT_LAST) {
             for (int j = tid; j < NSTAT; j += THREADS) {
                 double t = 0.0;
 #pragma unroll
-                for (int w = 0; w < THREADS / 32; ++w) t += s_red[w][j];
+                for (int w = 0; w < THREADS / 32; ++w) t += s_red[rbuf][w][j];
                 bc.partials[size_t(m.chunk) * NSTAT + j] = t;
             }
+            rbuf ^= 1;
         }
-        __syncthreads();                                    // stage s and s_red are free again
         if (tid == 0) issue_unit<S>(cu, bc, mode, smem + size_t(s) * B::STAGE_BYTES, &full[s], &meta[s]);
     }
     if (s_bad && tid == 0) {
