@@ -70,8 +70,10 @@ template <int S>
 struct BatchCfg {
     using C = SweepCfg<S>;
     static constexpr int THREADS = 256;
-    static constexpr int OPT = 3;                           // observations per thread per tile
-    static constexpr int T = THREADS * OPT;                 // 768 observations per tile
+    // observations per thread per tile: 4 (1,024 per tile) except at S = 8,
+    // where two blocks per SM need the 768-observation ring
+    static constexpr int OPT = (S == 8) ? 3 : 4;
+    static constexpr int T = THREADS * OPT;
     static constexpr int STAGES = 3;
     static constexpr uint32_t R_BYTES = T * 4u;
     static constexpr uint32_t D_BYTES = T * S * 4u;

@@ -38,9 +38,10 @@ def _check(got, ref, V, what):
 
 
 def _mixed_batch(seed0=500):
-    # uneven sizes: empty, smaller than a tile, ragged, several chunks
-    specs = [(3, 0), (1, 1000), (2, 767), (2, 768), (3, 96000), (4, 50001), (5, 12000), (6, 33333),
-             (7, 20000), (8, 60013), (9, 9600), (10, 15000), (11, 8000), (3, 250_000), (8, 700_001)]
+    # uneven sizes: empty, smaller than a tile, one observation either side of
+    # a tile (1,024 observations; 768 at S = 8), ragged, several chunks
+    specs = [(3, 0), (1, 1000), (2, 1023), (2, 1024), (8, 767), (8, 768), (3, 96000), (4, 50001), (5, 12000),
+             (6, 33333), (7, 20000), (8, 60013), (9, 9600), (10, 15000), (11, 8000), (3, 250_000), (8, 700_001)]
     rs, ds, Ss, host = [], [], [], []
     for k, (S, V) in enumerate(specs):
         r, d, _ = synth.generate(max(V, 1), S, seed=seed0 + k, alpha=0.5, p_const=0.05)
