@@ -34,8 +34,9 @@ WORKLOAD = {"name": "at-scale single data set", "cells": 4_194_304, "genes": 96,
 V_FULL = WORKLOAD["cells"] * WORKLOAD["genes"]
 METRIC = "cell.gene.K CAVI updates/s (observation x subpopulation updates per second, FP32 fused sweep)"
 UNIT = "updates/s"
-CPU_SAMPLE_V = 1 << 20          # oracle prefix for the cpu_baseline leg
+CPU_SAMPLE_V = 1 << 20          # oracle prefix for the single-core cpu_baseline leg
 CPU_SAMPLE_SWEEPS = 5
+CPU_ALL_V = 1 << 22             # oracle prefix for the all-cores cpu_baseline leg
 REF_SAMPLE_V = 1 << 17          # oracle prefix per step of the reference arm
 
 
@@ -140,19 +141,152 @@ class Clocks:
 
 def _oracle_sweeps(V, S, sweeps, warm=1):
     """Time `sweeps` oracle sweeps (Q(beta), sums, Q(rho), Q(K,Lambda), ELBO) on
-    the first V observations of the workload; returns seconds."""
+    the first V observations of the workload in this process; returns (wall
+    seconds, CPU seconds of this process over the same sweeps)."""
     from oracle import oracle as O
     from paper_2401_10068_gb300 import synth
     r, d, _ = synth.generate(V, S, seed=WORKLOAD["seed"], alpha=WORKLOAD["alpha"], p_const=WORKLOAD["p_const"])
     p = O.paper_prior(S)
     g = O.fit(r, d, p, tol=0.0, max_iter=warm)
-    t0 = time.perf_counter()
+    c0, t0 = time.process_time(), time.perf_counter()
     for _ in range(sweeps):
         mu, Sig = O.beta_update(r, d, p, g)
         s = O.sums_from_beta(r, d, p, mu, Sig)
         g = O.KLambda_update(p, s, O.rho_update(p, s, g))
         O.elbo(p, s, g)
-    return time.perf_counter() - t0
+    return time.perf_counter() - t0, time.process_time() - c0
+
+
+def _oracle_worker(conn, S, lo, hi):
+    """One host core of the all-cores oracle leg.  It generates observations
+    [lo, hi) of the workload (the generator is counter-based, so these are the
+    prefix's own values) and answers each message with the oracle's Q(beta)
+    and sufficient statistics of its chunk under the globals sent (sweep 0's
+    initial Q(beta) for None), flattened, and the CPU seconds it spent."""
+    from oracle import oracle as O
+    from paper_2401_10068_gb300 import synth
+    r, d, _ = synth.generate(hi - lo, S, seed=WORKLOAD["seed"], alpha=WORKLOAD["alpha"],
+                             p_const=WORKLOAD["p_const"], start=lo)
+    p = O.paper_prior(S)
+    conn.send("ready")
+    while True:
+        msg = conn.recv()
+        if msg == "stop":
+            break
+        c0 = time.process_time()
+        g = msg["g"]
+        if g is None:
+            mu, Sig = O.beta_init(p, hi - lo)
+        else:
+            mu, Sig = O.beta_update(r, d, p, g)
+        s = O.sums_from_beta(r, d, p, mu, Sig)
+        flat = np.concatenate([[s["V"], s["sum_S"], s["sum_logdet"]], np.ravel(s["sum_mu"]), np.ravel(s["sum_Ebb"])])
+        conn.send((flat, time.process_time() - c0))
+    conn.close()
+
+
+def _oracle_sweeps_all_cores(V, S, sweeps, procs, warm=1):
+    """The oracle on `procs` host cores: one spawn-started process per
+    contiguous chunk of the first V observations runs Q(beta) and the sums of
+    its chunk; the parent adds the chunks' FP64 statistics in chunk order (the
+    same bits whatever the timing) and runs Q(rho), Q(K, Lambda) and the ELBO.
+    Sweep 0 and `warm` sweeps run untimed.  Returns (wall seconds of the
+    `sweeps` timed sweeps, the workers' CPU seconds in them, final globals)."""
+    import multiprocessing as mp
+    from oracle import oracle as O
+    O.build()                                           # built once here, loaded by every worker
+    ctx = mp.get_context("spawn")
+    p = O.paper_prior(S)
+    M = S - 1
+    conns, workers = [], []
+    try:
+        for k in range(procs):
+            a, b = ctx.Pipe()
+            w = ctx.Process(target=_oracle_worker, args=(b, S, k * V // procs, (k + 1) * V // procs), daemon=True)
+            w.start()
+            b.close()
+            conns.append(a)
+            workers.append(w)
+        for c in conns:
+            if c.recv() != "ready":
+                raise RuntimeError("oracle worker failed to start")
+
+        def sweep(g):
+            for c in conns:
+                c.send({"g": g})
+            total, cpu = None, 0.0
+            for c in conns:                             # chunk order
+                flat, t = c.recv()
+                total = flat.copy() if total is None else total + flat
+                cpu += t
+            s = {"V": total[0], "sum_S": total[1], "sum_logdet": total[2], "sum_mu": total[3:3 + M],
+                 "sum_Ebb": total[3 + M:].reshape(M, M)}
+            g2 = O.KLambda_update(p, s, O.rho_update(p, s, g))
+            if g is not None:
+                O.elbo(p, s, g2)
+            return g2, cpu
+
+        g, _ = sweep(None)
+        for _ in range(warm):
+            g, _ = sweep(g)
+        cpu, t0 = 0.0, time.perf_counter()
+        for _ in range(sweeps):
+            g, c = sweep(g)
+            cpu += c
+        wall = time.perf_counter() - t0
+    finally:
+        for c in conns:
+            try:
+                c.send("stop")
+            except (OSError, ValueError):
+                pass
+        for w in workers:
+            w.join(timeout=30)
+            if w.is_alive():
+                w.terminate()
+    return wall, cpu, g
+
+
+def _cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.machine()
+
+
+def cpu_baseline(S):
+    """The oracle timed on the host cores: single-threaded on a 2^20 prefix,
+    and on all cores on a 2^22 prefix of the workload (the main figure)."""
+    sec, csec = _oracle_sweeps(CPU_SAMPLE_V, S, CPU_SAMPLE_SWEEPS)
+    single = {"value": CPU_SAMPLE_V * S * CPU_SAMPLE_SWEEPS / sec, "unit": UNIT, "cores": 1,
+              "effective_cores": csec / sec,
+              "sample": f"first {CPU_SAMPLE_V} observations of the workload, {CPU_SAMPLE_SWEEPS} sweeps after "
+                        f"sweep 0, single-process FP64 oracle ({sec:.1f} s)"}
+    host = {"nproc": os.cpu_count(), "cpu_model": _cpu_model()}
+    procs = max(1, os.cpu_count() or 1)
+    try:
+        wall, cpu, _ = _oracle_sweeps_all_cores(CPU_ALL_V, S, CPU_SAMPLE_SWEEPS, procs)
+    except Exception as e:                              # report the single-core leg alone
+        return dict(single, kind="oracle", host=host, all_cores_error=f"{type(e).__name__}: {e}")
+    return {"value": CPU_ALL_V * S * CPU_SAMPLE_SWEEPS / wall, "unit": UNIT, "cores": procs, "kind": "oracle",
+            "effective_cores": cpu / wall,
+            "sample": f"first {CPU_ALL_V} observations of the workload, {CPU_SAMPLE_SWEEPS} sweeps after sweep 0 "
+                      f"and one warm-up sweep; the FP64 oracle in {procs} processes over contiguous chunks, the "
+                      f"chunks' statistics summed in chunk order, the global update in the parent "
+                      f"({wall:.1f} s, {cpu:.1f} CPU s)",
+            "single_core": single, "host": host}
 
 
 def run_reference(args):
@@ -252,10 +386,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        sec = _oracle_sweeps(CPU_SAMPLE_V, S, CPU_SAMPLE_SWEEPS)
-        cpu = {"value": CPU_SAMPLE_V * S * CPU_SAMPLE_SWEEPS / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"first {CPU_SAMPLE_V} observations of the workload, {CPU_SAMPLE_SWEEPS} sweeps after "
-                         f"sweep 0, single-threaded FP64 oracle ({sec:.1f} s)"}
+        cpu = cpu_baseline(S)
     h.close()
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
