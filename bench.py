@@ -676,6 +676,54 @@ def run_grouped(args):
     return 0
 
 
+PER_S = {"V": 1 << 27, "S": (2, 3, 4, 6, 8, 10, 11), "seed": 9, "alpha": 0.5, "warm": 4, "sweeps": 20}
+
+
+def run_per_s(args):
+    """Bandwidth of the FP32 sweep kernel across S (one data set of 2^27
+    observations per S, the same recipe without constant profiles): per S, 4
+    untimed sweeps, then 20 sweeps timed with CUDA events on the handle's
+    stream; algorithmic bytes 4 (S + 1) per observation."""
+    import torch
+    from paper_2401_10068_gb300 import _build
+    _build.build_all()
+    from paper_2401_10068_gb300 import synth, vbh
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(dev)
+    h = vbh.Handle(0, stream)
+    peak, peak_kind = _peaks()
+    V, n = PER_S["V"], PER_S["sweeps"]
+    clocks = Clocks(0)
+    time.sleep(0.3)
+    rows = []
+    for S in PER_S["S"]:
+        with torch.cuda.stream(stream):
+            r, d, _ = synth.generate_device(V, S, seed=PER_S["seed"], alpha=PER_S["alpha"], device=dev)
+        stream.synchronize()
+        h.fit_begin(r, d, S, None, tol=0.0, max_iter=PER_S["warm"] + n)
+        h.fit_step(PER_S["warm"])
+        torch.cuda.synchronize(dev)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        h.fit_step(n)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = ev0.elapsed_time(ev1) / n
+        gbs = V * 4.0 * (S + 1) / (ms * 1e-3) / 1e9
+        rows.append({"S": S, "ms_per_sweep": ms, "achieved_gbs": gbs, "frac": gbs / peak})
+        del r, d
+    clk = clocks.stop()
+    h.close()
+    line = {"metric": "FP32 sweep kernel bandwidth across S", "unit": "GB/s", "n_gpus": 1, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "one data set per S", "V": V, "S": list(PER_S["S"]), "seed": PER_S["seed"],
+                       "warmup": PER_S["warm"], "sweeps": n, "l2": "inputs larger than L2 (129 MB), no flush"},
+            "peak": peak, "peak_kind": peak_kind, "rows": rows, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -686,9 +734,10 @@ def main():
                     help="N cells (x 96 genes); smaller values give the small case used for ncu captures")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
-    ap.add_argument("--workload", default="at-scale", choices=["at-scale", "batched", "precision", "grouped"],
+    ap.add_argument("--workload", default="at-scale", choices=["at-scale", "batched", "precision", "grouped", "per-s"],
                     help="batched: the 4,096-data-set form; precision: the S = 32 tensor-core form; grouped: "
-                         "the profile-grouped form (separate measurements, not the default step)")
+                         "the profile-grouped form; per-s: the FP32 sweep's bandwidth for S = 2..11 (separate "
+                         "measurements, not the default step)")
     ap.add_argument("--datasets", type=int, default=BATCH["datasets"])
     ap.add_argument("--plain-sample", type=int, default=32)
     args = ap.parse_args()
@@ -696,6 +745,8 @@ def main():
         return run_batched(args)
     if args.workload == "grouped":
         return run_grouped(args)
+    if args.workload == "per-s":
+        return run_per_s(args)
     if args.workload == "precision":
         if args.cells != WORKLOAD["cells"]:
             PREC["cells"] = args.cells
