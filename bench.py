@@ -37,7 +37,8 @@ UNIT = "updates/s"
 CPU_SAMPLE_V = 1 << 20          # oracle prefix for the single-core cpu_baseline leg
 CPU_SAMPLE_SWEEPS = 5
 CPU_ALL_V = 1 << 22             # oracle prefix for the all-cores cpu_baseline leg
-REF_SAMPLE_V = 1 << 17          # oracle prefix per step of the reference arm
+REF_SAMPLE_V = 1 << 17          # oracle prefix per step of the reference arm (single process)
+REF_ALL_V = 1 << 21             # oracle prefix per step of the reference arm (all host cores)
 
 
 def _dist():
@@ -185,65 +186,88 @@ def _oracle_worker(conn, S, lo, hi):
     conn.close()
 
 
-def _oracle_sweeps_all_cores(V, S, sweeps, procs, warm=1):
+class OraclePool:
     """The oracle on `procs` host cores: one spawn-started process per
-    contiguous chunk of the first V observations runs Q(beta) and the sums of
-    its chunk; the parent adds the chunks' FP64 statistics in chunk order (the
-    same bits whatever the timing) and runs Q(rho), Q(K, Lambda) and the ELBO.
-    Sweep 0 and `warm` sweeps run untimed.  Returns (wall seconds of the
-    `sweeps` timed sweeps, the workers' CPU seconds in them, final globals)."""
-    import multiprocessing as mp
-    from oracle import oracle as O
-    O.build()                                           # built once here, loaded by every worker
-    ctx = mp.get_context("spawn")
-    p = O.paper_prior(S)
-    M = S - 1
-    conns, workers = [], []
-    try:
-        for k in range(procs):
-            a, b = ctx.Pipe()
-            w = ctx.Process(target=_oracle_worker, args=(b, S, k * V // procs, (k + 1) * V // procs), daemon=True)
-            w.start()
-            b.close()
-            conns.append(a)
-            workers.append(w)
-        for c in conns:
-            if c.recv() != "ready":
-                raise RuntimeError("oracle worker failed to start")
+    contiguous chunk of the first V observations of the workload runs Q(beta)
+    and the sums of its chunk; the parent adds the chunks' FP64 statistics in
+    chunk order (the same bits whatever the timing) and runs Q(rho),
+    Q(K, Lambda) and the ELBO."""
 
-        def sweep(g):
-            for c in conns:
-                c.send({"g": g})
-            total, cpu = None, 0.0
-            for c in conns:                             # chunk order
-                flat, t = c.recv()
-                total = flat.copy() if total is None else total + flat
-                cpu += t
-            s = {"V": total[0], "sum_S": total[1], "sum_logdet": total[2], "sum_mu": total[3:3 + M],
-                 "sum_Ebb": total[3 + M:].reshape(M, M)}
-            g2 = O.KLambda_update(p, s, O.rho_update(p, s, g))
-            if g is not None:
-                O.elbo(p, s, g2)
-            return g2, cpu
+    def __init__(self, V, S, procs):
+        import multiprocessing as mp
+        from oracle import oracle as O
+        O.build()                                       # built once here, loaded by every worker
+        self.O, self.S, self.M = O, S, S - 1
+        self.p = O.paper_prior(S)
+        ctx = mp.get_context("spawn")
+        self.conns, self.workers = [], []
+        try:
+            for k in range(procs):
+                a, b = ctx.Pipe()
+                w = ctx.Process(target=_oracle_worker, args=(b, S, k * V // procs, (k + 1) * V // procs),
+                                daemon=True)
+                w.start()
+                b.close()
+                self.conns.append(a)
+                self.workers.append(w)
+            for c in self.conns:
+                if c.recv() != "ready":
+                    raise RuntimeError("oracle worker failed to start")
+        except BaseException:
+            self.close()
+            raise
 
-        g, _ = sweep(None)
-        for _ in range(warm):
-            g, _ = sweep(g)
-        cpu, t0 = 0.0, time.perf_counter()
-        for _ in range(sweeps):
-            g, c = sweep(g)
-            cpu += c
-        wall = time.perf_counter() - t0
-    finally:
-        for c in conns:
+    def sweep(self, g):
+        """One sweep from globals g (None: sweep 0 from the initial Q(beta));
+        returns (new globals, the workers' CPU seconds)."""
+        O, M = self.O, self.M
+        for c in self.conns:
+            c.send({"g": g})
+        total, cpu = None, 0.0
+        for c in self.conns:                            # chunk order
+            flat, t = c.recv()
+            total = flat.copy() if total is None else total + flat
+            cpu += t
+        s = {"V": total[0], "sum_S": total[1], "sum_logdet": total[2], "sum_mu": total[3:3 + M],
+             "sum_Ebb": total[3 + M:].reshape(M, M)}
+        g2 = O.KLambda_update(self.p, s, O.rho_update(self.p, s, g))
+        if g is not None:
+            O.elbo(self.p, s, g2)
+        return g2, cpu
+
+    def close(self):
+        for c in self.conns:
             try:
                 c.send("stop")
             except (OSError, ValueError):
                 pass
-        for w in workers:
+        for w in self.workers:
             w.join(timeout=30)
             if w.is_alive():
                 w.terminate()
+        self.conns, self.workers = [], []
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+        return False
+
+
+def _oracle_sweeps_all_cores(V, S, sweeps, procs, warm=1):
+    """`OraclePool` over the first V observations: sweep 0 and `warm` sweeps
+    untimed, then `sweeps` timed.  Returns (wall seconds of the timed sweeps,
+    the workers' CPU seconds in them, final globals)."""
+    with OraclePool(V, S, procs) as pool:
+        g, _ = pool.sweep(None)
+        for _ in range(warm):
+            g, _ = pool.sweep(g)
+        cpu, t0 = 0.0, time.perf_counter()
+        for _ in range(sweeps):
+            g, c = pool.sweep(g)
+            cpu += c
+        wall = time.perf_counter() - t0
     return wall, cpu, g
 
 
@@ -290,10 +314,48 @@ def cpu_baseline(S):
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle as it stands on the host cores, each
+    step a sweep over a bounded prefix of the at-scale data set (2^21
+    observations over every core with `OraclePool`; 2^17 in one process if
+    the pool cannot start).  Under torchrun only rank 0 runs it."""
     rank, world, _ = _dist()
     if rank != 0:
         return 0
     S = WORKLOAD["S"]
+    procs = max(1, os.cpu_count() or 1)
+    try:
+        with OraclePool(REF_ALL_V, S, procs) as pool:
+            g, _ = pool.sweep(None)
+            for _ in range(args.warmup):
+                g, _ = pool.sweep(g)
+            cpu, t0 = 0.0, time.perf_counter()
+            for _ in range(args.steps):
+                g, c = pool.sweep(g)
+                cpu += c
+            el = time.perf_counter() - t0
+        V, cores = REF_ALL_V, procs
+        how = (f"the FP64 oracle in {procs} processes over contiguous chunks, the chunks' statistics summed in "
+               f"chunk order, the global update in the parent ({cpu / el:.1f} effective cores)")
+    except Exception as e:                              # one process
+        V, cores, el = REF_SAMPLE_V, 1, _reference_one_process(args, S)
+        how = f"the FP64 oracle in one process (all-cores pool unavailable: {type(e).__name__}: {e})"
+    value = V * S * args.steps / el
+    sample = f"first {V} of the {V_FULL} observations per step (same seeded recipe), S = {S}; {how}"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD["name"], "N_cells": WORKLOAD["cells"], "G_genes": WORKLOAD["genes"],
+                       "S": S, "V": V_FULL, "sample_V": V},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                             "host": {"nproc": os.cpu_count(), "cpu_model": _cpu_model()}},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _reference_one_process(args, S):
+    """The reference arm's steps in one process on the first 2^17 observations;
+    returns the seconds of the timed steps."""
     from oracle import oracle as O
     from paper_2401_10068_gb300 import synth
     V = REF_SAMPLE_V
@@ -313,18 +375,7 @@ def run_reference(args):
     t0 = time.perf_counter()
     for _ in range(args.steps):
         g = step(g)
-    el = time.perf_counter() - t0
-    value = V * S * args.steps / el
-    sample = f"first {V} of the {V_FULL} observations per step (same seeded recipe), S = {S}"
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD["name"], "N_cells": WORKLOAD["cells"], "G_genes": WORKLOAD["genes"],
-                       "S": S, "V": V_FULL, "sample_V": V},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
-            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
-    return 0
+    return time.perf_counter() - t0
 
 
 def run_ours(args):

@@ -1,8 +1,13 @@
-"""The cpu_baseline leg of bench.py on CPU (no GPU): the oracle run over
-contiguous chunks in spawn-started processes, with the chunks' FP64
-statistics summed in chunk order, follows the single-process oracle fit
-(Section 3.5 schedule) up to the order of the FP64 additions, and gives the
-same bits on every run."""
+"""The oracle legs of bench.py on CPU (no GPU).
+
+* The all-cores oracle (contiguous chunks in spawn-started processes, the
+  chunks' FP64 statistics summed in chunk order) follows the single-process
+  oracle fit (Section 3.5 schedule) up to the order of the FP64 additions,
+  and gives the same bits on every run.
+* The reference arm runs it on every host core and prints one line, and
+  falls back to one process when the pool cannot start."""
+import argparse
+import json
 import os
 import sys
 
@@ -37,3 +42,26 @@ def test_all_cores_oracle_follows_the_single_process_fit():
 
 def test_cpu_model_is_reported():
     assert isinstance(bench._cpu_model(), str) and bench._cpu_model()
+
+
+def test_reference_arm_on_every_core(capsys):
+    args = argparse.Namespace(steps=1, warmup=3)
+    assert bench.run_reference(args) == 0
+    j = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert j["impl"] == "reference" and j["value"] > 0
+    assert j["cpu_baseline"]["cores"] == (os.cpu_count() or 1) and j["config"]["sample_V"] == bench.REF_ALL_V
+    assert j["e2e"]["h2d_bytes_per_step"] == 0 and j["e2e"]["d2h_bytes_per_step"] == 0
+
+
+def test_reference_arm_falls_back_to_one_process(monkeypatch, capsys):
+    class NoPool:
+        def __init__(self, *a, **k):
+            raise RuntimeError("no pool")
+
+    monkeypatch.setattr(bench, "OraclePool", NoPool)
+    monkeypatch.setattr(bench, "REF_SAMPLE_V", 2048)
+    args = argparse.Namespace(steps=1, warmup=3)
+    assert bench.run_reference(args) == 0
+    j = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert j["cpu_baseline"]["cores"] == 1 and j["config"]["sample_V"] == 2048
+    assert "no pool" in j["cpu_baseline"]["sample"] and j["value"] > 0
