@@ -68,3 +68,14 @@ def test_result_struct_layout_matches_header():
     assert vbh.Opts.refine_iters.offset == 20
     assert vbh.Opts.init_state.offset == 24 and vbh.Opts.elbo_trace.offset == 32
     assert vbh.Opts.method.offset == 40 and vbh.Opts.grouped.offset == 44 and ctypes.sizeof(vbh.Opts) == 48
+
+
+def test_create_fails_loudly_without_a_gpu():
+    """No CPU fallback: on a host without a GPU the library's first device
+    call fails and the binding raises with the library's status."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(vbh.VBHError) as e:
+        vbh.Handle(0, None)
+    assert e.value.args and "vbh_create" in str(e.value)
