@@ -617,29 +617,38 @@ int vbh_create(vbh_handle **hp, int device, void *stream)
 {
     if (!hp) return VBH_EINVAL;
     *hp = nullptr;
-    int ndev = 0;
-    if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
+    // a failing CUDA call is recorded for vbh_last_error_detail and mapped to a status
+    auto failed = [](cudaError_t e, const char *what, int line, int status) -> int {
+        if (e == cudaSuccess) return VBH_OK;
+        vbh::record_error(what, __FILE__, line, cudaGetErrorName(e));
         (void)cudaGetLastError();
-        return VBH_ECUDA;
-    }
+        return status;
+    };
+    int ndev = 0;
+    if (int rc0 = failed(cudaGetDeviceCount(&ndev), "cudaGetDeviceCount(&ndev)", __LINE__, VBH_ECUDA)) return rc0;
     if (device < 0 || device >= ndev) return VBH_EINVAL;
     DeviceGuard g(device);
-    if (!g.ok) return VBH_ECUDA;
+    if (!g.ok) {
+        const cudaError_t e = cudaGetLastError();
+        return failed(e != cudaSuccess ? e : cudaErrorInvalidDevice, "cudaSetDevice(device)", __LINE__, VBH_ECUDA);
+    }
     vbh_handle *h = new (std::nothrow) vbh_handle();
     if (!h) return VBH_ENOMEM;
     h->device = device;
     h->stream = static_cast<cudaStream_t>(stream);
     const char *launch = std::getenv("VBH_LAUNCH");
     h->direct = launch && std::strcmp(launch, "direct") == 0;
-    int rc = VBH_OK;
-    if (cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) rc = VBH_ECUDA;
-    if (!rc && cudaMalloc(&h->st, sizeof(DevState)) != cudaSuccess) rc = VBH_ENOMEM;
-    if (!rc && cudaMalloc(&h->st_aux, sizeof(DevState)) != cudaSuccess) rc = VBH_ENOMEM;
-    if (!rc && cudaMallocHost(&h->mirror, sizeof(DevState)) != cudaSuccess) rc = VBH_ENOMEM;
+    int rc = failed(cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, device),
+                    "cudaDeviceGetAttribute(MultiProcessorCount)", __LINE__, VBH_ECUDA);
+    if (!rc) rc = failed(cudaMalloc(&h->st, sizeof(DevState)), "cudaMalloc(state)", __LINE__, VBH_ENOMEM);
+    if (!rc) rc = failed(cudaMalloc(&h->st_aux, sizeof(DevState)), "cudaMalloc(state)", __LINE__, VBH_ENOMEM);
+    if (!rc) rc = failed(cudaMallocHost(&h->mirror, sizeof(DevState)), "cudaMallocHost(mirror)", __LINE__, VBH_ENOMEM);
     for (int i = 0; !rc && i < vbh_handle::NCOPY; ++i)
-        if (cudaStreamCreateWithFlags(&h->copy_stream[i], cudaStreamNonBlocking) != cudaSuccess) rc = VBH_ECUDA;
+        rc = failed(cudaStreamCreateWithFlags(&h->copy_stream[i], cudaStreamNonBlocking), "cudaStreamCreateWithFlags",
+                    __LINE__, VBH_ECUDA);
     for (int i = 0; !rc && i <= vbh_handle::NCOPY; ++i)
-        if (cudaEventCreateWithFlags(&h->copy_event[i], cudaEventDisableTiming) != cudaSuccess) rc = VBH_ECUDA;
+        rc = failed(cudaEventCreateWithFlags(&h->copy_event[i], cudaEventDisableTiming), "cudaEventCreateWithFlags",
+                    __LINE__, VBH_ECUDA);
     if (rc) {
         (void)cudaGetLastError();
         vbh_destroy(h);

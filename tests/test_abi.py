@@ -78,4 +78,5 @@ def test_create_fails_loudly_without_a_gpu():
         pytest.skip("a GPU is present")
     with pytest.raises(vbh.VBHError) as e:
         vbh.Handle(0, None)
-    assert e.value.args and "vbh_create" in str(e.value)
+    assert e.value.status == -3 and "vbh_create" in str(e.value)
+    assert "cudaGetDeviceCount" in vbh._lib().vbh_last_error_detail().decode()
