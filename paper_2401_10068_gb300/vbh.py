@@ -149,6 +149,30 @@ def _ptr(x):
     raise TypeError("expected a torch tensor or a numpy array")
 
 
+def _check_inputs(r, d, V: int, S: int, call: str):
+    """The library reads V float32 values of r and V*S of d through plain
+    pointers, which carry no size: refuse a tensor or array that is not
+    float32 or holds fewer values, with VBH_EINVAL, before the call.  Null
+    inputs and S outside 1..32 are left to the library's own checks."""
+    if not (1 <= int(S) <= 32) or int(V) < 0:
+        return
+    for x, n, what in ((r, int(V), "r"), (d, int(V) * int(S), "d")):
+        if x is None:
+            continue
+        if hasattr(x, "data_ptr"):
+            if str(x.dtype) != "torch.float32":
+                raise VBHError(-1, f"{call} ({what} is {x.dtype}, float32 is read)")
+            cnt = x.numel()
+        elif isinstance(x, np.ndarray):
+            if x.dtype != np.float32:
+                raise VBHError(-1, f"{call} ({what} is {x.dtype}, float32 is read)")
+            cnt = x.size
+        else:
+            continue
+        if cnt < n:
+            raise VBHError(-1, f"{call} ({what} holds {cnt} values, {n} are read)")
+
+
 class _PriorArgs:
     """Keeps the numpy buffers of a Prior alive."""
 
@@ -252,6 +276,7 @@ class Handle:
             init_state=None, trace: bool = False, V: int | None = None, precision: int = FP32,
             refine_iters: int = 10, method: int = CAVI, grouped: bool = False) -> dict:
         V = int(V if V is not None else (r.shape[0] if r is not None else 0))
+        _check_inputs(r, d, V, S, "vbh_fit")
         pa = _PriorArgs(prior, S)
         o, keep, buf = self._opts(tol, max_iter, init_state, S, trace, precision, refine_iters, method, grouped)
         res = Result()
@@ -268,6 +293,7 @@ class Handle:
                   init_state=None, trace: bool = False, V: int | None = None, precision: int = FP32,
                   refine_iters: int = 10, method: int = CAVI, grouped: bool = False):
         V = int(V if V is not None else (r.shape[0] if r is not None else 0))
+        _check_inputs(r, d, V, S, "vbh_fit_begin")
         pa = _PriorArgs(prior, S)
         o, keep, buf = self._opts(tol, max_iter, init_state, S, trace, precision, refine_iters, method, grouped)
         rc = _lib().vbh_fit_begin(self._h, _ptr(r), _ptr(d), V, int(S), ctypes.byref(pa.c), ctypes.byref(o))
@@ -302,6 +328,8 @@ class Handle:
             raise ValueError("rs, ds and Ss must have the same length")
         Vs = (ctypes.c_int64 * B)(*[int(r.shape[0]) if r is not None else 0 for r in rs])
         Sa = (ctypes.c_int * B)(*[int(x) for x in Ss])
+        for b in range(B):
+            _check_inputs(rs[b], ds[b], Vs[b], Sa[b], f"vbh_fit_batched (data set {b})")
         rp = (ctypes.c_void_p * B)(*[(_ptr(r).value if r is not None else None) for r in rs])
         dp = (ctypes.c_void_p * B)(*[(_ptr(d).value if d is not None else None) for d in ds])
         keep = []
@@ -343,6 +371,7 @@ class Handle:
 
     def elbo(self, r, d, S: int, state: dict, prior: dict | None = None, V: int | None = None) -> float:
         V = int(V if V is not None else (r.shape[0] if r is not None else 0))
+        _check_inputs(r, d, V, S, "vbh_elbo")
         pa = _PriorArgs(prior, S)
         q = dict_to_result(state, S)
         out = ctypes.c_double()
@@ -362,6 +391,7 @@ def fit_static(r, d, S: int, prior: dict | None = None, tol: float = 1e-8, max_i
     allocate device memory (no handle; the scratch is a static device array of
     the library).  r and d must be device tensors."""
     V = int(V if V is not None else (r.shape[0] if r is not None else 0))
+    _check_inputs(r, d, V, S, "vbh_fit_static")
     if stream is not None and hasattr(stream, "cuda_stream"):
         stream = stream.cuda_stream
     pa = _PriorArgs(prior, S)

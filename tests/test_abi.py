@@ -80,3 +80,23 @@ def test_create_fails_loudly_without_a_gpu():
         vbh.Handle(0, None)
     assert e.value.status == -3 and "vbh_create" in str(e.value)
     assert "cudaGetDeviceCount" in vbh._lib().vbh_last_error_detail().decode()
+
+
+def test_binding_refuses_short_or_non_float32_inputs():
+    """Plain pointers carry no size: the binding refuses, with VBH_EINVAL
+    before any library call, an input that holds fewer values than the call
+    reads or is not float32 (host arrays and tensors alike)."""
+    import numpy as np
+    import torch
+    V, S = 10, 3
+    r, d = np.zeros(V, np.float32), np.zeros((V, S), np.float32)
+    vbh._check_inputs(r, d, V, S, "vbh_fit")                           # exact sizes pass
+    vbh._check_inputs(None, None, 5, S, "vbh_fit")                     # null inputs: the library decides
+    vbh._check_inputs(r, d[:, :2], V, 33, "vbh_fit")                   # S out of range: the library decides
+    cases = [(r[:9], d, "r holds 9"), (r, d[:9], "d holds 27"), (r.astype(np.float64), d, "float64"),
+             (torch.zeros(V), torch.zeros(V * S - 1), "d holds 29"),
+             (torch.zeros(V, dtype=torch.float64), torch.zeros(V * S), "torch.float64")]
+    for rr, dd, msg in cases:
+        with pytest.raises(vbh.VBHError) as e:
+            vbh._check_inputs(rr, dd, V, S, "vbh_fit")
+        assert e.value.status == -1 and msg in str(e.value), (msg, str(e.value))
