@@ -159,22 +159,13 @@ def _mvn_logpdf_prec(x, mean, P):
     return -0.5 * M * math.log(2 * math.pi) + 0.5 * ld - 0.5 * np.einsum("...i,...ij,...j->...", dx, P, dx)
 
 
-def test_elbo_matches_monte_carlo_estimate():
-    S, V, N = 3, 5, 400_000
-    M = S - 1
-    p = _rich_prior(S, seed=11)
-    r, d, _ = synth.generate(V, S, seed=5)
-    f = O.fit(r, d, p, tol=0, max_iter=3)
-    mu, Sig = O.beta_update(r, d, p, f)
-    sums = O.sums_from_beta(r, d, p, mu, Sig)
-    # an arbitrary (not optimal) global factor set, so every term is exercised
-    g = dict(f)
-    g.update(a_rho=f["a_rho"] * 1.3, b_rho=f["b_rho"] * 0.7, kappa=f["kappa"] + np.array([0.05, -0.03]),
-             Winv=f["Winv"] * 1.2 + 0.01 * np.array([[0.0, 1.0], [1.0, 0.0]]), nu=f["nu"] + 2.0, lam=3.7)
-    L, dropped = O.elbo(p, sums, g)
-    assert not dropped
-
-    rng = np.random.default_rng(1234)
+def _mc_elbo(p, r, d, mu, Sig, g, N, seed, lam_prior_logpdf):
+    """Monte-Carlo estimate of E_Q[ln p(r, Z) - ln q(Z)] (Eq. 11) from scipy
+    densities of Eq. 3-7 and of the factors; ln p(Lambda) is passed in.
+    Returns (estimate, standard error)."""
+    M = int(p["S"]) - 1
+    V = r.shape[0]
+    rng = np.random.default_rng(seed)
     W = np.linalg.inv(g["Winv"])
     rho = st.gamma.rvs(g["a_rho"], scale=1.0 / g["b_rho"], size=N, random_state=rng)
     Lam = st.wishart.rvs(df=g["nu"], scale=W, size=N, random_state=rng)
@@ -183,7 +174,7 @@ def test_elbo_matches_monte_carlo_estimate():
     y = r.astype(np.float64) - d[:, M].astype(np.float64)
     D = d[:, :M].astype(np.float64) - d[:, M:].astype(np.float64)
     logp = st.gamma.logpdf(rho, p["a0"], scale=1.0 / p["b0"])
-    logp += st.wishart.logpdf(np.moveaxis(Lam, 0, -1), df=p["n0"], scale=np.linalg.inv(p["L0inv"]))
+    logp += lam_prior_logpdf(Lam)
     logp += _mvn_logpdf_prec(K, p["K0"], p["q0"] * Lam)
     logq = st.gamma.logpdf(rho, g["a_rho"], scale=1.0 / g["b_rho"])
     logq += st.wishart.logpdf(np.moveaxis(Lam, 0, -1), df=g["nu"], scale=W)
@@ -194,8 +185,54 @@ def test_elbo_matches_monte_carlo_estimate():
         logp += _mvn_logpdf_prec(b, K, Lam)
         logp += st.norm.logpdf(y[i], b @ D[i], 1.0 / np.sqrt(rho))
     diff = logp - logq
-    est, se = diff.mean(), diff.std() / math.sqrt(N)
+    return diff.mean(), diff.std() / math.sqrt(N)
+
+
+def _displaced_state(r, d, p):
+    """Q(beta) of a short fit and an arbitrary (not optimal) global factor set,
+    so that every term of the ELBO is exercised."""
+    f = O.fit(r, d, p, tol=0, max_iter=3)
+    mu, Sig = O.beta_update(r, d, p, f)
+    sums = O.sums_from_beta(r, d, p, mu, Sig)
+    g = dict(f)
+    g.update(a_rho=f["a_rho"] * 1.3, b_rho=f["b_rho"] * 0.7, kappa=f["kappa"] + np.array([0.05, -0.03]),
+             Winv=f["Winv"] * 1.2 + 0.01 * np.array([[0.0, 1.0], [1.0, 0.0]]), nu=f["nu"] + 2.0, lam=3.7)
+    return mu, Sig, sums, g
+
+
+def test_elbo_matches_monte_carlo_estimate():
+    S, V, N = 3, 5, 400_000
+    p = _rich_prior(S, seed=11)
+    r, d, _ = synth.generate(V, S, seed=5)
+    mu, Sig, sums, g = _displaced_state(r, d, p)
+    L, dropped = O.elbo(p, sums, g)
+    assert not dropped
+    est, se = _mc_elbo(p, r, d, mu, Sig, g, N, 1234, lambda Lam: st.wishart.logpdf(
+        np.moveaxis(Lam, 0, -1), df=p["n0"], scale=np.linalg.inv(p["L0inv"])))
     assert se < 0.02
+    assert abs(L - est) < 5 * se, (L, est, se)
+
+
+def test_elbo_with_the_improper_paper_prior_matches_a_sampled_estimate():
+    """The paper's n0 = 1 at M = 2 is not a proper Wishart: its log normaliser
+    is dropped, so the ELBO is E_Q[ln p] with the unnormalised prior density
+    (n0 - M - 1)/2 ln|Lambda| - tr(Lambda_0^{-1} Lambda)/2 minus E_Q[ln q].
+    Here the posterior Wishart's normaliser (its ln pi and ln 2 constants
+    included) is not cancelled by the prior's, so this case pins it."""
+    S, V, N = 3, 5, 40_000
+    M = S - 1
+    p = O.paper_prior(S)
+    r, d, _ = synth.generate(V, S, seed=5)
+    mu, Sig, sums, g = _displaced_state(r, d, p)
+    L, dropped = O.elbo(p, sums, g)
+    assert dropped
+
+    def unnormalised(Lam):
+        ld = np.linalg.slogdet(Lam)[1]
+        return 0.5 * (p["n0"] - M - 1.0) * ld - 0.5 * np.einsum("ij,nji->n", np.asarray(p["L0inv"]), Lam)
+
+    est, se = _mc_elbo(p, r, d, mu, Sig, g, N, 4321, unnormalised)
+    assert se < 0.08
     assert abs(L - est) < 5 * se, (L, est, se)
 
 
