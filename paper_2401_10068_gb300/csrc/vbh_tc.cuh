@@ -26,18 +26,25 @@
 //         tensor memory over an epoch of 16 tiles and is then added into
 //         compensated FP32 sums (sum and lost low part).
 // The scalar per-observation work (c_i, w_i, S_i, ln(1 + E[rho] q_i)) stays
-// on the CUDA cores; the consumer threads then build A2 from staged BF16 parts
-// of gamma in chunks of 8 observations.  Two tiles (17,408 contiguous bytes)
-// land in a pipeline stage by one bulk copy.
+// on the CUDA cores; the consumer threads then stage the BF16 parts of gamma
+// and build A2: in the FP32 form in shared memory, in chunks of 8
+// observations; in the BF16 form in tensor memory, each consumer thread
+// forming one A2 row (set, part, slot) over its set's 64 observations and
+// storing it with tcgen05.st, MMA2 then taking its A operand from tensor
+// memory.  Two tiles (17,408 contiguous bytes) land in a pipeline stage by one
+// bulk copy.
 //
 // Roles (15 warps): warps 0-7 are two groups of four consumer warps that take
 // alternate tiles, each warp owning one quarter of the tensor-memory lanes (32
 // observations); warps 8-11 flush the G'' epochs (one lane quarter each); lane
 // 0 of warp 12 issues the loads, of warp 13 the MMA1s and of warp 14 the
-// MMA2s.  MMA1 runs ahead of the consumers on its own (three U buffers in
-// tensor memory), and four A2 buffers in shared memory decouple the consumers
-// from MMA2.  Every wait is bounded: on a timeout the kernel records VBH_ETIMEOUT,
-// lets its copies and MMAs drain, frees its tensor memory and returns.
+// MMA2s.  MMA1 runs ahead of the consumers into one U buffer per consumer
+// group in tensor memory, and four A2 buffers decouple the consumers from
+// MMA2.  Every buffer is assigned so that all tiles using it belong to one
+// consumer group, so each mbarrier parity wait follows its waiter's wait of
+// the previous phase (static assertions below).  Every wait is bounded: on a
+// timeout the kernel records VBH_ETIMEOUT, lets its copies and MMAs drain,
+// frees its tensor memory and returns.
 #pragma once
 
 #include <cuda_bf16.h>
