@@ -426,6 +426,54 @@ def test_recovers_table1_truths():
     assert np.all(np.abs(np.array(rhos) - 100.0) < 15.0), rhos
 
 
+def _first_stop(trace, tol):
+    """Sweep at which the stopping rule fires: the first t >= 1 with
+    |L_t - L_{t-1}| < tol |L_t| (reading of Section 4.3), or None."""
+    for t in range(1, len(trace)):
+        if abs(trace[t] - trace[t - 1]) < tol * abs(trace[t]):
+            return t
+    return None
+
+
+@pytest.mark.parametrize("grouped", [False, True])
+def test_fits_stop_at_the_first_sweep_that_meets_the_tolerance(grouped):
+    r, d, _ = synth.generate(3000, 3, seed=77)
+    p = O.paper_prior(3)
+    tol = 1e-6
+    if grouped:
+        f = O.fit_grouped(O.group_profiles(r, d, 3), p, tol=tol, max_iter=2000)
+        full = O.fit_grouped(O.group_profiles(r, d, 3), p, tol=0.0, max_iter=f["iters"] + 5)
+    else:
+        f = O.fit(r, d, p, tol=tol, max_iter=2000)
+        full = O.fit(r, d, p, tol=0.0, max_iter=f["iters"] + 5)
+    assert f["converged"] and 1 <= f["iters"] < 2000
+    assert len(f["trace"]) == f["iters"] + 1
+    assert f["iters"] == _first_stop(full["trace"], tol)
+    assert np.array_equal(f["trace"], full["trace"][:f["iters"] + 1])
+    # a fit without a tolerance runs every sweep
+    assert full["iters"] == f["iters"] + 5 and not full["converged"]
+
+
+@pytest.mark.parametrize("S,prior", [(3, "paper"), (4, "rich")])
+def test_elbo_at_given_factors_takes_the_optimal_q_beta(S, prior):
+    """elbo_at(g) sets Q(beta) by Eq. 20-21 from g: for fixed global factors
+    that Q(beta) maximises the ELBO (Eq. 12), so every other Q(beta) -- the
+    initial one, or the optimal one displaced -- gives a lower ELBO."""
+    r, d, _ = synth.generate(400, S, seed=31 + S)
+    p = O.paper_prior(S) if prior == "paper" else _rich_prior(S, seed=S)
+    g = O.fit(r, d, p, tol=0.0, max_iter=4)
+    best, _ = O.elbo_at(r, d, p, g)
+    mu, Sig = O.beta_update(r, d, p, g)
+    assert best == pytest.approx(O.elbo(p, O.sums_from_beta(r, d, p, mu, Sig), g)[0], rel=1e-13)
+    mu0, Sig0 = O.beta_init(p, r.shape[0])
+    assert O.elbo(p, O.sums_from_beta(r, d, p, mu0, Sig0), g)[0] < best
+    rng = np.random.default_rng(S)
+    for scale in (1e-3, 1e-2):
+        dmu = scale * rng.normal(size=mu.shape)
+        assert O.elbo(p, O.sums_from_beta(r, d, p, mu + dmu, Sig), g)[0] < best
+        assert O.elbo(p, O.sums_from_beta(r, d, p, mu, Sig * (1.0 + 10 * scale)), g)[0] < best
+
+
 def test_large_S_runs_and_is_monotone():
     r, d, _ = synth.generate(400, 32, seed=8, alpha=0.5)
     f = O.fit(r, d, O.paper_prior(32), tol=0, max_iter=6)
