@@ -28,6 +28,8 @@
  *     are contiguous).  Device pointers must be 16-byte aligned.
  *   - The sweep is FP32 per observation with FP64 accumulation across blocks
  *     and FP64 global updates; non-finite results return VBH_ENONFINITE.
+ *     With a stopping test (tol > 0) the CUDA-core sweeps (S <= 11) also
+ *     carry the compensated statistics of the ELBO (vbh_opts.stats).
  *   - For 12 <= S <= 32 the two contractions per observation that grow with
  *     M^2 (q_i = D_i^T Sigma0 D_i of Eq. 20-21 and the sum of
  *     (w_i^2 - c_i) D_i D_i^T that enters Eq. 25) run on the tensor cores:
@@ -72,6 +74,16 @@ extern "C" {
 #define VBH_CAVI 0               /* variational Bayes: Q(rho) Q(beta) Q(K, Lambda) by coordinate ascent (Section 3.5) */
 #define VBH_EM 1                 /* expectation maximisation: point estimates of K, Lambda, rho (Section 4.2,
                                     Eq. 42-47); see vbh_opts.method */
+
+/* statistics of the per-observation sweep, S <= 11 (vbh_opts.stats) */
+#define VBH_STATS_AUTO 0         /* VBH_STATS_COMPENSATED when the fit has a stopping test (tol > 0), else plain */
+#define VBH_STATS_COMPENSATED 1  /* the pass also carries U = sum c_i e_i^2 and sum ln(1 + E[rho] q_i) in
+                                    two-part FP32 arithmetic (~2^-40), which replace the first-order part of the
+                                    FP32 sums in the ELBO: its rounding noise between sweeps drops from ~1e-8 |L|
+                                    (binary profiles repeat the same FP32 rounding in every observation of a
+                                    profile) to ~1e-11 |L|, so a relative stopping tolerance of 1e-8 is met by
+                                    convergence, not by noise.  About 1.5x the arithmetic per observation. */
+#define VBH_STATS_PLAIN 2        /* FP32 statistics only (the fastest pass; ELBO noise ~1e-8 |L|) */
 
 /* initial state of a fit */
 #define VBH_INIT_PAPER 0         /* Q(beta_i) = N(K0, Lambda_0^{-1}) before sweep 0 (Section 3.5) */
@@ -127,13 +139,16 @@ typedef struct {
                                     methods and results as the per-observation sweeps (up to their FP32
                                     rounding); the histogram's FP64 atomic sums make the last bits depend on
                                     the order of the additions.  Ignores precision. */
+    int stats;                   /* VBH_STATS_AUTO (0), VBH_STATS_COMPENSATED or VBH_STATS_PLAIN; only the
+                                    CUDA-core sweeps (S <= 11, not grouped) have the compensated form, the
+                                    others ignore it.  vbh_elbo always uses the compensated form there. */
 } vbh_opts;
 
 /* Fill *p with the paper's prior for S subpopulations (Section 3.5). */
 void vbh_prior_default(int S, vbh_prior *p);
 
 /* Fill *o with tol = 1e-8, max_iter = 200, VBH_FP32, VBH_INIT_PAPER, refine_iters = 10, no trace,
- * VBH_CAVI, not grouped. */
+ * VBH_CAVI, not grouped, VBH_STATS_AUTO. */
 void vbh_opts_default(vbh_opts *o);
 
 /* Create a handle on CUDA device `device` that issues all work on `stream`
@@ -237,15 +252,23 @@ int vbh_elbo(vbh_handle *h, const float *r, const float *d, int64_t V, int S, co
  *   r, d:    device pointers on `device` (16-byte aligned), layout as for
  *            vbh_fit; host pointers are rejected (staging them would allocate).
  *   p, o:    as for vbh_fit; with o->elbo_trace set, o->max_iter + 1 must not
- *            exceed VBH_STATIC_TRACE_MAX (else VBH_EINVAL).  S above the FP32
- *            sweep limit returns VBH_EUNSUPPORTED, as for vbh_fit.
+ *            exceed VBH_STATIC_TRACE_MAX (else VBH_EINVAL).  S > 11 returns
+ *            VBH_EUNSUPPORTED (vbh_fit runs it on the tensor-core path, which
+ *            this entry point lacks); so do o->method = VBH_EM and
+ *            o->grouped = 1.
  *   out:     the result, as for vbh_fit.
  *   stream:  a cudaStream_t on `device` (NULL = legacy default stream); the
  *            call is synchronous on it.
- * The sweeps run as one kernel launch each (a launch after convergence
- * returns at once).  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress, with that device current); make that first
- * call before any stream capture.  All calls on a device share the one array
+ * The sweeps run as one kernel launch each, issued in batches of 64; between
+ * batches the call reads the fit's control fields back and issues no more
+ * launches once the fit has stopped.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress, with that device
+ * current) and loads every kernel this entry point can launch, for every S:
+ * under CUDA's lazy module loading the first use of a kernel loads its
+ * module, which allocates device memory, so this first call per device is
+ * the only one that may load code or allocate.  Make it before any stream
+ * capture and before the caller's device memory is fully committed.  All
+ * calls on a device share the one array
  * and every call rewrites the whole fit state before its first kernel, so
  * nothing of an earlier call carries over; but calls whose work overlaps on
  * the GPU (other host threads, other streams) race on the array and must be

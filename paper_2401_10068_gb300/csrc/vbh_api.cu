@@ -28,6 +28,7 @@ struct Launch {
     int P = 0;                              // profile codes (2^S)
     const double *gstats = nullptr;         // their (n, sum y, sum y^2)
     bool tc = false;
+    bool comp = false;                      // compensated statistics (CUDA-core sweep only)
     int S = 0;
     int grid = 0;
     int nsplit = 3;
@@ -35,7 +36,10 @@ struct Launch {
     KernelInfo ki{};
     vbh::TcKernelInfo tki{};
     const unsigned char *tiles = nullptr;   // repacked inputs of the tensor-core sweep
-    const void *func() const { return grp ? vbh::grouped_sweep_func(S) : tc ? tki.sweep : ki.sweep; }
+    const void *func() const
+    {
+        return grp ? vbh::grouped_sweep_func(S) : tc ? tki.sweep : comp ? ki.sweep_comp : ki.sweep;
+    }
     const void *setup() const { return (tc || grp) ? tki.setup : ki.setup; }
     int threads() const { return grp ? vbh::GROUPED_THREADS : tc ? tki.threads : ki.threads; }
     size_t smem() const { return grp ? vbh::grouped_smem_bytes() : tc ? tki.smem : ki.smem; }
@@ -311,11 +315,11 @@ void fill_prior(DevState *s, const vbh_prior *p, int S, long long V)
 // Kernel choice, launch shape and partials buffer of a fit of (V, S).  For the
 // tensor-core path the BF16 profiles and the tensor maps are prepared too.
 int prepare_launch(vbh_handle *h, int S, long long V, int precision, const float *rd, const float *dd, Launch *L,
-                   bool grouped = false)
+                   bool grouped = false, bool comp = false)
 {
     L->S = S;
     const int M = S - 1;
-    const size_t nstat = size_t(M * (M + 1) / 2 + M + 3);
+    const size_t nstat = size_t(M * (M + 1) / 2 + M + 4);   // room for the compensated form's extra column
     if (grouped) {
         // one histogram pass, then sweeps over the 2^S profile codes
         if (S > vbh::GROUPED_SMAX) return VBH_EUNSUPPORTED;
@@ -344,9 +348,12 @@ int prepare_launch(vbh_handle *h, int S, long long V, int precision, const float
     }
     if (S <= vbh::S_FP32_MAX) {
         L->tc = false;
+        L->comp = comp;
         if (!kernel_info(S, &L->ki)) return VBH_EUNSUPPORTED;
         if (!h->attr_set[S]) {
             VBH_CK(cudaFuncSetAttribute(L->ki.sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, int(L->ki.smem)));
+            VBH_CK(cudaFuncSetAttribute(L->ki.sweep_comp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        int(L->ki.smem)));
             h->attr_set[S] = true;
         }
     } else {
@@ -421,7 +428,7 @@ int launch_sweep(vbh_handle *h, DevState *st, int mode, Launch &L, const float *
         VBH_CK(cudaLaunchKernel(L.tki.sweep, dim3(L.grid), dim3(L.tki.threads), args, L.tki.smem, h->stream));
     } else {
         void *args[] = {&a};
-        VBH_CK(cudaLaunchKernel(L.ki.sweep, dim3(L.grid), dim3(L.ki.threads), args, L.ki.smem, h->stream));
+        VBH_CK(cudaLaunchKernel(L.func(), dim3(L.grid), dim3(L.ki.threads), args, L.ki.smem, h->stream));
     }
     return VBH_OK;
 }
@@ -589,6 +596,7 @@ void vbh_opts_default(vbh_opts *o)
     o->refine_iters = 10;
     o->method = VBH_CAVI;
     o->grouped = 0;
+    o->stats = VBH_STATS_AUTO;
     o->init = VBH_INIT_PAPER;
     o->init_state = nullptr;
     o->elbo_trace = nullptr;
@@ -707,8 +715,11 @@ int vbh_fit_begin(vbh_handle *h, const float *r, const float *d, int64_t V, int 
     const float *rd = nullptr, *dd = nullptr;
     if ((rc = stage_inputs(h, r, d, V, S, &rd, &dd))) return rc;
     if (o->grouped != 0 && o->grouped != 1) return VBH_EINVAL;
+    if (o->stats != VBH_STATS_AUTO && o->stats != VBH_STATS_COMPENSATED && o->stats != VBH_STATS_PLAIN)
+        return VBH_EINVAL;
+    const bool comp = o->stats == VBH_STATS_COMPENSATED || (o->stats == VBH_STATS_AUTO && o->tol > 0.0);
     Launch L;
-    if ((rc = prepare_launch(h, S, V, o->precision, rd, dd, &L, o->grouped == 1))) return rc;
+    if ((rc = prepare_launch(h, S, V, o->precision, rd, dd, &L, o->grouped == 1, comp))) return rc;
     if (o->max_iter + 1 > h->trace_cap) {
         size_t cap = 0;
         cudaFree(h->trace);
@@ -727,6 +738,7 @@ int vbh_fit_begin(vbh_handle *h, const float *r, const float *d, int64_t V, int 
     s->target = 0;
     s->trace = h->trace;
     s->em = em ? 1 : 0;
+    s->comp = L.comp ? 1 : 0;
     const int M = S - 1;
     if (em && o->init == VBH_INIT_PAPER) {
         // theta^(0) from the prior: K0, Lambda_0^{-1}, rho = a0 / b0 (as (a_rho, b_rho) = (rho, 1), nu = 1)
@@ -897,11 +909,12 @@ int vbh_elbo(vbh_handle *h, const float *r, const float *d, int64_t V, int S, co
     // profiles or the partials buffer are reused here
     if (h->begun && (rd != h->r || dd != h->d || S > vbh::S_FP32_MAX || h->L.tc)) h->begun = false;
     Launch L;
-    if ((rc = prepare_launch(h, S, V, VBH_FP32, rd, dd, &L))) return rc;
+    if ((rc = prepare_launch(h, S, V, VBH_FP32, rd, dd, &L, false, true))) return rc;
     DevState *s = h->mirror;
     VBH_CK(cudaStreamSynchronize(h->stream));
     std::memset(s, 0, sizeof(DevState));
     fill_prior(s, p, S, V);
+    s->comp = L.comp ? 1 : 0;
     s->a_rho = q->a_rho;
     s->b_rho = q->b_rho;
     s->nu = q->nu;

@@ -134,6 +134,10 @@ int fit_batched_impl(BatchedHost &hb, cudaStream_t stream, int nsm, int B, const
     if (o->init != VBH_INIT_PAPER && o->init != VBH_INIT_GIVEN) return VBH_EINVAL;
     if (o->method != VBH_CAVI) return VBH_EUNSUPPORTED;           // this entry point runs CAVI only
     if (o->init == VBH_INIT_GIVEN && !o->init_state) return VBH_EINVAL;
+    if (o->stats != VBH_STATS_AUTO && o->stats != VBH_STATS_COMPENSATED && o->stats != VBH_STATS_PLAIN)
+        return VBH_EINVAL;
+    // the compensated statistics of the stopping test (one more partial column)
+    const bool comp = o->stats == VBH_STATS_COMPENSATED || (o->stats == VBH_STATS_AUTO && o->tol > 0.0);
     for (int b = 0; b < B; ++b) {
         if (S[b] < 1 || S[b] > VBH_SMAX || V[b] < 0 || V[b] > (int64_t(1) << 40)) return VBH_EINVAL;
         if (S[b] > S_FP32_MAX) return VBH_EUNSUPPORTED;
@@ -192,6 +196,10 @@ int fit_batched_impl(BatchedHost &hb, cudaStream_t stream, int nsm, int B, const
             if (S[b] == s) cp.ds.push_back(b);
         if (cp.ds.empty()) continue;
         if (!batch_info(s, &cp.bi)) return VBH_EUNSUPPORTED;
+        if (comp) {
+            cp.bi.pass = cp.bi.pass_comp;
+            cp.bi.nstat += 1;
+        }
         VBH_B_CK(cudaFuncSetAttribute(cp.bi.pass, cudaFuncAttributeMaxDynamicSharedMemorySize, int(cp.bi.pass_smem)));
         VBH_B_CK(cudaFuncSetAttribute(cp.bi.update, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       int(cp.bi.update_smem)));
@@ -308,6 +316,7 @@ int fit_batched_impl(BatchedHost &hb, cudaStream_t stream, int nsm, int B, const
         s.max_iter = o->max_iter;
         s.target = o->max_iter;
         s.trace = traces + size_t(b) * ntrace;
+        s.comp = comp ? 1 : 0;
         if (o->init == VBH_INIT_GIVEN) {
             const vbh_result &g = o->init_state[b];
             s.a_rho = g.a_rho;
@@ -357,6 +366,7 @@ int fit_batched_impl(BatchedHost &hb, cudaStream_t stream, int nsm, int B, const
             bc.order = cdev[c].order;
             bc.nchunks = int(n);
             bc.partials = cdev[c].partials;
+            bc.nstat = cp.bi.nstat;
             bc.next = counters + c;
             bc.ds_list = cdev[c].ds_list;
             bc.ds_first_chunk = ds_first;

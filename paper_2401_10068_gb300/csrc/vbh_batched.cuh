@@ -32,7 +32,8 @@ struct BatchClass {
     const long long *ds_V;          // [B] observations per data set
     const int *order;               // [nchunks] scheduling order (chunk ids)
     int nchunks;
-    double *partials;               // [nchunks][NSTAT]
+    double *partials;               // [nchunks][nstat]
+    int nstat;                      // columns of a chunk partial: NSTAT, or NSTAT + 1 for the compensated form
     unsigned int *next;             // work-queue counter of this class
     const int *ds_list;             // [nds] data sets of this class
     const int *ds_first_chunk;      // [B] first chunk id of each data set (within its class)
@@ -159,12 +160,15 @@ __device__ __forceinline__ void issue_unit(Cursor &cu, const BatchClass &bc, int
 // the stage.  A chunk's FP64 partial is staged in one of two reduction buffers
 // before that barrier and summed after it, so the next chunk's partial (into
 // the other buffer) cannot overwrite it while it is read.
-template <int S>
-__global__ void __launch_bounds__(BatchCfg<S>::THREADS, SweepCfg<S>::MINB) batched_pass_kernel(BatchClass bc)
+template <int S, bool COMP>
+__global__ void __launch_bounds__(BatchCfg<S>::THREADS, COMP ? SweepCfg<S>::MINB_C : SweepCfg<S>::MINB)
+    batched_pass_kernel(BatchClass bc)
 {
     using C = SweepCfg<S>;
     using B = BatchCfg<S>;
-    constexpr int M = C::M, NG = C::NG, NSTAT = C::NSTAT, NGRP = C::NGRP;
+    constexpr int M = C::M, NG = C::NG, NSTAT = C::NSTAT;
+    constexpr int NS = COMP ? C::NSTATC : C::NSTAT;        // columns of a chunk partial
+    constexpr int NGRP = COMP ? C::NGRPC : C::NGRP;
     constexpr int THREADS = B::THREADS, T = B::T, STAGES = B::STAGES;
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + B::RING_BYTES);
@@ -187,15 +191,19 @@ __global__ void __launch_bounds__(BatchCfg<S>::THREADS, SweepCfg<S>::MINB) batch
 
     float acc[NSTAT];
     double acc64[NGRP];
-    float prod = 1.0f;
+    float prod = 1.0f, pl = 0.0f, uh = 0.0f, ul = 0.0f;
     int ex = 0;
 #pragma unroll
     for (int i = 0; i < NSTAT; ++i) acc[i] = 0.0f;
 #pragma unroll
     for (int g = 0; g < NGRP; ++g) acc64[g] = 0.0;
-    float L[C::NGA], kap[C::MA], erho = 0.0f;
+    // plain form: L~ (L) and kappa~ (kap); compensated form: the grid and
+    // rest parts of Sigma0~ (L, L2) and kappa~ (kap, kap2)
+    float L[C::NGA], kap[C::MA], L2[COMP ? C::NGA : 1], kap2[COMP ? C::MA : 1], erho = 0.0f;
     if constexpr (NG == 0) L[0] = 0.0f;
     if constexpr (M == 0) kap[0] = 0.0f;
+    L2[0] = 0.0f;
+    kap2[0] = 0.0f;
     int cur_ds = -1;
     int ftile = 0;
     int rbuf = 0;                                           // reduction buffer of the next chunk partial
@@ -212,10 +220,23 @@ __global__ void __launch_bounds__(BatchCfg<S>::THREADS, SweepCfg<S>::MINB) batch
         if (work) {
             if (m.ds != cur_ds) {                           // a new data set: its FP32 globals (cached reads)
                 const DevState *st = bc.states + m.ds;
+                if constexpr (COMP) {
 #pragma unroll
-                for (int i = 0; i < NG; ++i) L[i] = st->sw.L[i];
+                    for (int i = 0; i < NG; ++i) {
+                        L[i] = st->sw.Sh[i];
+                        L2[i] = st->sw.Sl[i];
+                    }
 #pragma unroll
-                for (int i = 0; i < M; ++i) kap[i] = st->sw.kappa[i];
+                    for (int i = 0; i < M; ++i) {
+                        kap[i] = st->sw.kh[i];
+                        kap2[i] = st->sw.kl[i];
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < NG; ++i) L[i] = st->sw.L[i];
+#pragma unroll
+                    for (int i = 0; i < M; ++i) kap[i] = st->sw.kappa[i];
+                }
                 erho = (mode == MODE_INIT) ? 0.0f : st->sw.erho;
                 cur_ds = m.ds;
             }
@@ -227,11 +248,19 @@ __global__ void __launch_bounds__(BatchCfg<S>::THREADS, SweepCfg<S>::MINB) batch
                     const int j = tid + u * THREADS;
                     float x[S];
                     load_row<S>(dt, j, x);
-                    observe<S>(x, rt[j], L, kap, erho, acc, prod);
-                    peel_exponent(prod, ex);
+                    if constexpr (COMP) {
+                        observe_comp<S>(x, rt[j], L, L2, kap, kap2, erho, acc, prod, pl, uh, ul);
+                        peel_exponent2(prod, pl, ex);
+                    } else {
+                        observe<S>(x, rt[j], L, kap, erho, acc, prod);
+                        peel_exponent(prod, ex);
+                    }
                 }
                 if (++ftile == 16) {
-                    flush_warp<S>(acc, acc64, prod, ex, lane);
+                    if constexpr (COMP)
+                        flush_warp_comp<S>(acc, acc64, prod, pl, ex, uh, ul, lane);
+                    else
+                        flush_warp<S>(acc, acc64, prod, ex, lane);
                     ftile = 0;
                 }
             } else {
@@ -242,12 +271,20 @@ __global__ void __launch_bounds__(BatchCfg<S>::THREADS, SweepCfg<S>::MINB) batch
                     float x[S];
 #pragma unroll
                     for (int q = 0; q < S; ++q) x[q] = __ldg(dg + i * S + q);
-                    observe<S>(x, __ldg(rg + i), L, kap, erho, acc, prod);
-                    peel_exponent(prod, ex);
+                    if constexpr (COMP) {
+                        observe_comp<S>(x, __ldg(rg + i), L, L2, kap, kap2, erho, acc, prod, pl, uh, ul);
+                        peel_exponent2(prod, pl, ex);
+                    } else {
+                        observe<S>(x, __ldg(rg + i), L, kap, erho, acc, prod);
+                        peel_exponent(prod, ex);
+                    }
                 }
             }
             if (m.flags & UNIT_LAST) {                      // chunk done: stage its FP64 partial
-                flush_warp<S>(acc, acc64, prod, ex, lane);
+                if constexpr (COMP)
+                    flush_warp_comp<S>(acc, acc64, prod, pl, ex, uh, ul, lane);
+                else
+                    flush_warp<S>(acc, acc64, prod, ex, lane);
                 ftile = 0;
 #pragma unroll
                 for (int g = 0; g < NGRP; ++g) {
@@ -263,11 +300,11 @@ __global__ void __launch_bounds__(BatchCfg<S>::THREADS, SweepCfg<S>::MINB) batch
         }
         if (!work) break;                                   // the end mark (every thread read it)
         if (m.flags & UNIT_LAST) {
-            for (int j = tid; j < NSTAT; j += THREADS) {
+            for (int j = tid; j < NS; j += THREADS) {
                 double t = 0.0;
 #pragma unroll
                 for (int w = 0; w < THREADS / 32; ++w) t += s_red[rbuf][w][j];
-                bc.partials[size_t(m.chunk) * NSTAT + j] = t;
+                bc.partials[size_t(m.chunk) * NS + j] = t;
             }
             rbuf ^= 1;
         }
@@ -293,8 +330,7 @@ __global__ void __launch_bounds__(256) batched_update_kernel(BatchClass bc, Batc
     SweepArgs a{};
     a.mode = mode;
     a.use_cond = 0;
-    using C = SweepCfg<M + 1>;
-    global_update<M>(st, bc.partials + size_t(bc.ds_first_chunk[b]) * C::NSTAT, bc.ds_nchunks[b], a,
+    global_update<M>(st, bc.partials + size_t(bc.ds_first_chunk[b]) * bc.nstat, bc.ds_nchunks[b], a,
                      reinterpret_cast<double *>(smem));
     __syncthreads();                                       // the control fields were written by another warp
     if (threadIdx.x == 0 && ds_running(st)) atomicAdd(&ctl->active, 1u);

@@ -6,24 +6,26 @@
 namespace vbh {
 
 struct KernelInfo {
-    const void *sweep;     // sweep_kernel<S>
+    const void *sweep;     // sweep_kernel<S, false>
+    const void *sweep_comp;// sweep_kernel<S, true>: with the compensated statistics (one more column)
     const void *setup;     // setup_kernel<S - 1>
     size_t smem;           // dynamic shared memory of the sweep
     int threads;           // block size of the sweep
     int tile;              // observations per tile
-    int nstat;             // statistics per block partial
+    int nstat;             // statistics per block partial (plain form; the compensated form has nstat + 1)
 };
 
 // Kernels of the batched form for one S class.
 struct BatchKernelInfo {
-    const void *pass;      // batched_pass_kernel<S>
+    const void *pass;      // batched_pass_kernel<S, false>
+    const void *pass_comp; // batched_pass_kernel<S, true>
     const void *update;    // batched_update_kernel<S - 1>
     const void *setup;     // batched_setup_kernel<S - 1>
     size_t pass_smem;
     size_t update_smem;
     int threads;
     int tile;              // observations per tile of the pass
-    int nstat;
+    int nstat;             // statistics per chunk partial (plain form; the compensated form has nstat + 1)
 };
 
 // Each translation unit that instantiates sweep kernels fills the entries of
@@ -41,7 +43,8 @@ bool batch_kernel_info_s9_11(int S, BatchKernelInfo *out);
     case SV: {                                                                                                         \
         using C = ::vbh::SweepCfg<SV>;                                                                                 \
         static_assert(size_t(::vbh::gu_ws_doubles<SV - 1>()) * 8 <= C::RING_BYTES, "workspace exceeds the ring");    \
-        out->sweep = reinterpret_cast<const void *>(&::vbh::sweep_kernel<SV>);                                         \
+        out->sweep = reinterpret_cast<const void *>(&::vbh::sweep_kernel<SV, false>);                                  \
+        out->sweep_comp = reinterpret_cast<const void *>(&::vbh::sweep_kernel<SV, true>);                              \
         out->setup = reinterpret_cast<const void *>(&::vbh::setup_kernel<SV - 1>);                                     \
         out->smem = C::SMEM_BYTES;                                                                                     \
         out->threads = C::THREADS;                                                                                     \
@@ -53,7 +56,8 @@ bool batch_kernel_info_s9_11(int S, BatchKernelInfo *out);
 #define VBH_BATCH_KERNEL_INFO_CASE(SV)                                                                                 \
     case SV: {                                                                                                         \
         using BC = ::vbh::BatchCfg<SV>;                                                                                \
-        out->pass = reinterpret_cast<const void *>(&::vbh::batched_pass_kernel<SV>);                                   \
+        out->pass = reinterpret_cast<const void *>(&::vbh::batched_pass_kernel<SV, false>);                            \
+        out->pass_comp = reinterpret_cast<const void *>(&::vbh::batched_pass_kernel<SV, true>);                        \
         out->update = reinterpret_cast<const void *>(&::vbh::batched_update_kernel<SV - 1>);                           \
         out->setup = reinterpret_cast<const void *>(&::vbh::batched_setup_kernel<SV - 1>);                             \
         out->pass_smem = BC::SMEM_BYTES;                                                                               \

@@ -34,13 +34,21 @@ enum SweepMode : int {
 // Status codes (same values as the public header).
 enum : int { ST_OK = 0, ST_ENONFINITE = -4, ST_ETIMEOUT = -5 };
 
+constexpr int NG_COMP_MAX = (S_FP32_MAX - 1) * S_FP32_MAX / 2;   // packed entries of Sigma0 at S <= 11
+
 // What one data pass reads: the FP32 form of Sigma0 = W^{-1}/nu (its packed
-// lower Cholesky factor, row i at offset i(i+1)/2), kappa and E[rho].
+// lower Cholesky factor, row i at offset i(i+1)/2), kappa and E[rho].  For
+// the compensated statistics (S <= 11) also Sigma0~ = L~ L~^T, off-diagonal
+// entries doubled, and kappa~, each split into a part on a coarse grid
+// (Sh, kh) and the rest (Sl, kl), so that for profiles with entries in
+// {0, 1} the sums of the grid parts over D_j D_k (or D_j) are exact in FP32.
 struct SweepGlobalsF32 {
     float L[MMAX * (MMAX + 1) / 2];
     float kappa[MMAX];
     float erho;
     int pad;
+    float Sh[NG_COMP_MAX], Sl[NG_COMP_MAX];
+    float kh[S_FP32_MAX - 1], kl[S_FP32_MAX - 1];
 };
 
 // Functions of (a_rho, nu, lambda) that the ELBO needs.  In a fit these are
@@ -84,6 +92,8 @@ struct DevState {
     unsigned int ticket;             // last-block-done counter of a sweep launch
     unsigned int gticket[TICKET_GROUPS_MAX];   // per-group counters of the two-level reduction
     int em;                          // 1: expectation maximisation (Eq. 42-47) instead of CAVI
+    int comp;                        // 1: the data pass adds the compensated statistics U and T4 (one more
+                                     //    column of partials) and the ELBO takes their first-order correction
     double *trace;                   // device array [max_iter + 1] (may be null)
     // per-fit constants: kc_upd for (a0 + V/2, n0 + V, q0 + V), kc_given for
     // the factors a fit or vbh_elbo starts from; prior_const collects the

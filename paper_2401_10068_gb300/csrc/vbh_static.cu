@@ -16,11 +16,13 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstddef>
 #include <cstring>
 #include <mutex>
 
 #include "vbh.h"
 #include "vbh_dispatch.cuh"
+#include "vbh_error.h"
 #include "vbh_internal.cuh"
 
 namespace {
@@ -41,17 +43,39 @@ constexpr int MAX_DEVICES = 64;
 std::mutex g_mu;
 unsigned char *g_addr[MAX_DEVICES] = {};
 
-// Device address of the scratch on the current device (looked up once per
-// device, with that device current).
+bool kernel_info_any(int S, vbh::KernelInfo *ki)
+{
+    return vbh::kernel_info_s1_4(S, ki) || vbh::kernel_info_s5_8(S, ki) || vbh::kernel_info_s9_11(S, ki);
+}
+
+// Device address of the scratch on the current device, looked up once per
+// device with that device current.  The same first call loads every kernel
+// this entry point can launch (the sweeps, plain and compensated, and the
+// set-up kernels of S = 1..11): with CUDA's lazy module loading a module is
+// loaded, which allocates device memory, at the first use of one of its
+// symbols, so without this a later call at a new S would allocate.  After
+// the first call per device no call loads code or allocates.
 int scratch_address(int device, unsigned char **out)
 {
     if (device < 0 || device >= MAX_DEVICES) return VBH_EINVAL;
     std::lock_guard<std::mutex> lk(g_mu);
     if (!g_addr[device]) {
         void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, vbh_static_scratch) != cudaSuccess || !p) {
-            (void)cudaGetLastError();
+        VBH_CHECK_CUDA(cudaGetSymbolAddress(&p, vbh_static_scratch));
+        if (!p) {
+            vbh::record_error("cudaGetSymbolAddress(vbh_static_scratch)", __FILE__, __LINE__, "null address");
             return VBH_ECUDA;
+        }
+        for (int S = 1; S <= vbh::S_FP32_MAX; ++S) {
+            vbh::KernelInfo ki;
+            if (!kernel_info_any(S, &ki)) return VBH_EUNSUPPORTED;
+            cudaFuncAttributes fa;
+            VBH_CHECK_CUDA(cudaFuncGetAttributes(&fa, ki.sweep));
+            VBH_CHECK_CUDA(cudaFuncGetAttributes(&fa, ki.sweep_comp));
+            VBH_CHECK_CUDA(cudaFuncGetAttributes(&fa, ki.setup));
+            VBH_CHECK_CUDA(cudaFuncSetAttribute(ki.sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, int(ki.smem)));
+            VBH_CHECK_CUDA(
+                cudaFuncSetAttribute(ki.sweep_comp, cudaFuncAttributeMaxDynamicSharedMemorySize, int(ki.smem)));
         }
         g_addr[device] = static_cast<unsigned char *>(p);
     }
@@ -109,13 +133,7 @@ struct DeviceSwitch {
     }
 };
 
-#define VBH_S_CK(call)                                                                                                 \
-    do {                                                                                                               \
-        if ((call) != cudaSuccess) {                                                                                   \
-            (void)cudaGetLastError();                                                                                  \
-            return VBH_ECUDA;                                                                                          \
-        }                                                                                                              \
-    } while (0)
+#define VBH_S_CK(call) VBH_CHECK_CUDA(call)
 
 } // namespace
 
@@ -135,6 +153,10 @@ extern "C" int vbh_fit_static(const float *r, const float *d, int64_t V, int S, 
     if (o->max_iter < 0 || !(o->tol >= 0.0) || !std::isfinite(o->tol) || o->precision != VBH_FP32) return VBH_EINVAL;
     if (o->init != VBH_INIT_PAPER && o->init != VBH_INIT_GIVEN) return VBH_EINVAL;
     if (o->method != VBH_CAVI) return VBH_EUNSUPPORTED;           // this entry point runs CAVI only
+    if (o->grouped != 0) return VBH_EUNSUPPORTED;                 // and the per-observation sweep only
+    if (o->stats != VBH_STATS_AUTO && o->stats != VBH_STATS_COMPENSATED && o->stats != VBH_STATS_PLAIN)
+        return VBH_EINVAL;
+    const bool comp = o->stats == VBH_STATS_COMPENSATED || (o->stats == VBH_STATS_AUTO && o->tol > 0.0);
     if (o->elbo_trace && o->max_iter + 1 > VBH_STATIC_TRACE_MAX) return VBH_EINVAL;   // trace beyond the scratch
     const vbh_result *q = o->init_state;
     if (o->init == VBH_INIT_GIVEN) {
@@ -153,8 +175,9 @@ extern "C" int vbh_fit_static(const float *r, const float *d, int64_t V, int S, 
     if (V > 0 && (!r || !d || !device_ptr_on(r, device) || !device_ptr_on(d, device))) return VBH_EINVAL;
 
     vbh::KernelInfo ki;
-    if (!(vbh::kernel_info_s1_4(S, &ki) || vbh::kernel_info_s5_8(S, &ki) || vbh::kernel_info_s9_11(S, &ki)))
-        return VBH_EUNSUPPORTED;
+    if (!kernel_info_any(S, &ki)) return VBH_EUNSUPPORTED;
+    const void *sweep = comp ? ki.sweep_comp : ki.sweep;
+    const int nstat = ki.nstat + (comp ? 1 : 0);
     unsigned char *base = nullptr;
     int rc = scratch_address(device, &base);
     if (rc) return rc;
@@ -162,16 +185,20 @@ extern "C" int vbh_fit_static(const float *r, const float *d, int64_t V, int S, 
     double *trace = reinterpret_cast<double *>(base + TRACE_OFF);
     double *partials = reinterpret_cast<double *>(base + PART_OFF);
 
-    // ---- launch shape: the persistent grid, capped by the partials that fit ----
-    VBH_S_CK(cudaFuncSetAttribute(ki.sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, int(ki.smem)));
+    // ---- launch shape: the persistent grid, capped by the partials that fit
+    //      (the shared-memory attribute was set by the first call) ----
     int nsm = 0, per_sm = 0;
     VBH_S_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device));
-    VBH_S_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ki.sweep, ki.threads, ki.smem));
-    long long grid = (long long)nsm * (per_sm > 0 ? per_sm : 1);
+    VBH_S_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep, ki.threads, ki.smem));
+    if (per_sm < 1) {
+        vbh::record_error("occupancy of the sweep kernel", __FILE__, __LINE__, "no block fits on an SM");
+        return VBH_ECUDA;
+    }
+    long long grid = (long long)nsm * per_sm;
     const long long tiles = (V + ki.tile - 1) / ki.tile;
     if (tiles < grid) grid = tiles;
     if (grid > vbh::GRID_MAX) grid = vbh::GRID_MAX;
-    while (grid > 1 && size_t(vbh::partial_rows(grid)) * size_t(ki.nstat) > PART_DOUBLES) --grid;
+    while (grid > 1 && size_t(vbh::partial_rows(grid)) * size_t(nstat) > PART_DOUBLES) --grid;
     if (grid < 1) grid = 1;
 
     // ---- the whole state is written by each call: nothing of an earlier call
@@ -194,6 +221,7 @@ extern "C" int vbh_fit_static(const float *r, const float *d, int64_t V, int S, 
     hs.max_iter = o->max_iter;
     hs.target = o->max_iter;
     hs.trace = o->elbo_trace ? trace : nullptr;
+    hs.comp = comp ? 1 : 0;
     if (o->init == VBH_INIT_GIVEN) {
         hs.a_rho = q->a_rho;
         hs.b_rho = q->b_rho;
@@ -206,8 +234,10 @@ extern "C" int vbh_fit_static(const float *r, const float *d, int64_t V, int S, 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     VBH_S_CK(cudaMemcpyAsync(st, &hs, sizeof(hs), cudaMemcpyHostToDevice, s));
 
-    // ---- set-up, sweep 0, then one launch per sweep (a launch after the fit
-    //      has converged returns at once) ----
+    // ---- set-up, sweep 0, then one launch per sweep, issued in batches of
+    //      SWEEP_BATCH: between batches the control fields are read back and
+    //      no further launch is issued once the fit has stopped (converged,
+    //      failed or at max_iter; a launch after that returns at once) ----
     const int init = (o->init == VBH_INIT_GIVEN) ? 0 : 1;
     {
         void *args[] = {&st, const_cast<int *>(&init)};
@@ -222,10 +252,23 @@ extern "C" int vbh_fit_static(const float *r, const float *d, int64_t V, int S, 
     a.use_cond = 0;
     a.mode = init ? vbh::MODE_INIT : vbh::MODE_ELBO;
     void *args[] = {&a};
-    VBH_S_CK(cudaLaunchKernel(ki.sweep, dim3(unsigned(grid)), dim3(ki.threads), args, ki.smem, s));
+    VBH_S_CK(cudaLaunchKernel(sweep, dim3(unsigned(grid)), dim3(ki.threads), args, ki.smem, s));
     a.mode = vbh::MODE_ITER;
-    for (int t = 0; t < o->max_iter; ++t)
-        VBH_S_CK(cudaLaunchKernel(ki.sweep, dim3(unsigned(grid)), dim3(ki.threads), args, ki.smem, s));
+    constexpr int SWEEP_BATCH = 64;
+    struct Ctl {
+        int iter, target, max_iter, converged, status;
+    } ctl{};
+    static_assert(offsetof(DevState, status) - offsetof(DevState, iter) == 4 * sizeof(int), "control field layout");
+    for (int t = 0; t < o->max_iter;) {
+        const int n = (o->max_iter - t < SWEEP_BATCH) ? o->max_iter - t : SWEEP_BATCH;
+        for (int i = 0; i < n; ++i)
+            VBH_S_CK(cudaLaunchKernel(sweep, dim3(unsigned(grid)), dim3(ki.threads), args, ki.smem, s));
+        t += n;
+        if (t >= o->max_iter) break;
+        VBH_S_CK(cudaMemcpyAsync(&ctl, &st->iter, sizeof(ctl), cudaMemcpyDeviceToHost, s));
+        VBH_S_CK(cudaStreamSynchronize(s));
+        if (ctl.converged || ctl.status != VBH_OK || ctl.iter >= o->max_iter) break;
+    }
 
     // ---- results ----
     VBH_S_CK(cudaMemcpyAsync(&hs, st, sizeof(hs), cudaMemcpyDeviceToHost, s));

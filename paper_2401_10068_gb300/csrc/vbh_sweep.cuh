@@ -42,8 +42,11 @@ struct SweepCfg {
     static constexpr int I_G = 0, I_g = NG, I_T3 = NG + M, I_T4 = NG + M + 1, I_E4 = NG + M + 2;
     static constexpr int NSTAT = NG + M + 3;                // G, g, T3, T4 (ln of mantissas), E4 (exponents)
     static constexpr int NGRP = (NSTAT + 31) / 32;          // 32-wide butterfly groups
+    // compensated statistics: one more column, U = sum c_i e_i^2
+    static constexpr int I_U = NSTAT, NSTATC = NSTAT + 1, NGRPC = (NSTATC + 31) / 32;
     static constexpr int THREADS = 256;
     static constexpr int MINB = (S <= 8) ? 2 : 1;           // resident blocks per SM the registers are sized for
+    static constexpr int MINB_C = (S <= 6) ? 2 : 1;         // the same for the compensated form (more registers)
     static constexpr int OPT = 4;                           // observations per thread per tile
     static constexpr int T = THREADS * OPT;                 // observations per tile
     static constexpr int STAGES = 3;
@@ -135,6 +138,119 @@ __device__ __forceinline__ void observe(const float (&x)[S], float rr, const flo
     }
 }
 
+// ---------------------------------------------------------------------------
+// Compensated statistics for the stopping test.  With binary profiles every
+// observation of a profile repeats the FP32 rounding of the terms that depend
+// on the profile alone (q_i, 1 + E[rho] q_i, c_i, t_i), and FP32 chunk sums
+// round at the size of the running total; both leave a rounding noise of
+// about 1e-8 |L| in the ELBO that changes from sweep to sweep, which a
+// relative stopping tolerance of 1e-8 cannot tell from convergence.  The
+// ELBO depends on the statistics at first order only through
+//     E[rho] T3 + tr(Sigma0~ G) + T4,
+// and E[rho] S_i + (w_i^2 - c_i) q_i = c_i e_i^2 exactly (with
+// h_i = 1/(1 + E[rho] q_i): E[rho] e^2 h^2 + E[rho] q h + E[rho]^2 h^2 e^2 q
+// - E[rho] h q = E[rho] e^2 h).  So the compensated pass carries, next to the
+// FP32 statistics of the update, U = sum c_i e_i^2 and T4 = sum ln(1 +
+// E[rho] q_i) as two-part FP32 numbers (hi + lo) evaluated to ~2^-40:
+//   q_i and t_i from the split Sigma0~ = Sh + Sl and kappa~ = kh + kl of the
+//   pass globals (the Sh and kh sums are exact for entries in {0, 1}),
+//   e_i = y_i - t_i, 1 + E[rho] q_i, 1/(1 + E[rho] q_i) and c_i by
+//   error-free transformations (two-sum, FMA products) and one Newton
+//   correction, U by a two-part running sum, T4 as a two-part running
+//   product of (1 + E[rho] q_i) with one logarithm per warp and chunk.
+// The global update then replaces the first-order part of the FP32
+// statistics in the ELBO by these.  y_i and D_i are formed in FP32 once per
+// observation, independent of the globals, so their rounding is part of the
+// data and cancels in the ELBO differences.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+template <int S>
+__device__ __forceinline__ void observe_comp(const float (&x)[S], float rr, const float (&Sh)[SweepCfg<S>::NGA],
+                                             const float (&Sl)[SweepCfg<S>::NGA], const float (&kh)[SweepCfg<S>::MA],
+                                             const float (&kl)[SweepCfg<S>::MA], float erho,
+                                             float (&acc)[SweepCfg<S>::NSTAT], float &ph, float &pl, float &uh,
+                                             float &ul)
+{
+    using C = SweepCfg<S>;
+    constexpr int M = C::M;
+    const float dS = x[S - 1];
+    const float y = rr - dS;
+    float D[C::MA];
+    float qh = 0.0f, ql = 0.0f, th = 0.0f, tl = 0.0f;
+#pragma unroll
+    for (int j = 0; j < M; ++j) D[j] = x[j] - dS;
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+#pragma unroll
+        for (int k = 0; k <= j; ++k) {
+            const int e = j * (j + 1) / 2 + k;
+            const float P = D[j] * D[k];
+            qh = fmaf(Sh[e], P, qh);
+            ql = fmaf(Sl[e], P, ql);
+        }
+        th = fmaf(kh[j], D[j], th);
+        tl = fmaf(kl[j], D[j], tl);
+    }
+    float eh, el;                                          // e = y - t
+    two_sum(y, -th, eh, el);
+    el -= tl;
+    const float p = erho * qh;                             // 1 + E[rho] q = dh + dl
+    const float pe = fmaf(erho, qh, -p);
+    const float big = fmaxf(1.0f, p), sml = fminf(1.0f, p);
+    const float dh = big + sml;
+    const float dl = fmaf(erho, ql, (sml - (dh - big)) + pe);
+    float h = rcp_approx(dh);                              // 1/(1 + E[rho] q) = h + hl
+    h = fmaf(h, fmaf(-dh, h, 1.0f), h);
+    const float res = fmaf(-dl, h, fmaf(-dh, h, 1.0f));
+    const float hl = h * res;
+    const float ch = erho * h;                             // c = ch + cl
+    const float cl = fmaf(erho, hl, fmaf(erho, h, -ch));
+    // the FP32 statistics of the update
+    const float q = qh + ql;
+    const float w = ch * eh;
+    const float gam = fmaf(w, w, -ch);
+    const float ei = eh * h;
+    acc[C::I_T3] += fmaf(ei, ei, q * h);
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+        acc[C::I_g + j] = fmaf(w, D[j], acc[C::I_g + j]);
+        const float gd = gam * D[j];
+#pragma unroll
+        for (int k = 0; k <= j; ++k) acc[j * (j + 1) / 2 + k] = fmaf(gd, D[k], acc[j * (j + 1) / 2 + k]);
+    }
+    // U += c e^2
+    const float e2h = eh * eh;
+    const float e2l = fmaf(eh + eh, el, fmaf(eh, eh, -e2h));
+    const float u = ch * e2h;
+    const float ue = fmaf(cl, e2h, fmaf(ch, e2l, fmaf(ch, e2h, -u)));
+    float su, sue;
+    two_sum(uh, u, su, sue);
+    uh = su;
+    ul += sue + ue;
+    // running product of (1 + E[rho] q)
+    const float m = ph * dh;
+    const float me = fmaf(pl, dh, fmaf(ph, dl, fmaf(ph, dh, -m)));
+    ph = m + me;
+    pl = me - (ph - m);
+}
+
+// (ph + pl) = m 2^E with m in [1, 2): keep m, scale pl alike, add E to ex.
+// Valid while the product stays finite (each factor below 2^62).
+__device__ __forceinline__ void peel_exponent2(float &ph, float &pl, int &ex)
+{
+    const uint32_t b = __float_as_uint(ph);
+    const int E = int(b >> 23) - 127;
+    ex += E;
+    ph = __uint_as_float((b & 0x007fffffu) | 0x3f800000u);
+    pl *= __uint_as_float(uint32_t(127 - E) << 23);
+}
+
 // prod = m 2^(E - 127) with m in [1, 2): keep m, add E - 127 to ex.  Valid
 // while prod stays finite, i.e. for (1 + E[rho] q_i) < 2^62 per observation.
 __device__ __forceinline__ void peel_exponent(float &prod, int &ex)
@@ -176,6 +292,66 @@ __device__ __forceinline__ void flush_warp(float (&acc)[SweepCfg<S>::NSTAT], dou
         }
         acc64[g] += static_cast<double>(v[0]);
     }
+#pragma unroll
+    for (int i = 0; i < NSTAT; ++i) acc[i] = 0.0f;
+}
+
+// Flush of the compensated pass: the running products of the warp's lanes
+// are multiplied (two-part) and lane 0 takes one logarithm, ln(ph + pl) =
+// ln ph + pl/ph (ph in [1, 2)); U is summed over the lanes in two parts and
+// added in FP64 by the lane that holds column I_U; the FP32 statistics go
+// through the butterfly of flush_warp.
+template <int S>
+__device__ __forceinline__ void flush_warp_comp(float (&acc)[SweepCfg<S>::NSTAT],
+                                                double (&acc64)[SweepCfg<S>::NGRPC], float &ph, float &pl, int &ex,
+                                                float &uh, float &ul, int lane)
+{
+    using C = SweepCfg<S>;
+    constexpr int NSTAT = C::NSTAT;
+    peel_exponent2(ph, pl, ex);
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, ph, off);
+        const float ol = __shfl_xor_sync(0xffffffffu, pl, off);
+        const int oe = __shfl_xor_sync(0xffffffffu, ex, off);
+        const float m = ph * oh;
+        const float me = fmaf(pl, oh, fmaf(ph, ol, fmaf(ph, oh, -m)));
+        ph = m + me;
+        pl = me - (ph - m);
+        ex += oe;
+        peel_exponent2(ph, pl, ex);
+        const float vh = __shfl_xor_sync(0xffffffffu, uh, off);
+        const float vl = __shfl_xor_sync(0xffffffffu, ul, off);
+        float s, e;
+        two_sum(uh, vh, s, e);
+        uh = s;
+        ul = (ul + vl) + e;
+    }
+    acc[C::I_T4] = (lane == 0) ? logf(ph) + pl / ph : 0.0f;
+    acc[C::I_E4] = (lane == 0) ? static_cast<float>(ex) : 0.0f;     // exact: |ex| < 2^24
+    ph = 1.0f;
+    pl = 0.0f;
+    ex = 0;
+#pragma unroll
+    for (int g = 0; g < C::NGRP; ++g) {
+        float v[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = (g * 32 + i < NSTAT) ? acc[(g * 32 + i < NSTAT) ? g * 32 + i : 0] : 0.0f;
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) {
+            const bool up = (lane & off) != 0;
+#pragma unroll
+            for (int i = 0; i < off; ++i) {
+                const float keep = up ? v[i + off] : v[i];
+                const float send = up ? v[i] : v[i + off];
+                v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+            }
+        }
+        acc64[g] += static_cast<double>(v[0]);
+    }
+    if (lane == C::I_U % 32) acc64[C::I_U / 32] += static_cast<double>(uh) + static_cast<double>(ul);
+    uh = 0.0f;
+    ul = 0.0f;
 #pragma unroll
     for (int i = 0; i < NSTAT; ++i) acc[i] = 0.0f;
 }
@@ -316,6 +492,80 @@ __device__ inline void write_pass_globals_rt(int M, DevState *st, const double *
     }
 }
 
+// The split pass globals of the compensated statistics, by one warp (lane =
+// 0..31), from the FP32 factor L~ and kappa~ already in sw (M <= 10).
+// Entry e of the packed lower triangle, (r, c), holds s = Sigma0~_rc (times 2
+// off the diagonal): the products L~_ri L~_ci are exact as two-part FP32
+// numbers and are summed in two parts.  With E the largest binary exponent
+// over the entries, Sh = s rounded to a multiple of 2^(E - 17) and Sl = the
+// rest: at most 55 grid parts of magnitude < 2^(E + 1) with signs from
+// D_j D_k in {-1, 0, 1} sum exactly in FP32 (every partial sum is a multiple
+// of 2^(E - 17) below 2^(E + 7)).  kappa~ likewise on the grid 2^(E' - 19)
+// (at most 10 parts).  Sl and kl are 2^-18 of the largest entry or less, so
+// their FP32 sums add about 2^-42 relative.
+__device__ inline void write_pass_splits_rt(int M, SweepGlobalsF32 *sw, int lane)
+{
+    const int NG = M * (M + 1) / 2;
+    float hi[2], lo[2];
+    int emax = -1000;
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const int e = lane + 32 * u;
+        hi[u] = 0.0f;
+        lo[u] = 0.0f;
+        if (e < NG) {
+            int r = 0;
+            while ((r + 1) * (r + 2) / 2 <= e) ++r;
+            const int c = e - r * (r + 1) / 2;
+            float sh = 0.0f, sl = 0.0f;
+            for (int i = 0; i <= c; ++i) {
+                const float a = sw->L[r * (r + 1) / 2 + i], b = sw->L[c * (c + 1) / 2 + i];
+                const float pp = a * b;
+                float t, te;
+                two_sum(sh, pp, t, te);
+                sh = t;
+                sl += te + fmaf(a, b, -pp);
+            }
+            const float t = sh + sl;                        // renormalise: |sl| <= ulp(sh) / 2
+            sl = sl - (t - sh);
+            sh = t;
+            if (r != c) {
+                sh *= 2.0f;
+                sl *= 2.0f;
+            }
+            hi[u] = sh;
+            lo[u] = sl;
+            if (sh != 0.0f) emax = max(emax, ilogbf(sh));
+        }
+    }
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, off));
+    const int eq = emax - 17;
+    const float qinv = (eq > -127 && eq < 127) ? __uint_as_float(uint32_t(127 - eq) << 23) : 1.0f;
+    const float qs = (eq > -127 && eq < 127) ? __uint_as_float(uint32_t(127 + eq) << 23) : 1.0f;
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const int e = lane + 32 * u;
+        if (e < NG) {
+            const float h = rintf(hi[u] * qinv) * qs;      // scalings by powers of two: exact
+            sw->Sh[e] = h;
+            sw->Sl[e] = (hi[u] - h) + lo[u];               // hi - h is exact
+        }
+    }
+    const float kv = (lane < M) ? sw->kappa[lane] : 0.0f;
+    int ek = (kv != 0.0f) ? ilogbf(kv) : -1000;
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) ek = max(ek, __shfl_xor_sync(0xffffffffu, ek, off));
+    const int eqk = ek - 19;
+    const float kqinv = (eqk > -127 && eqk < 127) ? __uint_as_float(uint32_t(127 - eqk) << 23) : 1.0f;
+    const float kqs = (eqk > -127 && eqk < 127) ? __uint_as_float(uint32_t(127 + eqk) << 23) : 1.0f;
+    if (lane < M) {
+        const float h = rintf(kv * kqinv) * kqs;
+        sw->kh[lane] = h;
+        sw->kl[lane] = kv - h;                              // exact
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Column sums of rows [0, nrows) of a row-major [nrows][ns] FP64 array in
 // global memory, in a fixed order: thread t (t < R ns, of the first nt
@@ -437,13 +687,13 @@ __device__ inline bool finish_ticket(DevState *st, double *part, int nblk, int n
 // finishes the launch (blockDim.x a multiple of 32, at least 96 threads).
 // part: nrows rows of per-block (or per-group) statistics, laid out as in
 // SweepCfg: packed lower G, g, T3, T4 (ln of mantissas), E4 (binary
-// exponents).  ws: shared-memory workspace of at least gu_ws_doubles(M)
-// doubles.
+// exponents), and with st->comp the compensated U.  ws: shared-memory
+// workspace of at least gu_ws_doubles(M) doubles.
 // ---------------------------------------------------------------------------
 __host__ __device__ constexpr int gu_ws_doubles_rt(int M)
 {
     // statistics (rounded up to 32), 10 M x M matrices, 10 M-vectors, 32 scalars, 512 of reduction scratch
-    return ((M * (M + 1) / 2 + M + 3 + 31) / 32) * 32 + 10 * (M > 0 ? M * M : 1) + 10 * (M > 0 ? M : 1) + 32 + 512;
+    return ((M * (M + 1) / 2 + M + 4 + 31) / 32) * 32 + 10 * (M > 0 ? M * M : 1) + 10 * (M > 0 ? M : 1) + 32 + 512;
 }
 
 template <int M>
@@ -456,8 +706,9 @@ __device__ __forceinline__ void global_update_rt(int M, DevState *st, const doub
                                                  const SweepArgs &a, double *ws)
 {
     const int NG = M * (M + 1) / 2;
-    const int NSTAT = NG + M + 3;
-    const int I_T3 = NG + M, I_T4 = NG + M + 1, I_E4 = NG + M + 2;
+    const bool comp = st->comp != 0;
+    const int NSTAT = NG + M + 3 + (comp ? 1 : 0);
+    const int I_T3 = NG + M, I_T4 = NG + M + 1, I_E4 = NG + M + 2, I_U = NG + M + 3;
     const int MM = M > 0 ? M * M : 1;
     const int MV = M > 0 ? M : 1;
     const int MD = M > 0 ? M : 1;                   // divisor (loops over M*M entries are empty at M = 0)
@@ -614,7 +865,8 @@ __device__ __forceinline__ void global_update_rt(int M, DevState *st, const doub
         }
         named_sync(BAR_MAIN, nthm);
         // 6. warp 0: tr(E[Lambda] X) with E[Lambda] = nu Li^T Li (Eq. 28);
-        //    warp 1 (EM): tr(Sigma0~ G); the other main warps: the new globals.
+        //    warp 1 (EM or the compensated form): tr(Sigma0~ G); the other main
+        //    warps: the new globals.
         //    After the CAVI update of Q(K, Lambda) X equals the new W'^{-1}: with
         //    a = K0 - kappa~, X - W'^{-1} = -(s + q0 a) delta^T - delta (s + q0 a)^T
         //    + 2 lam delta delta^T = 0 since lam delta = s + q0 a (Eq. 24-25), so
@@ -640,7 +892,7 @@ __device__ __forceinline__ void global_update_rt(int M, DevState *st, const doub
                 sc[6] = nu * M;
             }
         } else {
-            if (em && warp == 1) {
+            if ((em || comp) && warp == 1) {
                 double t1 = 0.0;
                 for (int e = lane; e < M * M; e += 32) t1 = fma(Sg[e], G[e], t1);
                 const double t = warp_sum(t1);
@@ -656,6 +908,9 @@ __device__ __forceinline__ void global_update_rt(int M, DevState *st, const doub
             }
         }
         __syncthreads();
+        // the split globals of the next compensated pass (from the FP32 L~
+        // and kappa~ just written by the other main warps)
+        if (comp && !elbo_only && warp == 0) write_pass_splits_rt(M, &st->sw, lane);
         return;
     }
 
@@ -679,6 +934,7 @@ __device__ __forceinline__ void global_update_rt(int M, DevState *st, const doub
     named_sync(BAR_T3, nth);
     const double T3 = stat[I_T3];
     const double T4 = fma(LN2, stat[I_E4], stat[I_T4]);
+    const double U = comp ? stat[I_U] : 0.0;
     double q, lb = 0.0, brho = 0.0;
     if (em) {
         q = V / T3;                                 // rho' (Eq. 45)
@@ -696,8 +952,10 @@ __device__ __forceinline__ void global_update_rt(int M, DevState *st, const doub
     bool finite;
     if (em) {
         // ln p(r | theta~) = sum_i ln N(y_i; D_i^T K~, 1/rho~ + q_i): with the pass's sums,
-        // V/2 (ln rho~ - ln 2 pi) - rho~/2 sum S_i - 1/2 sum ln(1 + rho~ q_i) - 1/2 tr(Sigma0~ G)
-        L = 0.5 * V * (lr - LN2PI) - 0.5 * (fma(static_cast<double>(erho_f), T3, T4) + sc[7]);
+        // V/2 (ln rho~ - ln 2 pi) - rho~/2 sum S_i - 1/2 sum ln(1 + rho~ q_i) - 1/2 tr(Sigma0~ G);
+        // rho~ T3 + tr(Sigma0~ G) = U exactly, which the compensated form carries
+        L = comp ? 0.5 * V * (lr - LN2PI) - 0.5 * (U + T4)
+                 : 0.5 * V * (lr - LN2PI) - 0.5 * (fma(static_cast<double>(erho_f), T3, T4) + sc[7]);
         finite = isfinite(L) && isfinite(q) && q > 0.0 && !s_fail;
         st->a_rho = q;                              // point estimate as (rho, 1)
         st->b_rho = 1.0;
@@ -707,6 +965,14 @@ __device__ __forceinline__ void global_update_rt(int M, DevState *st, const doub
     } else {
         const double erb = elbo_only ? q * fma(0.5, T3, b0) : a_rho;   // E[rho] (b0 + T3/2)
         L = (fma(e_logb, lb, e0) - fma(e_ldw, ldW, 0.5 * sc[6])) + (fma(0.5 * V, lnS0, -0.5 * T4) - erb);
+        if (comp) {
+            // The ELBO depends on T3 and G at first order through
+            // -1/2 (E[rho]' T3 + tr(E[Lambda]' Sigma0~ G Sigma0~)), which is
+            // -1/2 (E[rho]~ T3 + tr(Sigma0~ G)) = -1/2 U at the fixed point of
+            // the sweep (and exactly so for the ELBO of given factors): swap the
+            // FP32 sums' part of it for the compensated U.
+            L += 0.5 * (fma(static_cast<double>(erho_f), T3, sc[7]) - U);
+        }
         finite = isfinite(L) && isfinite(brho) && brho > 0.0 && !s_fail;
         st->const_dropped = prior_dropped;
         if (!elbo_only) {
@@ -756,14 +1022,19 @@ __device__ __forceinline__ void global_update(DevState *st, const double *__rest
 }
 
 // ---------------------------------------------------------------------------
-// The fused sweep kernel.
+// The fused sweep kernel.  COMP: the compensated form (U and the two-part T4
+// for the stopping test, one more column of partials).
 // ---------------------------------------------------------------------------
-template <int S>
-__global__ void __launch_bounds__(SweepCfg<S>::THREADS, SweepCfg<S>::MINB) sweep_kernel(SweepArgs a)
+template <int S, bool COMP>
+__global__ void __launch_bounds__(SweepCfg<S>::THREADS, COMP ? SweepCfg<S>::MINB_C : SweepCfg<S>::MINB)
+    sweep_kernel(SweepArgs a)
 {
     using C = SweepCfg<S>;
-    constexpr int M = C::M, NG = C::NG, NSTAT = C::NSTAT, NGRP = C::NGRP;
+    constexpr int M = C::M, NG = C::NG, NSTAT = C::NSTAT;
+    constexpr int NS = COMP ? C::NSTATC : C::NSTAT;        // columns of a partial row
+    constexpr int NGR = COMP ? C::NGRPC : C::NGRP;
     constexpr int THREADS = C::THREADS, T = C::T, STAGES = C::STAGES;
+    static_assert(!COMP || S <= S_FP32_MAX, "compensated form: S <= 11");
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + C::RING_BYTES);
     __shared__ int s_bad, s_last;
@@ -778,23 +1049,46 @@ __global__ void __launch_bounds__(SweepCfg<S>::THREADS, SweepCfg<S>::MINB) sweep
                      (st->status == ST_OK && !st->converged && st->iter < st->target && st->iter < st->max_iter);
 
     float acc[NSTAT];
-    double acc64[NGRP];
-    float prod = 1.0f;
+    double acc64[NGR];
+    float prod = 1.0f, pl = 0.0f, uh = 0.0f, ul = 0.0f;
     int ex = 0;
 #pragma unroll
     for (int i = 0; i < NSTAT; ++i) acc[i] = 0.0f;
 #pragma unroll
-    for (int g = 0; g < NGRP; ++g) acc64[g] = 0.0;
+    for (int g = 0; g < NGR; ++g) acc64[g] = 0.0;
 
     if (run) {
-        float L[C::NGA], kap[C::MA];
+        // plain form: L~ (in A) and kappa~ (in B); compensated form: the grid
+        // and rest parts of Sigma0~ (A, A2) and kappa~ (B, B2)
+        float A[C::NGA], B[C::MA], A2[COMP ? C::NGA : 1], B2[COMP ? C::MA : 1];
         const float erho = st->sw.erho;          // 0 in sweep 0 of a CAVI fit from the paper's start: c_i = 0
+        if constexpr (COMP) {
 #pragma unroll
-        for (int i = 0; i < NG; ++i) L[i] = st->sw.L[i];
+            for (int i = 0; i < NG; ++i) {
+                A[i] = st->sw.Sh[i];
+                A2[i] = st->sw.Sl[i];
+            }
 #pragma unroll
-        for (int i = 0; i < M; ++i) kap[i] = st->sw.kappa[i];
-        if constexpr (NG == 0) L[0] = 0.0f;
-        if constexpr (M == 0) kap[0] = 0.0f;
+            for (int i = 0; i < M; ++i) {
+                B[i] = st->sw.kh[i];
+                B2[i] = st->sw.kl[i];
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < NG; ++i) A[i] = st->sw.L[i];
+#pragma unroll
+            for (int i = 0; i < M; ++i) B[i] = st->sw.kappa[i];
+            A2[0] = 0.0f;
+            B2[0] = 0.0f;
+        }
+        if constexpr (NG == 0) {
+            A[0] = 0.0f;
+            if constexpr (COMP) A2[0] = 0.0f;
+        }
+        if constexpr (M == 0) {
+            B[0] = 0.0f;
+            if constexpr (COMP) B2[0] = 0.0f;
+        }
 
         const long long V = a.V;
         const long long ntf = V / T;                         // full tiles
@@ -829,8 +1123,13 @@ __global__ void __launch_bounds__(SweepCfg<S>::THREADS, SweepCfg<S>::MINB) sweep
                     const int j = tid + u * THREADS;
                     float x[S];
                     load_row<S>(dt, j, x);
-                    observe<S>(x, rt[j], L, kap, erho, acc, prod);
-                    if (u & 1) peel_exponent(prod, ex);
+                    if constexpr (COMP) {
+                        observe_comp<S>(x, rt[j], A, A2, B, B2, erho, acc, prod, pl, uh, ul);
+                        if (u & 1) peel_exponent2(prod, pl, ex);
+                    } else {
+                        observe<S>(x, rt[j], A, B, erho, acc, prod);
+                        if (u & 1) peel_exponent(prod, ex);
+                    }
                 }
             }
             if (__syncthreads_or(!ok)) {
@@ -846,7 +1145,10 @@ __global__ void __launch_bounds__(SweepCfg<S>::THREADS, SweepCfg<S>::MINB) sweep
                 bulk_load(stage + C::R_BYTES, a.d + tile * T * S, C::D_BYTES, &full[s]);
             }
             if (++ftile == C::FLUSH_TILES) {
-                flush_warp<S>(acc, acc64, prod, ex, lane);
+                if constexpr (COMP)
+                    flush_warp_comp<S>(acc, acc64, prod, pl, ex, uh, ul, lane);
+                else
+                    flush_warp<S>(acc, acc64, prod, ex, lane);
                 ftile = 0;
             }
         }
@@ -867,33 +1169,41 @@ __global__ void __launch_bounds__(SweepCfg<S>::THREADS, SweepCfg<S>::MINB) sweep
                     float x[S];
 #pragma unroll
                     for (int q = 0; q < S; ++q) x[q] = __ldg(a.d + i * S + q);
-                    observe<S>(x, __ldg(a.r + i), L, kap, erho, acc, prod);
-                    peel_exponent(prod, ex);
+                    if constexpr (COMP) {
+                        observe_comp<S>(x, __ldg(a.r + i), A, A2, B, B2, erho, acc, prod, pl, uh, ul);
+                        peel_exponent2(prod, pl, ex);
+                    } else {
+                        observe<S>(x, __ldg(a.r + i), A, B, erho, acc, prod);
+                        peel_exponent(prod, ex);
+                    }
                 }
             }
         }
     }
-    flush_warp<S>(acc, acc64, prod, ex, lane);
+    if constexpr (COMP)
+        flush_warp_comp<S>(acc, acc64, prod, pl, ex, uh, ul, lane);
+    else
+        flush_warp<S>(acc, acc64, prod, ex, lane);
     __syncthreads();   // the ring is idle from here on: reuse it for the block reduction
 
     // block reduction in FP64, fixed order, then this block's partials
-    double *s_red = reinterpret_cast<double *>(smem);      // [THREADS / 32][NGRP * 32]
+    double *s_red = reinterpret_cast<double *>(smem);      // [THREADS / 32][NGR * 32]
 #pragma unroll
-    for (int g = 0; g < NGRP; ++g) s_red[warp * (NGRP * 32) + g * 32 + lane] = acc64[g];
+    for (int g = 0; g < NGR; ++g) s_red[warp * (NGR * 32) + g * 32 + lane] = acc64[g];
     __syncthreads();
-    for (int j = tid; j < NSTAT; j += THREADS) {
-        double s = 0.0;
+    for (int j = tid; j < NS; j += THREADS) {
+        double sm = 0.0;
 #pragma unroll
-        for (int w = 0; w < THREADS / 32; ++w) s += s_red[w * (NGRP * 32) + j];
-        a.partials[size_t(blockIdx.x) * NSTAT + j] = s;
+        for (int w = 0; w < THREADS / 32; ++w) sm += s_red[w * (NGR * 32) + j];
+        a.partials[size_t(blockIdx.x) * NS + j] = sm;
     }
     int row0, nrows;
-    if (!finish_ticket(st, a.partials, gridDim.x, NSTAT, &s_last, &row0, &nrows, reinterpret_cast<double *>(smem)))
+    if (!finish_ticket(st, a.partials, gridDim.x, NS, &s_last, &row0, &nrows, reinterpret_cast<double *>(smem)))
         return;
     if (run && !s_bad) {
         // every copy of this block has landed, so the ring's shared memory
         // serves as the workspace of the global update
-        global_update<M>(st, a.partials + size_t(row0) * NSTAT, nrows, a, reinterpret_cast<double *>(smem));
+        global_update<M>(st, a.partials + size_t(row0) * NS, nrows, a, reinterpret_cast<double *>(smem));
     } else if (tid == 0 && a.use_cond) {
         cudaGraphSetConditional(a.cond, 0u);
     }
@@ -1009,6 +1319,8 @@ __device__ inline void setup_state_rt(int M, DevState *st, int init, int lane, d
         if (init) st->kappa[i] = kv;
     }
     for (int g = lane; g < TICKET_GROUPS_MAX; g += 32) st->gticket[g] = 0u;
+    __syncwarp();                                    // sw.L and sw.kappa are in place
+    if (st->comp && M < S_FP32_MAX) write_pass_splits_rt(M, &st->sw, lane);
     if (lane == 0) {
         st->lndetSigma0 = ld - M * log(nu);
         st->erho = init ? 0.0 : st->a_rho / st->b_rho;

@@ -23,6 +23,9 @@ CAVI = 0
 EM = 1
 INIT_PAPER = 0
 INIT_GIVEN = 1
+STATS_AUTO = 0          # compensated statistics when tol > 0 (vbh_opts.stats)
+STATS_COMPENSATED = 1
+STATS_PLAIN = 2
 
 STATUS = {0: "VBH_OK", -1: "VBH_EINVAL", -2: "VBH_ENOMEM", -3: "VBH_ECUDA", -4: "VBH_ENONFINITE",
           -5: "VBH_ETIMEOUT", -6: "VBH_ESTATE", -7: "VBH_EUNSUPPORTED"}
@@ -73,7 +76,7 @@ class Result(ctypes.Structure):
 class Opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("precision", ctypes.c_int),
                 ("init", ctypes.c_int), ("refine_iters", ctypes.c_int), ("init_state", ctypes.POINTER(Result)),
-                ("elbo_trace", _dp), ("method", ctypes.c_int), ("grouped", ctypes.c_int)]
+                ("elbo_trace", _dp), ("method", ctypes.c_int), ("grouped", ctypes.c_int), ("stats", ctypes.c_int)]
 
 
 _LIB = None
@@ -251,7 +254,8 @@ class Handle:
         self.close()
 
     @staticmethod
-    def _opts(tol, max_iter, init_state, S, trace, precision=FP32, refine_iters=10, method=CAVI, grouped=False):
+    def _opts(tol, max_iter, init_state, S, trace, precision=FP32, refine_iters=10, method=CAVI, grouped=False,
+              stats=STATS_AUTO):
         o = Opts()
         _lib().vbh_opts_default(ctypes.byref(o))
         o.tol = float(tol)
@@ -260,6 +264,7 @@ class Handle:
         o.refine_iters = int(refine_iters)
         o.method = int(method)
         o.grouped = 1 if grouped else 0
+        o.stats = int(stats)
         keep = []
         if init_state is not None:
             st = dict_to_result(init_state, S) if isinstance(init_state, dict) else init_state
@@ -274,11 +279,12 @@ class Handle:
 
     def fit(self, r, d, S: int, prior: dict | None = None, tol: float = 1e-8, max_iter: int = 200,
             init_state=None, trace: bool = False, V: int | None = None, precision: int = FP32,
-            refine_iters: int = 10, method: int = CAVI, grouped: bool = False) -> dict:
+            refine_iters: int = 10, method: int = CAVI, grouped: bool = False, stats: int = STATS_AUTO) -> dict:
         V = int(V if V is not None else (r.shape[0] if r is not None else 0))
         _check_inputs(r, d, V, S, "vbh_fit")
         pa = _PriorArgs(prior, S)
-        o, keep, buf = self._opts(tol, max_iter, init_state, S, trace, precision, refine_iters, method, grouped)
+        o, keep, buf = self._opts(tol, max_iter, init_state, S, trace, precision, refine_iters, method, grouped,
+                                  stats)
         res = Result()
         rc = _lib().vbh_fit(self._h, _ptr(r), _ptr(d), V, int(S), ctypes.byref(pa.c), ctypes.byref(o),
                             ctypes.byref(res))
@@ -291,11 +297,12 @@ class Handle:
 
     def fit_begin(self, r, d, S: int, prior: dict | None = None, tol: float = 1e-8, max_iter: int = 200,
                   init_state=None, trace: bool = False, V: int | None = None, precision: int = FP32,
-                  refine_iters: int = 10, method: int = CAVI, grouped: bool = False):
+                  refine_iters: int = 10, method: int = CAVI, grouped: bool = False, stats: int = STATS_AUTO):
         V = int(V if V is not None else (r.shape[0] if r is not None else 0))
         _check_inputs(r, d, V, S, "vbh_fit_begin")
         pa = _PriorArgs(prior, S)
-        o, keep, buf = self._opts(tol, max_iter, init_state, S, trace, precision, refine_iters, method, grouped)
+        o, keep, buf = self._opts(tol, max_iter, init_state, S, trace, precision, refine_iters, method, grouped,
+                                  stats)
         rc = _lib().vbh_fit_begin(self._h, _ptr(r), _ptr(d), V, int(S), ctypes.byref(pa.c), ctypes.byref(o))
         if rc != 0:
             raise VBHError(rc, "vbh_fit_begin")
@@ -320,7 +327,7 @@ class Handle:
         return out
 
     def fit_batched(self, rs, ds, Ss, priors=None, tol: float = 1e-8, max_iter: int = 200, init_states=None,
-                    trace: bool = False) -> list:
+                    trace: bool = False, stats: int = STATS_AUTO) -> list:
         """``vbh_fit_batched``: B independent fits (lists of inputs, one S per
         data set; priors and init_states are lists of dicts or None)."""
         B = len(rs)
@@ -344,6 +351,7 @@ class Handle:
         _lib().vbh_opts_default(ctypes.byref(o))
         o.tol = float(tol)
         o.max_iter = int(max_iter)
+        o.stats = int(stats)
         if init_states is not None:
             ia = (Result * B)()
             for b in range(B):
@@ -386,7 +394,8 @@ STATIC_TRACE_MAX = 4097
 
 
 def fit_static(r, d, S: int, prior: dict | None = None, tol: float = 1e-8, max_iter: int = 200,
-               init_state=None, trace: bool = False, device: int = 0, stream=None, V: int | None = None) -> dict:
+               init_state=None, trace: bool = False, device: int = 0, stream=None, V: int | None = None,
+               stats: int = STATS_AUTO) -> dict:
     """``vbh_fit_static``: the fit of ``Handle.fit`` for callers that cannot
     allocate device memory (no handle; the scratch is a static device array of
     the library).  r and d must be device tensors."""
@@ -395,7 +404,7 @@ def fit_static(r, d, S: int, prior: dict | None = None, tol: float = 1e-8, max_i
     if stream is not None and hasattr(stream, "cuda_stream"):
         stream = stream.cuda_stream
     pa = _PriorArgs(prior, S)
-    o, keep, buf = Handle._opts(tol, max_iter, init_state, S, trace)
+    o, keep, buf = Handle._opts(tol, max_iter, init_state, S, trace, stats=stats)
     res = Result()
     rc = _lib().vbh_fit_static(_ptr(r), _ptr(d), V, int(S), ctypes.byref(pa.c), ctypes.byref(o), ctypes.byref(res),
                                int(device), ctypes.c_void_p(stream) if stream else None)
