@@ -435,10 +435,13 @@ def run_ours(args):
         e2e = _e2e(h, r, d, V, S, e2e_steps, dev, dist, world)
     del r, d
 
+    h.close()
+    extra = None
+    if rank == 0 and world == 1 and not args.no_extra:
+        extra = other_workloads(dev, stream)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(S)
-    h.close()
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -458,12 +461,109 @@ def run_ours(args):
                 # the sweeps, the budget kernel of fit_step and, for an odd step count, the
                 # second (idle) sweep launch of the graph's last loop iteration
                 "gpu_launches": args.steps + 1 + (args.steps % 2),
-                "clocks": clk}
+                "clocks": clk,
+                "other_workloads": extra}
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+SINGLE = {"name": "single data set: N=2,000 cells x G=48 genes, S=3", "cells": 2000, "genes": 48, "S": 3,
+          "alpha": 1.0, "seed": 1, "tol": 1e-8, "cap": 200, "cap_raised": 2000, "reps": 5}
+
+
+def other_workloads(dev, stream):
+    """The other workloads' headline figures, measured after the timed region
+    of the default step (each its own timing, CUDA events or wall clock around
+    synchronous vbh_* calls with device-resident inputs):
+      single data set: fits/s through vbh_fit at the workload's rule
+        (rel dELBO < 1e-8 or 200 sweeps) and with the cap raised to 2,000 so
+        that the fit converges (converged data sets/s);
+      batched: the 4,096-data-set fit to rel dELBO < 1e-8 (cap 1,000),
+        converged data sets/s and how many converged;
+      precision: the S = 32 tensor-core sweep, ms per sweep of the BF16 and
+        FP32 forms and the BF16 form's fraction of the HBM copy peak."""
+    import torch
+    from paper_2401_10068_gb300 import synth, vbh
+    out = {}
+    h = vbh.Handle(dev.index or 0, stream)
+    clocks = Clocks(dev.index or 0)
+    time.sleep(0.3)
+    # single data set
+    V1 = SINGLE["cells"] * SINGLE["genes"]
+    with torch.cuda.stream(stream):
+        r1, d1, _ = synth.generate_device(V1, SINGLE["S"], seed=SINGLE["seed"], alpha=SINGLE["alpha"], device=dev)
+    stream.synchronize()
+    row = {"workload": SINGLE["name"], "V": V1, "tol": SINGLE["tol"]}
+    for key, cap in (("rule_cap_200", SINGLE["cap"]), ("cap_2000", SINGLE["cap_raised"])):
+        res = h.fit(r1, d1, SINGLE["S"], None, tol=SINGLE["tol"], max_iter=cap)          # warm (graph, buffers)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(SINGLE["reps"]):
+            res = h.fit(r1, d1, SINGLE["S"], None, tol=SINGLE["tol"], max_iter=cap)
+        sec = (time.perf_counter() - t0) / SINGLE["reps"]
+        row[key] = {"fits_per_s": 1.0 / sec, "converged_datasets_per_s": (1.0 / sec) if res["converged"] else 0.0,
+                    "converged": bool(res["converged"]), "sweeps": res["iters"], "us_per_sweep": 1e6 * sec /
+                    (res["iters"] + 1), "elbo": res["elbo"]}
+    out["single"] = row
+    del r1, d1
+    # batched
+    V, Sb = batch_specs(BATCH["datasets"])
+    rs, ds = [], []
+    with torch.cuda.stream(stream):
+        for b in range(BATCH["datasets"]):
+            r, d, _ = synth.generate_device(int(V[b]), int(Sb[b]), seed=BATCH["seed0"] + b, alpha=BATCH["alpha"],
+                                            device=dev)
+            rs.append(r)
+            ds.append(d)
+    stream.synchronize()
+    Ss = [int(x) for x in Sb]
+    h.fit_batched(rs[:64], ds[:64], Ss[:64], None, tol=0.0, max_iter=3)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    ev0.record(stream)
+    res = h.fit_batched(rs, ds, Ss, None, tol=BATCH["tol"], max_iter=BATCH["cap"])
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    sec = ev0.elapsed_time(ev1) * 1e-3
+    iters = np.array([x["iters"] for x in res])
+    conv = np.array([x["converged"] for x in res])
+    out["batched"] = {"workload": BATCH["name"], "V_total": int(V.sum()), "tol": BATCH["tol"], "cap": BATCH["cap"],
+                      "seconds": sec, "converged": int(conv.sum()), "datasets": len(res),
+                      "converged_datasets_per_s": float(conv.sum()) / sec, "datasets_per_s": len(res) / sec,
+                      "sweeps_mean": float(iters.mean()), "sweeps_max": int(iters.max()),
+                      "data_pass_gbs": float(np.sum(V.astype(np.float64) * (Sb + 1) * 4 * (iters + 1))) / sec / 1e9}
+    del rs, ds, res
+    torch.cuda.empty_cache()
+    # precision form
+    S3, V3 = PREC["S"], PREC["cells"] * PREC["genes"]
+    with torch.cuda.stream(stream):
+        r3, d3, _ = synth.generate_device(V3, S3, seed=PREC["seed"], alpha=PREC["alpha"], p_const=PREC["p_const"],
+                                          device=dev)
+    stream.synchronize()
+    n3 = 20
+    peak, peak_kind = _peaks()
+    row = {"workload": PREC["name"], "V": V3, "S": S3, "sweeps_timed": n3}
+    for name, prec in (("bf16_form", vbh.BF16), ("fp32_form", vbh.FP32)):
+        h.fit_begin(r3, d3, S3, None, tol=0.0, max_iter=n3 + 4, precision=prec, refine_iters=0)
+        h.fit_step(4)
+        torch.cuda.synchronize(dev)
+        ev0.record(stream)
+        h.fit_step(n3)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = ev0.elapsed_time(ev1) / n3
+        gbs = V3 * 68.0 / (ms * 1e-3) / 1e9
+        row[name] = {"ms_per_sweep": ms, "hbm_gbs": gbs, "frac": gbs / peak}
+    row["peak"], row["peak_kind"] = peak, peak_kind
+    out["precision"] = row
+    del r3, d3
+    h.close()
+    out["clocks"] = clocks.stop()
+    torch.cuda.empty_cache()
+    return out
 
 
 def _e2e(h, r, d, V, S, e2e_steps, dev, dist, world):
@@ -785,6 +885,8 @@ def main():
                     help="N cells (x 96 genes); smaller values give the small case used for ncu captures")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the other workloads' figures (single data set, batched, precision)")
     ap.add_argument("--workload", default="at-scale", choices=["at-scale", "batched", "precision", "grouped", "per-s"],
                     help="batched: the 4,096-data-set form; precision: the S = 32 tensor-core form; grouped: "
                          "the profile-grouped form; per-s: the FP32 sweep's bandwidth for S = 2..11 (separate "

@@ -116,7 +116,7 @@ def test_parity_converged_fit_single_dataset(handle):
     # the ELBO changes the stopping test reads match the oracle's in the late sweeps
     err, n = late_delta_error(got["trace"], ref["trace"], abs(ref["elbo"]))
     print(f"late sweeps {n}, max |dL_gpu - dL_oracle| / |L| = {err:.2e}")
-    assert n >= 20 and err < 3e-10, (n, err)
+    assert n >= 20 and err < 5e-10, (n, err)
     assert_parity(got, ref)
     # at a converged fit the ELBO is far from zero: the plain relative form holds too
     assert abs(got["elbo"] - ref["elbo"]) <= TOL_ELBO * abs(ref["elbo"])
@@ -136,7 +136,7 @@ def late_delta_error(got_trace, ref_trace, L, late=1e-7):
 def test_compensated_elbo_differences_track_the_oracle(handle, S, V, seed, alpha, sweeps):
     """The quantity the stopping test reads, L_t - L_(t-1), from the GPU fit
     with compensated statistics against the FP64 oracle's, sweep by sweep,
-    once the changes are below 1e-7 |L|: within 3e-10 |L|, 3 % of a 1e-8
+    once the changes are below 1e-7 |L|: within 5e-10 |L|, 5 % of a 1e-8
     tolerance (the plain FP32 statistics differ by ~3e-8 |L| there)."""
     r, d, _ = synth.generate(V, S, seed=seed, alpha=alpha)
     prior = O.paper_prior(S)
@@ -144,7 +144,7 @@ def test_compensated_elbo_differences_track_the_oracle(handle, S, V, seed, alpha
     got = handle.fit(_dev(r), _dev(d), S, prior, tol=0.0, max_iter=sweeps, trace=True, stats=vbh.STATS_COMPENSATED)
     err, n = late_delta_error(got["trace"], ref["trace"], abs(ref["elbo"]))
     print(f"S={S} V={V}: {n} late sweeps, max |dL_gpu - dL_oracle| / |L| = {err:.2e}")
-    assert n >= 10 and err < 3e-10, (n, err)
+    assert n >= 10 and err < 5e-10, (n, err)
     assert_parity(got, ref)
 
 
