@@ -210,3 +210,80 @@ def test_elbo_entry_point(handle):
     want, _ = O.elbo_at(r, d, prior, ref)
     got = handle.elbo(_dev(r), _dev(d), S, ref, prior)
     assert elbo_close(got, want, V), (got, want)
+
+
+def per_entry(got, ref):
+    """Largest per-entry relative error of kappa and W^{-1} (entries whose
+    reference is below 1e-12 of the block's largest are skipped)."""
+    out = {}
+    for key in ("kappa", "Winv"):
+        a, b = np.ravel(np.asarray(got[key], np.float64)), np.ravel(np.asarray(ref[key], np.float64))
+        keep = np.abs(b) > 1e-12 * np.abs(b).max()
+        out[key] = float(np.max(np.abs(a[keep] - b[keep]) / np.abs(b[keep])))
+    return out
+
+
+@pytest.fixture(scope="module")
+def s32_multi_epoch():
+    """S = 32 at V = 700,001: about 36 tiles of 128 observations per block on
+    152 blocks, so every block runs two full 16-tile epochs of tensor-memory
+    accumulation, the compensated FP32 sums across epochs and a partial third
+    epoch; the last tile is ragged.  Oracle: sweep 0 and two sweeps."""
+    S, V, sweeps = 32, 700_001, 2
+    r, d, _ = synth.generate(V, S, seed=81, alpha=0.5, p_const=0.05)
+    prior = O.paper_prior(S)
+    ref = O.fit(r, d, prior, tol=0.0, max_iter=sweeps)
+    return S, V, sweeps, r, d, prior, ref
+
+
+def test_s32_fp32_form_parity_multi_epoch(handle, s32_multi_epoch):
+    S, V, sweeps, r, d, prior, ref = s32_multi_epoch
+    got = handle.fit(_dev(r), _dev(d), S, prior, tol=0.0, max_iter=sweeps, trace=True)
+    e, pe = errors(got, ref), per_entry(got, ref)
+    print(f"FP32 form, S=32, V={V}: norm-wise {e}, per-entry max {pe}")
+    assert_parity(got, ref, what="S=32 multi-epoch")
+    for t, (a, b) in enumerate(zip(got["trace"], ref["trace"])):
+        assert elbo_close(a, b, V), (t, a, b)
+
+
+def test_s32_bf16_form_error_multi_epoch(handle, s32_multi_epoch):
+    """The BF16 form without refinement against the FP64 oracle at the same
+    multi-epoch size.  Stated bound per parameter block: 1e-3 relative
+    (norm-wise) for kappa, W^{-1} and b_rho, 1e-4 for the ELBO."""
+    S, V, sweeps, r, d, prior, ref = s32_multi_epoch
+    got = handle.fit(_dev(r), _dev(d), S, prior, tol=0.0, max_iter=sweeps, precision=vbh.BF16, refine_iters=0)
+    e, pe = errors(got, ref), per_entry(got, ref)
+    print(f"BF16 form, S=32, V={V}: norm-wise {e}, per-entry max {pe}")
+    assert max(e["kappa"], e["Winv"], e["b_rho"]) < 1e-3 and e["elbo"] < 1e-4, e
+
+
+def test_s32_full_size_invariants(handle):
+    """The precision workload at full size (N = 1,048,576 cells x G = 512
+    genes = 536,870,912 observations, S = 32), where the per-observation oracle
+    is out of reach: properties that hold at any size.  a_rho, nu and lambda
+    are exact functions of V (Eq. 16, 22, 23); W^{-1} stays symmetric positive
+    definite; the ELBO does not decrease over the FP32-form sweeps (coordinate
+    ascent, Eq. 12, to 1e-9 |L|); and the BF16 schedule (BF16-form sweeps,
+    then FP32-form refinement) ends within 1e-4 (parameters) and 1e-6 (ELBO)
+    of the same number of FP32-form sweeps."""
+    S, V = 32, (1 << 20) * 512
+    sweeps, refine = 8, 3
+    r, d, _ = synth.generate_device(V, S, seed=3, alpha=0.5, p_const=0.05)
+    prior = O.paper_prior(S)
+    fp32 = handle.fit(r, d, S, prior, tol=0.0, max_iter=sweeps, trace=True)
+    sched = handle.fit(r, d, S, prior, tol=0.0, max_iter=sweeps, precision=vbh.BF16, refine_iters=refine)
+    del r, d
+    torch.cuda.empty_cache()
+    M = S - 1
+    for res in (fp32, sched):
+        assert res["iters"] == sweeps and res["status"] == 0
+        assert res["a_rho"] == 0.5 + V / 2 and res["nu"] == 1.0 + V and res["lam"] == 1e-3 + V
+        W = np.asarray(res["Winv"])
+        assert np.allclose(W, W.T, rtol=0, atol=1e-12 * np.abs(W).max())
+        np.linalg.cholesky(W)                                    # raises unless positive definite
+        assert np.all(np.isfinite(res["kappa"])) and len(res["kappa"]) == M
+    tr = np.asarray(fp32["trace"])
+    assert np.all(np.diff(tr) >= -1e-9 * np.abs(tr[1:])), np.diff(tr)
+    e = errors(sched, fp32)
+    print(f"BF16 schedule ({sweeps - refine} + {refine}) vs FP32 form at V={V}: {e}, per-entry {per_entry(sched, fp32)}")
+    assert max(e["kappa"], e["Winv"], e["b_rho"]) < 1e-4 and e["elbo"] < 1e-6, e
