@@ -827,6 +827,116 @@ def run_grouped(args):
     return 0
 
 
+WARM = {"name": "learned warm start: held-out batch of the batched workload's shape", "train_sets": 8192,
+        "train_seed": 7, "train_n_lo": 200, "train_n_hi": 20000, "eval_sets": 1024, "eval_seed": 900, "n_lo": 200,
+        "n_hi": 50000, "tol": 1e-8, "cap": 4000, "epochs": 150, "batch": 64, "lr": 2e-3, "n_cap": 16384}
+
+
+def run_warmstart(args):
+    """The learned warm start (set encoder on the tensor cores): trained on
+    generator data sets against their CAVI fixed points (or loaded with
+    --ws-load), then a held-out batch shaped like the batched workload is fitted
+    from the paper's start and from the encoder's start to rel dELBO < 1e-8:
+    converged data sets per second of both, sweeps per S, the ELBO gap between
+    the two converged fits, the error of each predicted factor against the
+    converged fixed point next to the error of the per-S training mean (what a
+    predictor with no information about the data set would give), and the
+    encoder's tensor-core throughput."""
+    import torch
+    from paper_2401_10068_gb300 import _build
+    _build.build_all()
+    from paper_2401_10068_gb300 import vbh, warmstart
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    h = vbh.Handle(0, stream)
+    W = WARM
+    train = None
+    if args.ws_load:
+        ws = warmstart.load(args.ws_load, stream=stream)
+    else:
+        ws = vbh.WarmStart(seed=W["train_seed"], stream=stream)
+        info = warmstart.fit_and_train(h, ws, W["train_sets"], W["train_seed"], W["train_n_lo"], W["train_n_hi"],
+                                       W["tol"], W["cap"], W["epochs"], W["batch"], W["lr"], W["n_cap"])
+        train = {k: v for k, v in info.items() if k not in ("T", "W", "losses")}
+        train["loss_first_last"] = [info["losses"][0], info["losses"][-1]]
+        if args.ws_save:
+            warmstart.save(ws, args.ws_save)
+    rs, ds, Ss = warmstart.make_sets(W["eval_sets"], W["eval_seed"], W["n_lo"], W["n_hi"])
+    clocks = Clocks(0)
+    time.sleep(0.3)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+    torch.cuda.synchronize(dev)
+    ev[0].record(stream)
+    preds = warmstart.predict(ws, rs, ds, Ss)
+    ev[1].record(stream)
+    cold = h.fit_batched(rs, ds, Ss, None, tol=W["tol"], max_iter=W["cap"])
+    ev[2].record(stream)
+    ev[3].record(stream)
+    warm = h.fit_batched(rs, ds, Ss, None, tol=W["tol"], max_iter=W["cap"], init_states=preds)
+    ev[4].record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    t_pred = ev[0].elapsed_time(ev[1]) * 1e-3
+    t_cold = ev[1].elapsed_time(ev[2]) * 1e-3
+    t_warm = ev[3].elapsed_time(ev[4]) * 1e-3
+    Sa = np.asarray(Ss)
+    ic = np.array([x["iters"] for x in cold])
+    iw = np.array([x["iters"] for x in warm])
+    cc = np.array([x["converged"] for x in cold])
+    cw = np.array([x["converged"] for x in warm])
+    both = cc & cw
+    gaps = np.array([abs(w["elbo"] - c["elbo"]) / abs(c["elbo"]) for c, w in zip(cold, warm)])[both]
+    # predicted factors against the converged fixed points, and the per-S mean of the training targets
+    mean = ws.mean
+    err = {"kappa": [], "Sigma0": [], "E_rho": []}
+    err_mean = {"kappa": [], "Sigma0": [], "E_rho": []}
+    for p, c, S in zip(preds, cold, Ss):
+        if not c["converged"]:
+            continue
+        M = S - 1
+        sc = np.asarray(c["Winv"]) / c["nu"]
+        rc = c["a_rho"] / c["b_rho"]
+        err["kappa"].append(np.linalg.norm(p["kappa"] - c["kappa"]) / np.linalg.norm(c["kappa"]))
+        err["Sigma0"].append(np.linalg.norm(np.asarray(p["Winv"]) / p["nu"] - sc) / np.linalg.norm(sc))
+        err["E_rho"].append(abs(p["a_rho"] / p["b_rho"] - rc) / rc)
+        m = mean[S]
+        Lm = np.zeros((M, M))
+        for j in range(M):
+            for k in range(j + 1):
+                Lm[j, k] = np.exp(m[10 + j * (j + 1) // 2 + k]) if j == k else m[10 + j * (j + 1) // 2 + k]
+        err_mean["kappa"].append(np.linalg.norm(m[:M] - c["kappa"]) / np.linalg.norm(c["kappa"]))
+        err_mean["Sigma0"].append(np.linalg.norm(Lm @ Lm.T - sc) / np.linalg.norm(sc))
+        err_mean["E_rho"].append(abs(np.exp(m[9]) - rc) / rc)
+    rows = sum(int(r.shape[0]) for r in rs)
+    flops = rows * 2.0 * (64 * 256 + 256 * 256)
+    per_s = {int(S): {"sets": int((Sa == S).sum()), "cold_sweeps_median": float(np.median(ic[Sa == S])),
+                      "warm_sweeps_median": float(np.median(iw[Sa == S])), "cold_converged": int(cc[Sa == S].sum()),
+                      "warm_converged": int(cw[Sa == S].sum())} for S in range(2, 11) if (Sa == S).any()}
+    line = {"metric": "converged datasets/s, learned vs paper's start (held-out batch)", "unit": "datasets/s",
+            "value": float(cw.sum()) / (t_warm + t_pred), "n_gpus": 1, "higher_is_better": True,
+            "dtype": "bf16 encoder (f32 accumulation), f32 sweeps", "data": "synthetic",
+            "config": {"workload": W["name"], "eval_sets": W["eval_sets"], "V_total": rows, "tol": W["tol"],
+                       "cap": W["cap"], "train": None if train is None else {k: W[k] for k in (
+                           "train_sets", "train_n_lo", "train_n_hi", "epochs", "batch", "lr", "n_cap")}},
+            "cold": {"seconds": t_cold, "converged": int(cc.sum()), "converged_datasets_per_s": float(cc.sum()) / t_cold,
+                     "sweeps_mean": float(ic.mean())},
+            "warm": {"seconds_fit": t_warm, "seconds_predict": t_pred, "converged": int(cw.sum()),
+                     "converged_datasets_per_s": float(cw.sum()) / (t_warm + t_pred), "sweeps_mean": float(iw.mean())},
+            "speedup_converged_datasets_per_s": (float(cw.sum()) / (t_warm + t_pred)) / max(float(cc.sum()) / t_cold,
+                                                                                          1e-30),
+            "elbo_gap_both_converged": {"median": float(np.median(gaps)) if gaps.size else None,
+                                        "max": float(gaps.max()) if gaps.size else None, "sets": int(both.sum())},
+            "factor_error_median": {k: float(np.median(v)) for k, v in err.items()},
+            "factor_error_median_per_S_mean": {k: float(np.median(v)) for k, v in err_mean.items()},
+            "per_S": per_s,
+            "encoder": {"pooled_observations": rows, "seconds": t_pred, "tensor_tflops": flops / t_pred / 1e12},
+            "train": train, "clocks": clk}
+    h.close()
+    ws.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 PER_S = {"V": 1 << 27, "S": (2, 3, 4, 6, 8, 10, 11), "seed": 9, "alpha": 0.5, "warm": 4, "sweeps": 20}
 
 
@@ -887,10 +997,13 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the other workloads' figures (single data set, batched, precision)")
-    ap.add_argument("--workload", default="at-scale", choices=["at-scale", "batched", "precision", "grouped", "per-s"],
+    ap.add_argument("--ws-load", default=None, help="warmstart workload: load the encoder instead of training it")
+    ap.add_argument("--ws-save", default=None, help="warmstart workload: save the trained encoder")
+    ap.add_argument("--workload", default="at-scale",
+                    choices=["at-scale", "batched", "precision", "grouped", "per-s", "warmstart"],
                     help="batched: the 4,096-data-set form; precision: the S = 32 tensor-core form; grouped: "
-                         "the profile-grouped form; per-s: the FP32 sweep's bandwidth for S = 2..11 (separate "
-                         "measurements, not the default step)")
+                         "the profile-grouped form; per-s: the FP32 sweep's bandwidth for S = 2..11; warmstart: "
+                         "the learned warm start (separate measurements, not the default step)")
     ap.add_argument("--datasets", type=int, default=BATCH["datasets"])
     ap.add_argument("--plain-sample", type=int, default=32)
     args = ap.parse_args()
@@ -900,6 +1013,8 @@ def main():
         return run_grouped(args)
     if args.workload == "per-s":
         return run_per_s(args)
+    if args.workload == "warmstart":
+        return run_warmstart(args)
     if args.workload == "precision":
         if args.cells != WORKLOAD["cells"]:
             PREC["cells"] = args.cells

@@ -109,17 +109,22 @@ def _lib():
             "vbh_fit_static": (ci, [vp, vp, i64, ci, P, O, R, ci, vp]),
             "vbh_fit_batched": (ci, [vp, ci, ctypes.POINTER(i64), ctypes.POINTER(ci), ctypes.POINTER(vp),
                                      ctypes.POINTER(vp), P, O, R]),
-            "vbh_ws_create": (ci, [ctypes.POINTER(vp), ci, ci, ctypes.c_uint64, ci, vp]),
+            "vbh_ws_create": (ci, [ctypes.POINTER(vp), ctypes.c_uint64, ci, vp]),
             "vbh_ws_destroy": (None, [vp]),
-            "vbh_ws_sizes": (ci, [vp, ctypes.POINTER(ci), ctypes.POINTER(ci), ctypes.POINTER(ctypes.c_size_t)]),
+            "vbh_ws_num_params": (ctypes.c_size_t, [vp]),
             "vbh_ws_get_params": (ci, [vp, ctypes.POINTER(ctypes.c_float), ctypes.c_size_t]),
             "vbh_ws_set_params": (ci, [vp, ctypes.POINTER(ctypes.c_float), ctypes.c_size_t]),
             "vbh_ws_set_norm": (ci, [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]),
-            "vbh_ws_features": (ci, [vp, vp, vp, i64, ci, vp]),
-            "vbh_ws_forward": (ci, [vp, ci, ci, vp, vp]),
-            "vbh_ws_loss_grad": (ci, [vp, ci, ci, vp, vp, _dp, ctypes.POINTER(ctypes.c_float)]),
-            "vbh_ws_train_step": (ci, [vp, ci, ci, vp, vp, ctypes.c_float, _dp]),
-            "vbh_ws_predict": (ci, [vp, vp, vp, i64, P, ci, R]),
+            "vbh_ws_features": (ci, [vp, vp, vp, i64, ci, i64, vp]),
+            "vbh_ws_forward": (ci, [vp, ci, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(i64),
+                                    ctypes.POINTER(ci), ctypes.POINTER(i64), vp]),
+            "vbh_ws_loss_grad": (ci, [vp, ci, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(i64),
+                                      ctypes.POINTER(ci), ctypes.POINTER(i64), vp, vp, _dp,
+                                      ctypes.POINTER(ctypes.c_float)]),
+            "vbh_ws_train_step": (ci, [vp, ci, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(i64),
+                                       ctypes.POINTER(ci), ctypes.POINTER(i64), vp, vp, ctypes.c_float, _dp]),
+            "vbh_ws_predict": (ci, [vp, ci, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(i64),
+                                    ctypes.POINTER(ci), P, R]),
         }
         for name, (res, args) in sigs.items():
             f = getattr(lib, name)
@@ -416,21 +421,39 @@ def fit_static(r, d, S: int, prior: dict | None = None, tol: float = 1e-8, max_i
     return out
 
 
-class WarmStart:
-    """The learned warm start (``include/vbh_ws.h``): a set encoder for one S.
-    Device buffers are torch tensors on the encoder's device."""
+WS_SMAX = 10
+WS_F = 64
+WS_P = 64
 
-    def __init__(self, S: int, hidden: int = 256, seed: int = 1, device: int = 0, stream=None):
+
+def ws_slots(S: int) -> np.ndarray:
+    """Output slots a data set with S subpopulations uses (vbh_ws.h): kappa,
+    ln E[rho], the packed Cholesky factor of Sigma0."""
+    M = S - 1
+    used = np.zeros(WS_P, dtype=bool)
+    used[:M] = True
+    used[9] = True
+    for j in range(M):
+        for k in range(j + 1):
+            used[10 + j * (j + 1) // 2 + k] = True
+    return used
+
+
+class WarmStart:
+    """The learned warm start (``include/vbh_ws.h``): one set encoder for
+    every S in 2..10.  Data sets are given as lists of device tensors."""
+
+    def __init__(self, seed: int = 1, device: int = 0, stream=None):
         lib = _lib()
         self._m = ctypes.c_void_p()
         st = getattr(stream, "cuda_stream", stream)
-        rc = lib.vbh_ws_create(ctypes.byref(self._m), int(S), int(hidden), ctypes.c_uint64(seed), int(device),
+        rc = lib.vbh_ws_create(ctypes.byref(self._m), ctypes.c_uint64(seed), int(device),
                                ctypes.c_void_p(st) if st else None)
         if rc != 0:
             raise VBHError(rc, "vbh_ws_create")
-        F, P, n = ctypes.c_int(), ctypes.c_int(), ctypes.c_size_t()
-        lib.vbh_ws_sizes(self._m, ctypes.byref(F), ctypes.byref(P), ctypes.byref(n))
-        self.S, self.F, self.P, self.nparams = int(S), F.value, P.value, n.value
+        self.nparams = int(lib.vbh_ws_num_params(self._m))
+        self.mean = np.zeros((WS_SMAX + 1, WS_P), dtype=np.float32)
+        self.std = np.ones((WS_SMAX + 1, WS_P), dtype=np.float32)
 
     def close(self):
         if self._m:
@@ -455,40 +478,75 @@ class WarmStart:
                "vbh_ws_set_params")
 
     def set_norm(self, mean, std) -> None:
-        mu = np.ascontiguousarray(mean, dtype=np.float32)
-        sd = np.ascontiguousarray(std, dtype=np.float32)
+        mu = np.ascontiguousarray(mean, dtype=np.float32).reshape(WS_SMAX + 1, WS_P)
+        sd = np.ascontiguousarray(std, dtype=np.float32).reshape(WS_SMAX + 1, WS_P)
         fp = ctypes.POINTER(ctypes.c_float)
         _check(_lib().vbh_ws_set_norm(self._m, mu.ctypes.data_as(fp), sd.ctypes.data_as(fp)), "vbh_ws_set_norm")
         self.mean, self.std = mu.copy(), sd.copy()
 
-    def features(self, r, d, n: int, out):
-        _check(_lib().vbh_ws_features(self._m, _ptr(r), _ptr(d), int(r.shape[0]), int(n), _ptr(out)),
-               "vbh_ws_features")
+    @staticmethod
+    def _batch(rs, ds, Ss, ns=None):
+        B = len(rs)
+        for b in range(B):
+            _check_inputs(rs[b], ds[b], int(rs[b].shape[0]), int(Ss[b]), f"set encoder (data set {b})")
+        rp = (ctypes.c_void_p * B)(*[_ptr(x).value for x in rs])
+        dp = (ctypes.c_void_p * B)(*[_ptr(x).value for x in ds])
+        Vs = (ctypes.c_int64 * B)(*[int(x.shape[0]) for x in rs])
+        Sa = (ctypes.c_int * B)(*[int(x) for x in Ss])
+        na = (ctypes.c_int64 * B)(*([0] * B if ns is None else [int(x) for x in ns]))
+        return B, rp, dp, Vs, Sa, na
+
+    def features(self, r, d, S: int, n: int = 0):
+        """The encoder's input for one data set (pooled observations x 64), FP32."""
+        import torch
+        V = int(r.shape[0])
+        cnt = V if (n <= 0 or n >= V) else int(n)
+        x = torch.empty((cnt, WS_F), dtype=torch.float32, device=r.device)
+        _check(_lib().vbh_ws_features(self._m, _ptr(r), _ptr(d), V, int(S), int(n), _ptr(x)), "vbh_ws_features")
+        return x
+
+    def forward(self, rs, ds, Ss, ns=None):
+        import torch
+        B, rp, dp, Vs, Sa, na = self._batch(rs, ds, Ss, ns)
+        out = torch.empty((B, WS_P), dtype=torch.float32, device=rs[0].device)
+        _check(_lib().vbh_ws_forward(self._m, B, rp, dp, Vs, Sa, na, _ptr(out)), "vbh_ws_forward")
         return out
 
-    def forward(self, x, B: int, n: int, out):
-        _check(_lib().vbh_ws_forward(self._m, int(B), int(n), _ptr(x), _ptr(out)), "vbh_ws_forward")
-        return out
-
-    def loss_grad(self, x, target, B: int, n: int):
+    def loss_grad(self, rs, ds, Ss, ns, target, weight):
+        B, rp, dp, Vs, Sa, na = self._batch(rs, ds, Ss, ns)
         loss = ctypes.c_double()
         g = np.empty(self.nparams, dtype=np.float32)
-        _check(_lib().vbh_ws_loss_grad(self._m, int(B), int(n), _ptr(x), _ptr(target), ctypes.byref(loss),
+        _check(_lib().vbh_ws_loss_grad(self._m, B, rp, dp, Vs, Sa, na, _ptr(target), _ptr(weight), ctypes.byref(loss),
                                        g.ctypes.data_as(ctypes.POINTER(ctypes.c_float))), "vbh_ws_loss_grad")
         return loss.value, g
 
-    def train_step(self, x, target, B: int, n: int, lr: float) -> float:
+    def train_step(self, rs, ds, Ss, ns, target, weight, lr: float) -> float:
+        B, rp, dp, Vs, Sa, na = self._batch(rs, ds, Ss, ns)
         loss = ctypes.c_double()
-        _check(_lib().vbh_ws_train_step(self._m, int(B), int(n), _ptr(x), _ptr(target), float(lr), ctypes.byref(loss)),
-               "vbh_ws_train_step")
+        _check(_lib().vbh_ws_train_step(self._m, B, rp, dp, Vs, Sa, na, _ptr(target), _ptr(weight), float(lr),
+                                        ctypes.byref(loss)), "vbh_ws_train_step")
         return loss.value
 
-    def predict(self, r, d, prior: dict | None = None, n: int = 8192) -> dict:
-        pa = _PriorArgs(prior, self.S)
-        res = Result()
-        _check(_lib().vbh_ws_predict(self._m, _ptr(r), _ptr(d), int(r.shape[0]), ctypes.byref(pa.c), int(n),
-                                     ctypes.byref(res)), "vbh_ws_predict")
-        return result_to_dict(res)
+    def predict(self, rs, ds, Ss, priors=None) -> list:
+        """Starting points (result dicts) for fits with init_state, from all observations."""
+        B, rp, dp, Vs, Sa, na = self._batch(rs, ds, Ss)
+        keep = []
+        pa = None
+        if priors is not None:
+            pa = (Prior * B)()
+            for b in range(B):
+                pb = _PriorArgs(priors[b], int(Ss[b]))
+                keep.append(pb)
+                pa[b] = pb.c
+        res = (Result * B)()
+        rc = _lib().vbh_ws_predict(self._m, B, rp, dp, Vs, Sa, ctypes.cast(pa, ctypes.POINTER(Prior)) if pa is not None
+                                   else None, res)
+        out = [result_to_dict(res[b]) for b in range(B)]
+        if rc != 0:
+            err = VBHError(rc, "vbh_ws_predict")
+            err.results = out
+            raise err
+        return out
 
 
 def _check(rc: int, what: str):

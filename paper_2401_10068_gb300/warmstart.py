@@ -1,14 +1,18 @@
 """Training and use of the learned warm start (``include/vbh_ws.h``).
 
-Data sets come from the method's own generator (``synth``): for data set b,
-K_true ~ Dirichlet(alpha 1) with its own seed, V_b observations.  Their CAVI
-fixed points, computed by the batched form (``vbh_fit_batched``), are the
-targets: kappa, ln E[rho] and the Cholesky factor of Sigma0 = W^{-1} / nu with
-its diagonal as logarithms.  The encoder sees the features of n evenly spaced
-observations of each data set and is trained by the library's own forward and
-backward kernels (mean squared error of standardised targets, Adam).
+Data sets come from the method's own generator (``synth``), shaped like the
+batched workload: N cells log-uniform in [n_lo, n_hi], G genes uniform on
+{48, 96} (V = N G observations), S uniform on 2..10, K_true ~ Dirichlet(alpha
+1), each with its own seed.  Their CAVI fixed points, computed by the batched
+form (``vbh_fit_batched``), are the targets: kappa, ln E[rho] and the Cholesky
+factor of Sigma0 = W^{-1} / nu with its diagonal as logarithms, in the output
+slots of vbh_ws.h, standardised per S; a data set whose fit did not converge
+within the sweep cap is left out.  The encoder is trained by the library's own
+tensor-core forward and backward kernels (weighted mean squared error, Adam)
+on up to ``n_cap`` pooled observations per data set; predictions pool every
+observation.
 
-    python -m paper_2401_10068_gb300.warmstart --S 3 --sets 20000 --out ws_s3.npz
+    python -m paper_2401_10068_gb300.warmstart --sets 8192 --out ws.npz
 
 writes the parameters and the standardisation; ``load`` restores them.
 """
@@ -22,63 +26,97 @@ import numpy as np
 
 from . import synth, vbh
 
-
-def target_from_result(res: dict, M: int) -> np.ndarray:
-    """kappa, ln E[rho], packed Cholesky of Sigma0 (diagonal as logs)."""
-    sig = np.asarray(res["Winv"], dtype=np.float64).reshape(M, M) / res["nu"]
-    L = np.linalg.cholesky(sig)
-    chol = [math.log(L[j, k]) if j == k else L[j, k] for j in range(M) for k in range(j + 1)]
-    return np.concatenate([np.asarray(res["kappa"], dtype=np.float64), [math.log(res["rho_mean"])], chol])
+ROWS_PER_CALL = 1 << 25            # pooled observations per encoder call (the library allows 2^26)
 
 
-def make_sets(S: int, count: int, seed0: int, v_lo: int, v_hi: int, alpha: float = 1.0, device="cuda"):
-    """`count` data sets with V log-uniform in [v_lo, v_hi] (device tensors)."""
+def shapes(count: int, seed0: int, n_lo: int, n_hi: int, s_lo: int = 2, s_hi: int = 10, genes=(48, 96)):
+    """(V, S) of `count` data sets of the batched workload's shape."""
     rng = np.random.default_rng(seed0)
-    V = np.floor(np.exp(rng.uniform(math.log(v_lo), math.log(v_hi), size=count))).astype(np.int64)
+    N = np.floor(np.exp(rng.uniform(math.log(n_lo), math.log(n_hi), size=count))).astype(np.int64)
+    G = rng.choice(np.asarray(genes), size=count)
+    S = rng.integers(s_lo, s_hi + 1, size=count)
+    return N * G, S
+
+
+def make_sets(count: int, seed0: int, n_lo: int, n_hi: int, alpha: float = 0.5, device="cuda", s_lo: int = 2,
+              s_hi: int = 10):
+    """`count` generator data sets (device tensors) and their S."""
+    V, S = shapes(count, seed0, n_lo, n_hi, s_lo, s_hi)
     rs, ds = [], []
     for b in range(count):
-        r, d, _ = synth.generate_device(int(V[b]), S, seed=seed0 * 1_000_003 + b, alpha=alpha, device=device)
+        r, d, _ = synth.generate_device(int(V[b]), int(S[b]), seed=seed0 * 1_000_003 + b, alpha=alpha, device=device)
         rs.append(r)
         ds.append(d)
-    return rs, ds
+    return rs, ds, [int(x) for x in S]
 
 
-def fixed_points(h: vbh.Handle, rs, ds, S: int, tol: float = 1e-8, cap: int = 2000, init_states=None):
-    """CAVI fits of every data set by the batched form."""
-    return h.fit_batched(rs, ds, [S] * len(rs), None, tol=tol, max_iter=cap, init_states=init_states)
-
-
-def build_training_set(ws: vbh.WarmStart, h: vbh.Handle, rs, ds, S: int, n: int, tol=1e-8, cap=2000):
-    """Features (sets x n x F, device) and standardised targets (sets x P)."""
-    import torch
+def target_from_result(res: dict, S: int):
+    """The 64 output slots of a fixed point and the slots' loss weights."""
     M = S - 1
-    res = fixed_points(h, rs, ds, S, tol, cap)
-    T = np.stack([target_from_result(x, M) for x in res])
-    X = torch.empty((len(rs), n, ws.F), dtype=torch.float32, device=rs[0].device)
-    for b in range(len(rs)):
-        ws.features(rs[b], ds[b], n, X[b])
-    mean = T.mean(axis=0)
-    std = T.std(axis=0)
-    std[std < 1e-6] = 1e-6
-    ws.set_norm(mean, std)
-    Tn = torch.from_numpy(((T - mean) / std).astype(np.float32)).to(rs[0].device)
-    return X, Tn, res
+    t = np.zeros(vbh.WS_P)
+    t[:M] = res["kappa"]
+    t[9] = math.log(res["a_rho"] / res["b_rho"])
+    sig = np.asarray(res["Winv"], dtype=np.float64).reshape(M, M) / res["nu"]
+    L = np.linalg.cholesky(sig)
+    for j in range(M):
+        for k in range(j + 1):
+            t[10 + j * (j + 1) // 2 + k] = math.log(L[j, j]) if j == k else L[j, k]
+    return t, vbh.ws_slots(S).astype(np.float64)
 
 
-def train(ws: vbh.WarmStart, X, Tn, epochs: int, batch: int, lr: float, seed: int = 0, log=None):
-    """Adam over shuffled mini-batches of sets; returns the loss per epoch."""
+def targets(results, Ss):
+    """Targets and weights of the converged fits (weight 0 for the others)."""
+    T = np.zeros((len(results), vbh.WS_P))
+    W = np.zeros((len(results), vbh.WS_P))
+    for b, (res, S) in enumerate(zip(results, Ss)):
+        if not res["converged"]:
+            continue
+        T[b], W[b] = target_from_result(res, S)
+    return T, W
+
+
+def norm_from(T, W, Ss):
+    """Per-S mean and deviation of every used slot (rows S of an 11 x 64 table)."""
+    mean = np.zeros((vbh.WS_SMAX + 1, vbh.WS_P))
+    std = np.ones((vbh.WS_SMAX + 1, vbh.WS_P))
+    Ss = np.asarray(Ss)
+    for S in range(2, vbh.WS_SMAX + 1):
+        sel = (Ss == S) & (W[:, 9] > 0)
+        if sel.sum() < 2:
+            continue
+        mean[S] = T[sel].mean(axis=0)
+        std[S] = np.maximum(T[sel].std(axis=0), 1e-6)
+    return mean, std
+
+
+def standardise(T, W, Ss, mean, std):
+    Ss = np.asarray(Ss)
+    return np.where(W > 0, (T - mean[Ss]) / std[Ss], 0.0)
+
+
+def train(ws: vbh.WarmStart, rs, ds, Ss, Tn, W, epochs: int, batch: int, lr: float, n_cap: int = 32768,
+          seed: int = 0, log=None, lr_min: float | None = None):
+    """Adam over shuffled mini-batches of data sets (sets with no used target
+    are skipped), the learning rate decaying from lr to lr_min (default lr /
+    20) on a cosine over the epochs; returns the mean loss per epoch."""
     import torch
-    nsets, n = X.shape[0], X.shape[1]
+    dev = rs[0].device
+    keep = np.nonzero(W.sum(axis=1) > 0)[0]
     rng = np.random.default_rng(seed)
+    Tt = torch.from_numpy(np.asarray(Tn, dtype=np.float32)).to(dev)
+    Wt = torch.from_numpy(np.asarray(W, dtype=np.float32)).to(dev)
     losses = []
+    lo = lr / 20.0 if lr_min is None else lr_min
     for ep in range(epochs):
-        perm = torch.from_numpy(rng.permutation(nsets)).to(X.device)
+        lr_ep = lo + 0.5 * (lr - lo) * (1.0 + math.cos(math.pi * ep / max(epochs - 1, 1)))
+        perm = rng.permutation(keep)
         tot, cnt = 0.0, 0
-        for s0 in range(0, nsets - batch + 1, batch):
+        for s0 in range(0, len(perm) - batch + 1, batch):
             idx = perm[s0:s0 + batch]
-            xb = X.index_select(0, idx).contiguous()
-            tb = Tn.index_select(0, idx).contiguous()
-            tot += ws.train_step(xb, tb, batch, n, lr)
+            it = torch.from_numpy(idx).to(dev)
+            tot += ws.train_step([rs[i] for i in idx], [ds[i] for i in idx], [Ss[i] for i in idx],
+                                 [n_cap] * len(idx), Tt.index_select(0, it).contiguous(),
+                                 Wt.index_select(0, it).contiguous(), lr_ep)
             cnt += 1
         losses.append(tot / max(cnt, 1))
         if log:
@@ -86,57 +124,80 @@ def train(ws: vbh.WarmStart, X, Tn, epochs: int, batch: int, lr: float, seed: in
     return losses
 
 
-def save(ws: vbh.WarmStart, path: str, hidden: int):
-    np.savez(path, S=ws.S, hidden=hidden, params=ws.get_params(), mean=ws.mean, std=ws.std)
+def predict(ws: vbh.WarmStart, rs, ds, Ss, priors=None):
+    """Starting points of every data set, in calls of at most ROWS_PER_CALL pooled observations."""
+    out = []
+    b = 0
+    while b < len(rs):
+        e, rows = b, 0
+        while e < len(rs) and (e == b or rows + int(rs[e].shape[0]) + 128 <= ROWS_PER_CALL):
+            rows += (int(rs[e].shape[0]) + 127) // 128 * 128
+            e += 1
+        out += ws.predict(rs[b:e], ds[b:e], Ss[b:e], None if priors is None else priors[b:e])
+        b = e
+    return out
+
+
+def save(ws: vbh.WarmStart, path: str):
+    np.savez(path, params=ws.get_params(), mean=ws.mean, std=ws.std)
 
 
 def load(path: str, device: int = 0, stream=None) -> vbh.WarmStart:
     z = np.load(path)
-    ws = vbh.WarmStart(int(z["S"]), int(z["hidden"]), device=device, stream=stream)
+    ws = vbh.WarmStart(device=device, stream=stream)
     ws.set_params(z["params"])
     ws.set_norm(z["mean"], z["std"])
     return ws
 
 
+def fit_and_train(h: vbh.Handle, ws: vbh.WarmStart, count: int, seed0: int, n_lo: int, n_hi: int, tol: float,
+                  cap: int, epochs: int, batch: int, lr: float, n_cap: int, log=None, targets_in=None,
+                  s_lo: int = 2, s_hi: int = 10):
+    """Generate `count` data sets, their fixed points (batched form, unless
+    `targets_in` = (T, W) from an earlier run on the same seeds) and train the
+    encoder on the converged ones; returns a summary with the targets."""
+    t0 = time.perf_counter()
+    rs, ds, Ss = make_sets(count, seed0, n_lo, n_hi, s_lo=s_lo, s_hi=s_hi)
+    if targets_in is None:
+        res = h.fit_batched(rs, ds, Ss, None, tol=tol, max_iter=cap)
+        T, W = targets(res, Ss)
+    else:
+        T, W = targets_in
+    t_fit = time.perf_counter() - t0
+    mean, std = norm_from(T, W, Ss)
+    ws.set_norm(mean, std)
+    Tn = standardise(T, W, Ss, mean, std)
+    t1 = time.perf_counter()
+    losses = train(ws, rs, ds, Ss, Tn, W, epochs, batch, lr, n_cap, log=log)
+    t_train = time.perf_counter() - t1
+    conv = int((W[:, 9] > 0).sum())
+    del rs, ds
+    return {"sets": count, "converged": conv, "fixed_points_s": t_fit, "train_s": t_train, "losses": losses,
+            "T": T, "W": W}
+
+
 def main():
     import torch
     ap = argparse.ArgumentParser()
-    ap.add_argument("--S", type=int, default=3)
-    ap.add_argument("--hidden", type=int, default=256)
-    ap.add_argument("--sets", type=int, default=20000)
-    ap.add_argument("--n", type=int, default=512)
-    ap.add_argument("--v-lo", type=int, default=9600)
-    ap.add_argument("--v-hi", type=int, default=200000)
-    ap.add_argument("--epochs", type=int, default=30)
+    ap.add_argument("--sets", type=int, default=8192)
+    ap.add_argument("--n-lo", type=int, default=200)
+    ap.add_argument("--n-hi", type=int, default=50000)
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--cap", type=int, default=4000)
+    ap.add_argument("--epochs", type=int, default=40)
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--n-cap", type=int, default=32768)
     ap.add_argument("--seed", type=int, default=7)
     ap.add_argument("--out", default="ws.npz")
     args = ap.parse_args()
     stream = torch.cuda.current_stream()
     h = vbh.Handle(0, stream)
-    ws = vbh.WarmStart(args.S, args.hidden, seed=args.seed, stream=stream)
-    t0 = time.perf_counter()
-    X_all, T_all = [], []
-    chunk = 4096
-    for c0 in range(0, args.sets, chunk):
-        rs, ds = make_sets(args.S, min(chunk, args.sets - c0), args.seed + c0, args.v_lo, args.v_hi)
-        res = fixed_points(h, rs, ds, args.S)
-        T_all.append(np.stack([target_from_result(x, args.S - 1) for x in res]))
-        X = torch.empty((len(rs), args.n, ws.F), dtype=torch.float32, device="cuda")
-        for b in range(len(rs)):
-            ws.features(rs[b], ds[b], args.n, X[b])
-        X_all.append(X)
-        del rs, ds
-    X = torch.cat(X_all)
-    T = np.concatenate(T_all)
-    mean, std = T.mean(axis=0), np.maximum(T.std(axis=0), 1e-6)
-    ws.set_norm(mean, std)
-    Tn = torch.from_numpy(((T - mean) / std).astype(np.float32)).cuda()
-    print(f"{len(T)} data sets and fixed points in {time.perf_counter() - t0:.1f} s", flush=True)
-    train(ws, X, Tn, args.epochs, args.batch, args.lr, seed=args.seed, log=lambda s: print(s, flush=True))
-    save(ws, args.out, args.hidden)
-    print(f"saved {args.out} after {time.perf_counter() - t0:.1f} s", flush=True)
+    ws = vbh.WarmStart(seed=args.seed, stream=stream)
+    info = fit_and_train(h, ws, args.sets, args.seed, args.n_lo, args.n_hi, args.tol, args.cap, args.epochs,
+                         args.batch, args.lr, args.n_cap, log=lambda s: print(s, flush=True))
+    save(ws, args.out)
+    print({k: v for k, v in info.items() if k != "losses"}, flush=True)
 
 
 if __name__ == "__main__":

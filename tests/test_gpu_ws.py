@@ -1,17 +1,20 @@
-"""The learned warm start: its GPU forward and backward kernels against the
-FP64 set-encoder oracle, and what a trained encoder gains over the paper's
-start (the cold start) on held-out data sets from the generator.
+"""The learned warm start: its tensor-core forward and backward kernels against
+the FP64 set-encoder oracle, and what a trained encoder gains over the
+paper's start (the cold start) on held-out data sets shaped like the batched
+workload.
 
-Gradient check: the kernels keep the weight matrices in BF16 and accumulate in
-FP32; the oracle runs the same BF16-rounded weights in FP64, so the remaining
-difference is FP32 accumulation and FP32 GELU, bounded here by 1e-3 relative
-(norm-wise per parameter block) and 1e-4 on the loss."""
+Gradient check: the kernels keep the features, W1, W2, the layer-1
+activations and the per-observation gradients in BF16 and accumulate in
+FP32; the oracle rounds to BF16 at the same points and computes the rest in
+FP64, so what remains is FP32 accumulation order, the approximate exponential
+and reciprocal of the GELU, and BF16
+roundings that fall on the other side of a tie: bounded here by 2e-3
+relative (norm-wise per parameter block) and 1e-3 on the outputs and loss."""
 import numpy as np
 import pytest
 import torch
 
 from oracle import mlp_oracle as MO
-from oracle import oracle as O
 from paper_2401_10068_gb300 import synth, vbh, warmstart
 
 pytestmark = pytest.mark.gpu
@@ -23,114 +26,126 @@ def built():
     _build.build_all()
 
 
-def _blocks(F, H, P):
+def _blocks():
     o, out = 0, []
-    for name, s in MO.shapes(F, H, P):
+    for name, s in MO.shapes():
         n = int(np.prod(s))
         out.append((name, o, o + n))
         o += n
     return out
 
 
-@pytest.mark.parametrize("S,H,B,n", [(3, 64, 3, 50), (6, 128, 5, 37)])
-def test_forward_and_gradient_match_the_oracle(built, S, H, B, n):
-    ws = vbh.WarmStart(S, H, seed=11)
-    F, P = ws.F, ws.P
+def _sets(spec, seed0):
+    rs, ds, Ss, host = [], [], [], []
+    for k, (S, V) in enumerate(spec):
+        r, d, _ = synth.generate(V, S, seed=seed0 + k, alpha=0.5, p_const=0.05)
+        rs.append(torch.from_numpy(r).cuda())
+        ds.append(torch.from_numpy(d).cuda())
+        Ss.append(S)
+        host.append((r, d))
+    return rs, ds, Ss, host
+
+
+def test_forward_and_gradient_match_the_oracle(built):
+    # three sets of different S; one pooled in full (ragged last tile), two sampled
+    spec = [(2, 300), (5, 1000), (10, 3000)]
+    ns = [0, 700, 1024]
+    rs, ds, Ss, host = _sets(spec, 41)
+    ws = vbh.WarmStart(seed=11)
     theta = ws.get_params().astype(np.float64)
-    rng = np.random.default_rng(S)
-    X = rng.normal(0, 1, size=(B, n, F)).astype(np.float32)
-    T = rng.normal(0, 1, size=(B, P)).astype(np.float32)
-    xd, td = torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda()
-    out = torch.empty((B, P), dtype=torch.float32, device="cuda")
-    ws.forward(xd, B, n, out)
-    th16 = MO.weights_as_bf16(theta, F, H, P)
-    ref_out = MO.forward(th16, X.astype(np.float64), F, H, P)
-    assert np.max(np.abs(out.cpu().numpy() - ref_out)) <= 1e-4 * max(1.0, np.max(np.abs(ref_out)))
-    loss, g = ws.loss_grad(xd, td, B, n)
-    ref_loss, ref_g = MO.loss_and_grad(th16, X.astype(np.float64), T.astype(np.float64), F, H, P)
-    assert loss == pytest.approx(ref_loss, rel=1e-4)
-    for name, a, b in _blocks(F, H, P):
+    Xs = [MO.features(r, d, S, MO.pooled_index(r.shape[0], n)) for (r, d), S, n in zip(host, Ss, ns)]
+    out = ws.forward(rs, ds, Ss, ns).cpu().numpy()
+    ref = MO.forward(theta, Xs, quantized=True)
+    assert np.max(np.abs(out - ref)) <= 1e-3 * max(1.0, np.max(np.abs(ref))), np.max(np.abs(out - ref))
+    rng = np.random.default_rng(5)
+    T = rng.normal(0, 1, size=(3, vbh.WS_P)).astype(np.float32)
+    W = np.stack([vbh.ws_slots(S) for S in Ss]).astype(np.float32)
+    loss, g = ws.loss_grad(rs, ds, Ss, ns, torch.from_numpy(T).cuda(), torch.from_numpy(W).cuda())
+    ref_loss, ref_g = MO.loss_and_grad(theta, Xs, T, W, quantized=True)
+    assert loss == pytest.approx(ref_loss, rel=1e-3)
+    for name, a, b in _blocks():
         err = np.linalg.norm(g[a:b] - ref_g[a:b]) / max(np.linalg.norm(ref_g[a:b]), 1e-30)
-        assert err < 1e-3, (name, err)
-    # deterministic: the split-K partials are summed in a fixed order
-    loss2, g2 = ws.loss_grad(xd, td, B, n)
+        print(f"{name}: relative gradient error {err:.2e}")
+        assert err < 2e-3, (name, err)
+    # run-to-run identical: every sum is taken in a fixed order
+    loss2, g2 = ws.loss_grad(rs, ds, Ss, ns, torch.from_numpy(T).cuda(), torch.from_numpy(W).cuda())
     assert loss2 == loss and np.array_equal(g2, g)
     ws.close()
 
 
 def test_features_are_the_stated_ones(built):
-    S, V, n = 4, 10007, 333
-    r, d, _ = synth.generate(V, S, seed=3)
-    ws = vbh.WarmStart(S, 64)
-    x = torch.empty((n, ws.F), dtype=torch.float32, device="cuda")
-    ws.features(torch.from_numpy(r).cuda(), torch.from_numpy(d).cuda(), n, x)
-    idx = (np.arange(n, dtype=np.int64) * V) // n
-    M = S - 1
-    D = d[idx, :M] - d[idx, M:]
-    y = r[idx] - d[idx, M]
-    want = np.concatenate([D, y[:, None], (y * y)[:, None], y[:, None] * D], axis=1)
-    assert np.allclose(x.cpu().numpy(), want, rtol=1e-6, atol=1e-6)
+    ws = vbh.WarmStart()
+    for S, V, n in ((4, 10007, 333), (10, 500, 0)):
+        r, d, _ = synth.generate(V, S, seed=3)
+        x = ws.features(torch.from_numpy(r).cuda(), torch.from_numpy(d).cuda(), S, n).cpu().numpy()
+        want = MO.features(r, d, S, MO.pooled_index(V, n))
+        assert np.array_equal(x.astype(np.float64), want)
     ws.close()
 
 
 def test_training_lowers_the_loss(built):
-    ws = vbh.WarmStart(3, 64, seed=5)
+    rs, ds, Ss, _ = _sets([(3, 2000), (6, 1500), (9, 3000), (2, 800)], 77)
+    ws = vbh.WarmStart(seed=5)
     rng = np.random.default_rng(9)
-    B, n = 16, 64
-    X = torch.from_numpy(rng.normal(0, 1, size=(B, n, ws.F)).astype(np.float32)).cuda()
-    T = torch.from_numpy(rng.normal(0, 1, size=(B, ws.P)).astype(np.float32)).cuda()
-    first = ws.train_step(X, T, B, n, 3e-3)
-    for _ in range(200):
-        last = ws.train_step(X, T, B, n, 3e-3)
-    assert last < 0.5 * first
+    T = torch.from_numpy(rng.normal(0, 1, size=(4, vbh.WS_P)).astype(np.float32)).cuda()
+    W = torch.from_numpy(np.stack([vbh.ws_slots(S) for S in Ss]).astype(np.float32)).cuda()
+    first = ws.train_step(rs, ds, Ss, None, T, W, 3e-3)
+    for _ in range(150):
+        last = ws.train_step(rs, ds, Ss, None, T, W, 3e-3)
+    assert last < 0.5 * first, (first, last)
     ws.close()
 
 
-def _sweeps_to(trace, L_opt, eps):
-    """First sweep whose ELBO is within eps (relative) of the optimum."""
-    hit = np.nonzero((L_opt - np.asarray(trace)) <= eps * abs(L_opt))[0]
-    return int(hit[0]) if hit.size else None
+def test_prediction_is_a_valid_start(built):
+    """Whatever the weights, a prediction is a valid VBH_INIT_GIVEN state: nu,
+    lambda, a_rho from V and the prior, W^{-1} symmetric positive definite."""
+    rs, ds, Ss, _ = _sets([(3, 5000), (10, 2000)], 91)
+    ws = vbh.WarmStart(seed=2)
+    for p, S, r in zip(ws.predict(rs, ds, Ss), Ss, rs):
+        V = r.shape[0]
+        assert p["status"] == 0 and p["nu"] == 1.0 + V and p["lam"] == 1e-3 + V and p["a_rho"] == 0.5 + V / 2
+        W = np.asarray(p["Winv"])
+        assert np.allclose(W, W.T) and np.all(np.linalg.eigvalsh(W) > 0)
+    ws.close()
 
 
 def test_warm_start_saves_sweeps_at_an_equal_elbo(built):
-    """Train on generator data sets against CAVI fixed points, then fit held-out
-    data sets from the paper's start and from the encoder's start.  Each fit's
-    ELBO trace is compared with the data set's optimum (the exact profile-grouped
-    fit, FP64 sums, to rel dELBO < 1e-12); the measure is the number of sweeps
-    to come within eps of it (a stopping test at 1e-8 would fire on the FP32
-    rounding noise of the per-observation ELBO).  Both starts reach the optimum
-    within 1e-6 (equal ELBO).  The learned start saves most of the sweeps to
-    1e-4 and 1e-5; to 1e-6 a slow mode (the split between the spread of beta and
-    the noise precision) dominates both fits, and the encoder's Sigma0 and
-    E[rho] are not accurate enough to shorten it, so no gain is asserted there."""
-    S, M = 3, 2
+    """Train the encoder on generator data sets (S = 2..4) against their CAVI
+    fixed points, then fit held-out data sets of the batched workload's shape
+    (N log-uniform in [200, 50,000] cells, G in {48, 96}) to rel dELBO < 1e-8
+    from the paper's start and from the encoder's start.  Both converge, to
+    the same ELBO (median gap <= 1e-6; each pair stops at its own first sweep
+    under the tolerance, so individual gaps of slow fits can be larger), and the
+    learned start needs at least 15 % fewer sweeps in total.
+
+    This is where the encoder gains.  For S >= 5 the fixed point's Sigma0 and
+    E[rho] depend on data-set-specific fluctuations that the mean-pooled
+    features do not resolve (the encoder's error in them stays near that of the
+    per-S mean of the training targets, ~2 %), while a start must be within
+    ~1 % of the fixed point in Sigma0 to shorten the slow tail of these fits;
+    the bench's warmstart workload reports the whole range of S."""
     stream = torch.cuda.current_stream()
     h = vbh.Handle(0, stream)
-    ws = vbh.WarmStart(S, 256, seed=1, stream=stream)
-    rs, ds = warmstart.make_sets(S, 3072, 101, 4000, 40000)
-    X, Tn, _ = warmstart.build_training_set(ws, h, rs, ds, S, n=2048)
-    del rs, ds
-    losses = warmstart.train(ws, X, Tn, epochs=30, batch=32, lr=1e-3)
-    # kappa is predictable from the data; the fixed points' ln E[rho] and Sigma0 scatter around the
-    # generator's fixed truths, so once standardised they are mostly noise and the loss levels off
-    assert losses[-1] < 0.95 * losses[0], losses
-    del X, Tn
-    # held out
-    rs, ds = warmstart.make_sets(S, 48, 977, 20000, 96000)
-    budget = 1500
-    cold = h.fit_batched(rs, ds, [S] * len(rs), None, tol=0.0, max_iter=budget, trace=True)
-    inits = [ws.predict(rs[b], ds[b], None, n=8192) for b in range(len(rs))]
-    warm = h.fit_batched(rs, ds, [S] * len(rs), None, tol=0.0, max_iter=budget, trace=True, init_states=inits)
-    opt = [h.fit(rs[b], ds[b], S, None, tol=1e-12, max_iter=10000, grouped=True)["elbo"] for b in range(len(rs))]
-    med = {}
-    for eps in (1e-4, 1e-5, 1e-6):
-        sc = np.array([_sweeps_to(cold[b]["trace"], opt[b], eps) for b in range(len(rs))])
-        sw = np.array([_sweeps_to(warm[b]["trace"], opt[b], eps) for b in range(len(rs))])
-        assert np.all(sc != None) and np.all(sw != None), eps       # noqa: E711 (both reach the optimum)
-        med[eps] = (float(np.median(sc)), float(np.median(sw)))
-        print(f"sweeps to within {eps:g} of the optimum: paper's start mean {sc.mean():.1f} median {med[eps][0]:.0f}; "
-              f"learned start mean {sw.mean():.1f} median {med[eps][1]:.0f}")
-    assert med[1e-4][1] < 0.5 * med[1e-4][0]
-    assert med[1e-5][1] < 0.75 * med[1e-5][0]
+    ws = vbh.WarmStart(seed=3, stream=stream)
+    info = warmstart.fit_and_train(h, ws, 2048, 11, 200, 5000, 1e-8, 3000, 60, 64, 2e-3, 16384, s_lo=2, s_hi=4)
+    assert info["converged"] > 1900, info["converged"]
+    rs, ds, Ss = [], [], []
+    V, S = warmstart.shapes(96, 977, 200, 50000, 2, 4)
+    for b in range(96):
+        r, d, _ = synth.generate_device(int(V[b]), int(S[b]), seed=977_000 + b, alpha=0.5)
+        rs.append(r)
+        ds.append(d)
+        Ss.append(int(S[b]))
+    preds = warmstart.predict(ws, rs, ds, Ss)
+    cold = h.fit_batched(rs, ds, Ss, None, tol=1e-8, max_iter=4000)
+    warm = h.fit_batched(rs, ds, Ss, None, tol=1e-8, max_iter=4000, init_states=preds)
+    assert all(x["converged"] for x in cold) and all(x["converged"] for x in warm)
+    ic = np.array([x["iters"] for x in cold])
+    iw = np.array([x["iters"] for x in warm])
+    gaps = np.array([abs(w["elbo"] - c["elbo"]) / abs(c["elbo"]) for c, w in zip(cold, warm)])
+    print(f"sweeps: paper's start {ic.sum()} (median {np.median(ic):.0f}), learned start {iw.sum()} "
+          f"(median {np.median(iw):.0f}); ELBO gap median {np.median(gaps):.1e} max {gaps.max():.1e}")
+    assert np.median(gaps) <= 1e-6
+    assert iw.sum() <= 0.85 * ic.sum(), (iw.sum(), ic.sum())
     ws.close()
     h.close()
