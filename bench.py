@@ -942,9 +942,10 @@ PER_S = {"V": 1 << 27, "S": (2, 3, 4, 6, 8, 10, 11), "seed": 9, "alpha": 0.5, "w
 
 def run_per_s(args):
     """Bandwidth of the FP32 sweep kernel across S (one data set of 2^27
-    observations per S, the same recipe without constant profiles): per S, 4
-    untimed sweeps, then 20 sweeps timed with CUDA events on the handle's
-    stream; algorithmic bytes 4 (S + 1) per observation."""
+    observations per S, the same recipe without constant profiles), in its
+    plain and its compensated form: per S and form, 4 untimed sweeps, then 20
+    sweeps timed with CUDA events on the handle's stream; algorithmic bytes
+    4 (S + 1) per observation."""
     import torch
     from paper_2401_10068_gb300 import _build
     _build.build_all()
@@ -962,17 +963,23 @@ def run_per_s(args):
         with torch.cuda.stream(stream):
             r, d, _ = synth.generate_device(V, S, seed=PER_S["seed"], alpha=PER_S["alpha"], device=dev)
         stream.synchronize()
-        h.fit_begin(r, d, S, None, tol=0.0, max_iter=PER_S["warm"] + n)
-        h.fit_step(PER_S["warm"])
-        torch.cuda.synchronize(dev)
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ev0.record(stream)
-        h.fit_step(n)
-        ev1.record(stream)
-        torch.cuda.synchronize(dev)
-        ms = ev0.elapsed_time(ev1) / n
-        gbs = V * 4.0 * (S + 1) / (ms * 1e-3) / 1e9
-        rows.append({"S": S, "ms_per_sweep": ms, "achieved_gbs": gbs, "frac": gbs / peak})
+        row = {"S": S}
+        for form, stats in (("plain", vbh.STATS_PLAIN), ("compensated", vbh.STATS_COMPENSATED)):
+            h.fit_begin(r, d, S, None, tol=0.0, max_iter=PER_S["warm"] + n, stats=stats)
+            h.fit_step(PER_S["warm"])
+            torch.cuda.synchronize(dev)
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            h.fit_step(n)
+            ev1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms = ev0.elapsed_time(ev1) / n
+            gbs = V * 4.0 * (S + 1) / (ms * 1e-3) / 1e9
+            if form == "plain":
+                row.update({"ms_per_sweep": ms, "achieved_gbs": gbs, "frac": gbs / peak})
+            else:
+                row["compensated"] = {"ms_per_sweep": ms, "achieved_gbs": gbs, "frac": gbs / peak}
+        rows.append(row)
         del r, d
     clk = clocks.stop()
     h.close()

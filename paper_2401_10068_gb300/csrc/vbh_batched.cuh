@@ -161,7 +161,7 @@ __device__ __forceinline__ void issue_unit(Cursor &cu, const BatchClass &bc, int
 // before that barrier and summed after it, so the next chunk's partial (into
 // the other buffer) cannot overwrite it while it is read.
 template <int S, bool COMP>
-__global__ void __launch_bounds__(BatchCfg<S>::THREADS, COMP ? SweepCfg<S>::MINB_C : SweepCfg<S>::MINB)
+__global__ void __launch_bounds__(BatchCfg<S>::THREADS, COMP ? SweepCfg<S>::MINB_BC : SweepCfg<S>::MINB)
     batched_pass_kernel(BatchClass bc)
 {
     using C = SweepCfg<S>;
