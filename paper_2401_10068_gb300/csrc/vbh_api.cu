@@ -42,7 +42,7 @@ struct Launch {
     }
     const void *setup() const { return (tc || grp) ? tki.setup : ki.setup; }
     int threads() const { return grp ? vbh::GROUPED_THREADS : tc ? tki.threads : ki.threads; }
-    size_t smem() const { return grp ? vbh::grouped_smem_bytes() : tc ? tki.smem : ki.smem; }
+    size_t smem() const { return grp ? vbh::grouped_smem_bytes() : tc ? tki.smem : comp ? ki.smem_comp : ki.smem; }
     int tile() const { return tc ? tki.tile : ki.tile; }
 };
 
@@ -353,7 +353,7 @@ int prepare_launch(vbh_handle *h, int S, long long V, int precision, const float
         if (!h->attr_set[S]) {
             VBH_CK(cudaFuncSetAttribute(L->ki.sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, int(L->ki.smem)));
             VBH_CK(cudaFuncSetAttribute(L->ki.sweep_comp, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        int(L->ki.smem)));
+                                        int(L->ki.smem_comp)));
             h->attr_set[S] = true;
         }
     } else {
@@ -428,7 +428,7 @@ int launch_sweep(vbh_handle *h, DevState *st, int mode, Launch &L, const float *
         VBH_CK(cudaLaunchKernel(L.tki.sweep, dim3(L.grid), dim3(L.tki.threads), args, L.tki.smem, h->stream));
     } else {
         void *args[] = {&a};
-        VBH_CK(cudaLaunchKernel(L.func(), dim3(L.grid), dim3(L.ki.threads), args, L.ki.smem, h->stream));
+        VBH_CK(cudaLaunchKernel(L.func(), dim3(L.grid), dim3(L.ki.threads), args, L.smem(), h->stream));
     }
     return VBH_OK;
 }

@@ -198,6 +198,7 @@ int fit_batched_impl(BatchedHost &hb, cudaStream_t stream, int nsm, int B, const
         if (!batch_info(s, &cp.bi)) return VBH_EUNSUPPORTED;
         if (comp) {
             cp.bi.pass = cp.bi.pass_comp;
+            cp.bi.pass_smem = cp.bi.pass_smem_comp;
             cp.bi.nstat += 1;
         }
         VBH_B_CK(cudaFuncSetAttribute(cp.bi.pass, cudaFuncAttributeMaxDynamicSharedMemorySize, int(cp.bi.pass_smem)));

@@ -81,6 +81,9 @@ struct BatchCfg {
     static constexpr uint32_t STAGE_BYTES = R_BYTES + D_BYTES;
     static constexpr size_t RING_BYTES = size_t(STAGES) * STAGE_BYTES;
     static constexpr size_t SMEM_BYTES = RING_BYTES + 64;
+    // compensated form: the ring, the table of profile terms, the split pass globals
+    static constexpr size_t OFF_TAB = RING_BYTES, OFF_SPLIT = OFF_TAB + C::TAB_BYTES;
+    static constexpr size_t SMEM_BYTES_C = OFF_SPLIT + C::SPLIT_BYTES + 64;
 };
 
 // Producer state (thread 0 of a block): the chunk being issued and the next unit.
@@ -171,7 +174,9 @@ __global__ void __launch_bounds__(BatchCfg<S>::THREADS, COMP ? SweepCfg<S>::MINB
     constexpr int NGRP = COMP ? C::NGRPC : C::NGRP;
     constexpr int THREADS = B::THREADS, T = B::T, STAGES = B::STAGES;
     extern __shared__ __align__(128) unsigned char smem[];
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + B::RING_BYTES);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + (COMP ? B::SMEM_BYTES_C - 64 : B::RING_BYTES));
+    float4 *tab = reinterpret_cast<float4 *>(smem + B::OFF_TAB);     // compensated form only
+    float *split = reinterpret_cast<float *>(smem + B::OFF_SPLIT);
     __shared__ StageMeta meta[STAGES];
     __shared__ double s_red[2][THREADS / 32][NGRP * 32];
     __shared__ int s_bad;
@@ -197,14 +202,35 @@ __global__ void __launch_bounds__(BatchCfg<S>::THREADS, COMP ? SweepCfg<S>::MINB
     for (int i = 0; i < NSTAT; ++i) acc[i] = 0.0f;
 #pragma unroll
     for (int g = 0; g < NGRP; ++g) acc64[g] = 0.0;
-    // plain form: L~ (L) and kappa~ (kap); compensated form: the grid and
-    // rest parts of Sigma0~ (L, L2) and kappa~ (kap, kap2)
-    float L[C::NGA], kap[C::MA], L2[COMP ? C::NGA : 1], kap2[COMP ? C::MA : 1], erho = 0.0f;
-    if constexpr (NG == 0) L[0] = 0.0f;
-    if constexpr (M == 0) kap[0] = 0.0f;
-    L2[0] = 0.0f;
-    kap2[0] = 0.0f;
+    // plain form: L~ (L) and kappa~ (kap) in registers; compensated form: the
+    // split globals of the current data set and its table of profile terms in
+    // shared memory, switched by the whole block between units
+    float L[COMP ? 1 : C::NGA], kap[COMP ? 1 : C::MA], erho = 0.0f;
+    L[0] = 0.0f;
+    kap[0] = 0.0f;
     int cur_ds = -1;
+    // (compensated form) make data set ds current: split globals, E[rho], table.
+    // Called by every thread with the same ds, between units.
+    auto switch_to = [&](int ds) {
+        const DevState *st = bc.states + ds;
+        for (int i = tid; i < C::SPLIT_FLOATS; i += THREADS) {
+            float v;
+            if (i < NG) v = st->sw.Sh[i];
+            else if (i < 2 * NG) v = st->sw.Sl[i - NG];
+            else if (i < 2 * NG + M) v = st->sw.kh[i - 2 * NG];
+            else v = st->sw.kl[i - 2 * NG - M];
+            split[i] = v;
+        }
+        erho = (mode == MODE_INIT) ? 0.0f : st->sw.erho;
+        __syncthreads();
+        build_profile_table<S>(tab, split, erho, tid, THREADS);
+        __syncthreads();
+        cur_ds = ds;
+    };
+    if constexpr (COMP) {
+        __syncthreads();                                    // the first unit's metadata
+        if (meta[0].chunk >= 0) switch_to(meta[0].ds);
+    }
     int ftile = 0;
     int rbuf = 0;                                           // reduction buffer of the next chunk partial
 
@@ -218,27 +244,16 @@ __global__ void __launch_bounds__(BatchCfg<S>::THREADS, COMP ? SweepCfg<S>::MINB
         if (ok) m = meta[s];                                // the same for every thread once the stage is full
         const bool work = ok && m.chunk >= 0;
         if (work) {
-            if (m.ds != cur_ds) {                           // a new data set: its FP32 globals (cached reads)
-                const DevState *st = bc.states + m.ds;
-                if constexpr (COMP) {
-#pragma unroll
-                    for (int i = 0; i < NG; ++i) {
-                        L[i] = st->sw.Sh[i];
-                        L2[i] = st->sw.Sl[i];
-                    }
-#pragma unroll
-                    for (int i = 0; i < M; ++i) {
-                        kap[i] = st->sw.kh[i];
-                        kap2[i] = st->sw.kl[i];
-                    }
-                } else {
+            if constexpr (!COMP) {
+                if (m.ds != cur_ds) {                       // a new data set: its FP32 globals (cached reads)
+                    const DevState *st = bc.states + m.ds;
 #pragma unroll
                     for (int i = 0; i < NG; ++i) L[i] = st->sw.L[i];
 #pragma unroll
                     for (int i = 0; i < M; ++i) kap[i] = st->sw.kappa[i];
+                    erho = (mode == MODE_INIT) ? 0.0f : st->sw.erho;
+                    cur_ds = m.ds;
                 }
-                erho = (mode == MODE_INIT) ? 0.0f : st->sw.erho;
-                cur_ds = m.ds;
             }
             if (!(m.flags & UNIT_TAIL)) {
                 const float *rt = reinterpret_cast<const float *>(smem + size_t(s) * B::STAGE_BYTES);
@@ -249,7 +264,7 @@ __global__ void __launch_bounds__(BatchCfg<S>::THREADS, COMP ? SweepCfg<S>::MINB
                     float x[S];
                     load_row<S>(dt, j, x);
                     if constexpr (COMP) {
-                        observe_comp<S>(x, rt[j], L, L2, kap, kap2, erho, acc, prod, pl, uh, ul);
+                        observe_comp<S>(x, rt[j], tab, split, erho, acc, prod, pl, uh, ul);
                         peel_exponent2(prod, pl, ex);
                     } else {
                         observe<S>(x, rt[j], L, kap, erho, acc, prod);
@@ -272,7 +287,7 @@ __global__ void __launch_bounds__(BatchCfg<S>::THREADS, COMP ? SweepCfg<S>::MINB
 #pragma unroll
                     for (int q = 0; q < S; ++q) x[q] = __ldg(dg + i * S + q);
                     if constexpr (COMP) {
-                        observe_comp<S>(x, __ldg(rg + i), L, L2, kap, kap2, erho, acc, prod, pl, uh, ul);
+                        observe_comp<S>(x, __ldg(rg + i), tab, split, erho, acc, prod, pl, uh, ul);
                         peel_exponent2(prod, pl, ex);
                     } else {
                         observe<S>(x, __ldg(rg + i), L, kap, erho, acc, prod);
@@ -307,6 +322,12 @@ __global__ void __launch_bounds__(BatchCfg<S>::THREADS, COMP ? SweepCfg<S>::MINB
                 bc.partials[size_t(m.chunk) * NS + j] = t;
             }
             rbuf ^= 1;
+        }
+        if constexpr (COMP) {
+            // the next unit's metadata was written before this unit's barrier (it was issued
+            // STAGES - 1 units ago, or in the prologue); a new data set switches here, block-wide
+            const StageMeta nx = meta[(k + 1) % STAGES];
+            if (nx.chunk >= 0 && nx.ds != cur_ds) switch_to(nx.ds);
         }
         if (tid == 0) issue_unit<S>(cu, bc, mode, smem + size_t(s) * B::STAGE_BYTES, &full[s], &meta[s]);
     }

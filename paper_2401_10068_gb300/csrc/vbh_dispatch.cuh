@@ -10,6 +10,7 @@ struct KernelInfo {
     const void *sweep_comp;// sweep_kernel<S, true>: with the compensated statistics (one more column)
     const void *setup;     // setup_kernel<S - 1>
     size_t smem;           // dynamic shared memory of the sweep
+    size_t smem_comp;      // and of its compensated form
     int threads;           // block size of the sweep
     int tile;              // observations per tile
     int nstat;             // statistics per block partial (plain form; the compensated form has nstat + 1)
@@ -22,6 +23,7 @@ struct BatchKernelInfo {
     const void *update;    // batched_update_kernel<S - 1>
     const void *setup;     // batched_setup_kernel<S - 1>
     size_t pass_smem;
+    size_t pass_smem_comp;
     size_t update_smem;
     int threads;
     int tile;              // observations per tile of the pass
@@ -42,11 +44,11 @@ bool batch_kernel_info_s9_11(int S, BatchKernelInfo *out);
 #define VBH_KERNEL_INFO_CASE(SV)                                                                                       \
     case SV: {                                                                                                         \
         using C = ::vbh::SweepCfg<SV>;                                                                                 \
-        static_assert(size_t(::vbh::gu_ws_doubles<SV - 1>()) * 8 <= C::RING_BYTES, "workspace exceeds the ring");    \
         out->sweep = reinterpret_cast<const void *>(&::vbh::sweep_kernel<SV, false>);                                  \
         out->sweep_comp = reinterpret_cast<const void *>(&::vbh::sweep_kernel<SV, true>);                              \
         out->setup = reinterpret_cast<const void *>(&::vbh::setup_kernel<SV - 1>);                                     \
         out->smem = C::SMEM_BYTES;                                                                                     \
+        out->smem_comp = C::SMEM_BYTES_C;                                                                              \
         out->threads = C::THREADS;                                                                                     \
         out->tile = C::T;                                                                                              \
         out->nstat = C::NSTAT;                                                                                         \
@@ -61,6 +63,7 @@ bool batch_kernel_info_s9_11(int S, BatchKernelInfo *out);
         out->update = reinterpret_cast<const void *>(&::vbh::batched_update_kernel<SV - 1>);                           \
         out->setup = reinterpret_cast<const void *>(&::vbh::batched_setup_kernel<SV - 1>);                             \
         out->pass_smem = BC::SMEM_BYTES;                                                                               \
+        out->pass_smem_comp = BC::SMEM_BYTES_C;                                                                        \
         out->update_smem = size_t(::vbh::gu_ws_doubles<SV - 1>()) * 8;                                                 \
         out->threads = BC::THREADS;                                                                                    \
         out->tile = BC::T;                                                                                             \

@@ -75,7 +75,7 @@ int scratch_address(int device, unsigned char **out)
             VBH_CHECK_CUDA(cudaFuncGetAttributes(&fa, ki.setup));
             VBH_CHECK_CUDA(cudaFuncSetAttribute(ki.sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, int(ki.smem)));
             VBH_CHECK_CUDA(
-                cudaFuncSetAttribute(ki.sweep_comp, cudaFuncAttributeMaxDynamicSharedMemorySize, int(ki.smem)));
+                cudaFuncSetAttribute(ki.sweep_comp, cudaFuncAttributeMaxDynamicSharedMemorySize, int(ki.smem_comp)));
         }
         g_addr[device] = static_cast<unsigned char *>(p);
     }
@@ -177,6 +177,7 @@ extern "C" int vbh_fit_static(const float *r, const float *d, int64_t V, int S, 
     vbh::KernelInfo ki;
     if (!kernel_info_any(S, &ki)) return VBH_EUNSUPPORTED;
     const void *sweep = comp ? ki.sweep_comp : ki.sweep;
+    const size_t smem = comp ? ki.smem_comp : ki.smem;
     const int nstat = ki.nstat + (comp ? 1 : 0);
     unsigned char *base = nullptr;
     int rc = scratch_address(device, &base);
@@ -189,7 +190,7 @@ extern "C" int vbh_fit_static(const float *r, const float *d, int64_t V, int S, 
     //      (the shared-memory attribute was set by the first call) ----
     int nsm = 0, per_sm = 0;
     VBH_S_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device));
-    VBH_S_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep, ki.threads, ki.smem));
+    VBH_S_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep, ki.threads, smem));
     if (per_sm < 1) {
         vbh::record_error("occupancy of the sweep kernel", __FILE__, __LINE__, "no block fits on an SM");
         return VBH_ECUDA;
@@ -252,7 +253,7 @@ extern "C" int vbh_fit_static(const float *r, const float *d, int64_t V, int S, 
     a.use_cond = 0;
     a.mode = init ? vbh::MODE_INIT : vbh::MODE_ELBO;
     void *args[] = {&a};
-    VBH_S_CK(cudaLaunchKernel(sweep, dim3(unsigned(grid)), dim3(ki.threads), args, ki.smem, s));
+    VBH_S_CK(cudaLaunchKernel(sweep, dim3(unsigned(grid)), dim3(ki.threads), args, smem, s));
     a.mode = vbh::MODE_ITER;
     constexpr int SWEEP_BATCH = 64;
     struct Ctl {
@@ -262,7 +263,7 @@ extern "C" int vbh_fit_static(const float *r, const float *d, int64_t V, int S, 
     for (int t = 0; t < o->max_iter;) {
         const int n = (o->max_iter - t < SWEEP_BATCH) ? o->max_iter - t : SWEEP_BATCH;
         for (int i = 0; i < n; ++i)
-            VBH_S_CK(cudaLaunchKernel(sweep, dim3(unsigned(grid)), dim3(ki.threads), args, ki.smem, s));
+            VBH_S_CK(cudaLaunchKernel(sweep, dim3(unsigned(grid)), dim3(ki.threads), args, smem, s));
         t += n;
         if (t >= o->max_iter) break;
         VBH_S_CK(cudaMemcpyAsync(&ctl, &st->iter, sizeof(ctl), cudaMemcpyDeviceToHost, s));

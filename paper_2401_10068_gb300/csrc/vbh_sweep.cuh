@@ -57,6 +57,16 @@ struct SweepCfg {
     static constexpr uint32_t STAGE_BYTES = R_BYTES + D_BYTES;
     static constexpr size_t RING_BYTES = size_t(STAGES) * STAGE_BYTES;
     static constexpr size_t SMEM_BYTES = RING_BYTES + 64;   // + mbarriers
+    // compensated form: a ring of STAGES_C stages (two at S = 8, so that two blocks
+    // and their tables fit in an SM's shared memory), the table of profile terms
+    // (2^S entries of 32 bytes) and the split pass globals
+    static constexpr int STAGES_C = (S == 8) ? 2 : 3;
+    static constexpr size_t RING_BYTES_C = size_t(STAGES_C) * STAGE_BYTES;
+    static constexpr size_t TAB_BYTES = size_t(32) << S;
+    static constexpr int SPLIT_FLOATS = 2 * NG + 2 * M;
+    static constexpr size_t SPLIT_BYTES = ((size_t(SPLIT_FLOATS) * 4 + 63) / 64) * 64 + 64;
+    static constexpr size_t OFF_TAB = RING_BYTES_C, OFF_SPLIT = OFF_TAB + TAB_BYTES;
+    static constexpr size_t SMEM_BYTES_C = OFF_SPLIT + SPLIT_BYTES + 64;   // + mbarriers
 };
 
 // Load the S profile entries of row j of a shared-memory tile with the widest
@@ -171,21 +181,22 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
     e = (a - (s - bb)) + (b - bb);
 }
 
+// The profile-only terms of the compensated pass for one D (y enters only
+// through e = y - t): t = th + tl, 1 + E[rho] q = dh + dl, h = 1/(1 + E[rho] q)
+// (FP32), c = E[rho] h = ch + cl, and q h (FP32).  split: Sh[NG], Sl[NG],
+// kh[M], kl[M] (the split pass globals, in shared memory).
+struct ProfileTerms {
+    float th, tl, dh, dl, h, ch, cl, qh;
+};
+
 template <int S>
-__device__ __forceinline__ void observe_comp(const float (&x)[S], float rr, const float (&Sh)[SweepCfg<S>::NGA],
-                                             const float (&Sl)[SweepCfg<S>::NGA], const float (&kh)[SweepCfg<S>::MA],
-                                             const float (&kl)[SweepCfg<S>::MA], float erho,
-                                             float (&acc)[SweepCfg<S>::NSTAT], float &ph, float &pl, float &uh,
-                                             float &ul)
+__device__ __forceinline__ ProfileTerms profile_terms(const float (&D)[SweepCfg<S>::MA], const float *__restrict__ split,
+                                                      float erho)
 {
     using C = SweepCfg<S>;
-    constexpr int M = C::M;
-    const float dS = x[S - 1];
-    const float y = rr - dS;
-    float D[C::MA];
+    constexpr int M = C::M, NG = C::NG;
+    const float *Sh = split, *Sl = split + NG, *kh = split + 2 * NG, *kl = split + 2 * NG + M;
     float qh = 0.0f, ql = 0.0f, th = 0.0f, tl = 0.0f;
-#pragma unroll
-    for (int j = 0; j < M; ++j) D[j] = x[j] - dS;
 #pragma unroll
     for (int j = 0; j < M; ++j) {
 #pragma unroll
@@ -198,26 +209,83 @@ __device__ __forceinline__ void observe_comp(const float (&x)[S], float rr, cons
         th = fmaf(kh[j], D[j], th);
         tl = fmaf(kl[j], D[j], tl);
     }
-    float eh, el;                                          // e = y - t
-    two_sum(y, -th, eh, el);
-    el -= tl;
+    ProfileTerms pt;
+    pt.th = th;
+    pt.tl = tl;
     const float p = erho * qh;                             // 1 + E[rho] q = dh + dl
     const float pe = fmaf(erho, qh, -p);
     const float big = fmaxf(1.0f, p), sml = fminf(1.0f, p);
-    const float dh = big + sml;
-    const float dl = fmaf(erho, ql, (sml - (dh - big)) + pe);
-    float h = rcp_approx(dh);                              // 1/(1 + E[rho] q) = h + hl
-    h = fmaf(h, fmaf(-dh, h, 1.0f), h);
-    const float res = fmaf(-dl, h, fmaf(-dh, h, 1.0f));
+    pt.dh = big + sml;
+    pt.dl = fmaf(erho, ql, (sml - (pt.dh - big)) + pe);
+    float h = rcp_approx(pt.dh);                           // 1/(1 + E[rho] q) = h + hl
+    h = fmaf(h, fmaf(-pt.dh, h, 1.0f), h);
+    const float res = fmaf(-pt.dl, h, fmaf(-pt.dh, h, 1.0f));
     const float hl = h * res;
-    const float ch = erho * h;                             // c = ch + cl
-    const float cl = fmaf(erho, hl, fmaf(erho, h, -ch));
+    pt.h = h;
+    pt.ch = erho * h;                                      // c = ch + cl
+    pt.cl = fmaf(erho, hl, fmaf(erho, h, -pt.ch));
+    pt.qh = (qh + ql) * h;
+    return pt;
+}
+
+// The table of profile terms for 0/1 profiles: entry `code` (bit j = d_j,
+// j < S) holds the ProfileTerms of D_j = d_j - d_S as two float4.  Built by
+// threads t0, t0 + nt, ... of the block.
+template <int S>
+__device__ __forceinline__ void build_profile_table(float4 *__restrict__ tab, const float *__restrict__ split,
+                                                    float erho, int t0, int nt)
+{
+    using C = SweepCfg<S>;
+    for (int code = t0; code < (1 << S); code += nt) {
+        const float dS = float((code >> (S - 1)) & 1);
+        float D[C::MA];
+#pragma unroll
+        for (int j = 0; j < C::MA; ++j) D[j] = (j < C::M) ? float((code >> j) & 1) - dS : 0.0f;
+        const ProfileTerms pt = profile_terms<S>(D, split, erho);
+        tab[2 * code] = make_float4(pt.th, pt.tl, pt.dh, pt.dl);
+        tab[2 * code + 1] = make_float4(pt.h, pt.ch, pt.cl, pt.qh);
+    }
+}
+
+// Steps (a)-(c) of the compensated pass for one observation: the profile
+// terms from the table when every d_ij is 0 or 1, else computed; then the
+// FP32 statistics of the update, U += c e^2 and the two-part running product.
+template <int S>
+__device__ __forceinline__ void observe_comp(const float (&x)[S], float rr, const float4 *__restrict__ tab,
+                                             const float *__restrict__ split, float erho,
+                                             float (&acc)[SweepCfg<S>::NSTAT], float &ph, float &pl, float &uh,
+                                             float &ul)
+{
+    using C = SweepCfg<S>;
+    constexpr int M = C::M;
+    const float dS = x[S - 1];
+    const float y = rr - dS;
+    float D[C::MA];
+#pragma unroll
+    for (int j = 0; j < M; ++j) D[j] = x[j] - dS;
+    // code = sum d_j 2^j (exact for 0/1 entries); bad = sum |d_j - d_j^2| is 0 exactly when every d_j is 0 or 1
+    float code = 0.0f, bad = 0.0f;
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+        code = fmaf(x[j], float(1 << j), code);
+        bad += fabsf(fmaf(-x[j], x[j], x[j]));
+    }
+    ProfileTerms pt;
+    if (bad == 0.0f) {
+        const int c = __float2int_rz(code);
+        const float4 t0 = tab[2 * c], t1 = tab[2 * c + 1];
+        pt = ProfileTerms{t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
+    } else {
+        pt = profile_terms<S>(D, split, erho);
+    }
+    float eh, el;                                          // e = y - t
+    two_sum(y, -pt.th, eh, el);
+    el -= pt.tl;
     // the FP32 statistics of the update
-    const float q = qh + ql;
-    const float w = ch * eh;
-    const float gam = fmaf(w, w, -ch);
-    const float ei = eh * h;
-    acc[C::I_T3] += fmaf(ei, ei, q * h);
+    const float w = pt.ch * eh;
+    const float gam = fmaf(w, w, -pt.ch);
+    const float ei = eh * pt.h;
+    acc[C::I_T3] += fmaf(ei, ei, pt.qh);
 #pragma unroll
     for (int j = 0; j < M; ++j) {
         acc[C::I_g + j] = fmaf(w, D[j], acc[C::I_g + j]);
@@ -228,15 +296,15 @@ __device__ __forceinline__ void observe_comp(const float (&x)[S], float rr, cons
     // U += c e^2
     const float e2h = eh * eh;
     const float e2l = fmaf(eh + eh, el, fmaf(eh, eh, -e2h));
-    const float u = ch * e2h;
-    const float ue = fmaf(cl, e2h, fmaf(ch, e2l, fmaf(ch, e2h, -u)));
+    const float u = pt.ch * e2h;
+    const float ue = fmaf(pt.cl, e2h, fmaf(pt.ch, e2l, fmaf(pt.ch, e2h, -u)));
     float su, sue;
     two_sum(uh, u, su, sue);
     uh = su;
     ul += sue + ue;
     // running product of (1 + E[rho] q)
-    const float m = ph * dh;
-    const float me = fmaf(pl, dh, fmaf(ph, dl, fmaf(ph, dh, -m)));
+    const float m = ph * pt.dh;
+    const float me = fmaf(pl, pt.dh, fmaf(ph, pt.dl, fmaf(ph, pt.dh, -m)));
     ph = m + me;
     pl = me - (ph - m);
 }
@@ -1034,10 +1102,15 @@ __global__ void __launch_bounds__(SweepCfg<S>::THREADS, COMP ? SweepCfg<S>::MINB
     constexpr int M = C::M, NG = C::NG, NSTAT = C::NSTAT;
     constexpr int NS = COMP ? C::NSTATC : C::NSTAT;        // columns of a partial row
     constexpr int NGR = COMP ? C::NGRPC : C::NGRP;
-    constexpr int THREADS = C::THREADS, T = C::T, STAGES = C::STAGES;
+    constexpr int THREADS = C::THREADS, T = C::T;
+    constexpr int STAGES = COMP ? C::STAGES_C : C::STAGES;
+    constexpr size_t BAR_OFF = COMP ? C::SMEM_BYTES_C - 64 : C::RING_BYTES;
     static_assert(!COMP || S <= S_FP32_MAX, "compensated form: S <= 11");
+    static_assert(size_t(gu_ws_doubles_rt(M)) * 8 <= size_t(STAGES) * C::STAGE_BYTES, "workspace exceeds the ring");
     extern __shared__ __align__(128) unsigned char smem[];
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + C::RING_BYTES);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + BAR_OFF);
+    float4 *tab = reinterpret_cast<float4 *>(smem + C::OFF_TAB);     // compensated form only
+    float *split = reinterpret_cast<float *>(smem + C::OFF_SPLIT);
     __shared__ int s_bad, s_last;
 
     DevState *st = a.st;
@@ -1059,36 +1132,28 @@ __global__ void __launch_bounds__(SweepCfg<S>::THREADS, COMP ? SweepCfg<S>::MINB
     for (int g = 0; g < NGR; ++g) acc64[g] = 0.0;
 
     if (run) {
-        // plain form: L~ (in A) and kappa~ (in B); compensated form: the grid
-        // and rest parts of Sigma0~ (A, A2) and kappa~ (B, B2)
-        float A[C::NGA], B[C::MA], A2[COMP ? C::NGA : 1], B2[COMP ? C::MA : 1];
+        // plain form: L~ and kappa~ in registers; compensated form: the split
+        // globals in shared memory, and the table of profile terms built from them
+        float A[COMP ? 1 : C::NGA], B[COMP ? 1 : C::MA];
         const float erho = st->sw.erho;          // 0 in sweep 0 of a CAVI fit from the paper's start: c_i = 0
         if constexpr (COMP) {
-#pragma unroll
-            for (int i = 0; i < NG; ++i) {
-                A[i] = st->sw.Sh[i];
-                A2[i] = st->sw.Sl[i];
+            for (int i = tid; i < C::SPLIT_FLOATS; i += THREADS) {
+                float v;
+                if (i < NG) v = st->sw.Sh[i];
+                else if (i < 2 * NG) v = st->sw.Sl[i - NG];
+                else if (i < 2 * NG + M) v = st->sw.kh[i - 2 * NG];
+                else v = st->sw.kl[i - 2 * NG - M];
+                split[i] = v;
             }
-#pragma unroll
-            for (int i = 0; i < M; ++i) {
-                B[i] = st->sw.kh[i];
-                B2[i] = st->sw.kl[i];
-            }
+            A[0] = 0.0f;
+            B[0] = 0.0f;
         } else {
 #pragma unroll
             for (int i = 0; i < NG; ++i) A[i] = st->sw.L[i];
 #pragma unroll
             for (int i = 0; i < M; ++i) B[i] = st->sw.kappa[i];
-            A2[0] = 0.0f;
-            B2[0] = 0.0f;
-        }
-        if constexpr (NG == 0) {
-            A[0] = 0.0f;
-            if constexpr (COMP) A2[0] = 0.0f;
-        }
-        if constexpr (M == 0) {
-            B[0] = 0.0f;
-            if constexpr (COMP) B2[0] = 0.0f;
+            if constexpr (NG == 0) A[0] = 0.0f;
+            if constexpr (M == 0) B[0] = 0.0f;
         }
 
         const long long V = a.V;
@@ -1110,6 +1175,10 @@ __global__ void __launch_bounds__(SweepCfg<S>::THREADS, COMP ? SweepCfg<S>::MINB
                 bulk_load(stage + C::R_BYTES, a.d + tile * T * S, C::D_BYTES, &full[k]);
             }
         }
+        if constexpr (COMP) {
+            build_profile_table<S>(tab, split, erho, tid, THREADS);      // overlaps the first copies
+            __syncthreads();
+        }
         long long k = 0;
         int ftile = 0;
         for (; k < nk; ++k) {
@@ -1125,7 +1194,7 @@ __global__ void __launch_bounds__(SweepCfg<S>::THREADS, COMP ? SweepCfg<S>::MINB
                     float x[S];
                     load_row<S>(dt, j, x);
                     if constexpr (COMP) {
-                        observe_comp<S>(x, rt[j], A, A2, B, B2, erho, acc, prod, pl, uh, ul);
+                        observe_comp<S>(x, rt[j], tab, split, erho, acc, prod, pl, uh, ul);
                         if (u & 1) peel_exponent2(prod, pl, ex);
                     } else {
                         observe<S>(x, rt[j], A, B, erho, acc, prod);
@@ -1171,7 +1240,7 @@ __global__ void __launch_bounds__(SweepCfg<S>::THREADS, COMP ? SweepCfg<S>::MINB
 #pragma unroll
                     for (int q = 0; q < S; ++q) x[q] = __ldg(a.d + i * S + q);
                     if constexpr (COMP) {
-                        observe_comp<S>(x, __ldg(a.r + i), A, A2, B, B2, erho, acc, prod, pl, uh, ul);
+                        observe_comp<S>(x, __ldg(a.r + i), tab, split, erho, acc, prod, pl, uh, ul);
                         peel_exponent2(prod, pl, ex);
                     } else {
                         observe<S>(x, __ldg(a.r + i), A, B, erho, acc, prod);
