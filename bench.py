@@ -507,6 +507,18 @@ def other_workloads(dev, stream):
         row[key] = {"fits_per_s": 1.0 / sec, "converged_datasets_per_s": (1.0 / sec) if res["converged"] else 0.0,
                     "converged": bool(res["converged"]), "sweeps": res["iters"], "us_per_sweep": 1e6 * sec /
                     (res["iters"] + 1), "elbo": res["elbo"]}
+    # device time per sweep of the two sweep loops (200 sweeps in one vbh_fit_step, statistics as at tol > 0);
+    # vbh_fit above runs the resident loop (VBH_LOOP_AUTO: the data set fits in shared memory)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for name, loop in (("resident_loop", vbh.LOOP_RESIDENT), ("stream_loop", vbh.LOOP_STREAM)):
+        h.fit_begin(r1, d1, SINGLE["S"], None, tol=0.0, max_iter=205, stats=vbh.STATS_COMPENSATED, loop=loop)
+        h.fit_step(5)
+        torch.cuda.synchronize(dev)
+        ev0.record(stream)
+        h.fit_step(200)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        row[name] = {"us_per_sweep": ev0.elapsed_time(ev1) * 1e3 / 200}
     out["single"] = row
     del r1, d1
     # batched

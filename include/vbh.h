@@ -85,6 +85,20 @@ extern "C" {
                                     convergence, not by noise.  About 1.5x the arithmetic per observation. */
 #define VBH_STATS_PLAIN 2        /* FP32 statistics only (the fastest pass; ELBO noise ~1e-8 |L|) */
 
+/* sweep loop of the per-observation FP32 sweep, S <= 11, not grouped (vbh_opts.loop) */
+#define VBH_LOOP_AUTO 0          /* VBH_LOOP_RESIDENT when the data set fits, else VBH_LOOP_STREAM */
+#define VBH_LOOP_STREAM 1        /* one launch per sweep, reading (r, d) from device memory (the sweep loop of
+                                    vbh_create's note) */
+#define VBH_LOOP_RESIDENT 2      /* one cooperative launch per vbh_fit_step call runs all its sweeps: every block
+                                    keeps a slice of (r, d) in shared memory, and the blocks meet at one grid
+                                    barrier per sweep, after which each runs the FP64 global update on the same
+                                    partial sums (identical results in every block).  The data set must fit in
+                                    the shared memory of one block per SM: about 14,000 observations per SM at
+                                    S = 3, 3,000 at S = 11 with the compensated statistics (VBH_EUNSUPPORTED
+                                    otherwise).  Same arithmetic per observation as the streaming sweep; the
+                                    sums are taken over other blocks, so results agree to FP32 rounding.  A
+                                    barrier wait that runs out (2 s) ends the fit with VBH_ETIMEOUT. */
+
 /* initial state of a fit */
 #define VBH_INIT_PAPER 0         /* Q(beta_i) = N(K0, Lambda_0^{-1}) before sweep 0 (Section 3.5) */
 #define VBH_INIT_GIVEN 1         /* start from the global factors in vbh_opts.init_state (warm start / resume) */
@@ -142,22 +156,26 @@ typedef struct {
     int stats;                   /* VBH_STATS_AUTO (0), VBH_STATS_COMPENSATED or VBH_STATS_PLAIN; only the
                                     CUDA-core sweeps (S <= 11, not grouped) have the compensated form, the
                                     others ignore it.  vbh_elbo always uses the compensated form there. */
+    int loop;                    /* VBH_LOOP_AUTO (0), VBH_LOOP_STREAM or VBH_LOOP_RESIDENT: how vbh_fit and
+                                    vbh_fit_step run the sweeps (sweep 0 of a fit always streams) */
 } vbh_opts;
 
 /* Fill *p with the paper's prior for S subpopulations (Section 3.5). */
 void vbh_prior_default(int S, vbh_prior *p);
 
 /* Fill *o with tol = 1e-8, max_iter = 200, VBH_FP32, VBH_INIT_PAPER, refine_iters = 10, no trace,
- * VBH_CAVI, not grouped, VBH_STATS_AUTO. */
+ * VBH_CAVI, not grouped, VBH_STATS_AUTO, VBH_LOOP_AUTO. */
 void vbh_opts_default(vbh_opts *o);
 
 /* Create a handle on CUDA device `device` that issues all work on `stream`
  * (a cudaStream_t; NULL = the legacy default stream).  The stream is borrowed:
  * it must outlive the handle.  Returns VBH_EINVAL for a bad device.
- * The sweep loop runs as a CUDA graph with a conditional while node; with the
- * environment variable VBH_LAUNCH=direct at creation the handle instead issues
- * one kernel launch per sweep (same kernels and results; for profilers that
- * cannot look inside conditional graphs). */
+ * The streaming sweep loop (VBH_LOOP_STREAM) runs as a CUDA graph with a
+ * conditional while node; with the environment variable VBH_LAUNCH=direct at
+ * creation the handle instead issues one kernel launch per sweep (same kernels
+ * and results; for profilers that cannot look inside conditional graphs).  The
+ * resident loop (VBH_LOOP_RESIDENT) sizes its blocks for about
+ * VBH_RESIDENT_OBS (environment, default 8) observations per thread and sweep. */
 int vbh_create(vbh_handle **h, int device, void *stream);
 
 /* Release every resource of the handle (NULL is allowed). */
@@ -183,6 +201,17 @@ const char *vbh_last_error_detail(void);
  * the copied bytes are right).  *waited_ns receives the time the first wait
  * took.  Allocates and frees about 1 KiB of device memory; synchronous. */
 int vbh_selftest_wait(int device, void *stream, uint64_t budget_ns, int *status, uint64_t *waited_ns);
+
+/* Diagnostic of two short-latency FP64 functions of the global updates, out[i]
+ * = f(x[i]) for n (1 .. 2^24) host doubles:
+ *   fn 0: the natural logarithm the resident sweep loop's ELBO uses (Tang's
+ *         table-driven method: 128 tabulated ln F and 1/F, F = 1 + j/128, and
+ *         a degree-8 series of ln(1 + u), |u| < 2^-7); absolute error a few
+ *         units in the last place of max(|ln x|, ln 2);
+ *   fn 1: the reciprocal square root of the Cholesky factorisations (an FP32
+ *         seed and one third-order correction); within about an ulp.
+ * Allocates and frees 16 n bytes of device memory; synchronous. */
+int vbh_selftest_math(int device, void *stream, int fn, const double *x, double *out, int n);
 
 /* Bytes of the device-resident fit state that each vbh_fit_begin,
  * vbh_fit_step and vbh_fit_result call copies back to the host (a vbh_fit

@@ -44,6 +44,13 @@ struct Launch {
     int threads() const { return grp ? vbh::GROUPED_THREADS : tc ? tki.threads : ki.threads; }
     size_t smem() const { return grp ? vbh::grouped_smem_bytes() : tc ? tki.smem : comp ? ki.smem_comp : ki.smem; }
     int tile() const { return tc ? tki.tile : ki.tile; }
+    // the resident sweep loop (S <= 11, CUDA-core sweep): one cooperative launch per step
+    bool res = false;
+    int res_grid = 0;
+    int res_per_block = 0;
+    int res_ns = 0;                         // columns of its partial rows
+    size_t res_smem = 0;
+    const void *res_func() const { return comp ? ki.resident_comp : ki.resident; }
 };
 
 struct vbh_handle {
@@ -92,6 +99,13 @@ struct vbh_handle {
     const void *g_func = nullptr;
     bool attr_set[vbh::SMAX + 1] = {};
     bool direct = false;               // VBH_LAUNCH=direct: one stream launch per sweep, no graph
+    // the resident sweep loop
+    bool coop = false;                 // the device supports cooperative launches
+    int smem_optin = 0;                // dynamic shared memory a block may opt in to
+    int res_obs = 8;                   // observations per thread and sweep the block count aims at
+    size_t res_attr[vbh::S_FP32_MAX + 1][2] = {};   // shared memory the resident kernels were opted in to
+    DevState *res_priv = nullptr;      // private state copies of blocks 1 ..
+    size_t res_priv_cap = 0;           // bytes
     vbh::BatchedHost batched;          // buffers of vbh_fit_batched
 };
 
@@ -314,15 +328,43 @@ void fill_prior(DevState *s, const vbh_prior *p, int S, long long V)
 
 // Kernel choice, launch shape and partials buffer of a fit of (V, S).  For the
 // tensor-core path the BF16 profiles and the tensor maps are prepared too.
+// Shape of the resident sweep loop for (V, S): blocks of at most
+// res_obs x threads observations, fewer and larger ones when the SMs would not
+// suffice, none (false) when the data set does not fit in the shared memory of
+// h->nsm blocks.
+bool resident_shape(const vbh_handle *h, const KernelInfo &ki, bool comp, long long V, int *grid, int *per_block,
+                    int *ns, size_t *smem)
+{
+    if (V <= 0 || !h->coop) return false;
+    const size_t fixed = comp ? ki.res_fixed_comp : ki.res_fixed;
+    const size_t budget = size_t(h->smem_optin) - 1024;        // room for the kernel's static shared memory
+    if (budget <= fixed + 64 * ki.res_obs_bytes) return false;
+    const long long cap = (static_cast<long long>(budget - fixed) / static_cast<long long>(ki.res_obs_bytes)) & ~3LL;
+    const long long want = (long long)ki.res_threads * h->res_obs;
+    const int rows = comp ? ki.res_max_blocks_comp : ki.res_max_blocks;   // rows the block's buffer holds
+    const long long nb_max = h->nsm < rows ? h->nsm : rows;
+    long long nb = (V + want - 1) / want;
+    if (nb > nb_max) nb = nb_max;
+    long long per = (((V + nb - 1) / nb) + 3) & ~3LL;
+    if (per > cap) per = cap;
+    nb = (V + per - 1) / per;
+    if (nb > nb_max) return false;
+    *grid = int(nb);
+    *per_block = int(per);
+    *ns = comp ? ki.nstat + 1 : ki.nstat;
+    *smem = fixed + size_t(per) * ki.res_obs_bytes;
+    return true;
+}
+
 int prepare_launch(vbh_handle *h, int S, long long V, int precision, const float *rd, const float *dd, Launch *L,
-                   bool grouped = false, bool comp = false)
+                   bool grouped = false, bool comp = false, int loop = VBH_LOOP_STREAM)
 {
     L->S = S;
     const int M = S - 1;
     const size_t nstat = size_t(M * (M + 1) / 2 + M + 4);   // room for the compensated form's extra column
     if (grouped) {
         // one histogram pass, then sweeps over the 2^S profile codes
-        if (S > vbh::GROUPED_SMAX) return VBH_EUNSUPPORTED;
+        if (S > vbh::GROUPED_SMAX || loop == VBH_LOOP_RESIDENT) return VBH_EUNSUPPORTED;
         L->grp = true;
         L->P = 1 << S;
         if (!vbh::tc_kernel_info(3, &L->tki)) return VBH_EUNSUPPORTED;          // the runtime-M set-up kernel
@@ -376,8 +418,34 @@ int prepare_launch(vbh_handle *h, int S, long long V, int precision, const float
     if (g > vbh::GRID_MAX) g = vbh::GRID_MAX;
     if (g < 1) g = 1;
     L->grid = int(g);
-    int rc = ensure(reinterpret_cast<void **>(&h->partials), &h->partials_cap,
-                    size_t(vbh::partial_rows(g)) * nstat * sizeof(double));
+    long long rows = vbh::partial_rows(g);
+    if (!L->tc && loop != VBH_LOOP_STREAM) {
+        L->res = resident_shape(h, L->ki, L->comp, V, &L->res_grid, &L->res_per_block, &L->res_ns, &L->res_smem);
+        if (!L->res && loop == VBH_LOOP_RESIDENT) return VBH_EUNSUPPORTED;
+        if (L->res) {
+            int per = 0;
+            size_t &set = h->res_attr[S][L->comp ? 1 : 0];
+            if (set < L->res_smem) {
+                VBH_CK(cudaFuncSetAttribute(L->res_func(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            int(L->res_smem)));
+                set = L->res_smem;
+            }
+            VBH_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, L->res_func(), L->ki.res_threads, L->res_smem));
+            if (per < 1) {
+                L->res = false;
+                if (loop == VBH_LOOP_RESIDENT) return VBH_EUNSUPPORTED;
+            }
+        }
+        if (L->res) {
+            if (2LL * L->res_grid > rows) rows = 2LL * L->res_grid;
+            int rc = ensure(reinterpret_cast<void **>(&h->res_priv), &h->res_priv_cap,
+                            sizeof(DevState) * size_t(L->res_grid > 1 ? L->res_grid - 1 : 1));
+            if (rc) return rc;
+        }
+    } else if (loop == VBH_LOOP_RESIDENT) {
+        return VBH_EUNSUPPORTED;
+    }
+    int rc = ensure(reinterpret_cast<void **>(&h->partials), &h->partials_cap, size_t(rows) * nstat * sizeof(double));
     if (rc) return rc;
     if (L->tc && V > 0) {
         if ((rc = ensure(&h->tc_tiles, &h->tc_cap, vbh::tc_input_bytes(V)))) return rc;
@@ -430,6 +498,25 @@ int launch_sweep(vbh_handle *h, DevState *st, int mode, Launch &L, const float *
         void *args[] = {&a};
         VBH_CK(cudaLaunchKernel(L.func(), dim3(L.grid), dim3(L.ki.threads), args, L.smem(), h->stream));
     }
+    return VBH_OK;
+}
+
+// Every sweep of a step in one cooperative launch of the resident kernel.
+int launch_resident(vbh_handle *h)
+{
+    Launch &L = h->L;
+    vbh::ResidentArgs ra{};
+    ra.r = h->r;
+    ra.d = h->d;
+    ra.V = h->V;
+    ra.st = h->st;
+    ra.priv = h->res_priv;
+    ra.partials = h->partials;
+    ra.per_block = L.res_per_block;
+    VBH_CK(cudaMemsetAsync(h->partials, 0, sizeof(double) * 2 * size_t(L.res_grid) * L.res_ns, h->stream));
+    void *args[] = {&ra};
+    VBH_CK(cudaLaunchCooperativeKernel(L.res_func(), dim3(L.res_grid), dim3(L.ki.res_threads), args, L.res_smem,
+                                       h->stream));
     return VBH_OK;
 }
 
@@ -597,6 +684,7 @@ void vbh_opts_default(vbh_opts *o)
     o->method = VBH_CAVI;
     o->grouped = 0;
     o->stats = VBH_STATS_AUTO;
+    o->loop = VBH_LOOP_AUTO;
     o->init = VBH_INIT_PAPER;
     o->init_state = nullptr;
     o->elbo_trace = nullptr;
@@ -646,8 +734,18 @@ int vbh_create(vbh_handle **hp, int device, void *stream)
     h->stream = static_cast<cudaStream_t>(stream);
     const char *launch = std::getenv("VBH_LAUNCH");
     h->direct = launch && std::strcmp(launch, "direct") == 0;
+    if (const char *ro = std::getenv("VBH_RESIDENT_OBS")) {
+        const int v = std::atoi(ro);
+        if (v >= 1 && v <= 4096) h->res_obs = v;
+    }
+    int coop = 0;
     int rc = failed(cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, device),
                     "cudaDeviceGetAttribute(MultiProcessorCount)", __LINE__, VBH_ECUDA);
+    if (!rc) rc = failed(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device),
+                         "cudaDeviceGetAttribute(CooperativeLaunch)", __LINE__, VBH_ECUDA);
+    if (!rc) rc = failed(cudaDeviceGetAttribute(&h->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device),
+                         "cudaDeviceGetAttribute(MaxSharedMemoryPerBlockOptin)", __LINE__, VBH_ECUDA);
+    h->coop = coop != 0;
     if (!rc) rc = failed(cudaMalloc(&h->st, sizeof(DevState)), "cudaMalloc(state)", __LINE__, VBH_ENOMEM);
     if (!rc) rc = failed(cudaMalloc(&h->st_aux, sizeof(DevState)), "cudaMalloc(state)", __LINE__, VBH_ENOMEM);
     if (!rc) rc = failed(cudaMallocHost(&h->mirror, sizeof(DevState)), "cudaMallocHost(mirror)", __LINE__, VBH_ENOMEM);
@@ -681,6 +779,7 @@ void vbh_destroy(vbh_handle *h)
     cudaFree(h->tc_tiles);
     cudaFree(h->gstats);
     cudaFree(h->counts);
+    cudaFree(h->res_priv);
     if (h->mirror) cudaFreeHost(h->mirror);
     for (int i = 0; i < vbh_handle::NCOPY; ++i)
         if (h->copy_stream[i]) {
@@ -717,9 +816,10 @@ int vbh_fit_begin(vbh_handle *h, const float *r, const float *d, int64_t V, int 
     if (o->grouped != 0 && o->grouped != 1) return VBH_EINVAL;
     if (o->stats != VBH_STATS_AUTO && o->stats != VBH_STATS_COMPENSATED && o->stats != VBH_STATS_PLAIN)
         return VBH_EINVAL;
+    if (o->loop != VBH_LOOP_AUTO && o->loop != VBH_LOOP_STREAM && o->loop != VBH_LOOP_RESIDENT) return VBH_EINVAL;
     const bool comp = o->stats == VBH_STATS_COMPENSATED || (o->stats == VBH_STATS_AUTO && o->tol > 0.0);
     Launch L;
-    if ((rc = prepare_launch(h, S, V, o->precision, rd, dd, &L, o->grouped == 1, comp))) return rc;
+    if ((rc = prepare_launch(h, S, V, o->precision, rd, dd, &L, o->grouped == 1, comp, o->loop))) return rc;
     if (o->max_iter + 1 > h->trace_cap) {
         size_t cap = 0;
         cudaFree(h->trace);
@@ -801,7 +901,9 @@ int run_sweeps(vbh_handle *h, int n)
     int rc = VBH_OK;
     vbh::set_target_kernel<<<1, 32, 0, h->stream>>>(h->st, n);
     VBH_CK(cudaGetLastError());
-    if (h->direct) {
+    if (h->L.res) {
+        if ((rc = launch_resident(h))) return rc;
+    } else if (h->direct) {
         // each launch checks the control fields first and does nothing once the
         // fit has converged or reached its target
         const int m = n < h->max_iter ? n : h->max_iter;

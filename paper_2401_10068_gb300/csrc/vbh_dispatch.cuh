@@ -14,6 +14,14 @@ struct KernelInfo {
     int threads;           // block size of the sweep
     int tile;              // observations per tile
     int nstat;             // statistics per block partial (plain form; the compensated form has nstat + 1)
+    const void *resident;      // resident_kernel<S, false>: every sweep of a step in one cooperative launch
+    const void *resident_comp; // resident_kernel<S, true>
+    size_t res_fixed;          // its dynamic shared memory before the slice of observations
+    size_t res_fixed_comp;
+    size_t res_obs_bytes;      // shared memory per resident observation
+    int res_threads;
+    int res_max_blocks;        // blocks whose partial rows a block's buffer holds
+    int res_max_blocks_comp;
 };
 
 // Kernels of the batched form for one S class.
@@ -52,6 +60,14 @@ bool batch_kernel_info_s9_11(int S, BatchKernelInfo *out);
         out->threads = C::THREADS;                                                                                     \
         out->tile = C::T;                                                                                              \
         out->nstat = C::NSTAT;                                                                                         \
+        out->resident = reinterpret_cast<const void *>(&::vbh::resident_kernel<SV, false>);                            \
+        out->resident_comp = reinterpret_cast<const void *>(&::vbh::resident_kernel<SV, true>);                        \
+        out->res_fixed = ::vbh::ResidentCfg<SV, false>::OFF_SLICE;                                                     \
+        out->res_fixed_comp = ::vbh::ResidentCfg<SV, true>::OFF_SLICE;                                                 \
+        out->res_obs_bytes = ::vbh::ResidentCfg<SV, false>::OBS_BYTES;                                                 \
+        out->res_threads = ::vbh::ResidentCfg<SV, false>::THREADS;                                                     \
+        out->res_max_blocks = ::vbh::ResidentCfg<SV, false>::RB_ROWS;                                                  \
+        out->res_max_blocks_comp = ::vbh::ResidentCfg<SV, true>::RB_ROWS;                                              \
         return true;                                                                                                   \
     }
 

@@ -102,6 +102,12 @@ struct DevState {
     double prior_const;
     int prior_dropped, pad1;
     SweepGlobalsF32 sw;
+    // ln|W^{-1}| and the Cholesky pivots of W^{-1} behind the current pass
+    // factors (S <= 11), left by the last update for the resident loop's ELBO
+    // of the next sweep; carry_ok = 0 after a set-up (the factors were given)
+    double carry_ldw;
+    double carry_piv[S_FP32_MAX - 1];
+    int carry_ok, pad2;
 };
 
 // Arguments of one launch of the fused sweep kernel.
@@ -114,6 +120,18 @@ struct SweepArgs {
     cudaGraphConditionalHandle cond;  // while-loop condition of the sweep graph
     int use_cond;
     int mode;
+};
+
+// Arguments of the resident sweep loop (every sweep of a step in one
+// cooperative launch, the observations held in shared memory).
+struct ResidentArgs {
+    const float *r;
+    const float *d;
+    long long V;
+    DevState *st;        // the fit's state (block 0)
+    DevState *priv;      // [gridDim.x - 1] private state copies (blocks 1 ..)
+    double *partials;    // [2][gridDim.x][statistics per block], zero at launch
+    int per_block;       // observations of every block but the last (a multiple of 4)
 };
 
 // ---------------------------------------------------------------------------
@@ -385,6 +403,74 @@ __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Natural logarithm of a positive normal double by the table-driven method of
+// P. T. P. Tang ("Table-driven implementation of the logarithm function in
+// IEEE floating-point arithmetic", ACM TOMS 16(4), 1990): x = 2^e m with m in
+// [1, 2); F = 1 + j/128 from the leading seven fraction bits of m, f = m - F
+// (exact), u = f / F in [0, 2^-7) (as f times a tabulated 1/F); then
+//   ln x = e ln 2 + ln F + ln(1 + u),
+// ln(1 + u) = sum_{i=1..8} (-1)^(i+1) u^i / i (truncation below 2^-59),
+// evaluated in Estrin's scheme (dependency depth 6 instead of 9).  ln F and
+// 1/F are tabulated by the block at start-up (ln F by the library logarithm).
+// The absolute error is within a few units in the last place of
+// max(|ln x|, ln 2); zero, negative, subnormal and non-finite x take the
+// library path.
+// ---------------------------------------------------------------------------
+constexpr double LN2_HI = 0.6931471805599453094;      // ln 2 rounded to double
+constexpr double LN2_LO = 2.319046813846299558e-17;   // ln 2 - LN2_HI
+
+__device__ inline void log_tang_table(double *tab, int t0, int nt)
+{
+    for (int j = t0; j < 128; j += nt) {
+        const double F = 1.0 + double(j) * (1.0 / 128.0);
+        tab[j] = 1.0 / F;
+        tab[128 + j] = log(F);
+    }
+}
+
+__device__ __forceinline__ double log_tang(double x, const double *tab)
+{
+    const long long b = __double_as_longlong(x);
+    const int eb = int((b >> 52) & 0x7ff);
+    if (b <= 0 || eb == 0 || eb == 0x7ff) return log(x);      // <= 0, -0, subnormal, inf, nan
+    const int j = int((b >> 45) & 127);
+    const double m = __longlong_as_double((b & 0x000fffffffffffffLL) | 0x3ff0000000000000LL);
+    const double F = __longlong_as_double((b & 0x000fe00000000000LL) | 0x3ff0000000000000LL);
+    const double u = (m - F) * tab[j];
+    const double u2 = u * u;
+    const double u4 = u2 * u2;
+    const double p01 = fma(-0.5, u, 1.0);
+    const double p23 = fma(-0.25, u, 1.0 / 3.0);
+    const double p45 = fma(-1.0 / 6.0, u, 0.2);
+    const double p67 = fma(-0.125, u, 1.0 / 7.0);
+    const double q = fma(u4, fma(u2, p67, p45), fma(u2, p23, p01));
+    const double e = double(eb - 1023);
+    return fma(e, LN2_HI, tab[128 + j]) + fma(e, LN2_LO, u * q);
+}
+
+
+// ---------------------------------------------------------------------------
+// 1/sqrt(p) for positive normal p with a short dependency chain: an FP32 seed
+// (p scaled by an even power of two into [1, 4), rsqrtf), then one step of
+// the third-order iteration y' = y (1 + e/2 + 3e^2/8), e = 1 - p y^2 (the
+// binomial series of (1 - e)^(-1/2) to second order); the seed's relative
+// error ~2^-22 leaves ~2^-65 before the final rounding.  Zero, negative,
+// subnormal and non-finite p take the library path.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double rsqrt_fast(double p)
+{
+    const long long b = __double_as_longlong(p);
+    const int eb = int((b >> 52) & 0x7ff);
+    if (b <= 0 || eb == 0 || eb == 0x7ff) return rsqrt(p);
+    const int E2 = (eb - 1023) & ~1;                                   // even, rounded down
+    const double pm = __longlong_as_double(b - ((long long)E2 << 52)); // p 2^-E2 in [1, 4)
+    double y = static_cast<double>(rsqrtf(static_cast<float>(pm)));
+    const double e = fma(-(pm * y), y, 1.0);
+    y = fma(y, e * fma(0.375, e, 0.5), y);
+    return __longlong_as_double(__double_as_longlong(y) - ((long long)(E2 / 2) << 52));
 }
 
 // ---------------------------------------------------------------------------

@@ -1,4 +1,6 @@
-// vbh_selftest.cu -- diagnostic of the bounded device waits (vbh_selftest_wait).
+// vbh_selftest.cu -- diagnostics: the bounded device waits (vbh_selftest_wait)
+// and the short-latency FP64 functions of the global updates
+// (vbh_selftest_math).
 //
 // Every kernel of the library waits on mbarriers (bulk copies landing, MMAs
 // completing) through mbar_wait_bounded / mbar_wait_backoff, which give up
@@ -47,8 +49,50 @@ __global__ void selftest_wait_kernel(const unsigned char *src, unsigned long lon
     out[3] = (c && !bad) ? VBH_OK : VBH_ENONFINITE;
 }
 
+// out[i] = f(x[i]): fn 0 log_tang (its table built by the block as the
+// resident loop builds it), fn 1 rsqrt_fast.
+__global__ void selftest_math_kernel(int fn, const double *x, double *out, int n)
+{
+    __shared__ double tab[256];
+    log_tang_table(tab, threadIdx.x, blockDim.x);
+    __syncthreads();
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        out[i] = (fn == 0) ? log_tang(x[i], tab) : rsqrt_fast(x[i]);
+}
+
 } // namespace
 } // namespace vbh
+
+extern "C" int vbh_selftest_math(int device, void *stream, int fn, const double *x, double *out, int n)
+{
+    if (!x || !out || n < 1 || n > (1 << 24) || fn < 0 || fn > 1) return VBH_EINVAL;
+    int prev = -1;
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (cudaSetDevice(device) != cudaSuccess) return VBH_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    double *mem = nullptr;
+    int rc = VBH_OK;
+    const size_t bytes = sizeof(double) * size_t(n);
+    if (cudaMalloc(&mem, 2 * bytes) != cudaSuccess) {
+        vbh::record_error("cudaMalloc", __FILE__, __LINE__, cudaGetErrorName(cudaGetLastError()));
+        rc = VBH_ENOMEM;
+    }
+    if (!rc) {
+        auto run = [&]() -> int {
+            VBH_CHECK_CUDA(cudaMemcpyAsync(mem, x, bytes, cudaMemcpyHostToDevice, s));
+            const int blocks = (n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024;
+            vbh::selftest_math_kernel<<<blocks, 256, 0, s>>>(fn, mem, mem + n, n);
+            VBH_CHECK_CUDA(cudaGetLastError());
+            VBH_CHECK_CUDA(cudaMemcpyAsync(out, mem + n, bytes, cudaMemcpyDeviceToHost, s));
+            VBH_CHECK_CUDA(cudaStreamSynchronize(s));
+            return VBH_OK;
+        };
+        rc = run();
+    }
+    if (mem) cudaFree(mem);
+    if (prev >= 0) cudaSetDevice(prev);
+    return rc;
+}
 
 extern "C" int vbh_selftest_wait(int device, void *stream, uint64_t budget_ns, int *status, uint64_t *waited_ns)
 {

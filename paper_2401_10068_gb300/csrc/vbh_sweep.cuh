@@ -436,13 +436,17 @@ __device__ __forceinline__ void flush_warp_comp(float (&acc)[SweepCfg<S>::NSTAT]
 // ---------------------------------------------------------------------------
 constexpr int BAR_MAIN = 1, BAR_T3 = 2, BAR_PIV = 3;
 
+// Both are aligned barriers (every thread of the calling warp reaches them
+// together), so the warp reconverges first.
 __device__ __forceinline__ void named_sync(int id, int count)
 {
+    __syncwarp();
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
 __device__ __forceinline__ void named_arrive(int id, int count)
 {
+    __syncwarp();
     asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
@@ -474,6 +478,48 @@ __device__ inline int warp_cholesky_rt(int M, const double *__restrict__ A, doub
                                        double *__restrict__ rd, double *__restrict__ piv, double *__restrict__ col,
                                        int lane)
 {
+    if (M <= 3) {
+        // the same operations in the same order by lane 0 alone, in registers:
+        // for three columns or fewer the warp's shared-memory steps and
+        // synchronisations cost more than they save
+        int fail = 0;
+        if (lane == 0) {
+            double a[3][3];
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) a[i][k] = (i < M && k <= i) ? A[i * M + k] : 0.0;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                if (j >= M) break;
+                double p = a[j][j];
+                const long long pb = __double_as_longlong(p);
+                const bool bad = pb <= 0 || ((pb >> 52) & 0x7ff) == 0x7ff;
+                if (bad) p = 1.0;
+                fail |= bad ? 1 : 0;
+                const double r = rsqrt_fast(p);
+                a[j][j] = p * r;
+                rd[j] = r;
+                piv[j] = p;
+#pragma unroll
+                for (int i = j + 1; i < 3; ++i)
+                    if (i < M) a[i][j] *= r;
+#pragma unroll
+                for (int i = j + 1; i < 3; ++i)
+#pragma unroll
+                    for (int k = j + 1; k <= i; ++k)
+                        if (i < M) a[i][k] = fma(-a[i][j], a[k][j], a[i][k]);
+            }
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int k = 0; k < 3; ++k)
+                    if (i < M && k < M) L[i * M + k] = (k <= i) ? a[i][k] : 0.0;
+        }
+        fail = __shfl_sync(0xffffffffu, fail, 0);
+        __syncwarp();
+        return fail;
+    }
     const int MD = M > 0 ? M : 1;
     for (int e = lane; e < M * M; e += 32) {
         const int r = e / MD, c = e - (e / MD) * MD;
@@ -484,10 +530,11 @@ __device__ inline int warp_cholesky_rt(int M, const double *__restrict__ A, doub
     const int NG = M * (M + 1) / 2;
     for (int j = 0; j < M; ++j) {
         double p = L[j * M + j];
-        const bool bad = !(p > 0.0) || !isfinite(p);
+        const long long pb = __double_as_longlong(p);
+        const bool bad = pb <= 0 || ((pb >> 52) & 0x7ff) == 0x7ff;   // not positive, or not finite (integer tests)
         if (bad) p = 1.0;
         fail |= bad ? 1 : 0;
-        const double r = rsqrt(p);
+        const double r = rsqrt_fast(p);
         __syncwarp();                               // the pivot is read before lane j overwrites it
         if (lane > j && lane < M) {
             const double lij = L[lane * M + j] * r;
@@ -976,6 +1023,7 @@ __device__ __forceinline__ void global_update_rt(int M, DevState *st, const doub
                 }
             }
         }
+        __syncwarp();
         __syncthreads();
         // the split globals of the next compensated pass (from the FP32 L~
         // and kappa~ just written by the other main warps)
@@ -1058,6 +1106,11 @@ __device__ __forceinline__ void global_update_rt(int M, DevState *st, const doub
         st->erho = q;
         st->sw.erho = static_cast<float>(q);
         st->lndetSigma0 = em ? ldW : fma(-double(M), log_nu, ldW);
+        if (M <= S_FP32_MAX - 1) {
+            st->carry_ldw = ldW;
+            for (int j = 0; j < M; ++j) st->carry_piv[j] = piv[j];
+            st->carry_ok = 1;
+        }
         if (mode != MODE_INIT) {
             it = iter + 1;
             conv = (fabs(L - elbo_prev) < tol * fabs(L)) ? 1 : 0;
@@ -1396,6 +1449,7 @@ __device__ inline void setup_state_rt(int M, DevState *st, int init, int lane, d
         st->erho = init ? 0.0 : st->a_rho / st->b_rho;
         st->sw.erho = static_cast<float>(st->erho);
         st->ticket = 0u;
+        st->carry_ok = 0;
         if (fail) st->status = ST_ENONFINITE;
     }
 }

@@ -1,6 +1,7 @@
 // Instantiations of the fused sweep (single and batched forms) for S in {1, 2, 3, 4}.
 #include "vbh_batched.cuh"
 #include "vbh_sweep.cuh"
+#include "vbh_resident.cuh"
 #include "vbh_dispatch.cuh"
 
 namespace vbh {

@@ -26,6 +26,9 @@ INIT_GIVEN = 1
 STATS_AUTO = 0          # compensated statistics when tol > 0 (vbh_opts.stats)
 STATS_COMPENSATED = 1
 STATS_PLAIN = 2
+LOOP_AUTO = 0           # resident sweep loop when the data set fits in shared memory (vbh_opts.loop)
+LOOP_STREAM = 1
+LOOP_RESIDENT = 2
 
 STATUS = {0: "VBH_OK", -1: "VBH_EINVAL", -2: "VBH_ENOMEM", -3: "VBH_ECUDA", -4: "VBH_ENONFINITE",
           -5: "VBH_ETIMEOUT", -6: "VBH_ESTATE", -7: "VBH_EUNSUPPORTED"}
@@ -76,7 +79,8 @@ class Result(ctypes.Structure):
 class Opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("precision", ctypes.c_int),
                 ("init", ctypes.c_int), ("refine_iters", ctypes.c_int), ("init_state", ctypes.POINTER(Result)),
-                ("elbo_trace", _dp), ("method", ctypes.c_int), ("grouped", ctypes.c_int), ("stats", ctypes.c_int)]
+                ("elbo_trace", _dp), ("method", ctypes.c_int), ("grouped", ctypes.c_int), ("stats", ctypes.c_int),
+                ("loop", ctypes.c_int)]
 
 
 _LIB = None
@@ -101,6 +105,7 @@ def _lib():
             "vbh_last_error_detail": (ctypes.c_char_p, []),
             "vbh_selftest_wait": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_uint64,
                                                  ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_uint64)]),
+            "vbh_selftest_math": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_int, _dp, _dp, ctypes.c_int]),
             "vbh_fit": (ci, [vp, vp, vp, i64, ci, P, O, R]),
             "vbh_fit_begin": (ci, [vp, vp, vp, i64, ci, P, O]),
             "vbh_fit_step": (ci, [vp, ci, ctypes.POINTER(ci)]),
@@ -260,7 +265,7 @@ class Handle:
 
     @staticmethod
     def _opts(tol, max_iter, init_state, S, trace, precision=FP32, refine_iters=10, method=CAVI, grouped=False,
-              stats=STATS_AUTO):
+              stats=STATS_AUTO, loop=LOOP_AUTO):
         o = Opts()
         _lib().vbh_opts_default(ctypes.byref(o))
         o.tol = float(tol)
@@ -270,6 +275,7 @@ class Handle:
         o.method = int(method)
         o.grouped = 1 if grouped else 0
         o.stats = int(stats)
+        o.loop = int(loop)
         keep = []
         if init_state is not None:
             st = dict_to_result(init_state, S) if isinstance(init_state, dict) else init_state
@@ -284,12 +290,13 @@ class Handle:
 
     def fit(self, r, d, S: int, prior: dict | None = None, tol: float = 1e-8, max_iter: int = 200,
             init_state=None, trace: bool = False, V: int | None = None, precision: int = FP32,
-            refine_iters: int = 10, method: int = CAVI, grouped: bool = False, stats: int = STATS_AUTO) -> dict:
+            refine_iters: int = 10, method: int = CAVI, grouped: bool = False, stats: int = STATS_AUTO,
+            loop: int = LOOP_AUTO) -> dict:
         V = int(V if V is not None else (r.shape[0] if r is not None else 0))
         _check_inputs(r, d, V, S, "vbh_fit")
         pa = _PriorArgs(prior, S)
         o, keep, buf = self._opts(tol, max_iter, init_state, S, trace, precision, refine_iters, method, grouped,
-                                  stats)
+                                  stats, loop)
         res = Result()
         rc = _lib().vbh_fit(self._h, _ptr(r), _ptr(d), V, int(S), ctypes.byref(pa.c), ctypes.byref(o),
                             ctypes.byref(res))
@@ -302,12 +309,13 @@ class Handle:
 
     def fit_begin(self, r, d, S: int, prior: dict | None = None, tol: float = 1e-8, max_iter: int = 200,
                   init_state=None, trace: bool = False, V: int | None = None, precision: int = FP32,
-                  refine_iters: int = 10, method: int = CAVI, grouped: bool = False, stats: int = STATS_AUTO):
+                  refine_iters: int = 10, method: int = CAVI, grouped: bool = False, stats: int = STATS_AUTO,
+                  loop: int = LOOP_AUTO):
         V = int(V if V is not None else (r.shape[0] if r is not None else 0))
         _check_inputs(r, d, V, S, "vbh_fit_begin")
         pa = _PriorArgs(prior, S)
         o, keep, buf = self._opts(tol, max_iter, init_state, S, trace, precision, refine_iters, method, grouped,
-                                  stats)
+                                  stats, loop)
         rc = _lib().vbh_fit_begin(self._h, _ptr(r), _ptr(d), V, int(S), ctypes.byref(pa.c), ctypes.byref(o))
         if rc != 0:
             raise VBHError(rc, "vbh_fit_begin")

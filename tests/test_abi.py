@@ -59,7 +59,7 @@ def test_host_only_entry_points():
     lib.vbh_opts_default(ctypes.byref(o))
     assert (o.tol, o.max_iter, o.precision, o.init, o.refine_iters, o.method) == (1e-8, 200, vbh.FP32,
                                                                                  vbh.INIT_PAPER, 10, vbh.CAVI)
-    assert o.grouped == 0 and o.stats == vbh.STATS_AUTO
+    assert o.grouped == 0 and o.stats == vbh.STATS_AUTO and o.loop == vbh.LOOP_AUTO
 
 
 def test_result_struct_layout_matches_header():
@@ -68,6 +68,7 @@ def test_result_struct_layout_matches_header():
     assert vbh.Opts.refine_iters.offset == 20
     assert vbh.Opts.init_state.offset == 24 and vbh.Opts.elbo_trace.offset == 32
     assert vbh.Opts.method.offset == 40 and vbh.Opts.grouped.offset == 44 and vbh.Opts.stats.offset == 48
+    assert vbh.Opts.loop.offset == 52
     assert ctypes.sizeof(vbh.Opts) == 56
 
 

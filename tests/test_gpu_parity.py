@@ -65,7 +65,7 @@ CASES = [
     (1, 5003, 1, 3, 0.0),
     (2, 20011, 2, 10, 0.0),
     (3, 96000, 1, 25, 0.0),          # the single-data-set workload shape (2,000 cells x 48 genes, S = 3)
-    (3, 1_500_007, 7, 4, 0.0),       # several tiles per block: the shared-memory ring wraps
+    (3, 1_500_007, 7, 4, 0.0),       # streaming: the shared-memory ring wraps; resident: 152 large slices
     (4, 33333, 4, 8, 0.05),
     (5, 40000, 5, 8, 0.05),
     (6, 25000, 6, 6, 0.0),
@@ -78,13 +78,19 @@ CASES = [
 ]
 
 
+# both sweep loops: one launch per sweep streaming (r, d), and the resident loop
+# (one launch, the data in shared memory) wherever the data set fits
+LOOPS = [vbh.LOOP_STREAM, vbh.LOOP_AUTO]
+
+
+@pytest.mark.parametrize("loop", LOOPS)
 @pytest.mark.parametrize("S,V,seed,sweeps,p_const", CASES)
-def test_parity_fixed_sweeps(handle, S, V, seed, sweeps, p_const):
+def test_parity_fixed_sweeps(handle, S, V, seed, sweeps, p_const, loop):
     alpha = 1.0 if S == 3 else 0.5
     r, d, _ = synth.generate(V, S, seed=seed, alpha=alpha, p_const=p_const)
     prior = O.paper_prior(S)
     ref = O.fit(r, d, prior, tol=0.0, max_iter=sweeps)
-    got = handle.fit(_dev(r), _dev(d), S, prior, tol=0.0, max_iter=sweeps, trace=True)
+    got = handle.fit(_dev(r), _dev(d), S, prior, tol=0.0, max_iter=sweeps, trace=True, loop=loop)
     assert got["iters"] == sweeps and not got["converged"]
     assert got["const_dropped"] == ref["const_dropped"]
     assert_parity(got, ref, what=(S, V))
@@ -93,7 +99,8 @@ def test_parity_fixed_sweeps(handle, S, V, seed, sweeps, p_const):
         assert elbo_close(a, b, V), (t, a, b)
 
 
-def test_parity_converged_fit_single_dataset(handle):
+@pytest.mark.parametrize("loop", LOOPS)
+def test_parity_converged_fit_single_dataset(handle, loop):
     """2,000 x 48 = 96,000 observations, S = 3, run to the workload's own
     stopping rule, rel dELBO < 1e-8 (the sweep cap raised to 2,000).
 
@@ -108,7 +115,7 @@ def test_parity_converged_fit_single_dataset(handle):
     r, d, _ = synth.generate(V, S, seed=1)
     prior = O.paper_prior(S)
     ref = O.fit(r, d, prior, tol=1e-8, max_iter=2000)
-    got = handle.fit(_dev(r), _dev(d), S, prior, tol=1e-8, max_iter=2000, trace=True)
+    got = handle.fit(_dev(r), _dev(d), S, prior, tol=1e-8, max_iter=2000, trace=True, loop=loop)
     assert ref["converged"] and got["converged"]
     assert abs(got["iters"] - ref["iters"]) <= max(2, ref["iters"] // 50), (got["iters"], ref["iters"])
     # monotone to the precision of the compensated statistics
@@ -148,15 +155,17 @@ def test_compensated_elbo_differences_track_the_oracle(handle, S, V, seed, alpha
     assert_parity(got, ref)
 
 
+@pytest.mark.parametrize("loop", LOOPS)
 @pytest.mark.parametrize("S,V,seed,sweeps,p_const", [c for c in CASES if c[1] <= 100_000 or c[0] == 3])
-def test_parity_compensated_statistics(handle, S, V, seed, sweeps, p_const):
+def test_parity_compensated_statistics(handle, S, V, seed, sweeps, p_const, loop):
     """The compensated form of every CUDA-core sweep (S = 1..11) at fixed
     sweeps: same parity bar as the plain form."""
     alpha = 1.0 if S == 3 else 0.5
     r, d, _ = synth.generate(V, S, seed=seed, alpha=alpha, p_const=p_const)
     prior = O.paper_prior(S)
     ref = O.fit(r, d, prior, tol=0.0, max_iter=sweeps)
-    got = handle.fit(_dev(r), _dev(d), S, prior, tol=0.0, max_iter=sweeps, trace=True, stats=vbh.STATS_COMPENSATED)
+    got = handle.fit(_dev(r), _dev(d), S, prior, tol=0.0, max_iter=sweeps, trace=True, stats=vbh.STATS_COMPENSATED,
+                     loop=loop)
     assert got["iters"] == sweeps
     assert_parity(got, ref, what=(S, V))
     for t, (a, b) in enumerate(zip(got["trace"], ref["trace"])):
