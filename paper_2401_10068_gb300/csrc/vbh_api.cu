@@ -102,7 +102,7 @@ struct vbh_handle {
     // the resident sweep loop
     bool coop = false;                 // the device supports cooperative launches
     int smem_optin = 0;                // dynamic shared memory a block may opt in to
-    int res_obs = 8;                   // observations per thread and sweep the block count aims at
+    int res_obs = 3;                   // observations per thread and sweep the block count aims at
     size_t res_attr[vbh::S_FP32_MAX + 1][2] = {};   // shared memory the resident kernels were opted in to
     DevState *res_priv = nullptr;      // private state copies of blocks 1 ..
     size_t res_priv_cap = 0;           // bytes
@@ -420,18 +420,20 @@ int prepare_launch(vbh_handle *h, int S, long long V, int precision, const float
     L->grid = int(g);
     long long rows = vbh::partial_rows(g);
     if (!L->tc && loop != VBH_LOOP_STREAM) {
+        // the resident kernels are opted in to the whole shared-memory budget once, so
+        // that the shape below can take any block size within it
+        const size_t budget = size_t(h->smem_optin) - 1024;
+        size_t &set = h->res_attr[S][L->comp ? 1 : 0];
+        if (set < budget) {
+            VBH_CK(cudaFuncSetAttribute(L->res_func(), cudaFuncAttributeMaxDynamicSharedMemorySize, int(budget)));
+            set = budget;
+        }
         L->res = resident_shape(h, L->ki, L->comp, V, &L->res_grid, &L->res_per_block, &L->res_ns, &L->res_smem);
         if (!L->res && loop == VBH_LOOP_RESIDENT) return VBH_EUNSUPPORTED;
         if (L->res) {
             int per = 0;
-            size_t &set = h->res_attr[S][L->comp ? 1 : 0];
-            if (set < L->res_smem) {
-                VBH_CK(cudaFuncSetAttribute(L->res_func(), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            int(L->res_smem)));
-                set = L->res_smem;
-            }
             VBH_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, L->res_func(), L->ki.res_threads, L->res_smem));
-            if (per < 1) {
+            if (per < 1 || (long long)per * h->nsm < L->res_grid) {
                 L->res = false;
                 if (loop == VBH_LOOP_RESIDENT) return VBH_EUNSUPPORTED;
             }

@@ -92,14 +92,16 @@ struct ResidentCfg {
     static constexpr int D_RB = D_LOG + 256;
     // M <= 3: coefficients of the W'^{-1} step, from the pass factors (resident_pre_coef)
     static constexpr bool COEF = M <= 3;
-    static constexpr int D_CW = D_RB + RB_ROWS * NS;           // [MM]      W'^{-1} terms without the sums
-    static constexpr int D_QC = D_CW + MM;                     // [MM][NG]  weights of the packed G entries
-    static constexpr int D_SL = D_QC + MM * (C::NGA);          // [M][M]    weights of g in delta
+    // (packed lower-triangle entries pe = r (r + 1) / 2 + c, c <= r)
+    static constexpr int D_CW = D_RB + RB_ROWS * NS;           // [NG]      W'^{-1} terms without the sums
+    static constexpr int D_QC = D_CW + C::NGA;                 // [NG][NG]  weights of the packed G entries
+    static constexpr int D_SL = D_QC + C::NGA * C::NGA;        // [M][M]    weights of g in delta
     static constexpr int D_CD = D_SL + MM;                     // [M]       delta without the sums
-    static constexpr int D_TW = D_CD + MV;                     // [MM]      W'^{-1} before the delta term
-    static constexpr int D_END = COEF ? D_TW + MM : D_CW;
-    static constexpr int VPT = (RB_ROWS * NS + PT - 1) / PT;     // row values a pass thread collects
-    static_assert(VPT <= 32, "one pending bit per collected value");
+    static constexpr int D_TW = D_CD + MV;                     // [NG]      W'^{-1} before the delta term
+    static constexpr int D_LF = D_TW + C::NGA;                 // [NG]      L~ in FP64
+    static constexpr int D_END = COEF ? D_LF + C::NGA : D_CW;
+    static constexpr int IPT = (((RB_ROWS + 3) / 4) * NS + PT - 1) / PT;   // 4-row items a pass thread collects
+    static_assert(IPT * 4 <= 32, "one pending bit per collected value");
     static constexpr size_t OFF_WS = 0;
     static constexpr size_t OFF_EI = ((size_t(D_END) * 8 + 127) / 128) * 128;
     static constexpr size_t OFF_SG = OFF_EI + ((2 * sizeof(ElboIn) + 127) / 128) * 128;
@@ -372,32 +374,96 @@ __device__ __forceinline__ void resident_pre_mat(const SweepGlobalsF32 *sg, doub
 //   Qc_rc,kl = the weights above (EM: times 1/V),  Sl_rk = Sg_rk / lambda (EM: / V),
 //   cd_r = q0 a_r / lambda (EM: 0),
 // and after them W'^{-1}_rc = Cw_rc + sum Qc G - lambda delta_r delta_c (EM: - delta_r delta_c),
-// a few FP64 instructions per lane.  Threads t0, t0 + nt, ... (after
-// resident_pre_mat).
+// a few FP64 instructions per lane.
 // ---------------------------------------------------------------------------
-template <int M>
-__device__ __forceinline__ void resident_pre_coef(const double *Sg, const double *av, const double *L0s, double *Cw,
-                                                 double *Qc, double *Sl, double *cd, bool em, double V, double q0,
-                                                 double inv_lam, double inv_V, int t0, int nt)
+// The three stages, each a few FP64 instructions per item with the items
+// dealt round robin (threads t0, t0 + nt, ...; the caller synchronises
+// between stages): (1) L~ and kappa~ in FP64 and K0 - kappa~; (2) Sigma0~ =
+// L~ L~^T (lower triangle, mirrored; the expressions of resident_pre_mat);
+// (3) the coefficients, lower triangle only (W'^{-1} is formed symmetric).
+__device__ __forceinline__ void packed_rc(int pe, int &r, int &c)
 {
-    constexpr int MD = M > 0 ? M : 1, NG = M * (M + 1) / 2, NGA = NG > 0 ? NG : 1;
-    const double f = em ? inv_V : 1.0, f2 = em ? inv_V : inv_lam;
-    for (int t = t0; t < M * M * NG; t += nt) {
-        const int e = t / NGA, pk = t - e * NGA;
-        const int r = e / MD, c = e - r * MD;
-        int k = 0;
-        while ((k + 1) * (k + 2) / 2 <= pk) ++k;
-        const int l = pk - k * (k + 1) / 2;
-        const double w = (k == l) ? Sg[r * M + k] * Sg[k * M + c]
-                                  : fma(Sg[r * M + k], Sg[l * M + c], Sg[r * M + l] * Sg[k * M + c]);
-        Qc[e * NGA + pk] = em ? w * f : w;
+    r = 0;
+    while ((r + 1) * (r + 2) / 2 <= pe) ++r;
+    c = pe - r * (r + 1) / 2;
+}
+
+template <int M>
+__device__ __forceinline__ void resident_pre_small_1(const SweepGlobalsF32 *sg, double *Lf, double *ko, double *av,
+                                                    const double *K0s, int t0, int nt)
+{
+    constexpr int NG = M * (M + 1) / 2;
+    for (int i = t0; i < NG + M; i += nt) {
+        if (i < NG) {
+            Lf[i] = static_cast<double>(sg->L[i]);
+        } else {
+            const int j = i - NG;
+            ko[j] = static_cast<double>(sg->kappa[j]);
+            av[j] = K0s[j] - ko[j];
+        }
     }
-    for (int e = t0; e < M * M; e += nt) {
-        const int r = e / MD, c = e - r * MD;
-        Cw[e] = em ? Sg[e] : fma(q0 * av[r], av[c], fma(V, Sg[e], L0s[e]));
-        Sl[e] = Sg[e] * f2;
+}
+
+template <int M>
+__device__ __forceinline__ void resident_pre_small_2(const double *Lf, double *Sg, int t0, int nt)
+{
+    constexpr int NG = M * (M + 1) / 2;
+    for (int pe = t0; pe < NG; pe += nt) {
+        int r, c;
+        packed_rc(pe, r, c);
+        double s = 0.0;
+        for (int k = 0; k <= c; ++k) s = fma(Lf[r * (r + 1) / 2 + k], Lf[c * (c + 1) / 2 + k], s);
+        Sg[r * M + c] = s;
+        Sg[c * M + r] = s;
     }
-    for (int i = t0; i < M; i += nt) cd[i] = em ? 0.0 : q0 * av[i] * inv_lam;
+}
+
+template <int M>
+__device__ __forceinline__ void resident_pre_small_3(const double *Sg, const double *av, const double *L0s, double *Cw,
+                                                    double *Qc, double *Sl, double *cd, bool em, double V, double q0,
+                                                    double inv_lam, double inv_V, int t0, int nt)
+{
+    constexpr int NG = M * (M + 1) / 2, NGA = NG > 0 ? NG : 1;
+    const double f2 = em ? inv_V : inv_lam;
+    for (int t = t0; t < NG * NG + NG + M; t += nt) {
+        if (t < NG * NG) {
+            const int pe = t / NGA, pk = t - pe * NGA;
+            int r, c, k, l;
+            packed_rc(pe, r, c);
+            packed_rc(pk, k, l);
+            const double w = (k == l) ? Sg[r * M + k] * Sg[k * M + c]
+                                      : fma(Sg[r * M + k], Sg[l * M + c], Sg[r * M + l] * Sg[k * M + c]);
+            Qc[pe * NGA + pk] = em ? w * inv_V : w;
+        } else if (t < NG * NG + NG) {
+            const int pe = t - NG * NG;
+            int r, c;
+            packed_rc(pe, r, c);
+            Cw[pe] = em ? Sg[r * M + c] : fma(q0 * av[r], av[c], fma(V, Sg[r * M + c], L0s[r * M + c]));
+            const double sl = Sg[r * M + c] * f2;
+            Sl[r * M + c] = sl;
+            Sl[c * M + r] = sl;
+        } else {
+            const int i = t - NG * NG - NG;
+            cd[i] = em ? 0.0 : q0 * av[i] * inv_lam;
+        }
+    }
+}
+
+// Stages 1 and 2 by the pass warps (one kind of item per warp, on different SM
+// sub-partitions), between the block's row and the first barrier; stage 3 is
+// the ELBO warp's, while the rows are exchanged.
+template <int M>
+__device__ __forceinline__ void resident_pre_small_12(const SweepGlobalsF32 *sg, double *Lf, double *Sg, double *ko,
+                                                     double *av, const double *K0s, int warp, int lane, int pt)
+{
+    constexpr int NG = M * (M + 1) / 2;
+    if (warp == 0 && lane < NG) Lf[lane] = static_cast<double>(sg->L[lane]);
+    if (warp == 1 && lane < M) {
+        ko[lane] = static_cast<double>(sg->kappa[lane]);
+        av[lane] = K0s[lane] - ko[lane];
+    }
+    pass_sync(pt);
+    if (warp == 0) resident_pre_small_2<M>(Lf, Sg, lane, 32);
 }
 
 // ---------------------------------------------------------------------------
@@ -463,6 +529,7 @@ __global__ void __launch_bounds__(ResidentCfg<S, COMP>::THREADS, 1) resident_ker
     double *col = ws + R::D_COL, *red = ws + R::D_RED, *s_red = ws + R::D_SRED, *ltab = ws + R::D_LOG;
     double *rb = ws + R::D_RB;
     double *Cw = ws + R::D_CW, *Qc = ws + R::D_QC, *Sl = ws + R::D_SL, *cd = ws + R::D_CD, *Tw = ws + R::D_TW;
+    double *Lf = ws + R::D_LF;
     ElboIn *EI = reinterpret_cast<ElboIn *>(smem + R::OFF_EI);
     SweepGlobalsF32 *sg = reinterpret_cast<SweepGlobalsF32 *>(smem + R::OFF_SG);
     float4 *tab = reinterpret_cast<float4 *>(smem + R::OFF_TAB);
@@ -519,9 +586,15 @@ __global__ void __launch_bounds__(ResidentCfg<S, COMP>::THREADS, 1) resident_ker
     const double inv_V = st->kc_upd.inv_V, inv_lam = st->kc_upd.inv_lam, lam = fc.lam;
     const double rs_nu = st->kc_upd.rs_nu;
     if (elbo_warp) {
-        resident_pre_mat<M>(sg, Sg, ko, av, K0s, lane, 32);
-        __syncwarp();
-        if constexpr (R::COEF) resident_pre_coef<M>(Sg, av, L0s, Cw, Qc, Sl, cd, em, V, q0, inv_lam, inv_V, lane, 32);
+        if constexpr (R::COEF) {
+            resident_pre_small_1<M>(sg, Lf, ko, av, K0s, lane, 32);
+            __syncwarp();
+            resident_pre_small_2<M>(Lf, Sg, lane, 32);
+            __syncwarp();
+            resident_pre_small_3<M>(Sg, av, L0s, Cw, Qc, Sl, cd, em, V, q0, inv_lam, inv_V, lane, 32);
+        } else {
+            resident_pre_mat<M>(sg, Sg, ko, av, K0s, lane, 32);
+        }
         resident_pre_logs<M>(fc, sg, ltab, st->carry_ok ? st->carry_piv : nullptr, ldw, &EI[0], lane);
     }
     double elbo_prev = st->elbo_prev;            // ELBO warp, lane 0
@@ -569,6 +642,7 @@ __global__ void __launch_bounds__(ResidentCfg<S, COMP>::THREADS, 1) resident_ker
             // rounds of PT observations; the round count is the same for every
             // pass thread, so the warp-wide flushes are reached by whole warps
             int cnt = 0;
+            bool flushed = false;                         // acc64 still zero: the first flush assigns
             for (int j0 = 0; j0 < n; j0 += PT) {
                 const int j = j0 + tid;
                 if (j < n) {
@@ -584,16 +658,24 @@ __global__ void __launch_bounds__(ResidentCfg<S, COMP>::THREADS, 1) resident_ker
                 }
                 if (++cnt == R::FLUSH) {
                     if constexpr (COMP)
-                        flush_warp_comp<S>(acc, acc64, prod, pl, ex, uh, ul, lane);
+                        flush_warp_comp<S, true, true>(acc, acc64, prod, pl, ex, uh, ul, lane);
                     else
-                        flush_warp<S>(acc, acc64, prod, ex, lane);
+                        flush_warp<S, true, true>(acc, acc64, prod, ex, lane);
                     cnt = 0;
+                    flushed = true;
                 }
             }
-            if constexpr (COMP)
-                flush_warp_comp<S>(acc, acc64, prod, pl, ex, uh, ul, lane);
-            else
-                flush_warp<S>(acc, acc64, prod, ex, lane);
+            if (flushed) {
+                if constexpr (COMP)
+                    flush_warp_comp<S, true, true>(acc, acc64, prod, pl, ex, uh, ul, lane);
+                else
+                    flush_warp<S, true, true>(acc, acc64, prod, ex, lane);
+            } else {
+                if constexpr (COMP)
+                    flush_warp_comp<S, false, true>(acc, acc64, prod, pl, ex, uh, ul, lane);
+                else
+                    flush_warp<S, false, true>(acc, acc64, prod, ex, lane);
+            }
             // block reduction in FP64 (fixed order: a tree over the pass warps), this
             // block's row of tagged values
 #pragma unroll
@@ -608,7 +690,8 @@ __global__ void __launch_bounds__(ResidentCfg<S, COMP>::THREADS, 1) resident_ker
                     for (int h = 1; h < PW; h *= 2)
 #pragma unroll
                         for (int i = 0; i + h < PW; i += 2 * h) w[i] += w[i + h];
-                    const unsigned long long bits = (static_cast<unsigned long long>(__double_as_longlong(w[0])) & ~3ull) | tag;
+                    const unsigned long long bits =
+                        (static_cast<unsigned long long>(__double_as_longlong(w[0])) & ~3ull) | tag;
                     st_relaxed_u64(part + size_t(blockIdx.x) * NS + j, bits);
                 }
             }
@@ -618,10 +701,12 @@ __global__ void __launch_bounds__(ResidentCfg<S, COMP>::THREADS, 1) resident_ker
             // sub-partitions: each FP64 instruction holds one for ~64 cycles)
             if (k > 0) {
                 const int tw = warp + PW * lane;
-                resident_pre_mat<M>(sg, Sg, ko, av, K0s, tw, PT);
                 if constexpr (R::COEF) {
-                    pass_sync(PT);
-                    resident_pre_coef<M>(Sg, av, L0s, Cw, Qc, Sl, cd, em, V, q0, inv_lam, inv_V, tw, PT);
+                    // (between the block's row and the wait for the other rows: off the path
+                    // that sets the sweep, which runs through the last row to arrive)
+                    resident_pre_small_12<M>(sg, Lf, Sg, ko, av, K0s, warp, lane, PT);
+                } else {
+                    resident_pre_mat<M>(sg, Sg, ko, av, K0s, tw, PT);
                 }
             }
         } else if (k > 0) {
@@ -634,32 +719,61 @@ __global__ void __launch_bounds__(ResidentCfg<S, COMP>::THREADS, 1) resident_ker
             // ---- ELBO warp, while the rows are exchanged: the state after sweep k - 1, then
             //      the logarithms of the pass factors sweep k read
             resident_elbo_store<M>(st, fc, EI[(k - 1) & 1], Wn, kn, sg, it0 + k, eo, elbo_prev, status, ldw, lane);
-            if (!s_stop) resident_pre_logs<M>(fc, sg, ltab, EI[(k - 1) & 1].piv, ldw, &EI[k & 1], lane);
+            if (!s_stop) {
+                resident_pre_logs<M>(fc, sg, ltab, EI[(k - 1) & 1].piv, ldw, &EI[k & 1], lane);
+                if constexpr (R::COEF)
+                    resident_pre_small_3<M>(Sg, av, L0s, Cw, Qc, Sl, cd, em, V, q0, inv_lam, inv_V, lane, 32);
+            }
         }
         if (s_stop) break;                  // sweep k - 1 ended the fit: sweep k's pass is dropped
 
-        // ---- every block's row of sweep k (pass warps): value v = (row, column) is
-        //      ready when its two low bits carry the tag of sweep k; summed in a fixed order
+        // ---- every block's row of sweep k (pass warps): value (row, column) is ready
+        //      when its two low bits carry the tag of sweep k.  Item (g, j) is column j
+        //      of rows 4g .. 4g + 3; its owner polls them and, once all are in, takes
+        //      their sum (the first level of a 4-ary tree over the rows)
         if (!elbo_warp) {
-            const int nv = nblk * NS;
-            uint32_t pending = 0;
+            const int ngrp = (nblk + 3) / 4, nitem = NS * ngrp;
+            uint32_t pending = 0;                        // bit 4i + u: row 4g + u of item i outstanding
 #pragma unroll
-            for (int c = 0; c < R::VPT; ++c)
-                if (tid + c * PT < nv) pending |= 1u << c;
+            for (int i = 0; i < R::IPT; ++i) {
+                const int q = tid + i * PT;
+                if (q < nitem) {
+                    const int g = q / NS, cnt = (nblk - 4 * g < 4) ? nblk - 4 * g : 4;
+                    pending |= ((1u << cnt) - 1u) << (4 * i);
+                }
+            }
             const uint64_t t0 = global_ns();
             for (uint32_t round = 0; pending; ++round) {
 #pragma unroll
-                for (int c0 = 0; c0 < R::VPT; c0 += 4) {
-                    unsigned long long g[4];
+                for (int i0 = 0; i0 < R::IPT; i0 += 2) {
+                    unsigned long long gv4[2][4];
 #pragma unroll
-                    for (int u = 0; u < 4; ++u)
-                        if (c0 + u < R::VPT && ((pending >> (c0 + u)) & 1u)) g[u] = ld_relaxed_u64(part + tid + (c0 + u) * PT);
+                    for (int i = i0; i < i0 + 2 && i < R::IPT; ++i) {
+                        const int q = tid + i * PT, g = q / NS, jj = q - g * NS;
 #pragma unroll
-                    for (int u = 0; u < 4; ++u)
-                        if (c0 + u < R::VPT && ((pending >> (c0 + u)) & 1u) && (g[u] & 3ull) == tag) {
-                            rb[tid + (c0 + u) * PT] = __longlong_as_double(static_cast<long long>(g[u] & ~3ull));
-                            pending &= ~(1u << (c0 + u));
+                        for (int u = 0; u < 4; ++u)
+                            if ((pending >> (4 * i + u)) & 1u) gv4[i - i0][u] = ld_relaxed_u64(part + (4 * g + u) * NS + jj);
+                    }
+#pragma unroll
+                    for (int i = i0; i < i0 + 2 && i < R::IPT; ++i) {
+                        if (!((pending >> (4 * i)) & 15u)) continue;
+                        const int q = tid + i * PT, g = q / NS, jj = q - g * NS;
+#pragma unroll
+                        for (int u = 0; u < 4; ++u)
+                            if (((pending >> (4 * i + u)) & 1u) && (gv4[i - i0][u] & 3ull) == tag) {
+                                rb[(4 * g + u) * NS + jj] =
+                                    __longlong_as_double(static_cast<long long>(gv4[i - i0][u] & ~3ull));
+                                pending &= ~(1u << (4 * i + u));
+                            }
+                        if (!((pending >> (4 * i)) & 15u)) {
+                            const int cnt = (nblk - 4 * g < 4) ? nblk - 4 * g : 4;
+                            const double *x = rb + 4 * g * NS + jj;
+                            // missing rows of the last group as zeros (x + 0 = x)
+                            const double x0 = x[0], x1 = cnt > 1 ? x[NS] : 0.0, x2 = cnt > 2 ? x[2 * NS] : 0.0,
+                                         x3 = cnt > 3 ? x[3 * NS] : 0.0;
+                            red[g * NS + jj] = (x0 + x1) + (x2 + x3);
                         }
+                    }
                 }
                 if (pending && (round & 15u) == 15u && global_ns() - t0 > RESIDENT_WAIT_NS) {
                     s_timeout = 1;
@@ -668,23 +782,22 @@ __global__ void __launch_bounds__(ResidentCfg<S, COMP>::THREADS, 1) resident_ker
             }
             pass_sync(PT);
             if (!s_timeout) {
-                // a 4-ary tree over the rows, level by level (rows 4g .. 4g + 3 ->
-                // row g, as (a + b) + (c + d)), between rb and red: on this GPU each
-                // FP64 warp instruction holds its SM sub-partition for ~64 cycles,
-                // so the levels pack one addition per lane over few warps
-                const double *src = rb;
-                double *dst = red;
-                int n = nblk;
+                // the rest of the tree, level by level (rows 4g .. 4g + 3 -> row g, as
+                // (a + b) + (c + d)), between red and rb: on this GPU each FP64 warp
+                // instruction holds its SM sub-partition for ~64 cycles, so the levels
+                // pack one addition per lane over few warps
+                const double *src = red;
+                double *dst = rb;
+                int n = ngrp;
                 while (n > 1) {
                     const int n4 = (n + 3) / 4;
                     for (int q = tid; q < NS * n4; q += PT) {
-                        const int g = q / NS, j = q - g * NS;
+                        const int g = q / NS, jj = q - g * NS;
                         const int b = 4 * g, cnt = (n - b < 4) ? n - b : 4;
-                        const double *x = src + b * NS + j;
-                        // missing rows of the last group as zeros (x + 0 = x): no divergence
+                        const double *x = src + b * NS + jj;
                         const double x0 = x[0], x1 = cnt > 1 ? x[NS] : 0.0, x2 = cnt > 2 ? x[2 * NS] : 0.0,
                                      x3 = cnt > 3 ? x[3 * NS] : 0.0;
-                        dst[g * NS + j] = (x0 + x1) + (x2 + x3);
+                        dst[g * NS + jj] = (x0 + x1) + (x2 + x3);
                     }
                     pass_sync(PT);
                     const double *t = src;
@@ -736,16 +849,19 @@ __global__ void __launch_bounds__(ResidentCfg<S, COMP>::THREADS, 1) resident_ker
                     for (int kk = 0; kk < M; ++kk) d = fma(Sl[lane * M + kk], gs[kk], d);
                     dv[lane] = d;
                     kn[lane] = ko[lane] + d;
-                } else if (warp == 1 && lane < M * M) {
+                } else if (warp == 1 && lane < NG) {
                     double t = Cw[lane];
 #pragma unroll
                     for (int pk = 0; pk < NG; ++pk) t = fma(Qc[lane * C::NGA + pk], Gp[pk], t);
                     Tw[lane] = t;
                 }
                 pass_sync(PT);
-                if (warp == 0 && lane < M * M) {
-                    const int r = lane / MD, c = lane - r * MD;
-                    Wn[lane] = fma(-(em ? dv[r] : lam * dv[r]), dv[c], Tw[lane]);
+                if (warp == 0 && lane < NG) {
+                    int r, c;
+                    packed_rc(lane, r, c);
+                    const double w = fma(-(em ? dv[r] : lam * dv[r]), dv[c], Tw[lane]);
+                    Wn[r * M + c] = w;
+                    Wn[c * M + r] = w;
                 }
                 pass_sync(PT);
             } else {
@@ -811,13 +927,15 @@ __global__ void __launch_bounds__(ResidentCfg<S, COMP>::THREADS, 1) resident_ker
                     const int r = e / MD, c = e - r * MD;
                     if (c <= r) sg->L[r * (r + 1) / 2 + c] = static_cast<float>(Lw[e] * rs);
                 }
-                for (int i = lane; i < M; i += 32) {
-                    sg->kappa[i] = static_cast<float>(kn[i]);
-                    EI[k & 1].piv[i] = piv[i];
-                }
+                for (int i = lane; i < M; i += 32) EI[k & 1].piv[i] = piv[i];
                 if (lane == 0) EI[k & 1].fail = fail;
                 __syncwarp();
-                if (COMP) write_pass_splits_rt(M, sg, lane);
+                if (COMP) write_pass_splits_sigma_rt(M, sg, lane);
+            } else if (warp == 1) {
+                // kappa~ and its split, beside the factorisation
+                for (int i = lane; i < M; i += 32) sg->kappa[i] = static_cast<float>(kn[i]);
+                __syncwarp();
+                if (COMP) write_pass_splits_kappa_rt(M, sg, lane);
             }
         }
         cta_sync();

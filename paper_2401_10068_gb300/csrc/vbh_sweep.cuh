@@ -329,11 +329,47 @@ __device__ __forceinline__ void peel_exponent(float &prod, int &ex)
     prod = __uint_as_float((b & 0x007fffffu) | 0x3f800000u);
 }
 
+// Warp totals of NSTAT <= 16 FP32 statistics with fewer shuffles than the
+// 32-slot reduce-scatter below: the values, padded to NV = 2^k >= NSTAT, are
+// halved per level while more than one remains (lane bit `off` keeps the upper
+// half), the remaining levels add; lane 4 s (for NV = 8) then holds the total
+// of statistic s, and one more shuffle gives lane j the total of statistic j.
+// A fixed order of additions, the same in every warp.
+template <int NSTAT>
+__device__ __forceinline__ float warp_totals_narrow(const float (&acc)[NSTAT], int lane)
+{
+    constexpr int NV = NSTAT <= 1 ? 1 : NSTAT <= 2 ? 2 : NSTAT <= 4 ? 4 : NSTAT <= 8 ? 8 : 16;
+    float v[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] = (i < NSTAT) ? acc[i < NSTAT ? i : 0] : 0.0f;
+    int n = NV;
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+        if (n > 1) {
+            const bool up = (lane & off) != 0;
+            const int h = n / 2;
+#pragma unroll
+            for (int i = 0; i < NV / 2; ++i) {
+                if (i < h) {
+                    const float keep = up ? v[i + h] : v[i];
+                    const float send = up ? v[i] : v[i + h];
+                    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+                }
+            }
+            n = h;
+        } else {
+            v[0] += __shfl_xor_sync(0xffffffffu, v[0], off);
+        }
+    }
+    // statistic s sits in the lanes whose top log2(NV) bits spell s
+    return __shfl_sync(0xffffffffu, v[0], (lane % NV) * (32 / NV));
+}
+
 // Move the FP32 chunk sums of a warp into FP64: first the product into
 // (ln mantissa, exponent), then a butterfly reduce-scatter over each group of
 // 32 statistics leaves lane l with the warp total of statistic 32 g + l,
 // which it adds to its FP64 accumulator.
-template <int S>
+template <int S, bool ADD = true, bool NARROW = false>
 __device__ __forceinline__ void flush_warp(float (&acc)[SweepCfg<S>::NSTAT], double (&acc64)[SweepCfg<S>::NGRP],
                                            float &prod, int &ex, int lane)
 {
@@ -344,6 +380,14 @@ __device__ __forceinline__ void flush_warp(float (&acc)[SweepCfg<S>::NSTAT], dou
     acc[C::I_E4] += static_cast<float>(ex);                // exact: |ex| < 2^24
     prod = 1.0f;
     ex = 0;
+    if constexpr (NARROW && NSTAT <= 16) {
+        const float t = warp_totals_narrow<NSTAT>(acc, lane);
+        const double x = (lane < NSTAT) ? static_cast<double>(t) : 0.0;
+        acc64[0] = ADD ? acc64[0] + x : x;
+#pragma unroll
+        for (int i = 0; i < NSTAT; ++i) acc[i] = 0.0f;
+        return;
+    }
 #pragma unroll
     for (int g = 0; g < C::NGRP; ++g) {
         float v[32];
@@ -359,7 +403,10 @@ __device__ __forceinline__ void flush_warp(float (&acc)[SweepCfg<S>::NSTAT], dou
                 v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
             }
         }
-        acc64[g] += static_cast<double>(v[0]);
+        if (ADD)
+            acc64[g] += static_cast<double>(v[0]);
+        else
+            acc64[g] = static_cast<double>(v[0]);              // the first flush: no FP64 addition
     }
 #pragma unroll
     for (int i = 0; i < NSTAT; ++i) acc[i] = 0.0f;
@@ -370,7 +417,7 @@ __device__ __forceinline__ void flush_warp(float (&acc)[SweepCfg<S>::NSTAT], dou
 // ln ph + pl/ph (ph in [1, 2)); U is summed over the lanes in two parts and
 // added in FP64 by the lane that holds column I_U; the FP32 statistics go
 // through the butterfly of flush_warp.
-template <int S>
+template <int S, bool ADD = true, bool NARROW = false>
 __device__ __forceinline__ void flush_warp_comp(float (&acc)[SweepCfg<S>::NSTAT],
                                                 double (&acc64)[SweepCfg<S>::NGRPC], float &ph, float &pl, int &ex,
                                                 float &uh, float &ul, int lane)
@@ -401,6 +448,17 @@ __device__ __forceinline__ void flush_warp_comp(float (&acc)[SweepCfg<S>::NSTAT]
     ph = 1.0f;
     pl = 0.0f;
     ex = 0;
+    if constexpr (NARROW && NSTAT <= 16) {
+        const float t = warp_totals_narrow<NSTAT>(acc, lane);
+        double x = (lane < NSTAT) ? static_cast<double>(t) : 0.0;
+        if (lane == C::I_U) x = static_cast<double>(uh) + static_cast<double>(ul);   // I_U = NSTAT < 32
+        acc64[0] = ADD ? acc64[0] + x : x;
+        uh = 0.0f;
+        ul = 0.0f;
+#pragma unroll
+        for (int i = 0; i < NSTAT; ++i) acc[i] = 0.0f;
+        return;
+    }
 #pragma unroll
     for (int g = 0; g < C::NGRP; ++g) {
         float v[32];
@@ -416,9 +474,15 @@ __device__ __forceinline__ void flush_warp_comp(float (&acc)[SweepCfg<S>::NSTAT]
                 v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
             }
         }
-        acc64[g] += static_cast<double>(v[0]);
+        if (ADD)
+            acc64[g] += static_cast<double>(v[0]);
+        else
+            acc64[g] = static_cast<double>(v[0]);
     }
-    if (lane == C::I_U % 32) acc64[C::I_U / 32] += static_cast<double>(uh) + static_cast<double>(ul);
+    if (lane == C::I_U % 32) {
+        const double u = static_cast<double>(uh) + static_cast<double>(ul);
+        acc64[C::I_U / 32] = ADD ? acc64[C::I_U / 32] + u : u;   // column I_U of the butterfly is zero
+    }
     uh = 0.0f;
     ul = 0.0f;
 #pragma unroll
@@ -619,7 +683,7 @@ __device__ inline void write_pass_globals_rt(int M, DevState *st, const double *
 // of 2^(E - 17) below 2^(E + 7)).  kappa~ likewise on the grid 2^(E' - 19)
 // (at most 10 parts).  Sl and kl are 2^-18 of the largest entry or less, so
 // their FP32 sums add about 2^-42 relative.
-__device__ inline void write_pass_splits_rt(int M, SweepGlobalsF32 *sw, int lane)
+__device__ inline void write_pass_splits_sigma_rt(int M, SweepGlobalsF32 *sw, int lane)
 {
     const int NG = M * (M + 1) / 2;
     float hi[2], lo[2];
@@ -654,8 +718,7 @@ __device__ inline void write_pass_splits_rt(int M, SweepGlobalsF32 *sw, int lane
             if (sh != 0.0f) emax = max(emax, ilogbf(sh));
         }
     }
-#pragma unroll
-    for (int off = 16; off >= 1; off >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, off));
+    emax = __reduce_max_sync(0xffffffffu, emax);
     const int eq = emax - 17;
     const float qinv = (eq > -127 && eq < 127) ? __uint_as_float(uint32_t(127 - eq) << 23) : 1.0f;
     const float qs = (eq > -127 && eq < 127) ? __uint_as_float(uint32_t(127 + eq) << 23) : 1.0f;
@@ -668,10 +731,13 @@ __device__ inline void write_pass_splits_rt(int M, SweepGlobalsF32 *sw, int lane
             sw->Sl[e] = (hi[u] - h) + lo[u];               // hi - h is exact
         }
     }
+}
+
+__device__ inline void write_pass_splits_kappa_rt(int M, SweepGlobalsF32 *sw, int lane)
+{
     const float kv = (lane < M) ? sw->kappa[lane] : 0.0f;
     int ek = (kv != 0.0f) ? ilogbf(kv) : -1000;
-#pragma unroll
-    for (int off = 16; off >= 1; off >>= 1) ek = max(ek, __shfl_xor_sync(0xffffffffu, ek, off));
+    ek = __reduce_max_sync(0xffffffffu, ek);
     const int eqk = ek - 19;
     const float kqinv = (eqk > -127 && eqk < 127) ? __uint_as_float(uint32_t(127 - eqk) << 23) : 1.0f;
     const float kqs = (eqk > -127 && eqk < 127) ? __uint_as_float(uint32_t(127 + eqk) << 23) : 1.0f;
@@ -680,6 +746,12 @@ __device__ inline void write_pass_splits_rt(int M, SweepGlobalsF32 *sw, int lane
         sw->kh[lane] = h;
         sw->kl[lane] = kv - h;                              // exact
     }
+}
+
+__device__ inline void write_pass_splits_rt(int M, SweepGlobalsF32 *sw, int lane)
+{
+    write_pass_splits_sigma_rt(M, sw, lane);
+    write_pass_splits_kappa_rt(M, sw, lane);
 }
 
 // ---------------------------------------------------------------------------
