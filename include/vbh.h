@@ -208,8 +208,9 @@ int vbh_selftest_wait(int device, void *stream, uint64_t budget_ns, int *status,
  *         table-driven method: 128 tabulated ln F and 1/F, F = 1 + j/128, and
  *         a degree-8 series of ln(1 + u), |u| < 2^-7); absolute error a few
  *         units in the last place of max(|ln x|, ln 2);
- *   fn 1: the reciprocal square root of the Cholesky factorisations (an FP32
- *         seed and one third-order correction); within about an ulp.
+ *   fn 1: the reciprocal square root of the Cholesky factorisations (the
+ *         PTX approximation as the seed and one third-order correction);
+ *         within about an ulp.
  * Allocates and frees 16 n bytes of device memory; synchronous. */
 int vbh_selftest_math(int device, void *stream, int fn, const double *x, double *out, int n);
 

@@ -453,11 +453,11 @@ __device__ __forceinline__ double log_tang(double x, const double *tab)
 
 
 // ---------------------------------------------------------------------------
-// 1/sqrt(p) for positive normal p with a short dependency chain: an FP32 seed
-// (p scaled by an even power of two into [1, 4), rsqrtf), then one step of
-// the third-order iteration y' = y (1 + e/2 + 3e^2/8), e = 1 - p y^2 (the
-// binomial series of (1 - e)^(-1/2) to second order); the seed's relative
-// error ~2^-22 leaves ~2^-65 before the final rounding.  Zero, negative,
+// 1/sqrt(p) for positive normal p with a short dependency chain: the PTX
+// approximation rsqrt.approx.f64 as the seed, then one step of the
+// third-order iteration y' = y (1 + e/2 + 3e^2/8), e = 1 - p y^2 (the
+// binomial series of (1 - e)^(-1/2) to second order), which takes a seed
+// error of 2^-20 below 2^-59 before the final rounding.  Zero, negative,
 // subnormal and non-finite p take the library path.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double rsqrt_fast(double p)
@@ -465,12 +465,10 @@ __device__ __forceinline__ double rsqrt_fast(double p)
     const long long b = __double_as_longlong(p);
     const int eb = int((b >> 52) & 0x7ff);
     if (b <= 0 || eb == 0 || eb == 0x7ff) return rsqrt(p);
-    const int E2 = (eb - 1023) & ~1;                                   // even, rounded down
-    const double pm = __longlong_as_double(b - ((long long)E2 << 52)); // p 2^-E2 in [1, 4)
-    double y = static_cast<double>(rsqrtf(static_cast<float>(pm)));
-    const double e = fma(-(pm * y), y, 1.0);
-    y = fma(y, e * fma(0.375, e, 0.5), y);
-    return __longlong_as_double(__double_as_longlong(y) - ((long long)(E2 / 2) << 52));
+    double y;
+    asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(p));
+    const double e = fma(-(p * y), y, 1.0);
+    return fma(y, e * fma(0.375, e, 0.5), y);
 }
 
 // ---------------------------------------------------------------------------

@@ -204,8 +204,8 @@ def test_table_driven_log_against_numpy(handle):
 
 
 def test_fast_rsqrt_against_numpy(handle):
-    """The Cholesky factorisations take 1/sqrt(p) from an FP32 seed and one
-    third-order correction: within one unit in the last place of the exact
+    """The Cholesky factorisations take 1/sqrt(p) from the PTX approximation
+    and one third-order correction: within one unit in the last place of the exact
     value (an extended-precision reference) over the whole exponent range;
     special inputs as the library's rsqrt."""
     rng = np.random.default_rng(1)
