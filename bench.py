@@ -542,7 +542,8 @@ def other_workloads(dev, stream):
     sec = ev0.elapsed_time(ev1) * 1e-3
     iters = np.array([x["iters"] for x in res])
     conv = np.array([x["converged"] for x in res])
-    out["batched"] = {"workload": BATCH["name"], "V_total": int(V.sum()), "tol": BATCH["tol"], "cap": BATCH["cap"],
+    plan = h.batched_plan()
+    out["batched"] = {"plan": plan, "workload": BATCH["name"], "V_total": int(V.sum()), "tol": BATCH["tol"], "cap": BATCH["cap"],
                       "seconds": sec, "converged": int(conv.sum()), "datasets": len(res),
                       "converged_datasets_per_s": float(conv.sum()) / sec, "datasets_per_s": len(res) / sec,
                       "sweeps_mean": float(iters.mean()), "sweeps_max": int(iters.max()),
@@ -652,6 +653,7 @@ def run_batched(args):
     torch.cuda.synchronize(dev)
     sec = ev0.elapsed_time(ev1) * 1e-3
     clk = clocks.stop()
+    plan = h.batched_plan()                  # per class: the autotuned pass shape and its pass time
     iters = np.array([x["iters"] for x in res])
     conv = np.array([x["converged"] for x in res])
     upd = float(np.sum(V.astype(np.float64) * S * (iters + 1)))
@@ -673,7 +675,7 @@ def run_batched(args):
             "n_gpus": 1, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
             "config": {"workload": BATCH["name"], "datasets": B, "V_total": int(V.sum()),
                        "bytes_resident": float(np.sum(V.astype(np.float64) * (S + 1) * 4)),
-                       "tol": BATCH["tol"], "cap": BATCH["cap"], "chunk_tiles": None},
+                       "tol": BATCH["tol"], "cap": BATCH["cap"], "pass_plan": plan},
             "seconds": sec, "converged": int(conv.sum()), "iters_mean": float(iters.mean()),
             "iters_max": int(iters.max()), "datasets_per_s_all": B / sec,
             "updates_per_s": upd / sec, "achieved_gbs_data_pass": byts / sec / 1e9,

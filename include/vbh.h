@@ -251,10 +251,28 @@ int vbh_fit_result(vbh_handle *h, vbh_result *out);
  * batched sweep is, per class of equal S, a persistent data-pass kernel over
  * chunks of contiguous observations taken from a work queue and one FP64
  * update per data set, and the loop is a CUDA graph with a conditional while
- * node.  The chunk size is autotuned by timing one data pass per candidate.
+ * node.  For batches of at least 2^26 observations the pass shape of each
+ * class (tiles per chunk and pipeline stages) is autotuned by timing one data
+ * pass per candidate; vbh_batched_plan reports the choice.
  * Returns the first non-zero per-data-set status (also in out[b].status). */
 int vbh_fit_batched(vbh_handle *h, int B, const int64_t *V, const int *S, const float *const *r,
                     const float *const *d, const vbh_prior *p, const vbh_opts *o, vbh_result *out);
+
+/* The data-pass shape of one class (equal S) in the last vbh_fit_batched call. */
+typedef struct vbh_batch_plan {
+    int S;
+    int tile;                    /* observations per tile (one bulk copy per tile) */
+    int chunk_tiles;             /* tiles per chunk (work-queue unit) */
+    int stages;                  /* pipeline stages of the shared-memory ring */
+    int blocks_per_sm;           /* resident pass blocks per SM at that ring */
+    float pass_ms;               /* the autotuner's time of one data pass of the class with that shape
+                                    (0 when the batch was too small to tune) */
+} vbh_batch_plan;
+
+/* Copy up to `cap` class plans of the last vbh_fit_batched call on h (classes
+ * in increasing S) into out (may be NULL when cap is 0) and their number into
+ * *n.  Returns VBH_EINVAL for a NULL h or n. */
+int vbh_batched_plan(vbh_handle *h, vbh_batch_plan *out, int cap, int *n);
 
 /* ELBO (Eq. 11) of the global factors in *q (kappa, W_inv, nu, lambda,
  * a_rho, b_rho) with Q(beta) set from them by Eq. 19-21: one data pass and no

@@ -994,6 +994,15 @@ int vbh_fit_batched(vbh_handle *h, int B, const int64_t *V, const int *S, const 
     return vbh::fit_batched_impl(h->batched, h->stream, h->nsm, B, V, S, r, d, p, o, out, h->direct);
 }
 
+int vbh_batched_plan(vbh_handle *h, vbh_batch_plan *out, int cap, int *n)
+{
+    if (!h || !n || cap < 0 || (cap > 0 && !out)) return VBH_EINVAL;
+    const auto &plan = h->batched.plan;
+    *n = int(plan.size());
+    for (int i = 0; i < cap && i < int(plan.size()); ++i) out[i] = plan[size_t(i)];
+    return VBH_OK;
+}
+
 int vbh_elbo(vbh_handle *h, const float *r, const float *d, int64_t V, int S, const vbh_prior *p,
              const vbh_result *q, double *elbo)
 {

@@ -93,7 +93,14 @@ struct ClassPlan {
     std::vector<int> chunk_ds;
     std::vector<long long> lo, hi;
     std::vector<int> order;
-    int grid = 0;
+    size_t fixed = 0;                       // shared memory of the pass without its ring (chosen form)
+    int max_stages = 0;                     // most stages whose ring fits one block
+    int stages = 0;                         // the pass's stages (autotuned)
+    int chunk_tiles = 0;                    // tiles per chunk (autotuned)
+    int grid = 0;                           // persistent blocks of the pass at `stages`
+    int per_sm = 0;
+    float pass_ms = 0.f;                    // the autotuner's time of the chosen pass (0: not timed)
+    size_t smem() const { return fixed + size_t(stages) * bi.stage_bytes; }
 };
 
 void build_chunks(ClassPlan &cp, const int64_t *V, int chunk_tiles, std::vector<int> &first, std::vector<int> &nch)
@@ -127,6 +134,7 @@ int fit_batched_impl(BatchedHost &hb, cudaStream_t stream, int nsm, int B, const
                      const float *const *r, const float *const *d, const vbh_prior *p, const vbh_opts *o,
                      vbh_result *out, bool direct)
 {
+    hb.plan.clear();
     // ---------------- arguments ----------------
     if (B < 0 || (B > 0 && (!V || !S || !r || !d || !out)) || !o) return VBH_EINVAL;
     if (B == 0) return VBH_OK;
@@ -188,6 +196,20 @@ int fit_batched_impl(BatchedHost &hb, cudaStream_t stream, int nsm, int B, const
     }
 
     // ---------------- classes and work lists ----------------
+    int smem_optin = 0, rc = VBH_OK;
+    VBH_B_CK(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+    static const int kCandidates[] = {8, 32, 128};            // tiles per chunk
+    static const int kStageCandidates[] = {2, 3, 4, 6, 8};
+    constexpr int kDefaultStages = 3;
+    // the pass's stages and, from its occupancy at that ring, its persistent grid
+    auto set_stages = [&](ClassPlan &cp, int st) -> int {
+        cp.stages = st;
+        int per_sm = 0;
+        VBH_B_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cp.bi.pass, cp.bi.threads, cp.smem()));
+        cp.per_sm = per_sm;
+        cp.grid = nsm * std::max(per_sm, 1);
+        return per_sm >= 1 ? VBH_OK : VBH_EUNSUPPORTED;
+    };
     std::vector<ClassPlan> classes;
     for (int s = 1; s <= S_FP32_MAX; ++s) {
         ClassPlan cp;
@@ -196,24 +218,27 @@ int fit_batched_impl(BatchedHost &hb, cudaStream_t stream, int nsm, int B, const
             if (S[b] == s) cp.ds.push_back(b);
         if (cp.ds.empty()) continue;
         if (!batch_info(s, &cp.bi)) return VBH_EUNSUPPORTED;
+        cp.fixed = comp ? cp.bi.pass_fixed_comp : cp.bi.pass_fixed;
         if (comp) {
             cp.bi.pass = cp.bi.pass_comp;
-            cp.bi.pass_smem = cp.bi.pass_smem_comp;
             cp.bi.nstat += 1;
         }
-        VBH_B_CK(cudaFuncSetAttribute(cp.bi.pass, cudaFuncAttributeMaxDynamicSharedMemorySize, int(cp.bi.pass_smem)));
+        cp.max_stages = 0;
+        for (int st = 1; st <= cp.bi.max_stages; ++st)
+            if (cp.fixed + size_t(st) * cp.bi.stage_bytes + 1024 <= size_t(smem_optin)) cp.max_stages = st;
+        if (cp.max_stages < 2) return VBH_EUNSUPPORTED;
+        VBH_B_CK(cudaFuncSetAttribute(cp.bi.pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      int(cp.fixed + size_t(cp.max_stages) * cp.bi.stage_bytes)));
         VBH_B_CK(cudaFuncSetAttribute(cp.bi.update, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       int(cp.bi.update_smem)));
-        int per_sm = 0;
-        VBH_B_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cp.bi.pass, cp.bi.threads, cp.bi.pass_smem));
-        cp.grid = nsm * std::max(per_sm, 1);
+        if ((rc = set_stages(cp, std::min(kDefaultStages, cp.max_stages)))) return rc;
+        cp.chunk_tiles = kCandidates[1];
         classes.push_back(std::move(cp));
     }
     const int nclass = int(classes.size());
     std::vector<int> first(B, 0), nch(B, 0);
 
     // upper bound of chunks: smallest candidate chunk size
-    static const int kCandidates[] = {8, 32, 128};
     size_t max_chunks = 0;
     for (auto &cp : classes) {
         build_chunks(cp, V, kCandidates[0], first, nch);
@@ -235,7 +260,7 @@ int fit_batched_impl(BatchedHost &hb, cudaStream_t stream, int nsm, int B, const
         add(sizeof(int) * cp.ds.size());
         add(sizeof(int) * max_chunks * 2);
         add(sizeof(long long) * max_chunks * 2);
-        add(sizeof(double) * max_chunks * cp.bi.nstat);
+        add(sizeof(double) * max_chunks * cp.bi.rows_per_chunk * cp.bi.nstat);
     }
     add(stage_bytes);
     need += 4096;
@@ -268,7 +293,8 @@ int fit_batched_impl(BatchedHost &hb, cudaStream_t stream, int nsm, int B, const
         cdev[c].order = static_cast<int *>(ar.take(sizeof(int) * max_chunks));
         cdev[c].lo = static_cast<long long *>(ar.take(sizeof(long long) * max_chunks));
         cdev[c].hi = static_cast<long long *>(ar.take(sizeof(long long) * max_chunks));
-        cdev[c].partials = static_cast<double *>(ar.take(sizeof(double) * max_chunks * classes[c].bi.nstat));
+        cdev[c].partials = static_cast<double *>(
+            ar.take(sizeof(double) * max_chunks * classes[c].bi.rows_per_chunk * classes[c].bi.nstat));
     }
     unsigned char *stage = static_cast<unsigned char *>(ar.take(stage_bytes));
     for (int b = 0; b < B; ++b) {
@@ -342,12 +368,13 @@ int fit_batched_impl(BatchedHost &hb, cudaStream_t stream, int nsm, int B, const
     VBH_B_CK(cudaMemsetAsync(counters, 0, sizeof(unsigned int) * (SMAX + 1), stream));
     VBH_B_CK(cudaStreamSynchronize(stream));                  // host vectors above go out of scope later
 
-    // Upload the work lists of one chunk size; returns the class arguments.
+    // Upload the work lists of every class (chunk size `chunk_tiles`, or each
+    // class's own when it is 0) and fill the class arguments.
     std::vector<BatchClass> bcs(nclass);
     auto upload = [&](int chunk_tiles, int mode) -> int {
         for (int c = 0; c < nclass; ++c) {
             ClassPlan &cp = classes[c];
-            build_chunks(cp, V, chunk_tiles, first, nch);
+            build_chunks(cp, V, chunk_tiles > 0 ? chunk_tiles : cp.chunk_tiles, first, nch);
             const size_t n = cp.chunk_ds.size();
             VBH_B_CK(cudaMemcpyAsync(cdev[c].ds_list, cp.ds.data(), sizeof(int) * cp.ds.size(), cudaMemcpyHostToDevice,
                                      stream));
@@ -368,6 +395,8 @@ int fit_batched_impl(BatchedHost &hb, cudaStream_t stream, int nsm, int B, const
             bc.nchunks = int(n);
             bc.partials = cdev[c].partials;
             bc.nstat = cp.bi.nstat;
+            bc.rows_per_chunk = cp.bi.rows_per_chunk;
+            bc.stages = cp.stages;
             bc.next = counters + c;
             bc.ds_list = cdev[c].ds_list;
             bc.ds_first_chunk = ds_first;
@@ -387,7 +416,7 @@ int fit_batched_impl(BatchedHost &hb, cudaStream_t stream, int nsm, int B, const
     auto launch_pass = [&](int c) -> int {
         void *args[] = {&bcs[c]};
         VBH_B_CK(cudaLaunchKernel(classes[c].bi.pass, dim3(pass_grid(c)), dim3(classes[c].bi.threads), args,
-                                  classes[c].bi.pass_smem, stream));
+                                  classes[c].smem(), stream));
         return VBH_OK;
     };
     auto launch_update = [&](int c) -> int {
@@ -398,7 +427,6 @@ int fit_batched_impl(BatchedHost &hb, cudaStream_t stream, int nsm, int B, const
     };
 
     // ---------------- set-up of every state ----------------
-    int rc;
     const int init = (o->init == VBH_INIT_GIVEN) ? 0 : 1;
     if ((rc = upload(kCandidates[1], MODE_INIT))) return rc;
     for (int c = 0; c < nclass; ++c) {
@@ -407,38 +435,61 @@ int fit_batched_impl(BatchedHost &hb, cudaStream_t stream, int nsm, int B, const
         VBH_B_CK(cudaLaunchKernel(classes[c].bi.setup, dim3(bcs[c].nds), dim3(32), args, 0, stream));
     }
 
-    // ---------------- chunk-size autotuner: time one data pass per candidate ----------------
-    int best = kCandidates[1];
+    // ---------------- autotuner: per class, tiles per chunk x pipeline stages ----------------
+    // Each candidate is timed on one data pass of its class alone (CUDA events);
+    // the fastest is kept.  Small batches (< 2^26 observations) keep the defaults.
     long long total_obs = 0;
     for (int b = 0; b < B; ++b) total_obs += V[b];
     if (total_obs >= (1LL << 26)) {
         cudaEvent_t e0, e1;
         VBH_B_CK(cudaEventCreate(&e0));
         VBH_B_CK(cudaEventCreate(&e1));
-        float best_ms = 1e30f;
+        std::vector<float> best_ms(nclass, 1e30f);
+        std::vector<int> best_chunk(nclass, kCandidates[1]), best_st(nclass, 0);
         for (int cand : kCandidates) {
             if ((rc = upload(cand, MODE_INIT))) break;
-            VBH_B_CK(cudaMemsetAsync(counters, 0, sizeof(unsigned int) * (SMAX + 1), stream));
-            VBH_B_CK(cudaEventRecord(e0, stream));
-            for (int c = 0; c < nclass && !rc; ++c) rc = launch_pass(c);
-            VBH_B_CK(cudaEventRecord(e1, stream));
-            VBH_B_CK(cudaEventSynchronize(e1));
-            float ms = 0.f;
-            VBH_B_CK(cudaEventElapsedTime(&ms, e0, e1));
-            if (ms < best_ms) {
-                best_ms = ms;
-                best = cand;
+            for (int c = 0; c < nclass && !rc; ++c) {
+                ClassPlan &cp = classes[c];
+                for (int st : kStageCandidates) {
+                    if (st > cp.max_stages) continue;
+                    if (set_stages(cp, st) != VBH_OK) continue;
+                    bcs[c].stages = st;
+                    VBH_B_CK(cudaMemsetAsync(counters + c, 0, sizeof(unsigned int), stream));
+                    VBH_B_CK(cudaEventRecord(e0, stream));
+                    if ((rc = launch_pass(c))) break;
+                    VBH_B_CK(cudaEventRecord(e1, stream));
+                    VBH_B_CK(cudaEventSynchronize(e1));
+                    float ms = 0.f;
+                    VBH_B_CK(cudaEventElapsedTime(&ms, e0, e1));
+                    if (ms < best_ms[c]) {
+                        best_ms[c] = ms;
+                        best_chunk[c] = cand;
+                        best_st[c] = st;
+                    }
+                }
             }
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         if (rc) return rc;
+        for (int c = 0; c < nclass; ++c) {
+            ClassPlan &cp = classes[c];
+            cp.chunk_tiles = best_chunk[c];
+            if (best_st[c] > 0) {
+                if ((rc = set_stages(cp, best_st[c]))) return rc;
+                cp.pass_ms = best_ms[c];
+            } else if ((rc = set_stages(cp, std::min(kDefaultStages, cp.max_stages)))) {
+                return rc;
+            }
+        }
         VBH_B_CK(cudaMemsetAsync(counters, 0, sizeof(unsigned int) * (SMAX + 1), stream));
     }
-    hb.last_chunk_tiles = best;
+    hb.plan.clear();
+    for (const ClassPlan &cp : classes)
+        hb.plan.push_back({cp.S, cp.bi.tile, cp.chunk_tiles, cp.stages, cp.per_sm, cp.pass_ms});
 
     // ---------------- sweep 0 ----------------
-    if ((rc = upload(best, init ? MODE_INIT : MODE_ELBO))) return rc;
+    if ((rc = upload(0, init ? MODE_INIT : MODE_ELBO))) return rc;
     for (int c = 0; c < nclass; ++c)
         if ((rc = launch_pass(c))) return rc;
     for (int c = 0; c < nclass; ++c)
@@ -488,7 +539,7 @@ int fit_batched_impl(BatchedHost &hb, cudaStream_t stream, int nsm, int B, const
                     kp.kernel.func = const_cast<void *>(classes[c].bi.pass);
                     kp.kernel.gridDim = dim3(pass_grid(c));
                     kp.kernel.blockDim = dim3(classes[c].bi.threads);
-                    kp.kernel.sharedMemBytes = unsigned(classes[c].bi.pass_smem);
+                    kp.kernel.sharedMemBytes = unsigned(classes[c].smem());
                     kp.kernel.kernelParams = pargs;
                     cudaGraphNode_t pn, un;
                     if (cudaGraphAddNode(&pn, body, nullptr, nullptr, 0, &kp) != cudaSuccess) {

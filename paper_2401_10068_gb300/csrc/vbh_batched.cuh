@@ -6,10 +6,11 @@
 //   data pass  (batched_pass_kernel<S>): persistent blocks take chunks --
 //              contiguous observation ranges of one data set -- from an
 //              atomic work queue (largest chunks first), stream them through
-//              the same shared-memory ring and per-observation algebra as the
-//              single-data-set kernel, and write one FP64 partial per chunk;
+//              a shared-memory ring filled by a producer warp, with the same
+//              per-observation algebra as the single-data-set kernel, and
+//              write one FP64 partial row per chunk and compute warp;
 //   update     (batched_update_kernel<M>): one block per data set adds its
-//              chunks' partials in chunk order and runs the FP64 global
+//              chunks' partial rows in order and runs the FP64 global
 //              update, ELBO and convergence test of that data set;
 // then batched_control_kernel counts the data sets still running and sets
 // the while condition of the CUDA graph that repeats the sweep.  Data sets
@@ -32,8 +33,10 @@ struct BatchClass {
     const long long *ds_V;          // [B] observations per data set
     const int *order;               // [nchunks] scheduling order (chunk ids)
     int nchunks;
-    double *partials;               // [nchunks][nstat]
-    int nstat;                      // columns of a chunk partial: NSTAT, or NSTAT + 1 for the compensated form
+    double *partials;               // [nchunks][rows_per_chunk][nstat]
+    int nstat;                      // columns of a partial row: NSTAT, or NSTAT + 1 for the compensated form
+    int rows_per_chunk;             // partial rows per chunk (the pass's compute warps)
+    int stages;                     // pipeline stages of the pass (1 .. BatchCfg<S>::MAX_STAGES)
     unsigned int *next;             // work-queue counter of this class
     const int *ds_list;             // [nds] data sets of this class
     const int *ds_first_chunk;      // [B] first chunk id of each data set (within its class)
@@ -58,6 +61,7 @@ __device__ __forceinline__ bool ds_running(const DevState *st)
 }
 
 // Stage metadata written by the producer thread when it fills a stage.
+// Stage metadata written by the producer when it fills a stage.
 struct StageMeta {
     int chunk;                      // -1: end of work
     int ds;
@@ -67,26 +71,41 @@ struct StageMeta {
 };
 enum : int { UNIT_TAIL = 1, UNIT_LAST = 2 };
 
+// Shape of the batched pass.  Warps 0-6 compute, warp 7 is the producer: its
+// lane 0 owns the work-queue cursor and refills a stage once the seven
+// compute warps have released it (per-stage empty mbarriers), so the compute
+// warps never meet at a block barrier.  The number of stages is chosen at
+// run time (the autotuner, up to MAX_STAGES); shared memory holds the
+// barriers and metadata, then (compensated form) the table of profile terms
+// and two copies of the split pass globals, then the ring.
 template <int S>
 struct BatchCfg {
     using C = SweepCfg<S>;
     static constexpr int THREADS = 256;
-    // observations per thread per tile: 4 (1,024 per tile) except at S = 8,
-    // where two blocks per SM need the 768-observation ring
-    static constexpr int OPT = (S == 8) ? 3 : 4;
-    static constexpr int T = THREADS * OPT;
-    static constexpr int STAGES = 3;
+    static constexpr int CW = 7;                                   // compute warps
+    static constexpr int CT = 32 * CW;                             // compute threads
+    static constexpr int PRODUCER_WARP = CW;
+    static constexpr int OPT = 4;                                  // observations per compute thread per tile
+    static constexpr int T = CT * OPT;                             // observations per tile (896)
+    static constexpr int MAX_STAGES = 8;
     static constexpr uint32_t R_BYTES = T * 4u;
     static constexpr uint32_t D_BYTES = T * S * 4u;
     static constexpr uint32_t STAGE_BYTES = R_BYTES + D_BYTES;
-    static constexpr size_t RING_BYTES = size_t(STAGES) * STAGE_BYTES;
-    static constexpr size_t SMEM_BYTES = RING_BYTES + 64;
-    // compensated form: the ring, the table of profile terms, the split pass globals
-    static constexpr size_t OFF_TAB = RING_BYTES, OFF_SPLIT = OFF_TAB + C::TAB_BYTES;
-    static constexpr size_t SMEM_BYTES_C = OFF_SPLIT + C::SPLIT_BYTES + 64;
+    static_assert(R_BYTES % 16 == 0 && D_BYTES % 16 == 0, "bulk copies need 16-byte sizes and offsets");
+    // mbarriers: full[MAX_STAGES], empty[MAX_STAGES], the compute warps' rendezvous
+    static constexpr size_t OFF_BAR = 0;
+    static constexpr size_t OFF_META = 256;
+    static_assert(size_t(2 * MAX_STAGES + 1) * 8 <= OFF_META, "barriers overlap the metadata");
+    static_assert(OFF_META + MAX_STAGES * sizeof(StageMeta) <= 512, "metadata overlaps the ring");
+    static constexpr size_t FIXED = 512;                           // plain form: the ring starts here
+    static constexpr size_t TAB_AL = (C::TAB_BYTES + 127) / 128 * 128;
+    static constexpr size_t SPLIT_AL = (C::SPLIT_BYTES + 127) / 128 * 128;
+    static constexpr size_t OFF_TAB = FIXED, OFF_SPLIT = OFF_TAB + TAB_AL;
+    static constexpr size_t FIXED_C = OFF_SPLIT + 2 * SPLIT_AL;    // compensated form: the ring starts here
+    static constexpr size_t smem(bool comp, int stages) { return (comp ? FIXED_C : FIXED) + size_t(stages) * STAGE_BYTES; }
 };
 
-// Producer state (thread 0 of a block): the chunk being issued and the next unit.
+// Producer state (lane 0 of the producer warp): the chunk being issued and the next unit.
 struct Cursor {
     int chunk;                      // current chunk (-1: none)
     int ds;
@@ -127,16 +146,19 @@ __device__ __forceinline__ bool cursor_advance(Cursor &cu, const BatchClass &bc,
 }
 
 // Fill stage s with the next unit (a full tile by bulk copy, or the ragged
+
+// Fill a stage with the next unit (a full tile by bulk copy, or the ragged
 // tail of a chunk, read later with plain loads), or with the end mark.
+// Returns false after writing the end mark.
 template <int S>
-__device__ __forceinline__ void issue_unit(Cursor &cu, const BatchClass &bc, int mode, unsigned char *stage,
+__device__ __forceinline__ bool issue_unit(Cursor &cu, const BatchClass &bc, int mode, unsigned char *stage,
                                            uint64_t *bar, StageMeta *meta)
 {
     using B = BatchCfg<S>;
     if (cu.done || !cursor_advance<S>(cu, bc, mode)) {
         meta->chunk = -1;
         mbar_arrive_expect_tx(bar, 0u);
-        return;
+        return false;
     }
     meta->chunk = cu.chunk;
     meta->ds = cu.ds;
@@ -156,13 +178,28 @@ __device__ __forceinline__ void issue_unit(Cursor &cu, const BatchClass &bc, int
         cu.next_obs = cu.hi;
         mbar_arrive_expect_tx(bar, 0u);
     }
+    return true;
 }
 
-// One block barrier per unit: every thread waits for the stage, consumes it,
-// and meets the others at the end of the unit, after which thread 0 refills
-// the stage.  A chunk's FP64 partial is staged in one of two reduction buffers
-// before that barrier and summed after it, so the next chunk's partial (into
-// the other buffer) cannot overwrite it while it is read.
+constexpr uint64_t BATCH_WAIT_NS = 2000000000ull;    // bound of every wait of the pass
+
+// Record a timed-out wait of the pass (any thread).
+__device__ __forceinline__ void batch_abort(const BatchClass &bc, volatile int *s_abort)
+{
+    *s_abort = 1;
+    atomicCAS(&bc.ctl->status, ST_OK, ST_ETIMEOUT);
+}
+
+// The data pass of one class.  Units flow through a ring of bc.stages stages:
+// the producer fills stage k % stages with unit k after the compute warps
+// released unit k - stages (empty[s]); every compute warp takes every unit
+// (thread t its observations t + CT u), releases the stage, and at the last
+// unit of a chunk writes its own FP64 row of the chunk partial
+// (partials[chunk][warp][NS]; the update adds the rows in order).  The
+// compensated form switches the table of profile terms when the data set
+// changes: the compute warps write the new split globals into the spare copy,
+// meet (every warp is then done with the old table), build the table and meet
+// again, both times at a bounded mbarrier rendezvous.
 template <int S, bool COMP>
 __global__ void __launch_bounds__(BatchCfg<S>::THREADS, COMP ? SweepCfg<S>::MINB_BC : SweepCfg<S>::MINB)
     batched_pass_kernel(BatchClass bc)
@@ -170,124 +207,171 @@ __global__ void __launch_bounds__(BatchCfg<S>::THREADS, COMP ? SweepCfg<S>::MINB
     using C = SweepCfg<S>;
     using B = BatchCfg<S>;
     constexpr int M = C::M, NG = C::NG, NSTAT = C::NSTAT;
-    constexpr int NS = COMP ? C::NSTATC : C::NSTAT;        // columns of a chunk partial
+    constexpr int NS = COMP ? C::NSTATC : C::NSTAT;        // columns of a partial row
     constexpr int NGRP = COMP ? C::NGRPC : C::NGRP;
-    constexpr int THREADS = B::THREADS, T = B::T, STAGES = B::STAGES;
+    constexpr int CW = B::CW, CT = B::CT, T = B::T;
     extern __shared__ __align__(128) unsigned char smem[];
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + (COMP ? B::SMEM_BYTES_C - 64 : B::RING_BYTES));
-    float4 *tab = reinterpret_cast<float4 *>(smem + B::OFF_TAB);     // compensated form only
-    float *split = reinterpret_cast<float *>(smem + B::OFF_SPLIT);
-    __shared__ StageMeta meta[STAGES];
-    __shared__ double s_red[2][THREADS / 32][NGRP * 32];
-    __shared__ int s_bad;
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + B::OFF_BAR);
+    uint64_t *empty = full + B::MAX_STAGES;
+    uint64_t *rdv = empty + B::MAX_STAGES;
+    StageMeta *meta = reinterpret_cast<StageMeta *>(smem + B::OFF_META);
+    unsigned char *ring = smem + (COMP ? B::FIXED_C : B::FIXED);
+    __shared__ int s_abort;
+    volatile int *abort_flag = &s_abort;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int mode = bc.mode;
+    const int stages = bc.stages;
 
     if (tid == 0) {
-        s_bad = 0;
-        for (int s = 0; s < STAGES; ++s) mbar_init(&full[s], 1);
+        s_abort = 0;
+        for (int s = 0; s < stages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], CW);
+        }
+        mbar_init(rdv, CW);
         fence_mbar_init();
     }
-    __syncthreads();
-    Cursor cu{-1, 0, 0, 0, 0, 1, 0};
-    if (tid == 0)
-        for (int s = 0; s < STAGES; ++s)
-            issue_unit<S>(cu, bc, mode, smem + size_t(s) * B::STAGE_BYTES, &full[s], &meta[s]);
+    __syncthreads();                                        // the only block barrier
 
-    float acc[NSTAT];
-    double acc64[NGRP];
-    float prod = 1.0f, pl = 0.0f, uh = 0.0f, ul = 0.0f;
-    int ex = 0;
-#pragma unroll
-    for (int i = 0; i < NSTAT; ++i) acc[i] = 0.0f;
-#pragma unroll
-    for (int g = 0; g < NGRP; ++g) acc64[g] = 0.0;
+    if (warp == B::PRODUCER_WARP) {
+        if (lane != 0) return;
+        Cursor cu{-1, 0, 0, 0, 0, 1, 0};
+        long long k = 0;
+        bool bad = false;
+        for (;; ++k) {
+            const int s = int(k % stages);
+            if (k >= stages && !mbar_wait_bounded(&empty[s], uint32_t(((k / stages) - 1) & 1), BATCH_WAIT_NS)) {
+                bad = true;
+                break;
+            }
+            if (*abort_flag) {
+                bad = true;
+                break;
+            }
+            if (!issue_unit<S>(cu, bc, mode, ring + size_t(s) * B::STAGE_BYTES, &full[s], &meta[s])) break;
+        }
+        if (bad) {
+            // a wait ran out: record it, then let the copies of the last units
+            // issued on each stage land before the block exits (bounded)
+            batch_abort(bc, abort_flag);
+            for (long long kk = (k > stages ? k - stages : 0); kk < k; ++kk)
+                (void)mbar_wait_bounded(&full[kk % stages], uint32_t((kk / stages) & 1), 100000000ull);
+        }
+        return;
+    }
+
+    // ---------------- compute warps ----------------
+    // One iteration of the outer loop per chunk: the statistics start at zero
+    // (each chunk's last unit flushed them into this warp's partial row), so
+    // a data-set switch at the chunk's first unit holds no accumulator live.
     // plain form: L~ (L) and kappa~ (kap) in registers; compensated form: the
-    // split globals of the current data set and its table of profile terms in
-    // shared memory, switched by the whole block between units
+    // split globals of the current data set (copy cur & 1) and its table of
+    // profile terms in shared memory
     float L[COMP ? 1 : C::NGA], kap[COMP ? 1 : C::MA], erho = 0.0f;
     L[0] = 0.0f;
     kap[0] = 0.0f;
-    int cur_ds = -1;
-    // (compensated form) make data set ds current: split globals, E[rho], table.
-    // Called by every thread with the same ds, between units.
-    auto switch_to = [&](int ds) {
-        const DevState *st = bc.states + ds;
-        for (int i = tid; i < C::SPLIT_FLOATS; i += THREADS) {
-            float v;
-            if (i < NG) v = st->sw.Sh[i];
-            else if (i < 2 * NG) v = st->sw.Sl[i - NG];
-            else if (i < 2 * NG + M) v = st->sw.kh[i - 2 * NG];
-            else v = st->sw.kl[i - 2 * NG - M];
-            split[i] = v;
-        }
-        erho = (mode == MODE_INIT) ? 0.0f : st->sw.erho;
-        __syncthreads();
-        build_profile_table<S>(tab, split, erho, tid, THREADS);
-        __syncthreads();
-        cur_ds = ds;
+    float4 *tab = reinterpret_cast<float4 *>(smem + B::OFF_TAB);
+    float *split = reinterpret_cast<float *>(smem + B::OFF_SPLIT);
+    int cur_ds = -1, nswitch = 0;
+    uint32_t rv = 0;                                        // rendezvous phases passed
+    // every compute warp arrives; true once all seven have (bounded)
+    auto rendezvous = [&]() -> bool {
+        __syncwarp();
+        if (lane == 0) mbar_arrive(rdv);
+        const bool ok = mbar_wait_bounded(rdv, rv & 1u, BATCH_WAIT_NS);
+        ++rv;
+        return __all_sync(0xffffffffu, ok);
     };
-    if constexpr (COMP) {
-        __syncthreads();                                    // the first unit's metadata
-        if (meta[0].chunk >= 0) switch_to(meta[0].ds);
-    }
-    int ftile = 0;
-    int rbuf = 0;                                           // reduction buffer of the next chunk partial
+    // wait for unit k (its stage and metadata); false on a timeout (recorded)
+    auto take = [&](long long k, StageMeta &m) -> bool {
+        const int s = int(k % stages);
+        if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[s], uint32_t((k / stages) & 1), BATCH_WAIT_NS))) {
+            if (lane == 0) batch_abort(bc, abort_flag);
+            return false;
+        }
+        m = meta[s];                                        // the same for every thread once the stage is full
+        return true;
+    };
 
-    long long kbreak = 0;
-    for (long long k = 0;; ++k) {
-        const int s = int(k % STAGES);
-        const bool ok = mbar_wait_bounded(&full[s], uint32_t((k / STAGES) & 1), 2000000000ull);
+    long long k = 0;
+    while (true) {
+        float acc[NSTAT];
+        double acc64[NGRP];
+        float prod = 1.0f, pl = 0.0f, uh = 0.0f, ul = 0.0f;
+        int ex = 0, ftile = 0;
+#pragma unroll
+        for (int i = 0; i < NSTAT; ++i) acc[i] = 0.0f;
+#pragma unroll
+        for (int g = 0; g < NGRP; ++g) acc64[g] = 0.0;
         StageMeta m;
-        m.chunk = -1;
-        m.flags = 0;
-        if (ok) m = meta[s];                                // the same for every thread once the stage is full
-        const bool work = ok && m.chunk >= 0;
-        if (work) {
-            if constexpr (!COMP) {
-                if (m.ds != cur_ds) {                       // a new data set: its FP32 globals (cached reads)
-                    const DevState *st = bc.states + m.ds;
-#pragma unroll
-                    for (int i = 0; i < NG; ++i) L[i] = st->sw.L[i];
-#pragma unroll
-                    for (int i = 0; i < M; ++i) kap[i] = st->sw.kappa[i];
-                    erho = (mode == MODE_INIT) ? 0.0f : st->sw.erho;
-                    cur_ds = m.ds;
+        if (!take(k, m) || m.chunk < 0) break;              // a timeout, or the end mark
+        if (m.ds != cur_ds) {
+            const DevState *st = bc.states + m.ds;
+            erho = (mode == MODE_INIT) ? 0.0f : st->sw.erho;
+            if constexpr (COMP) {
+                // the spare copy of the split globals is free: every warp passed the
+                // previous switch's first rendezvous, so none reads it any more
+                float *sp = split + (nswitch & 1) * (B::SPLIT_AL / 4);
+                for (int i = tid; i < C::SPLIT_FLOATS; i += CT) {
+                    float v;
+                    if (i < NG) v = st->sw.Sh[i];
+                    else if (i < 2 * NG) v = st->sw.Sl[i - NG];
+                    else if (i < 2 * NG + M) v = st->sw.kh[i - 2 * NG];
+                    else v = st->sw.kl[i - 2 * NG - M];
+                    sp[i] = v;
                 }
+                if (!rendezvous()) {                        // done with the old table; new split written
+                    if (lane == 0) batch_abort(bc, abort_flag);
+                    break;
+                }
+                build_profile_table<S>(tab, sp, erho, tid, CT);
+                if (!rendezvous()) {                        // the table is complete
+                    if (lane == 0) batch_abort(bc, abort_flag);
+                    break;
+                }
+                ++nswitch;
+            } else {
+#pragma unroll
+                for (int i = 0; i < NG; ++i) L[i] = st->sw.L[i];
+#pragma unroll
+                for (int i = 0; i < M; ++i) kap[i] = st->sw.kappa[i];
             }
+            cur_ds = m.ds;
+        }
+        const float *sp = split + ((nswitch + 1) & 1) * (B::SPLIT_AL / 4);   // copy of the current data set
+        bool ok = true;
+        while (true) {                                      // the units of chunk m.chunk
+            const int s = int(k % stages);
             if (!(m.flags & UNIT_TAIL)) {
-                const float *rt = reinterpret_cast<const float *>(smem + size_t(s) * B::STAGE_BYTES);
+                const float *rt = reinterpret_cast<const float *>(ring + size_t(s) * B::STAGE_BYTES);
                 const float *dt = rt + T;
 #pragma unroll
                 for (int u = 0; u < B::OPT; ++u) {
-                    const int j = tid + u * THREADS;
+                    const int j = tid + u * CT;
                     float x[S];
                     load_row<S>(dt, j, x);
                     if constexpr (COMP) {
-                        observe_comp<S>(x, rt[j], tab, split, erho, acc, prod, pl, uh, ul);
-                        peel_exponent2(prod, pl, ex);
+                        observe_comp<S>(x, rt[j], tab, sp, erho, acc, prod, pl, uh, ul);
+                        if (u & 1) peel_exponent2(prod, pl, ex);
                     } else {
                         observe<S>(x, rt[j], L, kap, erho, acc, prod);
-                        peel_exponent(prod, ex);
+                        if (u & 1) peel_exponent(prod, ex);
                     }
                 }
-                if (++ftile == 16) {
-                    if constexpr (COMP)
-                        flush_warp_comp<S>(acc, acc64, prod, pl, ex, uh, ul, lane);
-                    else
-                        flush_warp<S>(acc, acc64, prod, ex, lane);
-                    ftile = 0;
-                }
-            } else {
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);          // this warp's reads of stage s are done
+            ++k;
+            if (m.flags & UNIT_TAIL) {
                 const float *rg = bc.r[m.ds];
                 const float *dg = bc.d[m.ds];
                 const long long hi = bc.chunk_hi[m.chunk];
-                for (long long i = m.obs0 + tid; i < hi; i += THREADS) {
+                for (long long i = m.obs0 + tid; i < hi; i += CT) {
                     float x[S];
 #pragma unroll
                     for (int q = 0; q < S; ++q) x[q] = __ldg(dg + i * S + q);
                     if constexpr (COMP) {
-                        observe_comp<S>(x, __ldg(rg + i), tab, split, erho, acc, prod, pl, uh, ul);
+                        observe_comp<S>(x, __ldg(rg + i), tab, sp, erho, acc, prod, pl, uh, ul);
                         peel_exponent2(prod, pl, ex);
                     } else {
                         observe<S>(x, __ldg(rg + i), L, kap, erho, acc, prod);
@@ -295,48 +379,29 @@ __global__ void __launch_bounds__(BatchCfg<S>::THREADS, COMP ? SweepCfg<S>::MINB
                     }
                 }
             }
-            if (m.flags & UNIT_LAST) {                      // chunk done: stage its FP64 partial
+            if (m.flags & UNIT_LAST) break;
+            if (++ftile == 16) {
                 if constexpr (COMP)
                     flush_warp_comp<S>(acc, acc64, prod, pl, ex, uh, ul, lane);
                 else
                     flush_warp<S>(acc, acc64, prod, ex, lane);
                 ftile = 0;
-#pragma unroll
-                for (int g = 0; g < NGRP; ++g) {
-                    s_red[rbuf][warp][g * 32 + lane] = acc64[g];
-                    acc64[g] = 0.0;
-                }
+            }
+            if (!take(k, m)) {                              // the chunk's next unit
+                ok = false;
+                break;
             }
         }
-        if (__syncthreads_or(!ok)) {                        // stage s is free again; s_red[rbuf] is complete
-            if (tid == 0) s_bad = 1;
-            kbreak = k;
-            break;
-        }
-        if (!work) break;                                   // the end mark (every thread read it)
-        if (m.flags & UNIT_LAST) {
-            for (int j = tid; j < NS; j += THREADS) {
-                double t = 0.0;
+        if (!ok) break;
+        // chunk done: this warp's row of its partial
+        if constexpr (COMP)
+            flush_warp_comp<S>(acc, acc64, prod, pl, ex, uh, ul, lane);
+        else
+            flush_warp<S>(acc, acc64, prod, ex, lane);
+        double *row = bc.partials + (size_t(m.chunk) * CW + warp) * NS;
 #pragma unroll
-                for (int w = 0; w < THREADS / 32; ++w) t += s_red[rbuf][w][j];
-                bc.partials[size_t(m.chunk) * NS + j] = t;
-            }
-            rbuf ^= 1;
-        }
-        if constexpr (COMP) {
-            // the next unit's metadata was written before this unit's barrier (it was issued
-            // STAGES - 1 units ago, or in the prologue); a new data set switches here, block-wide
-            const StageMeta nx = meta[(k + 1) % STAGES];
-            if (nx.chunk >= 0 && nx.ds != cur_ds) switch_to(nx.ds);
-        }
-        if (tid == 0) issue_unit<S>(cu, bc, mode, smem + size_t(s) * B::STAGE_BYTES, &full[s], &meta[s]);
-    }
-    if (s_bad && tid == 0) {
-        // a wait ran out: record it, then let the copies this block issued and
-        // did not consume land before the block exits (bounded)
-        atomicCAS(&bc.ctl->status, ST_OK, ST_ETIMEOUT);
-        for (long long kk = kbreak; kk < kbreak + STAGES; ++kk)
-            (void)mbar_wait_bounded(&full[kk % STAGES], uint32_t((kk / STAGES) & 1), 100000000ull);
+        for (int g = 0; g < NGRP; ++g)
+            if (g * 32 + lane < NS) row[g * 32 + lane] = acc64[g];
     }
 }
 
@@ -351,8 +416,9 @@ __global__ void __launch_bounds__(256) batched_update_kernel(BatchClass bc, Batc
     SweepArgs a{};
     a.mode = mode;
     a.use_cond = 0;
-    global_update<M>(st, bc.partials + size_t(bc.ds_first_chunk[b]) * bc.nstat, bc.ds_nchunks[b], a,
-                     reinterpret_cast<double *>(smem));
+    // the data set's chunk partials: rows_per_chunk rows per chunk (one per compute warp of the pass)
+    global_update<M>(st, bc.partials + size_t(bc.ds_first_chunk[b]) * bc.rows_per_chunk * bc.nstat,
+                     bc.ds_nchunks[b] * bc.rows_per_chunk, a, reinterpret_cast<double *>(smem));
     __syncthreads();                                       // the control fields were written by another warp
     if (threadIdx.x == 0 && ds_running(st)) atomicAdd(&ctl->active, 1u);
 }

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstddef>
+#include <vector>
 
 #include "vbh.h"
 
@@ -14,7 +15,7 @@ struct BatchedHost {
     size_t arena_cap = 0;
     void *host_states = nullptr;     // pinned host copies of the states
     size_t host_states_cap = 0;
-    int last_chunk_tiles = 0;        // the autotuner's choice in the last call
+    std::vector<vbh_batch_plan> plan; // per class: the pass shape of the last call (the autotuner's choice)
 };
 
 int fit_batched_impl(BatchedHost &hb, cudaStream_t stream, int nsm, int B, const int64_t *V, const int *S,

@@ -30,12 +30,15 @@ struct BatchKernelInfo {
     const void *pass_comp; // batched_pass_kernel<S, true>
     const void *update;    // batched_update_kernel<S - 1>
     const void *setup;     // batched_setup_kernel<S - 1>
-    size_t pass_smem;
-    size_t pass_smem_comp;
+    size_t pass_fixed;     // shared memory of the pass without its ring (plain form)
+    size_t pass_fixed_comp; // the same for the compensated form
+    size_t stage_bytes;    // shared memory of one pipeline stage
+    int max_stages;
     size_t update_smem;
     int threads;
     int tile;              // observations per tile of the pass
-    int nstat;             // statistics per chunk partial (plain form; the compensated form has nstat + 1)
+    int rows_per_chunk;    // partial rows per chunk (compute warps of the pass)
+    int nstat;             // statistics per partial row (plain form; the compensated form has nstat + 1)
 };
 
 // Each translation unit that instantiates sweep kernels fills the entries of
@@ -78,11 +81,14 @@ bool batch_kernel_info_s9_11(int S, BatchKernelInfo *out);
         out->pass_comp = reinterpret_cast<const void *>(&::vbh::batched_pass_kernel<SV, true>);                        \
         out->update = reinterpret_cast<const void *>(&::vbh::batched_update_kernel<SV - 1>);                           \
         out->setup = reinterpret_cast<const void *>(&::vbh::batched_setup_kernel<SV - 1>);                             \
-        out->pass_smem = BC::SMEM_BYTES;                                                                               \
-        out->pass_smem_comp = BC::SMEM_BYTES_C;                                                                        \
+        out->pass_fixed = BC::FIXED;                                                                                   \
+        out->pass_fixed_comp = BC::FIXED_C;                                                                            \
+        out->stage_bytes = BC::STAGE_BYTES;                                                                            \
+        out->max_stages = BC::MAX_STAGES;                                                                              \
         out->update_smem = size_t(::vbh::gu_ws_doubles<SV - 1>()) * 8;                                                 \
         out->threads = BC::THREADS;                                                                                    \
         out->tile = BC::T;                                                                                             \
+        out->rows_per_chunk = BC::CW;                                                                                  \
         out->nstat = ::vbh::SweepCfg<SV>::NSTAT;                                                                       \
         return true;                                                                                                   \
     }

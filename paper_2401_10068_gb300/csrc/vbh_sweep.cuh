@@ -47,7 +47,7 @@ struct SweepCfg {
     static constexpr int THREADS = 256;
     static constexpr int MINB = (S <= 8) ? 2 : 1;           // resident blocks per SM the registers are sized for
     static constexpr int MINB_C = (S <= 8) ? 2 : 1;         // the same for the compensated form
-    static constexpr int MINB_BC = (S <= 6) ? 2 : 1;        // and for its batched pass (more live state)
+    static constexpr int MINB_BC = (S <= 9) ? 2 : 1;        // and for its batched pass
     static constexpr int OPT = 4;                           // observations per thread per tile
     static constexpr int T = THREADS * OPT;                 // observations per tile
     static constexpr int STAGES = 3;

@@ -83,6 +83,11 @@ class Opts(ctypes.Structure):
                 ("loop", ctypes.c_int)]
 
 
+class BatchPlan(ctypes.Structure):
+    _fields_ = [("S", ctypes.c_int), ("tile", ctypes.c_int), ("chunk_tiles", ctypes.c_int), ("stages", ctypes.c_int),
+                ("blocks_per_sm", ctypes.c_int), ("pass_ms", ctypes.c_float)]
+
+
 _LIB = None
 
 
@@ -114,6 +119,7 @@ def _lib():
             "vbh_fit_static": (ci, [vp, vp, i64, ci, P, O, R, ci, vp]),
             "vbh_fit_batched": (ci, [vp, ci, ctypes.POINTER(i64), ctypes.POINTER(ci), ctypes.POINTER(vp),
                                      ctypes.POINTER(vp), P, O, R]),
+            "vbh_batched_plan": (ci, [vp, ctypes.POINTER(BatchPlan), ci, ctypes.POINTER(ci)]),
             "vbh_ws_create": (ci, [ctypes.POINTER(vp), ctypes.c_uint64, ci, vp]),
             "vbh_ws_destroy": (None, [vp]),
             "vbh_ws_num_params": (ctypes.c_size_t, [vp]),
@@ -389,6 +395,16 @@ class Handle:
             err.results = res
             raise err
         return res
+
+    def batched_plan(self) -> list:
+        """``vbh_batched_plan``: per class of the last ``fit_batched`` call, the
+        data-pass shape (tile, tiles per chunk, stages, blocks per SM) and the
+        autotuner's pass time."""
+        n = ctypes.c_int(0)
+        _check(_lib().vbh_batched_plan(self._h, None, 0, ctypes.byref(n)), "vbh_batched_plan")
+        buf = (BatchPlan * max(n.value, 1))()
+        _check(_lib().vbh_batched_plan(self._h, buf, n.value, ctypes.byref(n)), "vbh_batched_plan")
+        return [{f: getattr(buf[i], f) for f, _ in BatchPlan._fields_} for i in range(n.value)]
 
     def elbo(self, r, d, S: int, state: dict, prior: dict | None = None, V: int | None = None) -> float:
         V = int(V if V is not None else (r.shape[0] if r is not None else 0))

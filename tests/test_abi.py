@@ -70,6 +70,13 @@ def test_result_struct_layout_matches_header():
     assert vbh.Opts.method.offset == 40 and vbh.Opts.grouped.offset == 44 and vbh.Opts.stats.offset == 48
     assert vbh.Opts.loop.offset == 52
     assert ctypes.sizeof(vbh.Opts) == 56
+    assert ctypes.sizeof(vbh.BatchPlan) == 24 and vbh.BatchPlan.pass_ms.offset == 20
+
+
+def test_batched_plan_refuses_null_arguments():
+    lib = vbh._lib()
+    n = ctypes.c_int(-1)
+    assert lib.vbh_batched_plan(None, None, 0, ctypes.byref(n)) == -1 and n.value == -1
 
 
 def test_create_fails_loudly_without_a_gpu():

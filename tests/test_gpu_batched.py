@@ -39,8 +39,8 @@ def _check(got, ref, V, what):
 
 def _mixed_batch(seed0=500):
     # uneven sizes: empty, smaller than a tile, one observation either side of
-    # a tile (1,024 observations; 768 at S = 8), ragged, several chunks
-    specs = [(3, 0), (1, 1000), (2, 1023), (2, 1024), (8, 767), (8, 768), (3, 96000), (4, 50001), (5, 12000),
+    # a tile (896 observations), two tiles, ragged, several chunks
+    specs = [(3, 0), (1, 1000), (2, 895), (2, 896), (8, 897), (8, 1792), (3, 96000), (4, 50001), (5, 12000),
              (6, 33333), (7, 20000), (8, 60013), (9, 9600), (10, 15000), (11, 8000), (3, 250_000), (8, 700_001)]
     rs, ds, Ss, host = [], [], [], []
     for k, (S, V) in enumerate(specs):
@@ -146,3 +146,59 @@ def test_batched_errors(handle):
         handle.fit_batched([torch.from_numpy(r).cuda()], [d], [3], None, tol=0.0, max_iter=2)
     assert e.value.status == -1
     assert handle.fit_batched([], [], [], None) == []
+
+
+def test_batched_many_small_data_sets_compensated(handle):
+    """Dozens of small data sets per class: a pass block changes data set
+    every few tiles, so the compensated form rebuilds its table of profile
+    terms at nearly every chunk (the compute warps' rendezvous), and chunks
+    of one tile or only a tail are common.  Each data set against the oracle
+    at equal sweeps."""
+    rng = np.random.default_rng(77)
+    specs = [(4, int(v)) for v in rng.integers(100, 6000, 40)] + [(9, int(v)) for v in rng.integers(800, 5000, 16)]
+    specs += [(4, 896), (4, 1), (9, 895)]
+    rs, ds, Ss, host = [], [], [], []
+    for k, (S, V) in enumerate(specs):
+        r, d, _ = synth.generate(V, S, seed=4000 + k, alpha=0.5)
+        host.append((r, d))
+        rs.append(torch.from_numpy(r).cuda())
+        ds.append(torch.from_numpy(d).cuda())
+        Ss.append(S)
+    sweeps = 4
+    priors = [O.paper_prior(S, n0=S + 1.0) for S, _ in specs]     # proper even at V = 1
+    got = handle.fit_batched(rs, ds, Ss, priors, tol=0.0, max_iter=sweeps, trace=True, stats=vbh.STATS_COMPENSATED)
+    for (S, V), g, (r, d), p in zip(specs, got, host, priors):
+        ref = O.fit(r, d, p, tol=0.0, max_iter=sweeps)
+        assert g["iters"] == sweeps
+        _check(g, ref, V, (S, V))
+        for t, (a, b) in enumerate(zip(g["trace"], ref["trace"])):
+            assert abs(a - b) <= TOL_E * max(abs(b), V, 1.0), (S, V, t)
+    plan = handle.batched_plan()
+    assert [p["S"] for p in plan] == [4, 9]
+    for p in plan:           # below 2^26 observations: the default shape, not timed
+        assert p["tile"] == 896 and p["chunk_tiles"] == 32 and p["stages"] == 3 and p["pass_ms"] == 0.0
+        assert p["blocks_per_sm"] >= 1
+
+
+def test_batched_autotuned_shape_matches_default_shape(handle):
+    """At >= 2^26 observations the pass shape (tiles per chunk, stages) is
+    autotuned per class; the statistics do not depend on the stage count and
+    the chunk rows are summed in order, so the fit equals the oracle's as
+    before, and the plan reports a timed candidate for every class."""
+    specs = [(3, 30_000_000), (6, 20_000_000), (6, 7_000_001), (10, 12_000_000)]
+    rs, ds, Ss = [], [], []
+    for k, (S, V) in enumerate(specs):
+        r, d, _ = synth.generate_device(V, S, seed=5100 + k, alpha=0.5)
+        rs.append(r)
+        ds.append(d)
+        Ss.append(S)
+    got = handle.fit_batched(rs, ds, Ss, None, tol=0.0, max_iter=2, trace=True)
+    plan = handle.batched_plan()
+    assert [p["S"] for p in plan] == [3, 6, 10]
+    for p in plan:
+        assert p["chunk_tiles"] in (8, 32, 128) and 2 <= p["stages"] <= 8 and p["pass_ms"] > 0.0
+    for (S, V), g, r, d in zip(specs, got, rs, ds):
+        one = handle.fit(r, d, S, None, tol=0.0, max_iter=2, trace=True)
+        _check(g, one, V, (S, V))
+        for t, (a, b) in enumerate(zip(g["trace"], one["trace"])):
+            assert abs(a - b) <= TOL_E * max(abs(b), V, 1.0), (S, V, t)
