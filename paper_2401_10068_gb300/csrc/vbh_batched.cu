@@ -89,18 +89,18 @@ struct Arena {
 struct ClassPlan {
     int S = 0;
     BatchKernelInfo bi{};
+    BatchPassInfo pi{};                     // the pass of the chosen form (plain or compensated)
     std::vector<int> ds;                    // data sets of the class
     std::vector<int> chunk_ds;
     std::vector<long long> lo, hi;
     std::vector<int> order;
-    size_t fixed = 0;                       // shared memory of the pass without its ring (chosen form)
     int max_stages = 0;                     // most stages whose ring fits one block
     int stages = 0;                         // the pass's stages (autotuned)
     int chunk_tiles = 0;                    // tiles per chunk (autotuned)
     int grid = 0;                           // persistent blocks of the pass at `stages`
     int per_sm = 0;
     float pass_ms = 0.f;                    // the autotuner's time of the chosen pass (0: not timed)
-    size_t smem() const { return fixed + size_t(stages) * bi.stage_bytes; }
+    size_t smem() const { return pi.fixed + size_t(stages) * pi.stage_bytes; }
 };
 
 void build_chunks(ClassPlan &cp, const int64_t *V, int chunk_tiles, std::vector<int> &first, std::vector<int> &nch)
@@ -108,7 +108,7 @@ void build_chunks(ClassPlan &cp, const int64_t *V, int chunk_tiles, std::vector<
     cp.chunk_ds.clear();
     cp.lo.clear();
     cp.hi.clear();
-    const long long T = cp.bi.tile;
+    const long long T = cp.pi.tile;
     for (int b : cp.ds) {
         const long long ntiles = V[b] / T;
         const long long per = chunk_tiles;
@@ -205,7 +205,7 @@ int fit_batched_impl(BatchedHost &hb, cudaStream_t stream, int nsm, int B, const
     auto set_stages = [&](ClassPlan &cp, int st) -> int {
         cp.stages = st;
         int per_sm = 0;
-        VBH_B_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cp.bi.pass, cp.bi.threads, cp.smem()));
+        VBH_B_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cp.pi.pass, cp.pi.threads, cp.smem()));
         cp.per_sm = per_sm;
         cp.grid = nsm * std::max(per_sm, 1);
         return per_sm >= 1 ? VBH_OK : VBH_EUNSUPPORTED;
@@ -218,17 +218,14 @@ int fit_batched_impl(BatchedHost &hb, cudaStream_t stream, int nsm, int B, const
             if (S[b] == s) cp.ds.push_back(b);
         if (cp.ds.empty()) continue;
         if (!batch_info(s, &cp.bi)) return VBH_EUNSUPPORTED;
-        cp.fixed = comp ? cp.bi.pass_fixed_comp : cp.bi.pass_fixed;
-        if (comp) {
-            cp.bi.pass = cp.bi.pass_comp;
-            cp.bi.nstat += 1;
-        }
+        cp.pi = comp ? cp.bi.comp : cp.bi.plain;
+        if (comp) cp.bi.nstat += 1;
         cp.max_stages = 0;
-        for (int st = 1; st <= cp.bi.max_stages; ++st)
-            if (cp.fixed + size_t(st) * cp.bi.stage_bytes + 1024 <= size_t(smem_optin)) cp.max_stages = st;
+        for (int st = 1; st <= cp.pi.max_stages; ++st)
+            if (cp.pi.fixed + size_t(st) * cp.pi.stage_bytes + 1024 <= size_t(smem_optin)) cp.max_stages = st;
         if (cp.max_stages < 2) return VBH_EUNSUPPORTED;
-        VBH_B_CK(cudaFuncSetAttribute(cp.bi.pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      int(cp.fixed + size_t(cp.max_stages) * cp.bi.stage_bytes)));
+        VBH_B_CK(cudaFuncSetAttribute(cp.pi.pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      int(cp.pi.fixed + size_t(cp.max_stages) * cp.pi.stage_bytes)));
         VBH_B_CK(cudaFuncSetAttribute(cp.bi.update, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       int(cp.bi.update_smem)));
         if ((rc = set_stages(cp, std::min(kDefaultStages, cp.max_stages)))) return rc;
@@ -260,7 +257,7 @@ int fit_batched_impl(BatchedHost &hb, cudaStream_t stream, int nsm, int B, const
         add(sizeof(int) * cp.ds.size());
         add(sizeof(int) * max_chunks * 2);
         add(sizeof(long long) * max_chunks * 2);
-        add(sizeof(double) * max_chunks * cp.bi.rows_per_chunk * cp.bi.nstat);
+        add(sizeof(double) * max_chunks * cp.pi.rows_per_chunk * cp.bi.nstat);
     }
     add(stage_bytes);
     need += 4096;
@@ -294,7 +291,7 @@ int fit_batched_impl(BatchedHost &hb, cudaStream_t stream, int nsm, int B, const
         cdev[c].lo = static_cast<long long *>(ar.take(sizeof(long long) * max_chunks));
         cdev[c].hi = static_cast<long long *>(ar.take(sizeof(long long) * max_chunks));
         cdev[c].partials = static_cast<double *>(
-            ar.take(sizeof(double) * max_chunks * classes[c].bi.rows_per_chunk * classes[c].bi.nstat));
+            ar.take(sizeof(double) * max_chunks * classes[c].pi.rows_per_chunk * classes[c].bi.nstat));
     }
     unsigned char *stage = static_cast<unsigned char *>(ar.take(stage_bytes));
     for (int b = 0; b < B; ++b) {
@@ -395,7 +392,7 @@ int fit_batched_impl(BatchedHost &hb, cudaStream_t stream, int nsm, int B, const
             bc.nchunks = int(n);
             bc.partials = cdev[c].partials;
             bc.nstat = cp.bi.nstat;
-            bc.rows_per_chunk = cp.bi.rows_per_chunk;
+            bc.rows_per_chunk = cp.pi.rows_per_chunk;
             bc.stages = cp.stages;
             bc.next = counters + c;
             bc.ds_list = cdev[c].ds_list;
@@ -415,7 +412,7 @@ int fit_batched_impl(BatchedHost &hb, cudaStream_t stream, int nsm, int B, const
     };
     auto launch_pass = [&](int c) -> int {
         void *args[] = {&bcs[c]};
-        VBH_B_CK(cudaLaunchKernel(classes[c].bi.pass, dim3(pass_grid(c)), dim3(classes[c].bi.threads), args,
+        VBH_B_CK(cudaLaunchKernel(classes[c].pi.pass, dim3(pass_grid(c)), dim3(classes[c].pi.threads), args,
                                   classes[c].smem(), stream));
         return VBH_OK;
     };
@@ -486,7 +483,7 @@ int fit_batched_impl(BatchedHost &hb, cudaStream_t stream, int nsm, int B, const
     }
     hb.plan.clear();
     for (const ClassPlan &cp : classes)
-        hb.plan.push_back({cp.S, cp.bi.tile, cp.chunk_tiles, cp.stages, cp.per_sm, cp.pass_ms});
+        hb.plan.push_back({cp.S, cp.pi.tile, cp.chunk_tiles, cp.stages, cp.per_sm, cp.pass_ms});
 
     // ---------------- sweep 0 ----------------
     if ((rc = upload(0, init ? MODE_INIT : MODE_ELBO))) return rc;
@@ -536,9 +533,9 @@ int fit_batched_impl(BatchedHost &hb, cudaStream_t stream, int nsm, int B, const
                     cudaGraphNodeParams kp{};
                     kp.type = cudaGraphNodeTypeKernel;
                     void *pargs[] = {&bcs[c]};
-                    kp.kernel.func = const_cast<void *>(classes[c].bi.pass);
+                    kp.kernel.func = const_cast<void *>(classes[c].pi.pass);
                     kp.kernel.gridDim = dim3(pass_grid(c));
-                    kp.kernel.blockDim = dim3(classes[c].bi.threads);
+                    kp.kernel.blockDim = dim3(classes[c].pi.threads);
                     kp.kernel.sharedMemBytes = unsigned(classes[c].smem());
                     kp.kernel.kernelParams = pargs;
                     cudaGraphNode_t pn, un;

@@ -36,7 +36,7 @@ struct BatchClass {
     double *partials;               // [nchunks][rows_per_chunk][nstat]
     int nstat;                      // columns of a partial row: NSTAT, or NSTAT + 1 for the compensated form
     int rows_per_chunk;             // partial rows per chunk (the pass's compute warps)
-    int stages;                     // pipeline stages of the pass (1 .. BatchCfg<S>::MAX_STAGES)
+    int stages;                     // pipeline stages of the pass (2 .. BatchCfg<S, COMP>::MAX_STAGES)
     unsigned int *next;             // work-queue counter of this class
     const int *ds_list;             // [nds] data sets of this class
     const int *ds_first_chunk;      // [B] first chunk id of each data set (within its class)
@@ -71,22 +71,26 @@ struct StageMeta {
 };
 enum : int { UNIT_TAIL = 1, UNIT_LAST = 2 };
 
-// Shape of the batched pass.  Warps 0-6 compute, warp 7 is the producer: its
-// lane 0 owns the work-queue cursor and refills a stage once the seven
-// compute warps have released it (per-stage empty mbarriers), so the compute
-// warps never meet at a block barrier.  The number of stages is chosen at
-// run time (the autotuner, up to MAX_STAGES); shared memory holds the
-// barriers and metadata, then (compensated form) the table of profile terms
-// and two copies of the split pass globals, then the ring.
-template <int S>
+// Shape of the batched pass.  Warps 0 .. CW-1 compute, warp CW is the
+// producer: its lane 0 owns the work-queue cursor and refills a stage once
+// the compute warps have released it (per-stage empty mbarriers), so the
+// compute warps never meet at a block barrier.  Seven compute warps where
+// two or more blocks share an SM (registers for 128 per thread), nine where
+// one block holds it (the larger S: up to 204 registers per thread), so that
+// an SM keeps at least 14 compute warps or 9 wider ones.  The number of
+// stages is chosen at run time (the autotuner, up to MAX_STAGES); shared
+// memory holds the barriers and metadata, then (compensated form) the table
+// of profile terms and two copies of the split pass globals, then the ring.
+template <int S, bool COMP>
 struct BatchCfg {
     using C = SweepCfg<S>;
-    static constexpr int THREADS = 256;
-    static constexpr int CW = 7;                                   // compute warps
+    static constexpr int MINB = COMP ? C::MINB_BC : C::MINB;       // resident blocks per SM the registers allow
+    static constexpr int CW = (MINB >= 2) ? 7 : 9;                 // compute warps
+    static constexpr int THREADS = 32 * (CW + 1);
     static constexpr int CT = 32 * CW;                             // compute threads
     static constexpr int PRODUCER_WARP = CW;
     static constexpr int OPT = 4;                                  // observations per compute thread per tile
-    static constexpr int T = CT * OPT;                             // observations per tile (896)
+    static constexpr int T = CT * OPT;                             // observations per tile (896 or 1,152)
     static constexpr int MAX_STAGES = 8;
     static constexpr uint32_t R_BYTES = T * 4u;
     static constexpr uint32_t D_BYTES = T * S * 4u;
@@ -114,12 +118,13 @@ struct Cursor {
     long long full_hi;              // end of the chunk's full tiles
     int tail_done;
     int done;                       // no more work
+    const float *rp, *dp;           // the data set's inputs
 };
 
-template <int S>
+template <int S, bool COMP>
 __device__ __forceinline__ bool cursor_advance(Cursor &cu, const BatchClass &bc, int mode)
 {
-    using B = BatchCfg<S>;
+    using B = BatchCfg<S, COMP>;
     while (true) {
         if (cu.chunk >= 0 && (cu.next_obs < cu.full_hi || !cu.tail_done)) return true;
         const unsigned int q = atomicAdd(bc.next, 1u);
@@ -132,6 +137,8 @@ __device__ __forceinline__ bool cursor_advance(Cursor &cu, const BatchClass &bc,
         if (mode == MODE_ITER && !ds_running(bc.states + ds)) continue;      // retired data set
         cu.chunk = c;
         cu.ds = ds;
+        cu.rp = bc.r[ds];
+        cu.dp = bc.d[ds];
         cu.next_obs = bc.chunk_lo[c];
         cu.hi = bc.chunk_hi[c];
         // full tiles are those whose observations all lie in the chunk; chunk
@@ -150,12 +157,12 @@ __device__ __forceinline__ bool cursor_advance(Cursor &cu, const BatchClass &bc,
 // Fill a stage with the next unit (a full tile by bulk copy, or the ragged
 // tail of a chunk, read later with plain loads), or with the end mark.
 // Returns false after writing the end mark.
-template <int S>
+template <int S, bool COMP>
 __device__ __forceinline__ bool issue_unit(Cursor &cu, const BatchClass &bc, int mode, unsigned char *stage,
                                            uint64_t *bar, StageMeta *meta)
 {
-    using B = BatchCfg<S>;
-    if (cu.done || !cursor_advance<S>(cu, bc, mode)) {
+    using B = BatchCfg<S, COMP>;
+    if (cu.done || !cursor_advance<S, COMP>(cu, bc, mode)) {
         meta->chunk = -1;
         mbar_arrive_expect_tx(bar, 0u);
         return false;
@@ -170,8 +177,8 @@ __device__ __forceinline__ bool issue_unit(Cursor &cu, const BatchClass &bc, int
         meta->flags = last ? UNIT_LAST : 0;
         fence_proxy_async_smem();
         mbar_arrive_expect_tx(bar, B::STAGE_BYTES);
-        bulk_load(stage, bc.r[cu.ds] + o, B::R_BYTES, bar);
-        bulk_load(stage + B::R_BYTES, bc.d[cu.ds] + o * S, B::D_BYTES, bar);
+        bulk_load(stage, cu.rp + o, B::R_BYTES, bar);
+        bulk_load(stage + B::R_BYTES, cu.dp + o * S, B::D_BYTES, bar);
     } else {
         meta->flags = UNIT_TAIL | UNIT_LAST;
         cu.tail_done = 1;
@@ -201,11 +208,11 @@ __device__ __forceinline__ void batch_abort(const BatchClass &bc, volatile int *
 // meet (every warp is then done with the old table), build the table and meet
 // again, both times at a bounded mbarrier rendezvous.
 template <int S, bool COMP>
-__global__ void __launch_bounds__(BatchCfg<S>::THREADS, COMP ? SweepCfg<S>::MINB_BC : SweepCfg<S>::MINB)
+__global__ void __launch_bounds__(BatchCfg<S, COMP>::THREADS, BatchCfg<S, COMP>::MINB)
     batched_pass_kernel(BatchClass bc)
 {
     using C = SweepCfg<S>;
-    using B = BatchCfg<S>;
+    using B = BatchCfg<S, COMP>;
     constexpr int M = C::M, NG = C::NG, NSTAT = C::NSTAT;
     constexpr int NS = COMP ? C::NSTATC : C::NSTAT;        // columns of a partial row
     constexpr int NGRP = COMP ? C::NGRPC : C::NGRP;
@@ -235,12 +242,12 @@ __global__ void __launch_bounds__(BatchCfg<S>::THREADS, COMP ? SweepCfg<S>::MINB
 
     if (warp == B::PRODUCER_WARP) {
         if (lane != 0) return;
-        Cursor cu{-1, 0, 0, 0, 0, 1, 0};
+        Cursor cu{-1, 0, 0, 0, 0, 1, 0, nullptr, nullptr};
         long long k = 0;
+        int s = 0, round = 0;                               // unit k = round * stages + s
         bool bad = false;
         for (;; ++k) {
-            const int s = int(k % stages);
-            if (k >= stages && !mbar_wait_bounded(&empty[s], uint32_t(((k / stages) - 1) & 1), BATCH_WAIT_NS)) {
+            if (round > 0 && !mbar_wait_bounded(&empty[s], uint32_t((round - 1) & 1), BATCH_WAIT_NS)) {
                 bad = true;
                 break;
             }
@@ -248,7 +255,11 @@ __global__ void __launch_bounds__(BatchCfg<S>::THREADS, COMP ? SweepCfg<S>::MINB
                 bad = true;
                 break;
             }
-            if (!issue_unit<S>(cu, bc, mode, ring + size_t(s) * B::STAGE_BYTES, &full[s], &meta[s])) break;
+            if (!issue_unit<S, COMP>(cu, bc, mode, ring + size_t(s) * B::STAGE_BYTES, &full[s], &meta[s])) break;
+            if (++s == stages) {
+                s = 0;
+                ++round;
+            }
         }
         if (bad) {
             // a wait ran out: record it, then let the copies of the last units
@@ -282,18 +293,19 @@ __global__ void __launch_bounds__(BatchCfg<S>::THREADS, COMP ? SweepCfg<S>::MINB
         ++rv;
         return __all_sync(0xffffffffu, ok);
     };
-    // wait for unit k (its stage and metadata); false on a timeout (recorded)
-    auto take = [&](long long k, StageMeta &m) -> bool {
-        const int s = int(k % stages);
-        if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[s], uint32_t((k / stages) & 1), BATCH_WAIT_NS))) {
+    // the next unit is in stage cs, whose fill has parity cph
+    int cs = 0;
+    uint32_t cph = 0;
+    // wait for the next unit (its stage and metadata); false on a timeout (recorded)
+    auto take = [&](StageMeta &m) -> bool {
+        if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[cs], cph, BATCH_WAIT_NS))) {
             if (lane == 0) batch_abort(bc, abort_flag);
             return false;
         }
-        m = meta[s];                                        // the same for every thread once the stage is full
+        m = meta[cs];                                       // the same for every thread once the stage is full
         return true;
     };
 
-    long long k = 0;
     while (true) {
         float acc[NSTAT];
         double acc64[NGRP];
@@ -304,7 +316,7 @@ __global__ void __launch_bounds__(BatchCfg<S>::THREADS, COMP ? SweepCfg<S>::MINB
 #pragma unroll
         for (int g = 0; g < NGRP; ++g) acc64[g] = 0.0;
         StageMeta m;
-        if (!take(k, m) || m.chunk < 0) break;              // a timeout, or the end mark
+        if (!take(m) || m.chunk < 0) break;                 // a timeout, or the end mark
         if (m.ds != cur_ds) {
             const DevState *st = bc.states + m.ds;
             erho = (mode == MODE_INIT) ? 0.0f : st->sw.erho;
@@ -341,9 +353,8 @@ __global__ void __launch_bounds__(BatchCfg<S>::THREADS, COMP ? SweepCfg<S>::MINB
         const float *sp = split + ((nswitch + 1) & 1) * (B::SPLIT_AL / 4);   // copy of the current data set
         bool ok = true;
         while (true) {                                      // the units of chunk m.chunk
-            const int s = int(k % stages);
             if (!(m.flags & UNIT_TAIL)) {
-                const float *rt = reinterpret_cast<const float *>(ring + size_t(s) * B::STAGE_BYTES);
+                const float *rt = reinterpret_cast<const float *>(ring + size_t(cs) * B::STAGE_BYTES);
                 const float *dt = rt + T;
 #pragma unroll
                 for (int u = 0; u < B::OPT; ++u) {
@@ -360,8 +371,11 @@ __global__ void __launch_bounds__(BatchCfg<S>::THREADS, COMP ? SweepCfg<S>::MINB
                 }
             }
             __syncwarp();
-            if (lane == 0) mbar_arrive(&empty[s]);          // this warp's reads of stage s are done
-            ++k;
+            if (lane == 0) mbar_arrive(&empty[cs]);         // this warp's reads of stage cs are done
+            if (++cs == stages) {
+                cs = 0;
+                cph ^= 1u;
+            }
             if (m.flags & UNIT_TAIL) {
                 const float *rg = bc.r[m.ds];
                 const float *dg = bc.d[m.ds];
@@ -387,7 +401,7 @@ __global__ void __launch_bounds__(BatchCfg<S>::THREADS, COMP ? SweepCfg<S>::MINB
                     flush_warp<S>(acc, acc64, prod, ex, lane);
                 ftile = 0;
             }
-            if (!take(k, m)) {                              // the chunk's next unit
+            if (!take(m)) {                                 // the chunk's next unit
                 ok = false;
                 break;
             }

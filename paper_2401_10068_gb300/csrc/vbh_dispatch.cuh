@@ -24,20 +24,23 @@ struct KernelInfo {
     int res_max_blocks_comp;
 };
 
-// Kernels of the batched form for one S class.
-struct BatchKernelInfo {
-    const void *pass;      // batched_pass_kernel<S, false>
-    const void *pass_comp; // batched_pass_kernel<S, true>
-    const void *update;    // batched_update_kernel<S - 1>
-    const void *setup;     // batched_setup_kernel<S - 1>
-    size_t pass_fixed;     // shared memory of the pass without its ring (plain form)
-    size_t pass_fixed_comp; // the same for the compensated form
+// One form (plain or compensated statistics) of the batched data pass.
+struct BatchPassInfo {
+    const void *pass;      // batched_pass_kernel<S, COMP>
+    size_t fixed;          // shared memory without the ring
     size_t stage_bytes;    // shared memory of one pipeline stage
     int max_stages;
-    size_t update_smem;
     int threads;
-    int tile;              // observations per tile of the pass
-    int rows_per_chunk;    // partial rows per chunk (compute warps of the pass)
+    int tile;              // observations per tile
+    int rows_per_chunk;    // partial rows per chunk (compute warps)
+};
+
+// Kernels of the batched form for one S class.
+struct BatchKernelInfo {
+    BatchPassInfo plain, comp;
+    const void *update;    // batched_update_kernel<S - 1>
+    const void *setup;     // batched_setup_kernel<S - 1>
+    size_t update_smem;
     int nstat;             // statistics per partial row (plain form; the compensated form has nstat + 1)
 };
 
@@ -74,21 +77,25 @@ bool batch_kernel_info_s9_11(int S, BatchKernelInfo *out);
         return true;                                                                                                   \
     }
 
+#define VBH_BATCH_PASS_INFO(DST, SV, CMP)                                                                             \
+    do {                                                                                                               \
+        using BC = ::vbh::BatchCfg<SV, CMP>;                                                                           \
+        (DST).pass = reinterpret_cast<const void *>(&::vbh::batched_pass_kernel<SV, CMP>);                             \
+        (DST).fixed = CMP ? BC::FIXED_C : BC::FIXED;                                                                   \
+        (DST).stage_bytes = BC::STAGE_BYTES;                                                                           \
+        (DST).max_stages = BC::MAX_STAGES;                                                                             \
+        (DST).threads = BC::THREADS;                                                                                   \
+        (DST).tile = BC::T;                                                                                            \
+        (DST).rows_per_chunk = BC::CW;                                                                                 \
+    } while (0)
+
 #define VBH_BATCH_KERNEL_INFO_CASE(SV)                                                                                 \
     case SV: {                                                                                                         \
-        using BC = ::vbh::BatchCfg<SV>;                                                                                \
-        out->pass = reinterpret_cast<const void *>(&::vbh::batched_pass_kernel<SV, false>);                            \
-        out->pass_comp = reinterpret_cast<const void *>(&::vbh::batched_pass_kernel<SV, true>);                        \
+        VBH_BATCH_PASS_INFO(out->plain, SV, false);                                                                    \
+        VBH_BATCH_PASS_INFO(out->comp, SV, true);                                                                      \
         out->update = reinterpret_cast<const void *>(&::vbh::batched_update_kernel<SV - 1>);                           \
         out->setup = reinterpret_cast<const void *>(&::vbh::batched_setup_kernel<SV - 1>);                             \
-        out->pass_fixed = BC::FIXED;                                                                                   \
-        out->pass_fixed_comp = BC::FIXED_C;                                                                            \
-        out->stage_bytes = BC::STAGE_BYTES;                                                                            \
-        out->max_stages = BC::MAX_STAGES;                                                                              \
         out->update_smem = size_t(::vbh::gu_ws_doubles<SV - 1>()) * 8;                                                 \
-        out->threads = BC::THREADS;                                                                                    \
-        out->tile = BC::T;                                                                                             \
-        out->rows_per_chunk = BC::CW;                                                                                  \
         out->nstat = ::vbh::SweepCfg<SV>::NSTAT;                                                                       \
         return true;                                                                                                   \
     }
