@@ -75,9 +75,9 @@ enum : int { UNIT_TAIL = 1, UNIT_LAST = 2 };
 // producer: its lane 0 owns the work-queue cursor and refills a stage once
 // the compute warps have released it (per-stage empty mbarriers), so the
 // compute warps never meet at a block barrier.  Seven compute warps where
-// two or more blocks share an SM (registers for 128 per thread), nine where
-// one block holds it (the larger S: up to 204 registers per thread), so that
-// an SM keeps at least 14 compute warps or 9 wider ones.  The number of
+// two or more blocks share an SM (registers for 128 per thread), eleven where
+// one block holds it (the larger S: up to 168 registers per thread), so that
+// an SM keeps at least 14 compute warps or 11 wider ones.  The number of
 // stages is chosen at run time (the autotuner, up to MAX_STAGES); shared
 // memory holds the barriers and metadata, then (compensated form) the table
 // of profile terms and two copies of the split pass globals, then the ring.
@@ -85,12 +85,12 @@ template <int S, bool COMP>
 struct BatchCfg {
     using C = SweepCfg<S>;
     static constexpr int MINB = COMP ? C::MINB_BC : C::MINB;       // resident blocks per SM the registers allow
-    static constexpr int CW = (MINB >= 2) ? 7 : 9;                 // compute warps
+    static constexpr int CW = (MINB >= 2) ? 7 : 11;                // compute warps
     static constexpr int THREADS = 32 * (CW + 1);
     static constexpr int CT = 32 * CW;                             // compute threads
     static constexpr int PRODUCER_WARP = CW;
     static constexpr int OPT = 4;                                  // observations per compute thread per tile
-    static constexpr int T = CT * OPT;                             // observations per tile (896 or 1,152)
+    static constexpr int T = CT * OPT;                             // observations per tile (896 or 1,408)
     static constexpr int MAX_STAGES = 8;
     static constexpr uint32_t R_BYTES = T * 4u;
     static constexpr uint32_t D_BYTES = T * S * 4u;
