@@ -9,6 +9,7 @@ import torch
 
 from oracle import oracle as O
 from paper_2401_10068_gb300 import _build, synth, vbh
+from test_gpu_parity import elementwise_errors
 
 pytestmark = pytest.mark.gpu
 
@@ -62,6 +63,9 @@ def test_batched_matches_oracle_fixed_sweeps(handle):
         ref = O.fit(r, d, p, tol=0.0, max_iter=sweeps)
         assert g["iters"] == sweeps
         _check(g, ref, V, (S, V))
+        if V > 0:
+            ew = elementwise_errors(g, ref)
+            assert all(v < TOL_P for v in ew.values()), (S, V, ew)
         for t, (a, b) in enumerate(zip(g["trace"], ref["trace"])):
             assert abs(a - b) <= TOL_E * max(abs(b), V, 1.0), (S, V, t)
 

@@ -3,7 +3,8 @@
 Same seeded inputs, same schedule (sweep 0 from the initial Q(beta), then t
 sweeps of Q(beta) -> Q(rho) -> Q(K, Lambda) -> ELBO), same number of sweeps.
 Tolerances: every variational parameter block (kappa, W^{-1}, b_rho, E[rho])
-within 1e-4 relative (norm-wise); the ELBO within 1e-6 relative; a_rho, nu and
+within 1e-4 relative (norm-wise), and at fixed sweeps every entry within 1e-4
+of its own scale (element-wise); the ELBO within 1e-6 relative; a_rho, nu and
 lambda are exact functions of V and must agree to rounding.
 """
 import ctypes
@@ -60,6 +61,24 @@ def assert_parity(got, ref, tol_param=TOL_PARAM, tol_elbo=TOL_ELBO, what="", V=N
     assert elbo_close(got["elbo"], ref["elbo"], V, tol_elbo), (what, "elbo", got["elbo"], ref["elbo"])
 
 
+def elementwise_errors(got, ref):
+    """Largest per-entry errors, each on the entry's own scale: kappa_j
+    relative to max(|kappa_j|, 1e-2 max|kappa|); W^{-1}_ij relative to
+    sqrt(W^{-1}_ii W^{-1}_jj) (the diagonal entries' plain relative error;
+    an off-diagonal entry on the scale of its row and column, so a small
+    correlation is not judged against its own near-zero value); b_rho
+    relative."""
+    out = {}
+    k, kr = np.asarray(got["kappa"], np.float64), np.asarray(ref["kappa"], np.float64)
+    if kr.size:
+        out["kappa"] = float(np.max(np.abs(k - kr) / np.maximum(np.abs(kr), 1e-2 * np.max(np.abs(kr)))))
+        W, Wr = np.asarray(got["Winv"], np.float64), np.asarray(ref["Winv"], np.float64)
+        dg = np.sqrt(np.abs(np.diag(Wr)))
+        out["Winv"] = float(np.max(np.abs(W - Wr) / np.outer(dg, dg)))
+    out["b_rho"] = abs(got["b_rho"] - ref["b_rho"]) / abs(ref["b_rho"])
+    return out
+
+
 CASES = [
     # (S, V, seed, sweeps, p_const)
     (1, 5003, 1, 3, 0.0),
@@ -94,6 +113,10 @@ def test_parity_fixed_sweeps(handle, S, V, seed, sweeps, p_const, loop):
     assert got["iters"] == sweeps and not got["converged"]
     assert got["const_dropped"] == ref["const_dropped"]
     assert_parity(got, ref, what=(S, V))
+    # entry by entry, each on its own scale
+    ew = elementwise_errors(got, ref)
+    print(f"S={S} V={V} loop={loop} element-wise: " + ", ".join(f"{k} {v:.2e}" for k, v in ew.items()))
+    assert all(v < TOL_PARAM for v in ew.values()), (S, V, ew)
     # the whole ELBO trace
     for t, (a, b) in enumerate(zip(got["trace"], ref["trace"])):
         assert elbo_close(a, b, V), (t, a, b)
