@@ -474,24 +474,13 @@ SINGLE = {"name": "single data set: N=2,000 cells x G=48 genes, S=3", "cells": 2
           "alpha": 1.0, "seed": 1, "tol": 1e-8, "cap": 200, "cap_raised": 2000, "reps": 5}
 
 
-def other_workloads(dev, stream):
-    """The other workloads' headline figures, measured after the timed region
-    of the default step (each its own timing, CUDA events or wall clock around
-    synchronous vbh_* calls with device-resident inputs):
-      single data set: fits/s through vbh_fit at the workload's rule
-        (rel dELBO < 1e-8 or 200 sweeps) and with the cap raised to 2,000 so
-        that the fit converges (converged data sets/s);
-      batched: the 4,096-data-set fit to rel dELBO < 1e-8 (cap 1,000),
-        converged data sets/s and how many converged;
-      precision: the S = 32 tensor-core sweep, ms per sweep of the BF16 and
-        FP32 forms and the BF16 form's fraction of the HBM copy peak."""
+def single_workload(h, dev, stream):
+    """The single data set (N = 2,000 cells x G = 48 genes, S = 3): fits/s
+    through vbh_fit at the workload's rule (rel dELBO < 1e-8 or 200 sweeps)
+    and with the cap raised to 2,000 (converged data sets/s), and the device
+    time per sweep of the resident and the streaming sweep loops."""
     import torch
     from paper_2401_10068_gb300 import synth, vbh
-    out = {}
-    h = vbh.Handle(dev.index or 0, stream)
-    clocks = Clocks(dev.index or 0)
-    time.sleep(0.3)
-    # single data set
     V1 = SINGLE["cells"] * SINGLE["genes"]
     with torch.cuda.stream(stream):
         r1, d1, _ = synth.generate_device(V1, SINGLE["S"], seed=SINGLE["seed"], alpha=SINGLE["alpha"], device=dev)
@@ -519,8 +508,49 @@ def other_workloads(dev, stream):
         ev1.record(stream)
         torch.cuda.synchronize(dev)
         row[name] = {"us_per_sweep": ev0.elapsed_time(ev1) * 1e3 / 200}
-    out["single"] = row
-    del r1, d1
+    return row
+
+
+def run_single(args):
+    """``--workload single``: the single-data-set figures alone (the small
+    case for captures of the resident kernel)."""
+    import torch
+    from paper_2401_10068_gb300 import _build
+    _build.build_all()
+    from paper_2401_10068_gb300 import vbh
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    h = vbh.Handle(0, stream)
+    clocks = Clocks(0)
+    time.sleep(0.3)
+    row = single_workload(h, dev, stream)
+    h.close()
+    line = {"metric": "converged datasets/s (single data set)",
+            "value": row["cap_2000"]["converged_datasets_per_s"], "unit": "datasets/s", "n_gpus": 1,
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic", "config": {"workload": SINGLE["name"]},
+            "single": row, "clocks": clocks.stop()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def other_workloads(dev, stream):
+    """The other workloads' headline figures, measured after the timed region
+    of the default step (each its own timing, CUDA events or wall clock around
+    synchronous vbh_* calls with device-resident inputs):
+      single data set: fits/s through vbh_fit at the workload's rule
+        (rel dELBO < 1e-8 or 200 sweeps) and with the cap raised to 2,000 so
+        that the fit converges (converged data sets/s);
+      batched: the 4,096-data-set fit to rel dELBO < 1e-8 (cap 1,000),
+        converged data sets/s and how many converged;
+      precision: the S = 32 tensor-core sweep, ms per sweep of the BF16 and
+        FP32 forms and the BF16 form's fraction of the HBM copy peak."""
+    import torch
+    from paper_2401_10068_gb300 import synth, vbh
+    out = {}
+    h = vbh.Handle(dev.index or 0, stream)
+    clocks = Clocks(dev.index or 0)
+    time.sleep(0.3)
+    out["single"] = single_workload(h, dev, stream)
     # batched
     V, Sb = batch_specs(BATCH["datasets"])
     rs, ds = [], []
@@ -1034,7 +1064,7 @@ def main():
     ap.add_argument("--ws-load", default=None, help="warmstart workload: load the encoder instead of training it")
     ap.add_argument("--ws-save", default=None, help="warmstart workload: save the trained encoder")
     ap.add_argument("--workload", default="at-scale",
-                    choices=["at-scale", "batched", "precision", "grouped", "per-s", "warmstart"],
+                    choices=["at-scale", "single", "batched", "precision", "grouped", "per-s", "warmstart"],
                     help="batched: the 4,096-data-set form; precision: the S = 32 tensor-core form; grouped: "
                          "the profile-grouped form; per-s: the FP32 sweep's bandwidth for S = 2..11; warmstart: "
                          "the learned warm start (separate measurements, not the default step)")
@@ -1045,6 +1075,8 @@ def main():
     args = ap.parse_args()
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "single":
+        return run_single(args)
     if args.workload == "grouped":
         return run_grouped(args)
     if args.workload == "per-s":
