@@ -9,12 +9,14 @@
 // since D has M <= 31 entries) and y_i = r_i - d_iS in FP32.  The BF16 part of
 // a tile is slot-major ("comp-major"): for each slot, the tile's observations
 // are contiguous, so that both operands of MMA2 are K-major.
-//   MMA1  U = D~_tile (128 x 32) . B1 (32 x N1): per observation the NSPLIT
-//         BF16 parts of v = L~^T D_i (q_i = |v|^2) and of t_i = kappa~^T D_i,
-//         side by side in N; L~ and kappa~ (the FP32 globals of the pass) are
-//         split into NSPLIT BF16 parts.  With D in {-1, 0, 1} every product is
-//         exact: NSPLIT = 3 carries the FP32 values (24 bits), NSPLIT = 2 keeps
-//         16 bits (the BF16 form).
+//   MMA1  U = [D~_tile .. D~_tile] (128 x 32 NSPLIT) . [B1_0; ..; B1_{NSPLIT-1}]
+//         (32 NSPLIT x 32): per observation v = L~^T D_i in columns 0..30
+//         (q_i = |v|^2) and t_i = kappa~^T D_i in column 31.  L~ and kappa~
+//         (the FP32 globals of the pass) are split into NSPLIT BF16 parts; the
+//         parts are stacked along K (part p meets the tile's slots in K steps
+//         2p, 2p + 1), so the tensor core adds them in its FP32 accumulator.
+//         With D in {-1, 0, 1} every product is exact: NSPLIT = 3 carries the
+//         FP32 values (24 bits), NSPLIT = 2 keeps 16 bits (the BF16 form).
 //   MMA2  G'' = A2 . D~_tile^T: row (p, j) of A2 holds part p of
 //         gamma_i D_ij (gamma_i = w_i^2 - c_i) for j < 31 and part p of w_i in
 //         slot 31, with the observations along K; against the D~ rows this
@@ -78,7 +80,7 @@ template <int NSPLIT>
 struct TcCfg {
     static constexpr int TILE = 128;                                   // observations per tile
     static constexpr int SETS = (NSPLIT == 2) ? 2 : 1;                 // observation sets per MMA2
-    static constexpr int N1 = ((33 * NSPLIT + 15) / 16) * 16;          // MMA1 N: parts of v, then of t (80, 112)
+    static constexpr int N1 = 32;                                      // MMA1 N: v (31 columns), then t
     static constexpr int N2 = 32 * SETS;                               // MMA2 N
     static constexpr int NK2 = 8 / SETS;                               // MMA2 instructions per tile (K = 16)
     static constexpr int NCG = 2;                                      // consumer groups (tile k: group k % NCG)
@@ -88,7 +90,7 @@ struct TcCfg {
     static constexpr uint32_t D_BYTES = TILE * 64;                     // BF16 slots of a tile
     static constexpr uint32_t TILE_BYTES = TC_TILE_BYTES;              // + 128 y values
     static constexpr uint32_t STAGE_BYTES = 2 * TILE_BYTES;
-    static constexpr uint32_t B1_BYTES = N1 * 64;
+    static constexpr uint32_t B1_BYTES = NSPLIT * 32 * 64;             // NSPLIT blocks of 32 rows x 32 slots
     static constexpr uint32_t A2_BLOCK = 128 * 64;                     // 128 rows x 32 observations (or pairs)
     static constexpr uint32_t A2_BYTES = (TILE / SETS / 32) * A2_BLOCK;
     static constexpr bool TMEM_A2 = (NSPLIT == 2);                     // A2 in tensor memory (BF16 form)
@@ -263,21 +265,18 @@ __global__ void __launch_bounds__(TcCfg<NSPLIT>::THREADS, 1)
         }
         for (int i = tid; i < int(C::A2_REGION / 16); i += nth)
             reinterpret_cast<uint4 *>(a2)[i] = make_uint4(0, 0, 0, 0);
-        // B1 (N1 rows x 32 slots, K-major, 64-byte swizzle): row 32 p + c holds part p of column c
-        // of L~ (L~(k, c) at slot k), row 32 NSPLIT + p part p of kappa~; slot 31 (the constant 1
-        // of the tile rows) meets zeros.
+        // B1: NSPLIT blocks of 32 rows x 32 slots (K-major, 64-byte swizzle, 2 KiB each); row c < 31
+        // of block p holds part p of column c of L~ (L~(k, c) at slot k), row 31 part p of kappa~;
+        // slot 31 (the constant 1 of the tile rows) meets zeros.
         const float erho_f = st->sw.erho;       // 0 in sweep 0 of a CAVI fit from the paper's start
-        for (int idx = tid; idx < C::N1 * 32; idx += nth) {
+        for (int idx = tid; idx < NSPLIT * 32 * 32; idx += nth) {
             const int n = idx >> 5, k = idx & 31;
+            const int p = n >> 5, c = n & 31;
             double x = 0.0;
-            int p = 0;
-            if (n < 32 * NSPLIT) {
-                p = n >> 5;
-                const int c = n & 31;
+            if (c < 31) {
                 if (c < M && k < M && k >= c) x = static_cast<double>(st->sw.L[k * (k + 1) / 2 + c]);
-            } else if (n < 32 * NSPLIT + NSPLIT) {
-                p = n - 32 * NSPLIT;
-                if (k < M) x = static_cast<double>(st->sw.kappa[k]);
+            } else if (k < M) {
+                x = static_cast<double>(st->sw.kappa[k]);
             }
             *reinterpret_cast<__nv_bfloat16 *>(b1 + sw64(n, k >> 3) + (k & 7) * 2) = bf16_part(x, p);
         }
@@ -328,11 +327,14 @@ __global__ void __launch_bounds__(TcCfg<NSPLIT>::THREADS, 1)
                     tc_fence_after();
                     const uint32_t d0 = da + s * C::STAGE_BYTES + (k & 1) * C::TILE_BYTES;
                     // A = the tile's slots as an MN-major operand: four atoms of 32 observations
-                    // (2 KiB apart), K step 16 slots = 1 KiB
+                    // (2 KiB apart), K step 16 slots = 1 KiB; the same two K steps once per part
+                    // of B1 (block p, 2 KiB apart), all accumulating into one U
 #pragma unroll
-                    for (int kk = 0; kk < 2; ++kk)
-                        umma_bf16(tbase + C::COL_U + u * C::COL_U_STRIDE, umma_desc(d0 + kk * 1024, 2048, 512, 4),
-                                  umma_desc(b1a + kk * 32, 16, 512, 4), IDESC1, kk ? 1u : 0u);
+                    for (int p = 0; p < NSPLIT; ++p)
+#pragma unroll
+                        for (int kk = 0; kk < 2; ++kk)
+                            umma_bf16(tbase + C::COL_U + u * C::COL_U_STRIDE, umma_desc(d0 + kk * 1024, 2048, 512, 4),
+                                      umma_desc(b1a + p * 2048 + kk * 32, 16, 512, 4), IDESC1, (p | kk) ? 1u : 0u);
                     umma_commit(&ufull[u]);
                 }
                 umma_commit(&drain[0]);         // arrives once every MMA issued above has completed
@@ -479,52 +481,49 @@ __global__ void __launch_bounds__(TcCfg<NSPLIT>::THREADS, 1)
                     break;
                 }
                 tc_fence_after();
-                // v = L~^T D (q = |v|^2) and t = kappa~^T D: sums of the NSPLIT parts, loaded in two
-                // halves of 16 columns (fewer live registers; q's accumulation order is unchanged)
+                // v = L~^T D (columns 0..30, q = |v|^2) and t = kappa~^T D (column 31), the parts
+                // already added by MMA1: one tensor-memory round trip of 32 columns
                 const uint32_t tu = tbase + lanebase + C::COL_U + u * C::COL_U_STRIDE;
-                float q0 = 0.0f, q1 = 0.0f, q2 = 0.0f, q3 = 0.0f, tv[4];
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    uint32_t ur[NSPLIT][16], tr[4];
-#pragma unroll
-                    for (int p = 0; p < NSPLIT; ++p) tmem_ld16_nowait(tu + 32 * p + 16 * h, ur[p]);
-                    if (h == 0) tmem_ld4_nowait(tu + 32 * NSPLIT, tr);
+                float q0 = 0.0f, q1 = 0.0f, q2 = 0.0f, q3 = 0.0f, t;
+                {
+                    uint32_t ua[16], ub[16];
+                    tmem_ld16_nowait(tu, ua);
+                    tmem_ld16_nowait(tu + 16, ub);
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-                    for (int p = 0; p < NSPLIT; ++p)
-#pragma unroll
-                        for (int c = 0; c < 16; ++c) asm volatile("" : "+r"(ur[p][c]));
-                    if (h == 0) {
-#pragma unroll
-                        for (int c = 0; c < 4; ++c) {
-                            asm volatile("" : "+r"(tr[c]));
-                            tv[c] = __uint_as_float(tr[c]);
-                        }
+                    for (int c = 0; c < 16; ++c) {
+                        asm volatile("" : "+r"(ua[c]));
+                        asm volatile("" : "+r"(ub[c]));
                     }
 #pragma unroll
                     for (int c = 0; c < 16; c += 4) {
-                        float v0 = __uint_as_float(ur[0][c]), v1 = __uint_as_float(ur[0][c + 1]);
-                        float v2 = __uint_as_float(ur[0][c + 2]), v3 = __uint_as_float(ur[0][c + 3]);
-#pragma unroll
-                        for (int p = 1; p < NSPLIT; ++p) {
-                            v0 += __uint_as_float(ur[p][c]);
-                            v1 += __uint_as_float(ur[p][c + 1]);
-                            v2 += __uint_as_float(ur[p][c + 2]);
-                            v3 += __uint_as_float(ur[p][c + 3]);
-                        }
+                        const float v0 = __uint_as_float(ua[c]), v1 = __uint_as_float(ua[c + 1]);
+                        const float v2 = __uint_as_float(ua[c + 2]), v3 = __uint_as_float(ua[c + 3]);
                         q0 = fmaf(v0, v0, q0);
                         q1 = fmaf(v1, v1, q1);
                         q2 = fmaf(v2, v2, q2);
                         q3 = fmaf(v3, v3, q3);
                     }
+#pragma unroll
+                    for (int c = 0; c < 12; c += 4) {
+                        const float v0 = __uint_as_float(ub[c]), v1 = __uint_as_float(ub[c + 1]);
+                        const float v2 = __uint_as_float(ub[c + 2]), v3 = __uint_as_float(ub[c + 3]);
+                        q0 = fmaf(v0, v0, q0);
+                        q1 = fmaf(v1, v1, q1);
+                        q2 = fmaf(v2, v2, q2);
+                        q3 = fmaf(v3, v3, q3);
+                    }
+                    const float v12 = __uint_as_float(ub[12]), v13 = __uint_as_float(ub[13]);
+                    const float v14 = __uint_as_float(ub[14]);
+                    q0 = fmaf(v12, v12, q0);
+                    q1 = fmaf(v13, v13, q1);
+                    q2 = fmaf(v14, v14, q2);
+                    t = __uint_as_float(ub[15]);
                 }
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&uempty[u]);
                 const float qv = (q0 + q1) + (q2 + q3);
-                float t = tv[0];
-#pragma unroll
-                for (int p = 1; p < NSPLIT; ++p) t += tv[p];
                 const unsigned char *dt = dtile + s * C::STAGE_BYTES + (k & 1) * C::TILE_BYTES;
                 const float yv = reinterpret_cast<const float *>(dt + C::D_BYTES)[o_r];
                 const float e = yv - t;
