@@ -175,7 +175,7 @@ void vbh_opts_default(vbh_opts *o);
  * creation the handle instead issues one kernel launch per sweep (same kernels
  * and results; for profilers that cannot look inside conditional graphs).  The
  * resident loop (VBH_LOOP_RESIDENT) sizes its blocks for about
- * VBH_RESIDENT_OBS (environment, default 3) observations per thread and sweep. */
+ * VBH_RESIDENT_OBS (environment, default 2) observations per thread and sweep. */
 int vbh_create(vbh_handle **h, int device, void *stream);
 
 /* Release every resource of the handle (NULL is allowed). */

@@ -102,7 +102,7 @@ struct vbh_handle {
     // the resident sweep loop
     bool coop = false;                 // the device supports cooperative launches
     int smem_optin = 0;                // dynamic shared memory a block may opt in to
-    int res_obs = 3;                   // observations per thread and sweep the block count aims at
+    int res_obs = 2;                   // observations per thread and sweep the block count aims at
     size_t res_attr[vbh::S_FP32_MAX + 1][2] = {};   // shared memory the resident kernels were opted in to
     DevState *res_priv = nullptr;      // private state copies of blocks 1 ..
     size_t res_priv_cap = 0;           // bytes
