@@ -66,7 +66,7 @@ def elementwise_errors(got, ref):
     relative to max(|kappa_j|, 1e-2 max|kappa|); W^{-1}_ij relative to
     sqrt(W^{-1}_ii W^{-1}_jj) (the diagonal entries' plain relative error;
     an off-diagonal entry on the scale of its row and column, so a small
-    correlation is not judged against its own near-zero value); b_rho
+    correlation is not measured against its own near-zero value); b_rho
     relative."""
     out = {}
     k, kr = np.asarray(got["kappa"], np.float64), np.asarray(ref["kappa"], np.float64)
